@@ -1,0 +1,384 @@
+"""CPU oracle for the longest-overlap-region path.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The product library never
+imports, loads or executes anything under ``oracle/``; the two share no code.
+
+Everything here is the plain definition of what the method computes, written
+out slowly (paper: "Solving The Longest Overlap Region Problem for Noncoding
+DNA Sequences with GPU", arXiv 1404.3448):
+
+* concatenation of several sequences into one text with unique separators
+  (Section 3, "longest overlap prefix of two sequences"; the separator coding
+  is this library's reading, the paper states none);
+* suffix array by direct comparison sort (Section 3, Table 1);
+* LCP array by direct comparison, lcp[0] = 0 (Section 3, LCP table);
+* inverse suffix array / 1-based ranks (Section 3, Table 3);
+* longest overlap region = maximum LCP over adjacent suffixes of different
+  sequences, plus all positions of it (Section 3, lcp identity);
+* LCP of arbitrary suffixes by direct comparison (Section 3, RMQ reduction);
+* sparse table of range minima (the RMQ structure; Section 3 defines RMQ);
+* the 1-bit split primitive and the radix sort built from it (Section 4,
+  Algorithm 1) and the DC3 sample ranks / nonsample order (Section 3,
+  Steps 1-2, Table 2);
+* longest common substring by the O(n*m) dynamic program, a brute force that
+  does not use suffix arrays, used to pin the overlap.
+
+Heavy loops (suffix sort, LCP, DP) live in ``lor_oracle.c``; the rest is plain
+numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lor_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liblor_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+# Symbol codes of the concatenated text (library reading; the paper fixes
+# none): 0 is padding and never stored; the terminator of sequence i is
+# nseq - i (so the last terminator is the smallest symbol); A, C, G, T follow
+# as nseq+1 .. nseq+4, preserving A < C < G < T of Table 1.
+BASES = b"ACGT"
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle with gcc; returns the library path."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, i32p, u8p = ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p
+            lib.oracle_suffix_array.argtypes = [u8p, i64, i32p, ctypes.c_int]
+            lib.oracle_suffix_array.restype = ctypes.c_int
+            lib.oracle_lcp_array.argtypes = [u8p, i64, i32p, i32p, ctypes.c_int]
+            lib.oracle_lcp_array.restype = ctypes.c_int
+            lib.oracle_check_suffix_array.argtypes = [u8p, i64, i32p, ctypes.c_int]
+            lib.oracle_check_suffix_array.restype = ctypes.c_int64
+            lib.oracle_lcp_pairs.argtypes = [u8p, i64, i32p, i32p, i64, i32p]
+            lib.oracle_lcp_pairs.restype = ctypes.c_int
+            lib.oracle_lcs_dp.argtypes = [u8p, i64, u8p, i64, u8p, u8p]
+            lib.oracle_lcs_dp.restype = ctypes.c_int64
+            _lib = lib
+    return _lib
+
+
+def _u8(a) -> np.ndarray:
+    if isinstance(a, (bytes, bytearray)):
+        a = np.frombuffer(bytes(a), dtype=np.uint8)
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+# --------------------------------------------------------------------------
+# a1: encoding and concatenation
+# --------------------------------------------------------------------------
+
+def encode_concat(seqs):
+    """Concatenate DNA sequences S_0 t_0 S_1 t_1 ... with unique terminators.
+
+    Section 3 asks for the longest overlap of two (or more) sequences over one
+    suffix array; the concatenation with separators is this library's reading.
+    Returns (text uint8[n], seq_starts int64[nseq+1], sigma) where sigma is the
+    number of symbol codes including the padding code 0.
+    Raises ValueError on a symbol outside ACGT/acgt or on more than 250
+    sequences (codes must fit in one byte).
+    """
+    seqs = [_u8(s) for s in seqs]
+    nseq = len(seqs)
+    if nseq < 1 or nseq > 250:
+        raise ValueError("need 1..250 sequences")
+    lut = np.full(256, 255, dtype=np.int32)
+    for c, b in enumerate(BASES):
+        lut[b] = nseq + 1 + c
+        lut[ord(chr(b).lower())] = nseq + 1 + c
+    parts, starts = [], [0]
+    for i, s in enumerate(seqs):
+        codes = lut[s]
+        if codes.size and codes.max() == 255:
+            raise ValueError(f"sequence {i} holds a symbol outside ACGT")
+        parts.append(codes.astype(np.uint8))
+        parts.append(np.array([nseq - i], dtype=np.uint8))
+        starts.append(starts[-1] + len(s) + 1)
+    text = np.concatenate(parts) if parts else np.zeros(0, np.uint8)
+    return text, np.array(starts, dtype=np.int64), nseq + 5
+
+
+def encode_raw(ascii_text):
+    """Code one sequence without terminators: A=1, C=2, G=3, T=4.
+
+    This is the setting of the worked example (Table 1: S = ATTGCTAC with
+    eight suffixes and no terminator).  Returns (text, sigma=5).
+    """
+    s = _u8(ascii_text)
+    lut = np.full(256, 255, dtype=np.int32)
+    for c, b in enumerate(BASES):
+        lut[b] = 1 + c
+    codes = lut[s]
+    if codes.size and codes.max() == 255:
+        raise ValueError("symbol outside ACGT")
+    return codes.astype(np.uint8), 5
+
+
+# --------------------------------------------------------------------------
+# a2..a8: suffix array (definition: sorted suffixes, Section 3, Table 1)
+# --------------------------------------------------------------------------
+
+def suffix_array(text, nthreads: int = 1) -> np.ndarray:
+    t = _u8(text)
+    sa = np.empty(t.size, dtype=np.int32)
+    if _load().oracle_suffix_array(_ptr(t), t.size, _ptr(sa), int(nthreads)) != 0:
+        raise MemoryError("oracle_suffix_array failed")
+    return sa
+
+
+def check_suffix_array(text, sa, nthreads: int = 1) -> int:
+    """-1 if ``sa`` is the suffix array of ``text`` (permutation + every
+    adjacent pair strictly increasing by direct comparison); otherwise the
+    first rank where the definition fails (len(text) = not a permutation)."""
+    t = _u8(text)
+    s = np.ascontiguousarray(sa, dtype=np.int32)
+    if s.size != t.size:
+        return t.size
+    return int(_load().oracle_check_suffix_array(_ptr(t), t.size, _ptr(s), int(nthreads)))
+
+
+def inverse_suffix_array(sa) -> np.ndarray:
+    """isa[sa[k]] = k (0-based ranks; Table 3 prints them 1-based)."""
+    sa = np.asarray(sa)
+    isa = np.empty(sa.size, dtype=np.int32)
+    isa[sa] = np.arange(sa.size, dtype=np.int32)
+    return isa
+
+
+def sample_ranks(text) -> np.ndarray:
+    """DC3 Step 1 result (Section 3, Table 2): for i with i mod 3 != 0, the
+    1-based rank of suffix i among the sample suffixes; 0 (printed as the
+    undefined symbol) for i mod 3 == 0."""
+    sa = suffix_array(text)
+    out = np.zeros(len(sa), dtype=np.int32)
+    r = 0
+    for p in sa:
+        if p % 3 != 0:
+            r += 1
+            out[p] = r
+    return out
+
+
+def nonsample_order(text) -> np.ndarray:
+    """DC3 Step 2 result (Section 3): positions i mod 3 == 0 in suffix order."""
+    sa = suffix_array(text)
+    return sa[sa % 3 == 0].astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# a9: LCP array (Section 3, LCP table: lcp[0] = 0)
+# --------------------------------------------------------------------------
+
+def lcp_array(text, sa, nthreads: int = 1) -> np.ndarray:
+    t = _u8(text)
+    s = np.ascontiguousarray(sa, dtype=np.int32)
+    lcp = np.empty(t.size, dtype=np.int32)
+    if _load().oracle_lcp_array(_ptr(t), t.size, _ptr(s), _ptr(lcp), int(nthreads)) != 0:
+        raise ValueError("oracle_lcp_array failed")
+    return lcp
+
+
+# --------------------------------------------------------------------------
+# a10: longest overlap region and all of its positions
+# --------------------------------------------------------------------------
+
+def seq_of(positions, seq_starts) -> np.ndarray:
+    """Index of the sequence a text position belongs to (a terminator belongs
+    to the sequence it closes)."""
+    return (np.searchsorted(np.asarray(seq_starts), np.asarray(positions), side="right") - 1
+            ).astype(np.int64)
+
+
+def longest_overlap(text, sa, lcp, seq_starts):
+    """Longest overlap region over adjacent suffixes of different sequences.
+
+    Section 3: the LCP of two suffixes is the minimum of the adjacent LCPs
+    between them, so the longest region shared by two sequences is the largest
+    LCP between rank-adjacent suffixes that start in different sequences.
+    Readings (the paper is silent): ``rank`` is the smallest rank k attaining
+    the maximum; seq_a/pos_a is the suffix of the lower sequence id at ranks
+    k-1, k; ``positions`` lists every text position p whose length-L prefix
+    also occurs in another sequence, i.e. every member of a maximal rank run
+    with adjacent LCP >= L that holds suffixes of two or more sequences,
+    sorted ascending.  L == 0 gives rank = seq = pos = -1 and no positions.
+    """
+    sa = np.asarray(sa, dtype=np.int64)
+    lcp = np.asarray(lcp, dtype=np.int64)
+    n = sa.size
+    res = dict(length=0, rank=-1, seq_a=-1, pos_a=-1, seq_b=-1, pos_b=-1,
+               positions=np.zeros(0, dtype=np.int64))
+    if n < 2:
+        return res
+    sq = seq_of(sa, seq_starts)
+    cross = np.zeros(n, dtype=bool)
+    cross[1:] = sq[1:] != sq[:-1]
+    cand = np.where(cross, lcp, -1)
+    L = int(cand.max())
+    if L <= 0:
+        return res
+    k = int(np.argmax(cand == L))
+    a, b = int(sa[k - 1]), int(sa[k])
+    sa_, sb_ = int(sq[k - 1]), int(sq[k])
+    if sa_ > sb_:
+        a, b, sa_, sb_ = b, a, sb_, sa_
+    starts = np.asarray(seq_starts, dtype=np.int64)
+    res.update(length=L, rank=k, seq_a=sa_, pos_a=a - int(starts[sa_]),
+               seq_b=sb_, pos_b=b - int(starts[sb_]))
+    run_start = np.ones(n, dtype=bool)
+    run_start[1:] = lcp[1:] < L
+    run_id = np.cumsum(run_start) - 1
+    qual = np.zeros(int(run_id[-1]) + 1, dtype=bool)
+    seeds = (~run_start) & cross
+    qual[run_id[seeds]] = True
+    members = sa[qual[run_id]]
+    res["positions"] = np.sort(members)
+    return res
+
+
+def lcs_dp(a, b, with_positions: bool = True):
+    """Longest common substring of two ASCII sequences by the O(n*m) dynamic
+    program (brute force; no suffix array).  Returns (L, starts_a, starts_b):
+    the start offsets of every occurrence of a length-L common substring."""
+    a, b = _u8(a), _u8(b)
+    ma = np.zeros(max(a.size, 1), dtype=np.uint8)
+    mb = np.zeros(max(b.size, 1), dtype=np.uint8)
+    L = _load().oracle_lcs_dp(_ptr(a), a.size, _ptr(b), b.size,
+                              _ptr(ma) if with_positions else None,
+                              _ptr(mb) if with_positions else None)
+    if L < 0:
+        raise MemoryError("oracle_lcs_dp failed")
+    return int(L), np.flatnonzero(ma[:a.size]), np.flatnonzero(mb[:b.size])
+
+
+def overlap_by_dp(seqs):
+    """Overlap length and position set over several sequences by pairwise DP:
+    L = max over pairs of the longest common substring; a text position is in
+    the set when its length-L substring also occurs in another sequence."""
+    seqs = [_u8(s) for s in seqs]
+    best = 0
+    pair_res = {}
+    for i in range(len(seqs)):
+        for j in range(i + 1, len(seqs)):
+            r = lcs_dp(seqs[i], seqs[j])
+            pair_res[(i, j)] = r
+            best = max(best, r[0])
+    starts = np.cumsum([0] + [len(s) + 1 for s in seqs])
+    pos = set()
+    if best > 0:
+        for (i, j), (L, pa, pb) in pair_res.items():
+            if L == best:
+                pos.update(int(starts[i] + x) for x in pa)
+                pos.update(int(starts[j] + x) for x in pb)
+    return best, np.array(sorted(pos), dtype=np.int64)
+
+
+# --------------------------------------------------------------------------
+# a11..a12: sparse table and LCP queries between arbitrary suffixes
+# --------------------------------------------------------------------------
+
+def sparse_table_levels(n: int) -> int:
+    """floor(log2 n) + 1 levels (level j covers windows of 2**j entries)."""
+    return max(1, int(n).bit_length()) if n > 0 else 1
+
+
+def sparse_table(lcp) -> np.ndarray:
+    """ST[j][i] = min(lcp[i : min(i + 2**j, n)]) (range minima over windows
+    clipped at the end of the array), built level by level:
+    ST[j][i] = min(ST[j-1][i], ST[j-1][i + 2**(j-1)]) where that index exists."""
+    lcp = np.asarray(lcp, dtype=np.int32)
+    n = lcp.size
+    J = sparse_table_levels(n)
+    st = np.empty((J, n), dtype=np.int32)
+    st[0] = lcp
+    for j in range(1, J):
+        h = 1 << (j - 1)
+        st[j] = st[j - 1]
+        if h < n:
+            st[j, : n - h] = np.minimum(st[j - 1, : n - h], st[j - 1, h:])
+    return st
+
+
+def lcp_pairs(text, p, q) -> np.ndarray:
+    """LCP of suffixes p[i] and q[i] by direct symbol comparison; the LCP of a
+    suffix with itself is its length (Section 3, lcp of arbitrary suffixes)."""
+    t = _u8(text)
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    out = np.empty(p.size, dtype=np.int32)
+    if _load().oracle_lcp_pairs(_ptr(t), t.size, _ptr(p), _ptr(q), p.size, _ptr(out)) != 0:
+        raise ValueError("query position out of range")
+    return out
+
+
+# --------------------------------------------------------------------------
+# Section 4: the 1-bit split primitive and the radix sort built from it
+# --------------------------------------------------------------------------
+
+def split_1bit(keys, bit: int):
+    """One split step of Section 4 (Algorithm 1): b = bit of each key,
+    e = NOT b, f = exclusive prefix sum of e, totalFalse = e[n-1] + f[n-1],
+    destination = b ? i - f + totalFalse : f.  Returns (out, e, f, total)."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    n = keys.size
+    b = ((keys >> np.uint64(bit)) & np.uint64(1)).astype(np.int64)
+    e = 1 - b
+    f = np.zeros(n, dtype=np.int64)
+    if n > 1:
+        f[1:] = np.cumsum(e)[:-1]
+    total = int(e[-1] + f[-1]) if n else 0
+    i = np.arange(n, dtype=np.int64)
+    dest = np.where(b == 1, i - f + total, f)
+    out = np.empty_like(keys)
+    out[dest] = keys
+    return out, e, f, total
+
+
+def radix_sort_split(keys, nbits: int, values=None):
+    """LSD radix sort by repeated 1-bit splits over bits 0..nbits-1
+    (Section 4, Algorithm 1).  Stable; returns (keys, values)."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    vals = np.arange(keys.size, dtype=np.int64) if values is None else np.asarray(values)
+    for bit in range(nbits):
+        b = ((keys >> np.uint64(bit)) & np.uint64(1)).astype(np.int64)
+        e = 1 - b
+        f = np.zeros(keys.size, dtype=np.int64)
+        if keys.size > 1:
+            f[1:] = np.cumsum(e)[:-1]
+        total = int(e[-1] + f[-1]) if keys.size else 0
+        i = np.arange(keys.size, dtype=np.int64)
+        dest = np.where(b == 1, i - f + total, f)
+        nk = np.empty_like(keys)
+        nv = np.empty_like(vals)
+        nk[dest] = keys
+        nv[dest] = vals
+        keys, vals = nk, nv
+    return keys, vals

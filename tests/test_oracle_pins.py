@@ -1,0 +1,317 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test ties an oracle function to something other than itself: values the
+paper prints for its worked example (tests/golden/), closed forms, a theorem
+(the LCP identity of Section 3), an independent brute force (the O(n*m)
+longest-common-substring dynamic program; Python string comparison), or
+planted structure.  Chosen so that a dropped term, wrong sign, wrong index or
+transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from golden.load import load
+import lor_inputs as gen
+
+
+# ---------------------------------------------------------------- paper example
+
+@pytest.fixture(scope="module")
+def paper(oracle_mod):
+    g = load("paper_example.txt")
+    text, sigma = oracle_mod.encode_raw(g["text"][0].encode())
+    return g, text
+
+
+def test_table1_suffix_array(oracle_mod, paper):
+    g, text = paper
+    assert oracle_mod.suffix_array(text).tolist() == g["sa"]
+
+
+def test_table3_ranks(oracle_mod, paper):
+    g, text = paper
+    isa = oracle_mod.inverse_suffix_array(oracle_mod.suffix_array(text))
+    assert (isa + 1).tolist() == g["ranks1"]
+
+
+def test_table2_sample_ranks(oracle_mod, paper):
+    g, text = paper
+    n = len(text)
+    assert [i for i in range(n) if i % 3 != 0] == g["sample_set"]
+    assert [i for i in range(n) if i % 3 == 1] == g["b1"]
+    assert [i for i in range(n) if i % 3 == 2] == g["b2"]
+    assert oracle_mod.sample_ranks(text).tolist() == g["sample_ranks"]
+
+
+def test_step2_nonsample_order(oracle_mod, paper):
+    g, text = paper
+    order = oracle_mod.nonsample_order(text).tolist()
+    assert order == g["nonsample_order"]
+    ranks = oracle_mod.sample_ranks(text)
+    pairs = [v for i in order for v in (int(text[i]), int(ranks[i + 1]))]
+    assert pairs == g["nonsample_pairs"]
+    # the pairs themselves are in increasing lexicographic order
+    tup = list(zip(pairs[0::2], pairs[1::2]))
+    assert tup == sorted(tup)
+
+
+def test_lcp_table(oracle_mod, paper):
+    g, text = paper
+    sa = oracle_mod.suffix_array(text)
+    assert oracle_mod.lcp_array(text, sa).tolist() == g["lcp"]
+
+
+# ---------------------------------------------------------------- split / radix
+
+def test_split_example(oracle_mod):
+    g = load("split_example.txt")
+    out, e, f, total = oracle_mod.split_1bit(g["keys"], g["bit"][0])
+    bits = [(k >> g["bit"][0]) & 1 for k in g["keys"]]
+    assert bits == g["L"]
+    assert e.tolist() == g["E"]
+    assert f.tolist() == g["F"]
+    assert total == g["total_false"][0]
+    assert out.tolist() == g["out"]
+
+
+def test_radix_split_sort_matches_builtin_sort(oracle_mod):
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 1 << 12, size=3000, dtype=np.uint64)
+    k, v = oracle_mod.radix_sort_split(keys, 12)
+    ref = sorted(range(len(keys)), key=lambda i: (int(keys[i]), i))   # stable
+    assert v.tolist() == ref
+    assert k.tolist() == [int(keys[i]) for i in ref]
+
+
+def test_radix_split_sort_partial_bits_is_stable_on_low_bits(oracle_mod):
+    rng = np.random.default_rng(8)
+    keys = rng.integers(0, 1 << 16, size=2000, dtype=np.uint64)
+    _, v = oracle_mod.radix_sort_split(keys, 5)
+    ref = sorted(range(len(keys)), key=lambda i: (int(keys[i]) & 31, i))
+    assert v.tolist() == ref
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 50, 301])
+def test_single_symbol_run_closed_form(oracle_mod, k):
+    text, _ = oracle_mod.encode_raw(b"A" * k)
+    sa = oracle_mod.suffix_array(text)
+    assert sa.tolist() == list(range(k - 1, -1, -1))
+    assert oracle_mod.lcp_array(text, sa).tolist() == list(range(k))
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 40])
+def test_period_two_closed_form(oracle_mod, k):
+    text, _ = oracle_mod.encode_raw(b"AC" * k)
+    sa = oracle_mod.suffix_array(text)
+    a_part = list(range(2 * k - 2, -1, -2))
+    c_part = list(range(2 * k - 1, 0, -2))
+    assert sa.tolist() == a_part + c_part
+    lcp = oracle_mod.lcp_array(text, sa).tolist()
+    assert lcp == [0] + list(range(2, 2 * k - 1, 2)) + [0] + list(range(1, 2 * k - 2, 2))
+
+
+# ---------------------------------------------------------------- brute force
+
+def test_all_short_strings_against_python_string_order(oracle_mod):
+    alpha = "ACGT"
+    for L in range(1, 7):
+        for tup in itertools.product(alpha, repeat=L):
+            s = "".join(tup)
+            text, _ = oracle_mod.encode_raw(s.encode())
+            sa = oracle_mod.suffix_array(text).tolist()
+            ref = sorted(range(L), key=lambda i: s[i:])
+            assert sa == ref, s
+            lcp = oracle_mod.lcp_array(text, np.array(sa, np.int32)).tolist()
+            ref_lcp = [0] + [len(os.path.commonprefix([s[ref[k - 1]:], s[ref[k]:]]))
+                             for k in range(1, L)]
+            assert lcp == ref_lcp, s
+
+
+def test_terminated_text_order(oracle_mod):
+    # Separator codes sit below every base and the last terminator is the
+    # smallest symbol, so SA[0] = n-1 and SA[1] = |S1| for two sequences.
+    seqs = [np.frombuffer(b"GATTACA", np.uint8), np.frombuffer(b"TAGACAT", np.uint8)]
+    text, starts, sigma = oracle_mod.encode_concat(seqs)
+    assert sigma == 7
+    assert text.tolist() == [5, 3, 6, 6, 3, 4, 3, 2, 6, 3, 5, 3, 4, 3, 6, 1]
+    sa = oracle_mod.suffix_array(text)
+    assert sa[0] == len(text) - 1 and sa[1] == 7
+    assert oracle_mod.check_suffix_array(text, sa) == -1
+
+
+def test_check_suffix_array_rejects_wrong_arrays(oracle_mod):
+    seqs, _ = gen.pair_uniform(n_each=500, plant_len=40, seed=3)
+    text, _, _ = oracle_mod.encode_concat(seqs)
+    sa = oracle_mod.suffix_array(text)
+    assert oracle_mod.check_suffix_array(text, sa, nthreads=3) == -1
+    bad = sa.copy()
+    bad[10], bad[11] = bad[11], bad[10]
+    assert oracle_mod.check_suffix_array(text, bad) == 11
+    dup = sa.copy()
+    dup[5] = dup[6]
+    assert oracle_mod.check_suffix_array(text, dup) == len(text)
+
+
+def test_parallel_sort_equals_serial(oracle_mod):
+    seqs, _ = gen.pair_noncoding(n_each=20_000, seed=11, shared_len=3000, core=600)
+    text, _, _ = oracle_mod.encode_concat(seqs)
+    a = oracle_mod.suffix_array(text, nthreads=1)
+    b = oracle_mod.suffix_array(text, nthreads=8)
+    assert np.array_equal(a, b)
+    assert oracle_mod.check_suffix_array(text, a) == -1
+    assert np.array_equal(oracle_mod.lcp_array(text, a, 1), oracle_mod.lcp_array(text, a, 5))
+
+
+# ---------------------------------------------------------------- LCP identity
+
+def test_lcp_identity_of_section3(oracle_mod):
+    # lcp(S_SA[i], S_SA[j]) = min over i < k <= j of lcp[k]   (Section 3)
+    rng = np.random.default_rng(5)
+    for trial in range(30):
+        seqs = gen.fuzz_sequences(100 + trial, nseq=2, max_len=80,
+                                  alphabet=b"AC" if trial % 2 else b"ACGT")
+        text, _, _ = oracle_mod.encode_concat(seqs)
+        n = len(text)
+        sa = oracle_mod.suffix_array(text)
+        lcp = oracle_mod.lcp_array(text, sa)
+        isa = oracle_mod.inverse_suffix_array(sa)
+        p = rng.integers(0, n, 200).astype(np.int32)
+        q = rng.integers(0, n, 200).astype(np.int32)
+        got = oracle_mod.lcp_pairs(text, p, q)
+        for a, b, g in zip(p, q, got):
+            if a == b:
+                assert g == n - a
+            else:
+                r1, r2 = sorted((isa[a], isa[b]))
+                assert g == lcp[r1 + 1:r2 + 1].min()
+
+
+# ---------------------------------------------------------------- sparse table
+
+def test_sparse_table_is_window_minimum(oracle_mod):
+    rng = np.random.default_rng(9)
+    for n in [1, 2, 3, 7, 64, 100, 257]:
+        lcp = rng.integers(0, 20, n).astype(np.int32)
+        st = oracle_mod.sparse_table(lcp)
+        assert st.shape == (oracle_mod.sparse_table_levels(n), n)
+        for j in range(st.shape[0]):
+            for i in range(n):
+                assert st[j, i] == lcp[i:min(i + (1 << j), n)].min()
+
+
+# ---------------------------------------------------------------- LCS DP pins
+
+def _brute_lcs(a: bytes, b: bytes):
+    best, sa_, sb_ = 0, set(), set()
+    subs_b = {}
+    for j in range(len(b)):
+        for e in range(j + 1, len(b) + 1):
+            subs_b.setdefault(b[j:e], []).append(j)
+    for i in range(len(a)):
+        for e in range(i + 1, len(a) + 1):
+            w = a[i:e]
+            if w in subs_b:
+                if len(w) > best:
+                    best, sa_, sb_ = len(w), set(), set()
+                if len(w) == best:
+                    sa_.add(i)
+                    sb_.update(subs_b[w])
+    return best, sorted(sa_), sorted(sb_)
+
+
+def test_lcs_dp_against_substring_enumeration(oracle_mod):
+    assert oracle_mod.lcs_dp(b"GATTACA", b"TTAC")[0] == 4
+    assert oracle_mod.lcs_dp(b"AAAA", b"CCC")[0] == 0
+    for seed in range(40):
+        a, b = gen.fuzz_sequences(seed, nseq=2, max_len=25,
+                                  alphabet=b"AC" if seed % 3 == 0 else b"ACGT")
+        L, pa, pb = oracle_mod.lcs_dp(a, b)
+        rL, rpa, rpb = _brute_lcs(bytes(a), bytes(b))
+        assert L == rL
+        if L:
+            assert pa.tolist() == rpa and pb.tolist() == rpb
+
+
+# ---------------------------------------------------------------- overlap pins
+
+def _check_overlap_vs_dp(oracle_mod, seqs):
+    text, starts, _ = oracle_mod.encode_concat(seqs)
+    sa = oracle_mod.suffix_array(text)
+    lcp = oracle_mod.lcp_array(text, sa)
+    ov = oracle_mod.longest_overlap(text, sa, lcp, starts)
+    L, pos = oracle_mod.overlap_by_dp(seqs)
+    assert ov["length"] == L
+    assert ov["positions"].tolist() == pos.tolist()
+    if L == 0:
+        assert ov["rank"] == -1 and ov["seq_a"] == -1
+        return ov
+    # the canonical pair really shares L symbols and sits at adjacent ranks
+    k = ov["rank"]
+    assert lcp[k] == L and k >= 1
+    pa = starts[ov["seq_a"]] + ov["pos_a"]
+    pb = starts[ov["seq_b"]] + ov["pos_b"]
+    assert ov["seq_a"] < ov["seq_b"]
+    assert {int(pa), int(pb)} == {int(sa[k - 1]), int(sa[k])}
+    assert np.array_equal(text[pa:pa + L], text[pb:pb + L])
+    # smallest rank: no earlier cross pair reaches L
+    sq = oracle_mod.seq_of(sa, starts)
+    for kk in range(1, k):
+        assert not (sq[kk] != sq[kk - 1] and lcp[kk] >= L)
+    return ov
+
+
+def test_overlap_fuzz_against_dp(oracle_mod):
+    for seed in range(120):
+        nseq = 2 if seed % 4 else 3
+        alpha = [b"ACGT", b"AC", b"A"][seed % 3]
+        seqs = gen.fuzz_sequences(1000 + seed, nseq=nseq, max_len=40, alphabet=alpha)
+        _check_overlap_vs_dp(oracle_mod, seqs)
+
+
+@pytest.mark.parametrize("name", sorted(gen.degenerate_cases()))
+def test_overlap_degenerate_against_dp(oracle_mod, name):
+    _check_overlap_vs_dp(oracle_mod, gen.degenerate_cases()[name])
+
+
+def _assert_covers(ov, start, plant_len):
+    """Some listed occurrence of the length-L region contains the plant (the
+    plant may extend by chance when neighbouring bases agree)."""
+    L = ov["length"]
+    assert any(p <= start and start + plant_len <= p + L for p in ov["positions"].tolist())
+
+
+def test_overlap_planted_pair_against_dp(oracle_mod):
+    seqs, info = gen.pair_uniform(n_each=20_000, plant_len=500, seed=77)
+    ov = _check_overlap_vs_dp(oracle_mod, seqs)
+    assert ov["length"] >= 500
+    o1, o2 = info["plant_offsets"]
+    _assert_covers(ov, o1, 500)
+    _assert_covers(ov, 20_001 + o2, 500)
+
+
+def test_overlap_tiny_workload_planted_invariant(oracle_mod):
+    seqs, info = gen.pair_uniform()            # 2 x 100,000, 500-base plant
+    text, starts, _ = oracle_mod.encode_concat(seqs)
+    sa = oracle_mod.suffix_array(text, nthreads=4)
+    assert oracle_mod.check_suffix_array(text, sa, nthreads=4) == -1
+    lcp = oracle_mod.lcp_array(text, sa, nthreads=4)
+    ov = oracle_mod.longest_overlap(text, sa, lcp, starts)
+    assert ov["length"] >= 500
+    o1, o2 = info["plant_offsets"]
+    _assert_covers(ov, o1, 500)
+    _assert_covers(ov, int(starts[1]) + o2, 500)
+
+
+# ---------------------------------------------------------------- encoding
+
+def test_encode_concat_codes_and_errors(oracle_mod):
+    text, starts, sigma = oracle_mod.encode_concat([b"AC", b"gt"])
+    assert text.tolist() == [3, 4, 2, 5, 6, 1]
+    assert starts.tolist() == [0, 3, 6] and sigma == 7
+    with pytest.raises(ValueError):
+        oracle_mod.encode_concat([b"ACN", b"GT"])
