@@ -1,0 +1,207 @@
+/*
+ * lor.h -- C ABI of the GB300 longest-overlap-region library (liblor.so).
+ *
+ * Method: arXiv 1404.3448, "Solving The Longest Overlap Region Problem for
+ * Noncoding DNA Sequences with GPU".  Section 3 states the problem (longest
+ * common prefix of suffixes of the sequences and its positions in the suffix
+ * array), builds the suffix array with DC3 (Steps 1-3, Tables 1-3), derives
+ * the LCP array (LCP table), and answers LCP queries between arbitrary
+ * suffixes as range minima (the lcp identity and the RMQ definition).
+ * Section 4 (Algorithm 1) sorts DC3's keys with an LSD radix sort.
+ *
+ * Conventions shared by every call:
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
+ *     are host pointers.  The caller owns and allocates every buffer; the
+ *     library allocates no device memory and never frees caller memory.
+ *   - Calls only enqueue work on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream) and return without waiting, EXCEPT lor_build_sa, which
+ *     reads one 4-byte count back per DC3 recursion level and per radix sort
+ *     and therefore synchronises `stream` a few times per call.
+ *   - The return value reports errors found on the host (null pointers, bad
+ *     sizes, short workspace, CUDA launch errors).  Errors found by kernels
+ *     (bad symbols, out-of-range indices in inputs, a bounded wait that ran
+ *     out) are recorded in a per-device status word that lor_device_status()
+ *     reads and clears.  No call traps, aborts or throws.
+ *   - Indices are int32: texts hold at most LOR_MAX_N symbols.
+ */
+#ifndef LOR_H
+#define LOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lor_stream_t; /* same type as cudaStream_t */
+
+/* Status codes. */
+#define LOR_OK 0
+#define LOR_ERR_INVALID_ARG (-1) /* null pointer, negative or zero size, bad nseq */
+#define LOR_ERR_BAD_SYMBOL (-2)  /* input symbol outside ACGT/acgt, or text code out of [1, sigma) */
+#define LOR_ERR_TOO_LARGE (-3)   /* n > LOR_MAX_N */
+#define LOR_ERR_WORKSPACE (-4)   /* workspace null or smaller than the *_workspace_size query */
+#define LOR_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define LOR_ERR_TIMEOUT (-6)     /* a bounded inter-block wait ran out on the device */
+#define LOR_ERR_BAD_INPUT (-7)   /* an input array holds an out-of-range index (SA, ISA, query) */
+
+/* Largest supported text length (int32 indices with head-room for DC3's
+ * dummy sample and padding). */
+#define LOR_MAX_N 2147483000LL
+
+/* Largest number of sequences in one concatenated text (codes fit a byte). */
+#define LOR_MAX_SEQ 250
+
+/* Result of lor_longest_overlap (written to device memory). */
+typedef struct {
+    int32_t length; /* L: longest common region of two different sequences; 0 if none */
+    int32_t rank;   /* smallest suffix-array index k >= 1 with SA[k-1], SA[k] in
+                       different sequences and LCP[k] == L; -1 if L == 0 */
+    int32_t seq_a;  /* lower sequence id of the pair at rank k; -1 if L == 0 */
+    int32_t pos_a;  /* 0-based offset of that suffix inside sequence seq_a */
+    int32_t seq_b;  /* higher sequence id of the pair at rank k */
+    int32_t pos_b;  /* 0-based offset inside sequence seq_b */
+    int32_t n_pos;  /* number of text positions whose length-L prefix also occurs
+                       in another sequence (may exceed pos_cap) */
+    int32_t reserved;
+} lor_overlap;
+
+/* ---------------------------------------------------------------------------
+ * a1. Encode and concatenate (Section 3: the overlap of two or more
+ * sequences is read off one suffix array; the separator scheme is this
+ * library's reading, the paper states none).
+ *
+ * d_ascii    : device, the nseq sequences' ASCII bytes back to back
+ *              (sum(h_lens) bytes; A/C/G/T in either case).
+ * h_lens     : host, nseq lengths (each >= 0).
+ * d_text     : device, receives n = sum(h_lens) + nseq codes: sequence i is
+ *              followed by its terminator.  Codes: terminator of sequence i
+ *              = nseq - i (1..nseq), A,C,G,T = nseq+1 .. nseq+4.  0 is
+ *              reserved as padding and never written.  sigma = nseq + 5.
+ * d_seq_starts: device int32[nseq + 1]: start of each sequence in d_text,
+ *              d_seq_starts[nseq] = n.  May be NULL.
+ * A symbol outside ACGT/acgt sets LOR_ERR_BAD_SYMBOL in the status word and is
+ * stored as the code of A.  Returns LOR_ERR_INVALID_ARG for nseq outside
+ * [1, LOR_MAX_SEQ], LOR_ERR_TOO_LARGE when n > LOR_MAX_N.
+ * ------------------------------------------------------------------------- */
+int lor_encode_concat(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq,
+                      uint8_t *d_text, int32_t *d_seq_starts, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a2-a8. Suffix array by DC3 (Section 3, Steps 1-3; Tables 1-3), with the
+ * sample and nonsample keys sorted by LSD radix sort (Section 4,
+ * Algorithm 1).
+ *
+ * d_text : device uint8[n], codes in [1, sigma) (0 is reserved as padding);
+ *          any text works, terminated (lor_encode_concat) or raw.  The end of
+ *          the text compares smaller than every code.
+ * sigma  : number of codes including 0 (2..256).
+ * d_sa   : device int32[n], receives the suffix array: the start positions of
+ *          the suffixes in increasing lexicographic order.
+ * d_ws   : device workspace of at least lor_build_sa_workspace_size(n, sigma)
+ *          bytes, 256-byte aligned; contents on entry are ignored.
+ * A code outside [1, sigma) sets LOR_ERR_BAD_SYMBOL in the status word (the
+ * output is then unspecified but every access stays in bounds).
+ * Synchronises `stream` once per recursion level and per radix sort.
+ * ------------------------------------------------------------------------- */
+size_t lor_build_sa_workspace_size(int64_t n, int32_t sigma);
+int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
+                 void *d_ws, size_t ws_bytes, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a9. Inverse suffix array and LCP array (Section 3, LCP table; Kasai et al.,
+ * cited there).  ISA[SA[k]] = k; LCP[0] = 0 and LCP[k] is the length of the
+ * longest common prefix of the suffixes SA[k-1] and SA[k].
+ *
+ * d_text, n : as for lor_build_sa.   d_sa : device int32[n] suffix array.
+ * d_isa     : device int32[n] output.  d_lcp : device int32[n] output.
+ * An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT (and is skipped).
+ * ------------------------------------------------------------------------- */
+int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, int32_t *d_isa,
+            int32_t *d_lcp, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a10. Longest overlap region (Section 3: the longest common prefix between
+ * suffixes of the two sequences, with its positions in the suffix array).
+ * L = max over k in [1, n) with seq(SA[k-1]) != seq(SA[k]) of LCP[k].
+ *
+ * d_seq_starts : device int32[nseq + 1] as written by lor_encode_concat.
+ * d_out        : device, one lor_overlap (see the struct for the tie rule).
+ * d_pos        : device int32[pos_cap] (may be NULL when pos_cap == 0):
+ *                receives, sorted ascending, every text position p whose
+ *                length-L prefix also occurs in another sequence (every
+ *                member of a maximal rank run with adjacent LCP >= L that
+ *                holds suffixes of two or more sequences).  Only the first
+ *                pos_cap are written; d_out->n_pos holds the full count.
+ * d_ws         : device workspace of lor_longest_overlap_workspace_size(n)
+ *                bytes, 256-byte aligned.
+ * ------------------------------------------------------------------------- */
+size_t lor_longest_overlap_workspace_size(int64_t n);
+int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, int64_t n,
+                        const int32_t *d_seq_starts, int32_t nseq, lor_overlap *d_out,
+                        int32_t *d_pos, int64_t pos_cap, void *d_ws, size_t ws_bytes,
+                        lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a11. Sparse table over the LCP array for range-minimum queries (Section 3:
+ * RMQ definition; the LCP of arbitrary suffixes is a range minimum).
+ * Layout: level-major int32[levels][n] with levels = floor(log2 n) + 1;
+ * table[j*n + i] = min(lcp[i .. min(i + 2^j, n) - 1]).
+ * table_elems must be >= lor_rmq_table_elems(n).
+ * ------------------------------------------------------------------------- */
+int64_t lor_rmq_table_elems(int64_t n);
+int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
+                  lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * a12. LCP of arbitrary suffix pairs (Section 3: lcp(S_p, S_q) = min of the
+ * adjacent LCPs strictly between their ranks, through the RMQ).
+ * out[i] = length of the longest common prefix of suffixes p[i] and q[i]
+ * (n - p[i] when p[i] == q[i]).  All arrays device, int32[nq].
+ * A p or q outside [0, n) sets LOR_ERR_BAD_INPUT and yields -1 for that query.
+ * ------------------------------------------------------------------------- */
+int lor_rmq_query(const int32_t *d_table, const int32_t *d_isa, int64_t n, const int32_t *d_p,
+                  const int32_t *d_q, int64_t nq, int32_t *d_out, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * The radix sort of Section 4 (Algorithm 1) as a standalone primitive:
+ * stable LSD sort of m (key, value) pairs by the low key_bits bits of the
+ * keys, in place.  d_keys uint64[m], d_vals uint32[m]; d_ws of
+ * lor_radix_sort_workspace_size(m) bytes.  Synchronises `stream` once.
+ * ------------------------------------------------------------------------- */
+size_t lor_radix_sort_workspace_size(int64_t m);
+int lor_radix_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t m, int32_t key_bits,
+                         void *d_ws, size_t ws_bytes, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Status, diagnostics and instrumentation (no counterpart in the paper).
+ * ------------------------------------------------------------------------- */
+/* Synchronise `stream`, then return and clear the first device-side error
+ * recorded on the current device since the last call (LOR_OK if none). */
+int lor_device_status(lor_stream_t stream);
+const char *lor_status_string(int status);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t lor_launch_count(void);
+
+/* Per-level trace of the most recent lor_build_sa call in this process:
+ * fills up to cap entries of level length n_l, distinct names found at that
+ * level, and key bits sorted; returns the number of levels. */
+int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits, int32_t cap);
+
+/* Kernel timing: when enabled, every launch records a CUDA event pair on its
+ * stream together with the algorithmic bytes it moves.  lor_profile_read
+ * synchronises those events and returns, for one kernel kind, the launch
+ * count, summed device milliseconds and summed algorithmic bytes. */
+int lor_profile_enable(int on);
+int lor_profile_reset(void);
+int lor_profile_kinds(void);
+const char *lor_profile_kind_name(int kind);
+int lor_profile_read(int kind, int64_t *h_launches, double *h_ms, double *h_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOR_H */

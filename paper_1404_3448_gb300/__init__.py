@@ -1,0 +1,12 @@
+"""GB300-native longest-overlap-region library (arXiv 1404.3448).
+
+DC3 suffix array, Kasai LCP, cross-sequence max-LCP overlap and sparse-table
+RMQ as hand-written CUDA kernels for sm_103a behind the C ABI in
+include/lor.h; ``lor`` is the thin Python binding.
+"""
+from . import build  # noqa: F401
+from .lor import (  # noqa: F401
+    LorError, Pipeline, build_sa, check_device, device_status, encode_concat, last_dc3_trace,
+    lcp, load, longest_overlap, overlap_dict, profile_enable, profile_read, profile_reset,
+    radix_sort_pairs, rmq_build, rmq_query, workspace,
+)

@@ -1,0 +1,238 @@
+// common.cuh -- shared device/host helpers of liblor (status word, launch
+// accounting, kernel timing hooks, bounded waits, block scans).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "lor.h"
+
+namespace lor {
+
+// ---------------------------------------------------------------- sizes
+
+constexpr int kWarp = 32;
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline int bit_width_u64(uint64_t v) {  // number of bits needed to hold v
+    int b = 0;
+    while (v) { b++; v >>= 1; }
+    return b;
+}
+
+// ---------------------------------------------------------------- host side
+
+// Launch accounting and kernel timing (defined in abi.cu).
+void note_launch();
+enum ProfKind {
+    PK_ENCODE = 0,
+    PK_SAMPLE_KEYS,
+    PK_RADIX_HIST,
+    PK_RADIX_PASS,
+    PK_NAMING,
+    PK_RANK_SCATTER,
+    PK_NONSAMPLE,
+    PK_MERGE,
+    PK_ISA_SCATTER,
+    PK_KASAI,
+    PK_OVERLAP_SCAN,
+    PK_OVERLAP_COLLECT,
+    PK_RMQ_LEVEL,
+    PK_RMQ_QUERY,
+    PK_OTHER,
+    PK_COUNT
+};
+bool prof_enabled();
+// Records an event pair around one launch when profiling is on.
+struct ProfScope {
+    int slot = -1;
+    cudaStream_t stream;
+    ProfScope(int kind, double bytes, cudaStream_t s);
+    ~ProfScope();
+};
+
+// Scoped device status helpers: every translation unit owns one status word.
+#define LOR_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return LOR_ERR_CUDA;         \
+    } while (0)
+
+#define LOR_LAUNCH_CHECK()                                  \
+    do {                                                    \
+        lor::note_launch();                                 \
+        cudaError_t _e = cudaPeekAtLastError();             \
+        if (_e != cudaSuccess) return LOR_ERR_CUDA;         \
+    } while (0)
+
+// ---------------------------------------------------------------- device side
+
+// Monotonic nanosecond clock shared by all SMs.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every inter-block wait gives up after this long and reports LOR_ERR_TIMEOUT.
+constexpr uint64_t kSpinLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_volatile_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Decoupled look-back descriptors: [epoch:30 | flag:2 | value:32].
+constexpr uint64_t kFlagAgg = 1, kFlagIncl = 2;
+__device__ __forceinline__ uint64_t lb_pack(uint32_t epoch, uint64_t flag, uint32_t v) {
+    return (uint64_t(epoch) << 34) | (flag << 32) | uint64_t(v);
+}
+__device__ __forceinline__ uint32_t lb_epoch(uint64_t w) { return uint32_t(w >> 34); }
+__device__ __forceinline__ uint32_t lb_flag(uint64_t w) { return uint32_t((w >> 32) & 3); }
+__device__ __forceinline__ uint32_t lb_value(uint64_t w) { return uint32_t(w); }
+
+// Inclusive warp scan of 32-bit values.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Exclusive block scan of one value per thread (blockDim.x = NT, multiple of
+// 32, at most 1024).  `scratch` needs NT/32 + 1 words.  Returns the exclusive
+// prefix; *total receives the block sum.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *scratch, uint32_t *total) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? scratch[lane] : 0;
+        uint32_t wi = warp_incl_scan(w);
+        if (lane < NW) scratch[lane] = wi - w;
+        if (lane == NW - 1) scratch[NW] = wi;
+    }
+    __syncthreads();
+    uint32_t excl = scratch[warp] + inc - v;
+    *total = scratch[NW];
+    __syncthreads();
+    return excl;
+}
+
+// Single-value decoupled look-back performed by warp 0 of a block: publishes
+// the tile aggregate, walks back over predecessors 32 at a time, publishes
+// the inclusive prefix and returns the exclusive prefix (to lane 0..31).
+// Every wait is bounded; on expiry *status gets LOR_ERR_TIMEOUT.
+__device__ __forceinline__ uint32_t warp_lookback(uint64_t *lb, int64_t tile, uint32_t agg,
+                                                  uint32_t epoch, int *status) {
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) st_volatile_u64(&lb[0], lb_pack(epoch, kFlagIncl, agg));
+        return 0;
+    }
+    if (lane == 0) st_volatile_u64(&lb[tile], lb_pack(epoch, kFlagAgg, agg));
+    uint32_t excl = 0;
+    int64_t j = tile - 1;
+    const uint64_t t0 = global_ns();
+    bool timed_out = false;
+    while (true) {
+        int64_t idx = j - lane;
+        uint64_t w = idx >= 0 ? ld_volatile_u64(&lb[idx]) : lb_pack(epoch, kFlagIncl, 0);
+        while (true) {
+            bool ready = lb_epoch(w) == epoch && lb_flag(w) != 0;
+            if (__all_sync(0xffffffffu, ready)) break;
+            if (!ready) w = ld_volatile_u64(&lb[idx]);
+            // warp-uniform decision: every lane leaves the loop together
+            if (__any_sync(0xffffffffu, global_ns() - t0 > kSpinLimitNs)) { timed_out = true; break; }
+        }
+        if (timed_out) {
+            if (lane == 0) atomicCAS(status, 0, LOR_ERR_TIMEOUT);
+            break;
+        }
+        uint32_t incl_mask = __ballot_sync(0xffffffffu, lb_flag(w) == kFlagIncl);
+        uint32_t v = lb_value(w);
+        if (incl_mask) {
+            int first = __ffs(incl_mask) - 1;
+            v = lane <= first ? v : 0;
+            excl += warp_sum(v);
+            break;
+        }
+        excl += warp_sum(v);
+        j -= 32;
+    }
+    if (lane == 0) {
+        __threadfence();
+        st_volatile_u64(&lb[tile], lb_pack(epoch, kFlagIncl, excl + agg));
+    }
+    return excl;
+}
+
+}  // namespace lor
+
+// One device status word per translation unit; kernels record the first
+// error with atomicCAS and the host reads it through the TU's accessor.
+#define LOR_DEFINE_TU_STATUS(name)                                                    \
+    static __device__ int g_tu_status;                                                \
+    int name(cudaStream_t s, int clear) {                                             \
+        int h = 0;                                                                    \
+        if (cudaMemcpyFromSymbolAsync(&h, g_tu_status, sizeof(int), 0,               \
+                                      cudaMemcpyDeviceToHost, s) != cudaSuccess)      \
+            return LOR_ERR_CUDA;                                                      \
+        if (cudaStreamSynchronize(s) != cudaSuccess) return LOR_ERR_CUDA;             \
+        if (clear && h != 0) {                                                        \
+            int z = 0;                                                                \
+            if (cudaMemcpyToSymbolAsync(g_tu_status, &z, sizeof(int), 0,              \
+                                        cudaMemcpyHostToDevice, s) != cudaSuccess)    \
+                return LOR_ERR_CUDA;                                                  \
+            if (cudaStreamSynchronize(s) != cudaSuccess) return LOR_ERR_CUDA;         \
+        }                                                                             \
+        return h;                                                                     \
+    }                                                                                 \
+    static int *tu_status_ptr() {                                                     \
+        static int *p = nullptr;                                                      \
+        static int dev = -1;                                                          \
+        int cur = -1;                                                                 \
+        cudaGetDevice(&cur);                                                          \
+        if (p == nullptr || dev != cur) {                                             \
+            void *q = nullptr;                                                        \
+            if (cudaGetSymbolAddress(&q, g_tu_status) != cudaSuccess) return nullptr; \
+            p = (int *)q;                                                             \
+            dev = cur;                                                                \
+        }                                                                             \
+        return p;                                                                     \
+    }
+
+// Accessors of every translation unit's status word (one per .cu file).
+int lor_status_encode(cudaStream_t s, int clear);
+int lor_status_dc3(cudaStream_t s, int clear);
+int lor_status_lcp(cudaStream_t s, int clear);
+int lor_status_overlap(cudaStream_t s, int clear);
+int lor_status_rmq(cudaStream_t s, int clear);
+int lor_status_abi(cudaStream_t s, int clear);

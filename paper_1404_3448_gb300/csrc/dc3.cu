@@ -1,0 +1,651 @@
+// dc3.cu -- suffix array by DC3 / skew (Section 3, Steps 1-3; Tables 1-3).
+//
+// One recursion level on a string s[0..n) over codes [1..K] (0 = padding):
+//   Step 1  sample positions C = {i : i mod 3 != 0} (plus the dummy position
+//           n when n mod 3 == 1) get keys from the symbols starting at i
+//           (the triple [t_i t_i+1 t_i+2]; level 0 may use a longer prefix),
+//           are radix sorted and named; R = R1 (i mod 3 == 1) followed by R2
+//           (i mod 3 == 2) holds the names.  Non-unique names -> recurse on R.
+//           The suffix array of R gives rank(S_i) for every sample i.
+//   Step 2  nonsample positions (i mod 3 == 0) ordered by (t_i, rank(S_i+1)):
+//           take them in the order of rank(S_i+1) from the sample order, then
+//           one stable radix sort by t_i.
+//   Step 3  merge: sample i in B1 against nonsample j compares
+//           (t_i, rank(S_i+1)) with (t_j, rank(S_j+1)); i in B2 compares
+//           (t_i, t_i+1, rank(S_i+2)) with (t_j, t_j+1, rank(S_j+2)).  (The
+//           paper prints rank(S_i+1) for B2; i+2 is the sample position.)
+// The host drives the recursion and reads one count per level.
+#include <cstdlib>
+#include <vector>
+
+#include "radix.cuh"
+
+LOR_DEFINE_TU_STATUS(lor_status_dc3)
+
+namespace lor {
+namespace {
+
+struct LevelSizes {
+    int64_t n, n0, n1, n2, n02;
+};
+inline LevelSizes level_sizes(int64_t n) {
+    LevelSizes z;
+    z.n = n;
+    z.n0 = (n + 2) / 3;
+    z.n1 = (n + 1) / 3;
+    z.n2 = n / 3;
+    z.n02 = z.n0 + z.n2;
+    return z;
+}
+
+// Lengths of every level the recursion could reach.
+std::vector<int64_t> level_chain(int64_t n) {
+    std::vector<int64_t> c{n};
+    while (c.back() > 3 && c.size() < 96) c.push_back(level_sizes(c.back()).n02);
+    return c;
+}
+
+constexpr size_t kPad = 4;  // zero symbols kept after every reduced string
+
+struct Dc3Layout {
+    size_t ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
+    size_t ka = 0, kb = 0, va = 0, vb = 0;
+    int64_t max_m = 0;
+    std::vector<int64_t> lev_n;
+    std::vector<size_t> lev_R, lev_SAR;
+    size_t total = 0;
+};
+
+Dc3Layout dc3_layout(int64_t n) {
+    Dc3Layout L;
+    L.lev_n = level_chain(n);
+    L.max_m = level_sizes(n).n02;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.ctrl = take(256);
+    L.hist = take(sizeof(uint32_t) * kMaxPasses * kRadix);
+    L.offsets = take(sizeof(uint32_t) * kMaxPasses * kRadix);
+    L.lookback_bytes = radix_lookback_bytes(L.max_m);
+    L.lookback = take(L.lookback_bytes);
+    L.ka = take(sizeof(uint64_t) * size_t(L.max_m));
+    L.kb = take(sizeof(uint64_t) * size_t(L.max_m));
+    L.va = take(sizeof(uint32_t) * size_t(L.max_m));
+    L.vb = take(sizeof(uint32_t) * size_t(L.max_m));
+    for (size_t l = 0; l < L.lev_n.size(); ++l) {
+        const int64_t m = level_sizes(L.lev_n[l]).n02;
+        L.lev_R.push_back(take(sizeof(int32_t) * (size_t(m) + kPad)));
+        L.lev_SAR.push_back(take(sizeof(int32_t) * size_t(m)));
+    }
+    L.total = off;
+    return L;
+}
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ int64_t sample_pos(int64_t j, int64_t n0) {
+    return j < n0 ? 3 * j + 1 : 3 * (j - n0) + 2;
+}
+
+// Step 1 keys: kchars symbols starting at the sample position, `bits` bits
+// each, most significant first; positions >= n read as 0.  At level 0 the
+// text codes are validated (must lie in [1, maxc]) and clamped.
+template <typename CharT, typename KeyT, bool kValidate>
+__global__ void __launch_bounds__(256) k_sample_keys(const CharT *__restrict__ s, int64_t n,
+                                                     int64_t n0, int64_t n02, int first, int kchars,
+                                                     int bits, int64_t maxc, KeyT *__restrict__ keys,
+                                                     int *status) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n02) return;
+    const int64_t p = sample_pos(j, n0);
+    KeyT key = 0;
+    bool bad = false;
+    for (int t = first; t < kchars; ++t) {
+        const int64_t q = p + t;
+        int64_t c = q < n ? int64_t(s[q]) : 0;
+        if (kValidate && q < n && (c < 1 || c > maxc)) {
+            bad = true;
+            c = c < 1 ? 1 : maxc;
+        }
+        key = (key << bits) | KeyT(c);
+    }
+    if (kValidate && j == 0 && n > 0) {
+        const int64_t c = int64_t(s[0]);
+        if (c < 1 || c > maxc) bad = true;
+    }
+    if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
+    keys[j] = key;
+}
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Step 1 naming: name(j) = 1 + number of key changes in sorted[0..j].
+// Writes R[val] = name, SA_R[j] = val, and the name count.
+template <typename KeyT>
+__global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ keys,
+                                                       const uint32_t *__restrict__ vals, int64_t m,
+                                                       int32_t *__restrict__ R, int32_t *__restrict__ SAR,
+                                                       uint32_t *n_names, uint64_t *lb,
+                                                       unsigned long long *ctr,
+                                                       unsigned long long tile_base, uint32_t epoch,
+                                                       int *status) {
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    KeyT prev = (base > 0 && base - 1 < m) ? keys[base - 1] : KeyT(0);
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m) {
+            const KeyT k = keys[j];
+            const uint32_t f = (j == 0 || k != prev) ? 1u : 0u;
+            flags |= f << i;
+            cnt += f;
+            prev = k;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) s_prefix = p;
+    }
+    __syncthreads();
+    uint32_t name = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m) {
+            name += (flags >> i) & 1u;
+            const uint32_t v = vals[j];
+            R[v] = int32_t(name);
+            SAR[j] = int32_t(v);
+            if (j == m - 1) *n_names = name;
+        }
+    }
+}
+
+// Naming after a two-stage sort: equality of triples is checked on the
+// string itself (the last sort key holds only the first symbol).
+template <typename CharT>
+__global__ void __launch_bounds__(kScanThreads) k_name_gather(
+    const uint32_t *__restrict__ vals, int64_t m, const CharT *__restrict__ s, int64_t n,
+    int64_t n0, int32_t *__restrict__ R, int32_t *__restrict__ SAR, uint32_t *n_names,
+    uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
+    int *status) {
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    auto ch = [&](int64_t q) -> int64_t { return q < n ? int64_t(s[q]) : 0; };
+    int64_t pp = (base > 0 && base - 1 < m) ? sample_pos(vals[base - 1], n0) : -1;
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m) {
+            const int64_t p = sample_pos(vals[j], n0);
+            const bool same = j > 0 && ch(p) == ch(pp) && ch(p + 1) == ch(pp + 1) &&
+                              ch(p + 2) == ch(pp + 2);
+            const uint32_t f = same ? 0u : 1u;
+            flags |= f << i;
+            cnt += f;
+            pp = p;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) s_prefix = p;
+    }
+    __syncthreads();
+    uint32_t name = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m) {
+            name += (flags >> i) & 1u;
+            const uint32_t v = vals[j];
+            R[v] = int32_t(name);
+            SAR[j] = int32_t(v);
+            if (j == m - 1) *n_names = name;
+        }
+    }
+}
+
+// First symbol of each sample in sorted order (second stage of a wide sort).
+template <typename CharT>
+__global__ void k_first_char(const uint32_t *__restrict__ vals, int64_t m, const CharT *__restrict__ s,
+                             int64_t n, int64_t n0, uint32_t *__restrict__ keys) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t p = sample_pos(vals[j], n0);
+    keys[j] = p < n ? uint32_t(s[p]) : 0u;
+}
+
+// rank(S_i) for every sample after recursion: rankR[SA_R[j]] = j + 1.
+__global__ void k_rank_scatter(const int32_t *__restrict__ SAR, int64_t m, int32_t *__restrict__ rankR,
+                               int *status) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int32_t r = SAR[j];
+    if (r < 0 || r >= m) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        return;
+    }
+    rankR[r] = int32_t(j + 1);
+}
+
+// Step 2 gather: nonsample positions 3r for every B1 sample r in rank order,
+// keyed by their first symbol (order-preserving compaction by look-back).
+template <typename CharT>
+__global__ void __launch_bounds__(kScanThreads) k_nonsample(
+    const int32_t *__restrict__ SAR, int64_t m, int64_t n0, const CharT *__restrict__ s, int64_t n,
+    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint64_t *lb, unsigned long long *ctr,
+    unsigned long long tile_base, uint32_t epoch, int *status) {
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    int32_t r[kScanItems];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        r[i] = j < m ? SAR[j] : -1;
+        if (r[i] >= 0 && r[i] < n0) cnt++;
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) s_prefix = p;
+    }
+    __syncthreads();
+    uint32_t o = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (r[i] >= 0 && r[i] < n0) {
+            const int64_t q = 3 * int64_t(r[i]);
+            keys[o] = q < n ? uint32_t(s[q]) : 0u;
+            vals[o] = uint32_t(q);
+            ++o;
+        }
+    }
+}
+
+// ---- Step 3: merge of sample and nonsample suffixes (merge path)
+
+template <typename CharT>
+struct MergeIn {
+    const CharT *s;
+    int64_t n, n0, n2;
+    const int32_t *rankR;  // rank(S_i) by reduced-string index, 1-based
+    const int32_t *A;      // sample order (reduced-string indices), dummy skipped
+    int64_t na;
+    const uint32_t *B;     // nonsample order (text positions)
+    int64_t nb;
+};
+
+template <typename CharT>
+__device__ __forceinline__ int32_t m_ch(const MergeIn<CharT> &a, int64_t q) {
+    return q < a.n ? int32_t(a.s[q]) : 0;
+}
+// rank(S_x) for a sample position x (the dummy x = n included), 0 beyond.
+template <typename CharT>
+__device__ __forceinline__ int32_t m_rk(const MergeIn<CharT> &a, int64_t x) {
+    const int64_t q = x / 3, rem = x - 3 * q;
+    if (rem == 1) return q < a.n0 ? a.rankR[q] : 0;
+    if (rem == 2) return q < a.n2 ? a.rankR[a.n0 + q] : 0;
+    return 0;
+}
+
+struct ARec { int32_t pos, c0, c1, r; };          // sample: r = rank(S_p+1) or rank(S_p+2)
+struct BRec { int32_t pos, c0, c1, r1, r2; };     // nonsample: r1 = rank(S_q+1), r2 = rank(S_q+2)
+
+template <typename CharT>
+__device__ __forceinline__ ARec load_a(const MergeIn<CharT> &a, int64_t i) {
+    const int64_t p = sample_pos(a.A[i], a.n0);
+    ARec x;
+    x.pos = int32_t(p);
+    x.c0 = m_ch(a, p);
+    x.c1 = m_ch(a, p + 1);
+    x.r = (p % 3 == 1) ? m_rk(a, p + 1) : m_rk(a, p + 2);
+    return x;
+}
+template <typename CharT>
+__device__ __forceinline__ BRec load_b(const MergeIn<CharT> &a, int64_t i) {
+    const int64_t q = a.B[i];
+    BRec y;
+    y.pos = int32_t(q);
+    y.c0 = m_ch(a, q);
+    y.c1 = m_ch(a, q + 1);
+    y.r1 = m_rk(a, q + 1);
+    y.r2 = m_rk(a, q + 2);
+    return y;
+}
+// Is the sample suffix x smaller than the nonsample suffix y?
+__device__ __forceinline__ bool a_less_b(const ARec &x, const BRec &y) {
+    if (x.c0 != y.c0) return x.c0 < y.c0;
+    if (x.pos % 3 == 1) return x.r < y.r1;
+    if (x.c1 != y.c1) return x.c1 < y.c1;
+    return x.r < y.r2;
+}
+
+constexpr int kMergeThreads = 128;
+constexpr int kMergeItems = 8;
+constexpr int kMergeTile = kMergeThreads * kMergeItems;
+
+// Number of sample suffixes among the first d merged suffixes.
+template <typename CharT>
+__device__ int64_t merge_split(const MergeIn<CharT> &a, int64_t d) {
+    int64_t lo = d - a.nb > 0 ? d - a.nb : 0;
+    int64_t hi = d < a.na ? d : a.na;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a_less_b(load_a(a, mid), load_b(a, d - 1 - mid))) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename CharT>
+__global__ void k_merge_partition(MergeIn<CharT> a, int64_t ntiles, int64_t *__restrict__ split) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    const int64_t tot = a.na + a.nb;
+    const int64_t d = t * kMergeTile < tot ? t * kMergeTile : tot;
+    split[t] = merge_split(a, d);
+}
+
+template <typename CharT>
+__global__ void __launch_bounds__(kMergeThreads) k_merge(MergeIn<CharT> a,
+                                                         const int64_t *__restrict__ split,
+                                                         int32_t *__restrict__ out, int *status) {
+    __shared__ ARec As[kMergeTile];
+    __shared__ BRec Bs[kMergeTile];
+    __shared__ int32_t Os[kMergeTile];
+    const int64_t t = blockIdx.x;
+    const int64_t tot = a.na + a.nb;
+    const int64_t d0 = t * kMergeTile;
+    const int64_t d1 = d0 + kMergeTile < tot ? d0 + kMergeTile : tot;
+    // Valid inputs give monotone splits; the clamps keep every access in
+    // bounds (and report it) if the inputs were not suffix-consistent.
+    int64_t a0 = split[t], a1 = split[t + 1];
+    const int64_t a0c = min64(max64(a0, max64(0, d0 - a.nb)), min64(d0, a.na));
+    int64_t a1c = min64(max64(a1, max64(0, d1 - a.nb)), min64(d1, a.na));
+    a1c = min64(max64(a1c, a0c), a0c + (d1 - d0));
+    if ((a0c != a0 || a1c != a1) && threadIdx.x == 0) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+    a0 = a0c;
+    a1 = a1c;
+    const int64_t b0 = d0 - a0, b1 = d1 - a1;
+    const int na = int(a1 - a0), nb = int(b1 - b0), nt = int(d1 - d0);
+    for (int i = threadIdx.x; i < na; i += kMergeThreads) As[i] = load_a(a, a0 + i);
+    for (int i = threadIdx.x; i < nb; i += kMergeThreads) Bs[i] = load_b(a, b0 + i);
+    __syncthreads();
+    const int dl = min(int(threadIdx.x) * kMergeItems, nt);
+    int lo = max(0, dl - nb), hi = min(dl, na);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a_less_b(As[mid], Bs[dl - 1 - mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    int ia = lo, ib = dl - lo;
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k) {
+        const int o = dl + k;
+        if (o >= nt) break;
+        const bool take_a = ib >= nb || (ia < na && a_less_b(As[ia], Bs[ib]));
+        Os[o] = take_a ? As[ia++].pos : Bs[ib++].pos;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += kMergeThreads) out[d0 + i] = Os[i];
+}
+
+// ---------------------------------------------------------------- host driver
+
+struct TraceRow {
+    int64_t n, names;
+    int32_t key_bits;
+};
+std::vector<TraceRow> g_trace;
+
+int level0_kchars(int bits) {
+    int k = 3;
+    if (const char *e = std::getenv("LOR_DC3_K0")) {
+        const int v = std::atoi(e);
+        if (v >= 3) k = v;
+    }
+    const int kmax = 64 / (bits > 0 ? bits : 1);
+    return k > kmax ? kmax : k;
+}
+
+struct Dc3Run {
+    cudaStream_t s;
+    int *status;
+    char *ws;
+    Dc3Layout L;
+    RadixScratch rs;
+    uint32_t *d_names;
+    void *ka, *kb;
+    uint32_t *va, *vb;
+    int64_t *split;  // merge partition, carved from the lookback area's tail use
+};
+
+inline unsigned grid_for(int64_t m, int nt) { return unsigned(cdiv(m > 0 ? m : 1, nt)); }
+
+template <typename CharT, typename KeyT>
+int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars,
+                         int bits, int64_t maxc, int32_t *Rl, int32_t *SAR) {
+    cudaStream_t st = D.s;
+    KeyT *k0 = (KeyT *)D.ka, *k1 = (KeyT *)D.kb;
+    {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (sizeof(KeyT) + (lvl == 0 ? 1.0 : 4.0) * kchars / 3.0), st);
+        if (lvl == 0)
+            k_sample_keys<CharT, KeyT, true><<<grid_for(z.n02, 256), 256, 0, st>>>(
+                s, z.n, z.n0, z.n02, 0, kchars, bits, maxc, k0, D.status);
+        else
+            k_sample_keys<CharT, KeyT, false><<<grid_for(z.n02, 256), 256, 0, st>>>(
+                s, z.n, z.n0, z.n02, 0, kchars, bits, maxc, k0, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    KeyT *kr;
+    uint32_t *vr;
+    int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.va, k1, D.vb, z.n02, 0, kchars * bits, true, &kr, &vr);
+    if (rc) return rc;
+    D.rs.epoch++;
+    {
+        ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 12), st);
+        k_name<KeyT><<<grid_for(z.n02, kScanTile), kScanThreads, 0, st>>>(
+            kr, vr, z.n02, Rl, SAR, D.d_names, D.rs.lookback, D.rs.tile_ctr, D.rs.tile_base,
+            D.rs.epoch, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    D.rs.tile_base += (unsigned long long)cdiv(z.n02, kScanTile);
+    return LOR_OK;
+}
+
+// Triples too wide for 64 bits: stable sort by (t_i+1, t_i+2), then by t_i.
+template <typename CharT>
+int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits, int64_t maxc,
+                              int32_t *Rl, int32_t *SAR) {
+    cudaStream_t st = D.s;
+    uint64_t *k0 = (uint64_t *)D.ka, *k1 = (uint64_t *)D.kb;
+    {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (8 + 8), st);
+        k_sample_keys<CharT, uint64_t, false><<<grid_for(z.n02, 256), 256, 0, st>>>(
+            s, z.n, z.n0, z.n02, 1, 3, bits, maxc, k0, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    uint64_t *kr;
+    uint32_t *vr;
+    int rc = radix_sort_pairs<uint64_t>(D.rs, k0, D.va, k1, D.vb, z.n02, 0, 2 * bits, true, &kr, &vr);
+    if (rc) return rc;
+    uint32_t *kx = (uint32_t *)(kr == k0 ? k1 : k0);  // free key buffer
+    uint32_t *ky = (uint32_t *)kr;
+    uint32_t *vx = vr, *vy = (vr == D.va ? D.vb : D.va);
+    {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (4 + 4 + 4), st);
+        k_first_char<CharT><<<grid_for(z.n02, 256), 256, 0, st>>>(vx, z.n02, s, z.n, z.n0, kx);
+    }
+    LOR_LAUNCH_CHECK();
+    uint32_t *kr2, *vr2;
+    rc = radix_sort_pairs<uint32_t>(D.rs, kx, vx, ky, vy, z.n02, 0, bits, false, &kr2, &vr2);
+    if (rc) return rc;
+    D.rs.epoch++;
+    {
+        ProfScope ps(PK_NAMING, double(z.n02) * (4 + 8 + 12 * 2), st);
+        k_name_gather<CharT><<<grid_for(z.n02, kScanTile), kScanThreads, 0, st>>>(
+            vr2, z.n02, s, z.n, z.n0, Rl, SAR, D.d_names, D.rs.lookback, D.rs.tile_ctr,
+            D.rs.tile_base, D.rs.epoch, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    D.rs.tile_base += (unsigned long long)cdiv(z.n02, kScanTile);
+    return LOR_OK;
+}
+
+template <typename CharT>
+int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32_t *out) {
+    cudaStream_t st = D.s;
+    if (lvl >= int(D.L.lev_R.size())) return LOR_ERR_WORKSPACE;
+    const LevelSizes z = level_sizes(n);
+    int32_t *Rl = (int32_t *)(D.ws + D.L.lev_R[lvl]);
+    int32_t *SAR = (int32_t *)(D.ws + D.L.lev_SAR[lvl]);
+    const int bits = bit_width_u64(uint64_t(maxc));
+    const int kchars = lvl == 0 ? level0_kchars(bits) : 3;
+    const int key_bits = kchars * bits;
+
+    // zero padding after R so that level lvl+1 may read past its end
+    LOR_CUDA_TRY(cudaMemsetAsync(Rl + z.n02, 0, sizeof(int32_t) * kPad, st));
+    int rc;
+    if (key_bits <= 32) rc = sample_sort_and_name<CharT, uint32_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR);
+    else if (key_bits <= 64) rc = sample_sort_and_name<CharT, uint64_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR);
+    else rc = sample_sort_and_name_wide<CharT>(D, s, z, bits, maxc, Rl, SAR);
+    if (rc) return rc;
+
+    uint32_t names = 0;
+    LOR_CUDA_TRY(cudaMemcpyAsync(&names, D.d_names, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    LOR_CUDA_TRY(cudaStreamSynchronize(st));
+    g_trace.push_back(TraceRow{n, int64_t(names), key_bits});
+    if (int64_t(names) < z.n02) {
+        rc = dc3_level<int32_t>(D, lvl + 1, Rl, z.n02, int64_t(names), SAR);
+        if (rc) return rc;
+        {
+            ProfScope ps(PK_RANK_SCATTER, double(z.n02) * 8, st);
+            k_rank_scatter<<<grid_for(z.n02, 256), 256, 0, st>>>(SAR, z.n02, Rl, D.status);
+        }
+        LOR_LAUNCH_CHECK();
+    }
+    // Rl now holds rank(S_i) by reduced-string index (unique names are ranks).
+
+    // Step 2: nonsample order
+    uint32_t *k0 = (uint32_t *)D.ka, *k1 = (uint32_t *)D.kb;
+    D.rs.epoch++;
+    {
+        ProfScope ps(PK_NONSAMPLE, double(z.n02) * 4 + double(z.n0) * (sizeof(CharT) + 8), st);
+        k_nonsample<CharT><<<grid_for(z.n02, kScanTile), kScanThreads, 0, st>>>(
+            SAR, z.n02, z.n0, s, n, k0, D.va, D.rs.lookback, D.rs.tile_ctr, D.rs.tile_base,
+            D.rs.epoch, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    D.rs.tile_base += (unsigned long long)cdiv(z.n02, kScanTile);
+    uint32_t *kr, *vr;
+    rc = radix_sort_pairs<uint32_t>(D.rs, k0, D.va, k1, D.vb, z.n0, 0, bits, false, &kr, &vr);
+    if (rc) return rc;
+
+    // Step 3: merge (the dummy, when present, is the smallest sample)
+    MergeIn<CharT> a;
+    a.s = s;
+    a.n = n;
+    a.n0 = z.n0;
+    a.n2 = z.n2;
+    a.rankR = Rl;
+    const int64_t dummy = (z.n0 > z.n1) ? 1 : 0;
+    a.A = SAR + dummy;
+    a.na = z.n02 - dummy;
+    a.B = vr;
+    a.nb = z.n0;
+    const int64_t ntiles = cdiv(n, kMergeTile);
+    // the merge partition reuses the free key buffer
+    int64_t *split = (int64_t *)(kr == k0 ? (void *)k1 : (void *)k0);
+    {
+        ProfScope ps(PK_MERGE, double(n) * (4 + 4) + double(z.n02) * (2 * sizeof(CharT) + 4) +
+                                   double(z.n0) * (2 * sizeof(CharT) + 8),
+                     st);
+        k_merge_partition<CharT><<<grid_for(ntiles + 1, 128), 128, 0, st>>>(a, ntiles, split);
+        LOR_LAUNCH_CHECK();
+        k_merge<CharT><<<unsigned(ntiles), kMergeThreads, 0, st>>>(a, split, out, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
+}  // namespace
+}  // namespace lor
+
+using namespace lor;
+
+extern "C" size_t lor_build_sa_workspace_size(int64_t n, int32_t sigma) {
+    (void)sigma;
+    if (n < 1 || n > LOR_MAX_N) return 0;
+    return dc3_layout(n).total;
+}
+
+extern "C" int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa, void *d_ws,
+                            size_t ws_bytes, lor_stream_t stream) {
+    if (!d_text || !d_sa || n < 1 || sigma < 2 || sigma > 256) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    Dc3Run D;
+    D.L = dc3_layout(n);
+    if (!d_ws || ws_bytes < D.L.total || (uintptr_t(d_ws) & 255)) return LOR_ERR_WORKSPACE;
+    D.s = (cudaStream_t)stream;
+    D.status = tu_status_ptr();
+    if (!D.status) return LOR_ERR_CUDA;
+    D.ws = (char *)d_ws;
+    D.d_names = (uint32_t *)(D.ws + D.L.ctrl);
+    D.rs.hist = (uint32_t *)(D.ws + D.L.hist);
+    D.rs.offsets = (uint32_t *)(D.ws + D.L.offsets);
+    D.rs.lookback = (uint64_t *)(D.ws + D.L.lookback);
+    D.rs.tile_ctr = (unsigned long long *)(D.ws + D.L.ctrl + 64);
+    D.rs.max_tiles = cdiv(D.L.max_m, kSortTile);
+    D.rs.status = D.status;
+    D.rs.stream = D.s;
+    D.ka = D.ws + D.L.ka;
+    D.kb = D.ws + D.L.kb;
+    D.va = (uint32_t *)(D.ws + D.L.va);
+    D.vb = (uint32_t *)(D.ws + D.L.vb);
+    LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.ctrl, 0, 256, D.s));
+    LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.lookback, 0, D.L.lookback_bytes, D.s));
+    g_trace.clear();
+    return dc3_level<uint8_t>(D, 0, d_text, n, int64_t(sigma - 1), d_sa);
+}
+
+extern "C" int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits, int32_t cap) {
+    const int cnt = int(g_trace.size());
+    for (int i = 0; i < cnt && i < cap; ++i) {
+        if (h_n) h_n[i] = g_trace[i].n;
+        if (h_names) h_names[i] = g_trace[i].names;
+        if (h_key_bits) h_key_bits[i] = g_trace[i].key_bits;
+    }
+    return cnt;
+}

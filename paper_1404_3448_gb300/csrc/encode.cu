@@ -1,0 +1,101 @@
+// encode.cu -- ASCII DNA to symbol codes, concatenated with one unique
+// terminator per sequence (Section 3: the overlap of two sequences is read
+// from one suffix array over both; the separator scheme is this library's
+// reading).  Terminator of sequence i = nseq - i, A/C/G/T = nseq+1..nseq+4,
+// so the last terminator is the smallest symbol and A < C < G < T as in
+// Table 1.
+#include "common.cuh"
+
+LOR_DEFINE_TU_STATUS(lor_status_encode)
+
+namespace lor {
+namespace {
+
+struct EncParams {
+    int32_t nseq;
+    int64_t out_start[LOR_MAX_SEQ + 1];  // start of sequence i in the text; [nseq] = n
+};
+
+constexpr int kEncThreads = 256;
+constexpr int kEncItems = 16;  // bytes per thread
+
+__global__ void __launch_bounds__(kEncThreads) k_encode(const uint8_t *__restrict__ ascii, EncParams P,
+                                                        uint8_t *__restrict__ text, int64_t n,
+                                                        int32_t *__restrict__ starts, int *status) {
+    __shared__ int64_t so[LOR_MAX_SEQ + 1];
+    __shared__ uint8_t lut[256];
+    const int nseq = P.nseq;
+    for (int i = threadIdx.x; i <= nseq; i += blockDim.x) so[i] = P.out_start[i];
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+        uint8_t v = 0;
+        if (c == 'A' || c == 'a') v = uint8_t(nseq + 1);
+        if (c == 'C' || c == 'c') v = uint8_t(nseq + 2);
+        if (c == 'G' || c == 'g') v = uint8_t(nseq + 3);
+        if (c == 'T' || c == 't') v = uint8_t(nseq + 4);
+        lut[c] = v;
+    }
+    __syncthreads();
+    const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (starts && gid <= nseq) starts[gid] = int32_t(so[gid]);
+    const int64_t o0 = gid * kEncItems;
+    if (o0 >= n) return;
+    // sequence holding o0
+    int lo = 0, hi = nseq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (so[mid] <= o0) lo = mid;
+        else hi = mid - 1;
+    }
+    int sq = lo;
+    bool bad = false;
+    for (int k = 0; k < kEncItems; ++k) {
+        const int64_t o = o0 + k;
+        if (o >= n) break;
+        while (o >= so[sq + 1]) ++sq;
+        const int64_t term = so[sq + 1] - 1;
+        uint8_t v;
+        if (o == term) {
+            v = uint8_t(nseq - sq);
+        } else {
+            v = lut[ascii[o - sq]];
+            if (v == 0) {
+                bad = true;
+                v = uint8_t(nseq + 1);
+            }
+        }
+        text[o] = v;
+    }
+    if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
+}
+
+}  // namespace
+}  // namespace lor
+
+using namespace lor;
+
+extern "C" int lor_encode_concat(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq,
+                                 uint8_t *d_text, int32_t *d_seq_starts, lor_stream_t stream) {
+    if (nseq < 1 || nseq > LOR_MAX_SEQ || !h_lens || !d_text) return LOR_ERR_INVALID_ARG;
+    EncParams P;
+    P.nseq = nseq;
+    int64_t total = 0;
+    for (int i = 0; i < nseq; ++i) {
+        if (h_lens[i] < 0) return LOR_ERR_INVALID_ARG;
+        P.out_start[i] = total;
+        total += h_lens[i] + 1;
+        if (total > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    }
+    P.out_start[nseq] = total;
+    if (total > nseq && !d_ascii) return LOR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *status = tu_status_ptr();
+    if (!status) return LOR_ERR_CUDA;
+    const int64_t threads = cdiv(total, kEncItems) > nseq + 1 ? cdiv(total, kEncItems) : nseq + 1;
+    {
+        ProfScope ps(PK_ENCODE, double(total) * 2, s);
+        k_encode<<<unsigned(cdiv(threads, kEncThreads)), kEncThreads, 0, s>>>(d_ascii, P, d_text, total,
+                                                                               d_seq_starts, status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}

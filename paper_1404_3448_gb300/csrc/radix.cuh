@@ -1,0 +1,269 @@
+// radix.cuh -- stable LSD radix sort of (key, uint32 value) pairs.
+//
+// The paper's DC3 sorts its sample triples and nonsample pairs with an LSD
+// radix sort (Section 4, Algorithm 1: one 1-bit split per pass, block-local
+// chunks merged afterwards).  Here one pass moves 8 bits: an up-front
+// histogram kernel counts every pass's digits in one read of the keys, and
+// each pass is a single "onesweep" kernel -- a block ranks its tile of keys
+// with warp match/popc, learns the global offset of each digit from its
+// predecessors by decoupled look-back (bounded waits), and scatters through
+// shared memory so that every digit run is written contiguously.
+#pragma once
+
+#include "common.cuh"
+
+namespace lor {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 256;
+constexpr int kSortThreads = 256;  // == kRadix: one thread per digit in the look-back
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
+constexpr int kMaxPasses = 8;                         // 64-bit keys
+
+template <typename KeyT>
+__device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
+    return uint32_t(k >> shift) & 0xFFu;
+}
+
+// Digit histograms of every pass in one read of the keys.
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_radix_hist(const KeyT *__restrict__ keys, int64_t m,
+                                                    int begin_bit, int npasses,
+                                                    uint32_t *__restrict__ hist) {
+    __shared__ uint32_t sh[kMaxPasses * kRadix];
+    for (int i = threadIdx.x; i < npasses * kRadix; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < m; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < m;
+        const KeyT k = valid ? keys[i] : KeyT(0);
+        for (int p = 0; p < npasses; ++p) {
+            const uint32_t d = valid ? digit_of(k, begin_bit + p * kRadixBits) : 0x100u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&sh[p * kRadix + d], __popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npasses * kRadix; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Exclusive scan of each pass's 256 digit counts (one block per pass).
+static __global__ void __launch_bounds__(256) k_radix_offsets(const uint32_t *__restrict__ hist,
+                                                       uint32_t *__restrict__ offsets) {
+    __shared__ uint32_t scratch[kRadix / 32 + 1];
+    const int p = blockIdx.x;
+    uint32_t total;
+    const uint32_t v = hist[p * kRadix + threadIdx.x];
+    offsets[p * kRadix + threadIdx.x] = block_excl_scan<kRadix>(v, scratch, &total);
+}
+
+template <typename KeyT>
+struct OnesweepSmem {
+    KeyT keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t warp_hist[kSortWarps][kRadix];
+    uint32_t local_start[kRadix];
+    long long gbase[kRadix];
+    uint32_t scratch[kSortWarps + 1];
+    long long tile;
+};
+
+// One LSD pass over digit (shift .. shift+7).  Tiles are claimed in launch
+// order from a running counter, so every predecessor a block waits on is
+// already resident; each wait is still bounded by kSpinLimitNs.
+template <typename KeyT, bool kIotaVals>
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t m, int shift, const uint32_t *__restrict__ offsets,
+    uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
+    uint32_t epoch, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnesweepSmem<KeyT> &S = *reinterpret_cast<OnesweepSmem<KeyT> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+    for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t tile = S.tile;
+    const int64_t base = tile * kSortTile;
+    const int64_t wbase = base + int64_t(warp) * (kSortItems * 32);
+
+    KeyT k[kSortItems];
+    uint32_t v[kSortItems], d[kSortItems], r[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = wbase + i * 32 + lane;
+        const bool valid = idx < m;
+        k[i] = valid ? kin[idx] : KeyT(0);
+        if (kIotaVals) v[i] = uint32_t(idx);
+        else v[i] = valid ? vin[idx] : 0u;
+        d[i] = valid ? digit_of(k[i], shift) : 0x100u;
+    }
+    // Stable rank inside the warp: items in order, lanes in order.
+    uint32_t *wh = S.warp_hist[warp];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, d[i]);
+        const uint32_t lt = __popc(peers & lanemask_lt());
+        const uint32_t cnt = d[i] < 256 ? wh[d[i]] : 0u;
+        r[i] = cnt + lt;
+        __syncwarp();
+        if (d[i] < 256 && lt == 0) wh[d[i]] = cnt + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int dg = tid;
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = S.warp_hist[w][dg];
+        S.warp_hist[w][dg] = total;
+        total += c;
+    }
+    uint32_t tile_total;
+    const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
+    S.local_start[dg] = lstart;
+
+    // Decoupled look-back, one digit per thread.
+    uint32_t excl = 0;
+    uint64_t *lb = lookback;
+    if (tile == 0) {
+        st_volatile_u64(&lb[dg], lb_pack(epoch, kFlagIncl, total));
+    } else {
+        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
+        int64_t j = tile - 1;
+        const uint64_t t0 = global_ns();
+        while (j >= 0) {
+            const uint64_t w = ld_volatile_u64(&lb[j * kRadix + dg]);
+            if (lb_epoch(w) != epoch || lb_flag(w) == 0) {
+                if (global_ns() - t0 > kSpinLimitNs) {
+                    atomicCAS(status, 0, LOR_ERR_TIMEOUT);
+                    break;
+                }
+                continue;
+            }
+            excl += lb_value(w);
+            if (lb_flag(w) == kFlagIncl) break;
+            --j;
+        }
+        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
+    }
+    S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        if (d[i] < 256) {
+            const uint32_t pos = S.local_start[d[i]] + S.warp_hist[warp][d[i]] + r[i];
+            S.keys[pos] = k[i];
+            S.vals[pos] = v[i];
+        }
+    }
+    __syncthreads();
+    const int cnt_tile = int(min(int64_t(kSortTile), m - base));
+    for (int i = tid; i < cnt_tile; i += kSortThreads) {
+        const KeyT kk = S.keys[i];
+        const long long o = S.gbase[digit_of(kk, shift)] + i;
+        kout[o] = kk;
+        vout[o] = S.vals[i];
+    }
+}
+
+static __global__ void k_iota_u32(uint32_t *__restrict__ v, int64_t m) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < m) v[i] = uint32_t(i);
+}
+
+// Scratch that one sort needs besides the two key/value buffer pairs.
+struct RadixScratch {
+    uint32_t *hist = nullptr;          // kMaxPasses * kRadix
+    uint32_t *offsets = nullptr;       // kMaxPasses * kRadix
+    uint64_t *lookback = nullptr;      // max_tiles * kRadix, zeroed before first use
+    unsigned long long *tile_ctr = nullptr;  // zeroed before first use
+    unsigned long long tile_base = 0;  // host mirror of *tile_ctr
+    uint32_t epoch = 0;                // host counter; 0 is never a valid epoch
+    int64_t max_tiles = 0;
+    int *status = nullptr;
+    cudaStream_t stream = 0;
+};
+
+inline size_t radix_lookback_bytes(int64_t max_m) {
+    return size_t(cdiv(max_m > 0 ? max_m : 1, kSortTile)) * kRadix * sizeof(uint64_t);
+}
+
+// Sort m pairs by bits [begin_bit, end_bit) of the keys.  (k0, v0) hold the
+// input; (k1, v1) are same-sized buffers.  On return *kres / *vres point at
+// whichever pair holds the sorted result.  When iota_vals is set the values
+// are taken to be 0..m-1 and v0 is not read.
+template <typename KeyT>
+int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v1, int64_t m,
+                     int begin_bit, int end_bit, bool iota_vals, KeyT **kres, uint32_t **vres) {
+    cudaStream_t s = rs.stream;
+    *kres = k0;
+    *vres = v0;
+    if (m <= 0) return LOR_OK;
+    const int npasses = int(cdiv(end_bit - begin_bit, kRadixBits));
+    if (begin_bit < 0 || end_bit < begin_bit || end_bit > int(8 * sizeof(KeyT)) ||
+        npasses > kMaxPasses)
+        return LOR_ERR_INVALID_ARG;
+    if (cdiv(m, kSortTile) > rs.max_tiles) return LOR_ERR_WORKSPACE;
+    uint32_t hh[kMaxPasses * kRadix];
+    if (npasses > 0) {
+        LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * npasses * kRadix, s));
+        {
+            ProfScope ps(PK_RADIX_HIST, double(m) * sizeof(KeyT), s);
+            const int grid = int(min64(cdiv(m, 256), 152 * 8));
+            k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, begin_bit, npasses, rs.hist);
+        }
+        LOR_LAUNCH_CHECK();
+        k_radix_offsets<<<npasses, kRadix, 0, s>>>(rs.hist, rs.offsets);
+        LOR_LAUNCH_CHECK();
+        LOR_CUDA_TRY(cudaMemcpyAsync(hh, rs.hist, sizeof(uint32_t) * npasses * kRadix,
+                                     cudaMemcpyDeviceToHost, s));
+        LOR_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    const size_t smem = sizeof(OnesweepSmem<KeyT>);
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    KeyT *ki = k0, *ko = k1;
+    uint32_t *vi = v0, *vo = v1;
+    bool vals_ready = !iota_vals;
+    const int64_t ntiles = cdiv(m, kSortTile);
+    for (int p = 0; p < npasses; ++p) {
+        bool trivial = false;
+        for (int dgt = 0; dgt < kRadix; ++dgt)
+            if (int64_t(hh[p * kRadix + dgt]) == m) trivial = true;
+        if (trivial) continue;  // every key has the same digit: order unchanged
+        const int shift = begin_bit + p * kRadixBits;
+        rs.epoch++;
+        {
+            ProfScope ps(PK_RADIX_PASS, double(m) * 2.0 * (sizeof(KeyT) + 4), s);
+            if (vals_ready)
+                k_onesweep<KeyT, false><<<unsigned(ntiles), kSortThreads, smem, s>>>(
+                    ki, vi, ko, vo, m, shift, rs.offsets + p * kRadix, rs.lookback, rs.tile_ctr,
+                    rs.tile_base, rs.epoch, rs.status);
+            else
+                k_onesweep<KeyT, true><<<unsigned(ntiles), kSortThreads, smem, s>>>(
+                    ki, vi, ko, vo, m, shift, rs.offsets + p * kRadix, rs.lookback, rs.tile_ctr,
+                    rs.tile_base, rs.epoch, rs.status);
+        }
+        LOR_LAUNCH_CHECK();
+        rs.tile_base += (unsigned long long)ntiles;
+        vals_ready = true;
+        KeyT *tk = ki; ki = ko; ko = tk;
+        uint32_t *tv = vi; vi = vo; vo = tv;
+    }
+    if (!vals_ready) {
+        k_iota_u32<<<unsigned(cdiv(m, 256)), 256, 0, s>>>(vi, m);
+        LOR_LAUNCH_CHECK();
+    }
+    *kres = ki;
+    *vres = vi;
+    return LOR_OK;
+}
+
+}  // namespace lor

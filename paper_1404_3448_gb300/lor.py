@@ -1,0 +1,375 @@
+"""Thin Python binding of liblor (include/lor.h).
+
+The ``lor_*`` functions take raw integers for device pointers and streams and
+return the C status; the lower-case helpers below marshal torch tensors
+(device memory, streams) into those calls and raise ``LorError`` on a
+non-zero status.  Every step of the path runs in the library's CUDA kernels;
+this module only allocates outputs and workspaces with torch and passes
+pointers.  It raises ImportError when the compiled library is missing --
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+LOR_OK = 0
+LOR_ERR_INVALID_ARG = -1
+LOR_ERR_BAD_SYMBOL = -2
+LOR_ERR_TOO_LARGE = -3
+LOR_ERR_WORKSPACE = -4
+LOR_ERR_CUDA = -5
+LOR_ERR_TIMEOUT = -6
+LOR_ERR_BAD_INPUT = -7
+LOR_MAX_SEQ = 250
+
+OVERLAP_FIELDS = ("length", "rank", "seq_a", "pos_a", "seq_b", "pos_b", "n_pos", "reserved")
+
+_lib = None
+
+
+class LorError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblor.so (built in-tree by ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"liblor.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "lor_encode_concat": ([vp, vp, i32, vp, vp, vp], ctypes.c_int),
+        "lor_build_sa_workspace_size": ([i64, i32], sz),
+        "lor_build_sa": ([vp, i64, i32, vp, vp, sz, vp], ctypes.c_int),
+        "lor_lcp": ([vp, vp, i64, vp, vp, vp], ctypes.c_int),
+        "lor_longest_overlap_workspace_size": ([i64], sz),
+        "lor_longest_overlap": ([vp, vp, i64, vp, i32, vp, vp, i64, vp, sz, vp], ctypes.c_int),
+        "lor_rmq_table_elems": ([i64], i64),
+        "lor_rmq_build": ([vp, i64, vp, i64, vp], ctypes.c_int),
+        "lor_rmq_query": ([vp, vp, i64, vp, vp, i64, vp, vp], ctypes.c_int),
+        "lor_radix_sort_workspace_size": ([i64], sz),
+        "lor_radix_sort_pairs": ([vp, vp, i64, i32, vp, sz, vp], ctypes.c_int),
+        "lor_device_status": ([vp], ctypes.c_int),
+        "lor_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "lor_launch_count": ([], ctypes.c_uint64),
+        "lor_last_dc3_trace": ([vp, vp, vp, i32], ctypes.c_int),
+        "lor_profile_enable": ([ctypes.c_int], ctypes.c_int),
+        "lor_profile_reset": ([], ctypes.c_int),
+        "lor_profile_kinds": ([], ctypes.c_int),
+        "lor_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
+        "lor_profile_read": ([ctypes.c_int, vp, vp, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------- raw C names
+
+def lor_encode_concat(d_ascii, h_lens, nseq, d_text, d_seq_starts, stream):
+    return load().lor_encode_concat(d_ascii, h_lens, nseq, d_text, d_seq_starts, stream)
+
+
+def lor_build_sa_workspace_size(n, sigma):
+    return load().lor_build_sa_workspace_size(n, sigma)
+
+
+def lor_build_sa(d_text, n, sigma, d_sa, d_ws, ws_bytes, stream):
+    return load().lor_build_sa(d_text, n, sigma, d_sa, d_ws, ws_bytes, stream)
+
+
+def lor_lcp(d_text, d_sa, n, d_isa, d_lcp, stream):
+    return load().lor_lcp(d_text, d_sa, n, d_isa, d_lcp, stream)
+
+
+def lor_longest_overlap_workspace_size(n):
+    return load().lor_longest_overlap_workspace_size(n)
+
+
+def lor_longest_overlap(d_sa, d_lcp, n, d_seq_starts, nseq, d_out, d_pos, pos_cap, d_ws, ws_bytes,
+                        stream):
+    return load().lor_longest_overlap(d_sa, d_lcp, n, d_seq_starts, nseq, d_out, d_pos, pos_cap,
+                                      d_ws, ws_bytes, stream)
+
+
+def lor_rmq_table_elems(n):
+    return load().lor_rmq_table_elems(n)
+
+
+def lor_rmq_build(d_lcp, n, d_table, table_elems, stream):
+    return load().lor_rmq_build(d_lcp, n, d_table, table_elems, stream)
+
+
+def lor_rmq_query(d_table, d_isa, n, d_p, d_q, nq, d_out, stream):
+    return load().lor_rmq_query(d_table, d_isa, n, d_p, d_q, nq, d_out, stream)
+
+
+def lor_radix_sort_workspace_size(m):
+    return load().lor_radix_sort_workspace_size(m)
+
+
+def lor_radix_sort_pairs(d_keys, d_vals, m, key_bits, d_ws, ws_bytes, stream):
+    return load().lor_radix_sort_pairs(d_keys, d_vals, m, key_bits, d_ws, ws_bytes, stream)
+
+
+def lor_device_status(stream):
+    return load().lor_device_status(stream)
+
+
+def lor_status_string(status):
+    return load().lor_status_string(status).decode()
+
+
+def lor_launch_count():
+    return int(load().lor_launch_count())
+
+
+# ---------------------------------------------------------------- helpers
+
+def status_string(status: int) -> str:
+    try:
+        return lor_status_string(status)
+    except ImportError:
+        return "liblor not loaded"
+
+
+def _check(rc: int, where: str):
+    if rc != LOR_OK:
+        raise LorError(rc, where)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor, dtype=None, name="tensor") -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A device byte buffer for the *_workspace_size queries (torch's
+    allocator returns 512-byte aligned blocks)."""
+    t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device or "cuda")
+    if t.data_ptr() % 256:
+        raise RuntimeError("workspace not 256-byte aligned")
+    return t
+
+
+def device_status(stream=None) -> int:
+    return lor_device_status(_stream(stream))
+
+
+def check_device(stream=None, where="device"):
+    _check(device_status(stream), where)
+
+
+def encode_concat(ascii_dev: torch.Tensor, lens, stream=None):
+    """ASCII sequences (back to back in one uint8 device tensor) -> text codes
+    with terminators, int32 sequence starts and sigma."""
+    lens = np.ascontiguousarray(np.asarray(lens, dtype=np.int64))
+    nseq = int(lens.size)
+    n = int(lens.sum()) + nseq
+    dev = ascii_dev.device
+    text = torch.empty(n, dtype=torch.uint8, device=dev)
+    starts = torch.empty(nseq + 1, dtype=torch.int32, device=dev)
+    rc = lor_encode_concat(_ptr(ascii_dev, torch.uint8, "ascii") if ascii_dev.numel() else None,
+                           lens.ctypes.data, nseq, _ptr(text), _ptr(starts), _stream(stream))
+    _check(rc, "lor_encode_concat")
+    return text, starts, nseq + 5
+
+
+def build_sa(text: torch.Tensor, sigma: int, sa=None, ws=None, stream=None) -> torch.Tensor:
+    n = text.numel()
+    if sa is None:
+        sa = torch.empty(n, dtype=torch.int32, device=text.device)
+    need = lor_build_sa_workspace_size(n, sigma)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, text.device)
+    rc = lor_build_sa(_ptr(text, torch.uint8, "text"), n, sigma, _ptr(sa, torch.int32, "sa"),
+                      ws.data_ptr(), ws.numel(), _stream(stream))
+    _check(rc, "lor_build_sa")
+    return sa
+
+
+def lcp(text: torch.Tensor, sa: torch.Tensor, isa=None, lcp_out=None, stream=None):
+    n = text.numel()
+    if isa is None:
+        isa = torch.empty(n, dtype=torch.int32, device=text.device)
+    if lcp_out is None:
+        lcp_out = torch.empty(n, dtype=torch.int32, device=text.device)
+    rc = lor_lcp(_ptr(text, torch.uint8, "text"), _ptr(sa, torch.int32, "sa"), n,
+                 _ptr(isa, torch.int32, "isa"), _ptr(lcp_out, torch.int32, "lcp"), _stream(stream))
+    _check(rc, "lor_lcp")
+    return isa, lcp_out
+
+
+def longest_overlap(sa, lcp_arr, seq_starts, nseq, pos_cap=1 << 16, out=None, pos=None, ws=None,
+                    stream=None):
+    """Returns (out int32[8] device tensor laid out as lor_overlap, pos device
+    tensor of pos_cap entries)."""
+    n = sa.numel()
+    if out is None:
+        out = torch.empty(8, dtype=torch.int32, device=sa.device)
+    if pos is None:
+        pos = torch.empty(max(int(pos_cap), 1), dtype=torch.int32, device=sa.device)
+    need = lor_longest_overlap_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, sa.device)
+    rc = lor_longest_overlap(_ptr(sa, torch.int32, "sa"), _ptr(lcp_arr, torch.int32, "lcp"), n,
+                             _ptr(seq_starts, torch.int32, "seq_starts"), int(nseq),
+                             _ptr(out, torch.int32, "out"), _ptr(pos, torch.int32, "pos"),
+                             int(pos_cap), ws.data_ptr(), ws.numel(), _stream(stream))
+    _check(rc, "lor_longest_overlap")
+    return out, pos
+
+
+def overlap_dict(out: torch.Tensor, pos: torch.Tensor, seq_starts=None) -> dict:
+    """Host view of a lor_overlap result (global positions, like the oracle)."""
+    vals = out.cpu().tolist()
+    d = dict(zip(OVERLAP_FIELDS, vals))
+    k = min(d["n_pos"], pos.numel())
+    d["positions"] = pos[:k].cpu().numpy().astype(np.int64)
+    return d
+
+
+def rmq_build(lcp_arr: torch.Tensor, table=None, stream=None) -> torch.Tensor:
+    n = lcp_arr.numel()
+    elems = lor_rmq_table_elems(n)
+    if table is None:
+        table = torch.empty(elems, dtype=torch.int32, device=lcp_arr.device)
+    rc = lor_rmq_build(_ptr(lcp_arr, torch.int32, "lcp"), n, _ptr(table, torch.int32, "table"),
+                       table.numel(), _stream(stream))
+    _check(rc, "lor_rmq_build")
+    return table
+
+
+def rmq_query(table, isa, p, q, out=None, stream=None) -> torch.Tensor:
+    n = isa.numel()
+    nq = p.numel()
+    if out is None:
+        out = torch.empty(nq, dtype=torch.int32, device=isa.device)
+    rc = lor_rmq_query(_ptr(table, torch.int32, "table"), _ptr(isa, torch.int32, "isa"), n,
+                       _ptr(p, torch.int32, "p"), _ptr(q, torch.int32, "q"), nq,
+                       _ptr(out, torch.int32, "out"), _stream(stream))
+    _check(rc, "lor_rmq_query")
+    return out
+
+
+def radix_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, key_bits: int, stream=None):
+    """Stable in-place sort of (int64-stored uint64 keys, int32-stored uint32
+    values) by the low key_bits bits."""
+    m = keys.numel()
+    ws = workspace(lor_radix_sort_workspace_size(m), keys.device)
+    rc = lor_radix_sort_pairs(_ptr(keys, torch.int64, "keys"), _ptr(vals, torch.int32, "vals"), m,
+                              int(key_bits), ws.data_ptr(), ws.numel(), _stream(stream))
+    _check(rc, "lor_radix_sort_pairs")
+    return keys, vals
+
+
+def last_dc3_trace():
+    cap = 128
+    n = np.zeros(cap, np.int64)
+    names = np.zeros(cap, np.int64)
+    bits = np.zeros(cap, np.int32)
+    cnt = load().lor_last_dc3_trace(n.ctypes.data, names.ctypes.data, bits.ctypes.data, cap)
+    cnt = min(cnt, cap)
+    return [dict(n=int(n[i]), names=int(names[i]), key_bits=int(bits[i])) for i in range(cnt)]
+
+
+def profile_enable(on=True):
+    _check(load().lor_profile_enable(1 if on else 0), "lor_profile_enable")
+
+
+def profile_reset():
+    _check(load().lor_profile_reset(), "lor_profile_reset")
+
+
+def profile_read() -> dict:
+    L = load()
+    out = {}
+    for k in range(L.lor_profile_kinds()):
+        c = ctypes.c_int64()
+        ms = ctypes.c_double()
+        b = ctypes.c_double()
+        _check(L.lor_profile_read(k, ctypes.byref(c), ctypes.byref(ms), ctypes.byref(b)),
+               "lor_profile_read")
+        if c.value:
+            out[L.lor_profile_kind_name(k).decode()] = dict(launches=c.value, ms=ms.value,
+                                                            bytes=b.value)
+    return out
+
+
+class Pipeline:
+    """Device-resident buffers for repeated runs of the whole path on texts of
+    one length: encode -> SA -> ISA/LCP -> overlap -> sparse table -> queries."""
+
+    def __init__(self, lens, device="cuda", pos_cap=1 << 16, with_rmq=True):
+        self.lens = np.asarray(lens, dtype=np.int64)
+        self.nseq = int(self.lens.size)
+        self.n = int(self.lens.sum()) + self.nseq
+        self.sigma = self.nseq + 5
+        dev = torch.device(device)
+        n = self.n
+        self.text = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.starts = torch.empty(self.nseq + 1, dtype=torch.int32, device=dev)
+        self.sa = torch.empty(n, dtype=torch.int32, device=dev)
+        self.isa = torch.empty(n, dtype=torch.int32, device=dev)
+        self.lcp = torch.empty(n, dtype=torch.int32, device=dev)
+        self.out = torch.empty(8, dtype=torch.int32, device=dev)
+        self.pos_cap = int(pos_cap)
+        self.pos = torch.empty(max(self.pos_cap, 1), dtype=torch.int32, device=dev)
+        ws_bytes = max(lor_build_sa_workspace_size(n, self.sigma),
+                       lor_longest_overlap_workspace_size(n))
+        self.ws = workspace(ws_bytes, dev)
+        self.table = (torch.empty(lor_rmq_table_elems(n), dtype=torch.int32, device=dev)
+                      if with_rmq else None)
+
+    def run(self, ascii_dev, p=None, q=None, answers=None, stream=None):
+        s = _stream(stream)
+        _check(lor_encode_concat(_ptr(ascii_dev, torch.uint8, "ascii"), self.lens.ctypes.data,
+                                 self.nseq, self.text.data_ptr(), self.starts.data_ptr(), s),
+               "lor_encode_concat")
+        _check(lor_build_sa(self.text.data_ptr(), self.n, self.sigma, self.sa.data_ptr(),
+                            self.ws.data_ptr(), self.ws.numel(), s), "lor_build_sa")
+        _check(lor_lcp(self.text.data_ptr(), self.sa.data_ptr(), self.n, self.isa.data_ptr(),
+                       self.lcp.data_ptr(), s), "lor_lcp")
+        _check(lor_longest_overlap(self.sa.data_ptr(), self.lcp.data_ptr(), self.n,
+                                   self.starts.data_ptr(), self.nseq, self.out.data_ptr(),
+                                   self.pos.data_ptr(), self.pos_cap, self.ws.data_ptr(),
+                                   self.ws.numel(), s), "lor_longest_overlap")
+        if self.table is not None:
+            _check(lor_rmq_build(self.lcp.data_ptr(), self.n, self.table.data_ptr(),
+                                 self.table.numel(), s), "lor_rmq_build")
+            if p is not None:
+                _check(lor_rmq_query(self.table.data_ptr(), self.isa.data_ptr(), self.n,
+                                     _ptr(p, torch.int32, "p"), _ptr(q, torch.int32, "q"),
+                                     p.numel(), _ptr(answers, torch.int32, "answers"), s),
+                       "lor_rmq_query")
+        return self.out, self.pos

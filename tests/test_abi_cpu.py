@@ -1,0 +1,99 @@
+"""Host-only checks of the C ABI: the library loads, exports every symbol the
+header declares, and rejects bad arguments before touching a device."""
+import ctypes
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_1404_3448_gb300 import build as lor_build
+from paper_1404_3448_gb300 import lor as L
+
+HEADER = lor_build.INCLUDE + "/lor.h"
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return L.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(lor_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_path(lib):
+    names = declared_functions()
+    for must in ["lor_encode_concat", "lor_build_sa", "lor_build_sa_workspace_size", "lor_lcp",
+                 "lor_longest_overlap", "lor_longest_overlap_workspace_size", "lor_rmq_build",
+                 "lor_rmq_query", "lor_rmq_table_elems", "lor_device_status", "lor_status_string"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_status_strings(lib):
+    for code in [0, -1, -2, -3, -4, -5, -6, -7]:
+        s = L.lor_status_string(code)
+        assert s and s != "unknown status"
+    assert L.lor_status_string(-99) == "unknown status"
+
+
+def test_workspace_queries_are_host_only(lib):
+    assert L.lor_build_sa_workspace_size(0, 7) == 0
+    prev = 0
+    for n in [1, 2, 3, 10, 1000, 10**6]:
+        w = L.lor_build_sa_workspace_size(n, 7)
+        assert w >= prev and w % 256 == 0
+        prev = w
+    # ~40 bytes per base at scale (sort buffers + per-level arrays)
+    assert L.lor_build_sa_workspace_size(10**8, 7) < 48 * 10**8
+    assert L.lor_longest_overlap_workspace_size(1000) > 0
+    assert L.lor_rmq_table_elems(1) == 1
+    assert L.lor_rmq_table_elems(8) == 4 * 8
+    assert L.lor_rmq_table_elems(1 << 20) == 21 * (1 << 20)
+    assert L.lor_radix_sort_workspace_size(0) > 0
+
+
+def test_bad_arguments_rejected_on_host(lib):
+    assert L.lor_build_sa(None, 10, 7, None, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_build_sa(1 << 20, 0, 7, 1 << 20, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_build_sa(1 << 20, 10, 1, 1 << 20, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_build_sa(1 << 20, 1 << 40, 7, 1 << 20, None, 0, None) == L.LOR_ERR_TOO_LARGE
+    assert L.lor_build_sa(1 << 20, 10, 7, 1 << 20, None, 0, None) == L.LOR_ERR_WORKSPACE
+    assert L.lor_build_sa(1 << 20, 10, 7, 1 << 20, (1 << 20) + 8, 1 << 30, None) == L.LOR_ERR_WORKSPACE
+    assert L.lor_lcp(None, None, 5, None, None, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_longest_overlap(1, 1, 5, 1, 0, 1, None, 0, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_longest_overlap(1, 1, 5, 1, 251, 1, None, 0, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_longest_overlap(256, 256, 5, 256, 2, 256, None, 4, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_longest_overlap(256, 256, 5, 256, 2, 256, None, 0, None, 0, None) == L.LOR_ERR_WORKSPACE
+    assert L.lor_rmq_build(None, 5, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_rmq_build(256, 5, 256, 4, None) == L.LOR_ERR_WORKSPACE
+    assert L.lor_rmq_query(None, None, 5, None, None, 1, None, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_rmq_query(256, 256, 5, None, None, 0, None, None) == L.LOR_OK
+    lens = (ctypes.c_int64 * 2)(3, 4)
+    assert L.lor_encode_concat(256, lens, 0, 256, None, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_encode_concat(256, lens, 251, 256, None, None) == L.LOR_ERR_INVALID_ARG
+    neg = (ctypes.c_int64 * 2)(3, -1)
+    assert L.lor_encode_concat(256, neg, 2, 256, None, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_radix_sort_pairs(None, None, 5, 8, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_radix_sort_pairs(None, None, 0, 8, None, 0, None) == L.LOR_OK
+    assert L.lor_radix_sort_pairs(256, 256, 5, 65, None, 0, None) == L.LOR_ERR_INVALID_ARG
+
+
+def test_no_oracle_in_product_path():
+    import os
+    pkg = os.path.dirname(lor_build.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(root, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "lor_oracle" not in txt, f
