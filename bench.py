@@ -1,0 +1,376 @@
+"""Benchmark of the longest-overlap-region path on GB300.
+
+One step = the whole path over one synthetic instance: encode + concatenate
+(a1), DC3 suffix array (a2-a8), ISA + LCP (a9), longest overlap with all
+positions (a10), sparse table (a11) and 1M LCP queries (a12).  The default
+workload is two iid-uniform sequences of 134,217,728 bases with one planted
+500-base common region (S1#S2$, n = 268,435,458), plus 1,000,000 uniform
+(p, q) queries.  ``value`` = input bases per second with inputs resident in
+HBM; ``e2e`` repeats it with the ASCII input and queries copied from pinned
+host memory and the results copied back inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lor|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator kwargs, queries, description)
+    "large": (dict(n_each=134_217_728, seed=140434483), 1_000_000,
+              "2x134217728 iid-uniform DNA with one 500-base plant, S1#S2$ (n=268435458); "
+              "1M uniform LCP queries"),
+    "noncoding": (None, 1_000_000,
+                  "2x16777216 noncoding-like DNA (40% GC, repeats, microsatellites, 10 kb shared "
+                  "region with exact 2 kb core), S1#S2$; 1M uniform LCP queries"),
+    "tiny": (dict(n_each=100_000, seed=140434481), 100_000,
+             "2x100000 iid-uniform DNA with one 500-base plant, S1#S2$; 100k LCP queries"),
+}
+METRIC = "input bases/s for SA+LCP+longest overlap (1 GB300)"
+UNIT = "bases/s"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(name):
+    import lor_inputs as gen
+    kw, nq, desc = WORKLOADS[name]
+    if name == "noncoding":
+        seqs, info = gen.pair_noncoding()
+    else:
+        seqs, info = gen.pair_uniform(**kw)
+    n = sum(len(s) for s in seqs) + len(seqs)
+    p, q = gen.random_queries(n, count=nq)
+    return seqs, info, p, q, desc
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1404_3448_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kind, workload):
+    """DRAM bytes per launch of `kind` from a committed ncu summary, only when
+    it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    ent = rec.get("kernels", {}).get(kind)
+    if not ent or ent.get("workload") != workload:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------- CPU (oracle)
+
+def cpu_sample_run(n_each, seed, nq):
+    """One pass of the oracle over a bounded sample of the same generator."""
+    import lor_inputs as gen
+    import oracle
+    seqs, _ = gen.pair_uniform(n_each=n_each, plant_len=500, seed=seed)
+    t0 = time.perf_counter()
+    text, starts, _ = oracle.encode_concat(seqs)
+    sa = oracle.suffix_array(text, nthreads=1)
+    lcp = oracle.lcp_array(text, sa, nthreads=1)
+    oracle.longest_overlap(text, sa, lcp, starts)
+    oracle.sparse_table(lcp)
+    p, q = gen.random_queries(len(text), count=nq, seed=seed)
+    oracle.lcp_pairs(text, p, q)
+    return time.perf_counter() - t0, 2 * n_each
+
+
+def cpu_baseline(budget_s=15.0):
+    import oracle
+    oracle.build()
+    n_each = 1 << 20
+    dt, bases = cpu_sample_run(n_each, 140434483, 10_000)
+    # scale the sample so it takes roughly the budget, then time it once more
+    scale = max(1, min(8, int(budget_s / max(dt, 1e-3))))
+    if scale > 1:
+        dt, bases = cpu_sample_run(n_each * scale, 140434483, 10_000 * scale)
+    return {"value": bases / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle (merge-sort SA, naive LCP, overlap scan, sparse table, direct-"
+                      f"comparison queries) on 2x{n_each * scale} iid-uniform bases, 1 thread, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n_each = 1 << 21
+    for i in range(args.warmup):
+        cpu_sample_run(n_each, 1000 + i, 20000)
+    total_t, total_b = 0.0, 0
+    for i in range(args.steps):
+        dt, b = cpu_sample_run(n_each, 2000 + i, 20000)
+        total_t += dt
+        total_b += b
+    value = total_b / total_t
+    sample = (f"oracle on 2x{n_each} iid-uniform bases per step (encode, merge-sort SA, naive "
+              f"LCP, overlap scan, sparse table, 20000 direct-comparison queries), 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload][2], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU
+
+def run_lor(args):
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3448_gb300 as lor
+    from paper_1404_3448_gb300 import lor as C
+
+    seqs, info, p_np, q_np, desc = make_inputs(args.workload)
+    lens = [len(s) for s in seqs]
+    n_bases = int(sum(lens))
+    host_ascii = torch.from_numpy(np.concatenate(seqs)).pin_memory()
+    host_p = torch.from_numpy(p_np).pin_memory()
+    host_q = torch.from_numpy(q_np).pin_memory()
+    ascii_dev = host_ascii.to(dev)
+    p_dev, q_dev = host_p.to(dev), host_q.to(dev)
+    ans_dev = torch.empty_like(p_dev)
+    pipe = lor.Pipeline(lens, device=dev, pos_cap=1 << 16)
+    host_out = torch.empty(8, dtype=torch.int32).pin_memory()
+    host_pos = torch.empty(1 << 16, dtype=torch.int32).pin_memory()
+    host_ans = torch.empty_like(host_p).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step():
+        pipe.run(ascii_dev, p_dev, q_dev, ans_dev)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    lor.check_device(where="warmup")
+
+    # ---- device-resident timed region
+    lor.profile_reset()
+    lor.profile_enable(True)
+    launches0 = C.lor_launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    launches = C.lor_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = lor.profile_read()
+    lor.profile_enable(False)
+    lor.check_device(where="timed")
+
+    # ---- end to end: pinned host in, results back to host
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    npos = 0
+    for _ in range(args.steps):
+        ascii_dev.copy_(host_ascii, non_blocking=True)
+        p_dev.copy_(host_p, non_blocking=True)
+        q_dev.copy_(host_q, non_blocking=True)
+        out, pos = pipe.run(ascii_dev, p_dev, q_dev, ans_dev)
+        host_out.copy_(out, non_blocking=True)
+        host_ans.copy_(ans_dev, non_blocking=True)
+        stream.synchronize()
+        npos = min(int(host_out[6]), pos.numel())
+        if npos:
+            host_pos[:npos].copy_(pos[:npos], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    ms_all = ms
+    e2e_all = e2e_ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all, e2e_all = float(t[0]), float(t[1])
+
+    if rank == 0:
+        value = world * n_bases / (ms_all / 1000.0)
+        e2e_value = world * n_bases / (e2e_all / 1000.0)
+        h2d = host_ascii.numel() + 4 * (host_p.numel() + host_q.numel())
+        d2h = 32 + 4 * host_ans.numel() + 4 * npos
+        stage_ms = {k: v["ms"] / args.steps for k, v in prof.items()}
+        dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
+        peak, peak_src = measured_peak_gbs()
+        roof = None
+        if dom:
+            d = prof[dom]
+            achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                    "launches_per_step": d["launches"] / args.steps,
+                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                    "avg_launch_ms": d["ms"] / d["launches"],
+                    "traffic": ncu_traffic(dom, args.workload)}
+        path_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": desc, "n": pipe.n, "input_bases": n_bases,
+                       "queries": int(p_np.size), "parallelism": "replicas" if world > 1 else "none",
+                       "l2": "inputs larger than L2 (268 MB text, >10 GB working set)",
+                       "step": "a1-a12: encode, DC3 SA, ISA+LCP, overlap+positions, sparse "
+                               "table, LCP queries"},
+            "roofline": roof,
+            "path_model_bytes_per_step": path_bytes,
+            "path_model_gbs": path_bytes / (ms / 1000.0) / 1e9,
+            "stage_ms": stage_ms,
+            "overlap": {"length": int(host_out[0]), "n_pos": int(host_out[6])},
+            "dc3_levels": len(lor.last_dc3_trace()),
+            "clocks": clocks.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / args.steps,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lor", choices=["lor", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_lor(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -23,14 +23,19 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
 constexpr int kMaxPasses = 8;                         // 64-bit keys
 
 template <typename KeyT>
-__device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
-    return uint32_t(k >> shift) & 0xFFu;
+__device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask = 0xFFu) {
+    return uint32_t(k >> shift) & mask;
+}
+// Digit mask of the pass starting at `shift` when the key ends at end_bit.
+__host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int end_bit) {
+    const int w = end_bit - shift < kRadixBits ? end_bit - shift : kRadixBits;
+    return (1u << w) - 1u;
 }
 
 // Digit histograms of every pass in one read of the keys.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_radix_hist(const KeyT *__restrict__ keys, int64_t m,
-                                                    int begin_bit, int npasses,
+                                                    int begin_bit, int end_bit, int npasses,
                                                     uint32_t *__restrict__ hist) {
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     for (int i = threadIdx.x; i < npasses * kRadix; i += blockDim.x) sh[i] = 0;
@@ -41,7 +46,8 @@ __global__ void __launch_bounds__(256) k_radix_hist(const KeyT *__restrict__ key
         const bool valid = i < m;
         const KeyT k = valid ? keys[i] : KeyT(0);
         for (int p = 0; p < npasses; ++p) {
-            const uint32_t d = valid ? digit_of(k, begin_bit + p * kRadixBits) : 0x100u;
+            const int sft = begin_bit + p * kRadixBits;
+            const uint32_t d = valid ? digit_of(k, sft, digit_mask(sft, end_bit)) : 0x100u;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&sh[p * kRadix + d], __popc(peers));
         }
@@ -78,7 +84,8 @@ struct OnesweepSmem {
 template <typename KeyT, bool kIotaVals>
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t m, int shift, const uint32_t *__restrict__ offsets,
+    uint32_t *__restrict__ vout, int64_t m, int shift, uint32_t dmask,
+    const uint32_t *__restrict__ offsets,
     uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
     uint32_t epoch, int *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         k[i] = valid ? kin[idx] : KeyT(0);
         if (kIotaVals) v[i] = uint32_t(idx);
         else v[i] = valid ? vin[idx] : 0u;
-        d[i] = valid ? digit_of(k[i], shift) : 0x100u;
+        d[i] = valid ? digit_of(k[i], shift, dmask) : 0x100u;
     }
     // Stable rank inside the warp: items in order, lanes in order.
     uint32_t *wh = S.warp_hist[warp];
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const int cnt_tile = int(min(int64_t(kSortTile), m - base));
     for (int i = tid; i < cnt_tile; i += kSortThreads) {
         const KeyT kk = S.keys[i];
-        const long long o = S.gbase[digit_of(kk, shift)] + i;
+        const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
         kout[o] = kk;
         vout[o] = S.vals[i];
     }
@@ -215,7 +222,7 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
         {
             ProfScope ps(PK_RADIX_HIST, double(m) * sizeof(KeyT), s);
             const int grid = int(min64(cdiv(m, 256), 152 * 8));
-            k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, begin_bit, npasses, rs.hist);
+            k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, begin_bit, end_bit, npasses, rs.hist);
         }
         LOR_LAUNCH_CHECK();
         k_radix_offsets<<<npasses, kRadix, 0, s>>>(rs.hist, rs.offsets);
@@ -244,12 +251,12 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
             ProfScope ps(PK_RADIX_PASS, double(m) * 2.0 * (sizeof(KeyT) + 4), s);
             if (vals_ready)
                 k_onesweep<KeyT, false><<<unsigned(ntiles), kSortThreads, smem, s>>>(
-                    ki, vi, ko, vo, m, shift, rs.offsets + p * kRadix, rs.lookback, rs.tile_ctr,
-                    rs.tile_base, rs.epoch, rs.status);
+                    ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
+                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status);
             else
                 k_onesweep<KeyT, true><<<unsigned(ntiles), kSortThreads, smem, s>>>(
-                    ki, vi, ko, vo, m, shift, rs.offsets + p * kRadix, rs.lookback, rs.tile_ctr,
-                    rs.tile_base, rs.epoch, rs.status);
+                    ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
+                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status);
         }
         LOR_LAUNCH_CHECK();
         rs.tile_base += (unsigned long long)ntiles;
