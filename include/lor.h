@@ -110,6 +110,21 @@ int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
                  void *d_ws, size_t ws_bytes, lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Suffix array without a workspace argument, for callers that cannot
+ * allocate device memory (the paper has no counterpart; this is a library
+ * convenience).  Same result, arguments and errors as lor_build_sa, for
+ * n <= LOR_NOALLOC_MAX_N; larger n returns LOR_ERR_TOO_LARGE before touching
+ * the device.  The scratch is one 16 MiB array compiled into the library:
+ * every GPU that loads liblor holds it until the process exits.  The first
+ * call on a device looks up the array's device address (call it once before
+ * any stream capture).  All calls share the array, so calls that can overlap
+ * on the GPU race and must be serialised by the caller.  Allocates nothing.
+ * ------------------------------------------------------------------------- */
+#define LOR_NOALLOC_MAX_N 262144LL
+int lor_build_sa_noalloc(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
+                         lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * a9. Inverse suffix array and LCP array (Section 3, LCP table; Kasai et al.,
  * cited there).  ISA[SA[k]] = k; LCP[0] = 0 and LCP[k] is the length of the
  * longest common prefix of the suffixes SA[k-1] and SA[k].

@@ -57,6 +57,7 @@ def load():
         "lor_encode_concat": ([vp, vp, i32, vp, vp, vp], ctypes.c_int),
         "lor_build_sa_workspace_size": ([i64, i32], sz),
         "lor_build_sa": ([vp, i64, i32, vp, vp, sz, vp], ctypes.c_int),
+        "lor_build_sa_noalloc": ([vp, i64, i32, vp, vp], ctypes.c_int),
         "lor_lcp": ([vp, vp, i64, vp, vp, vp], ctypes.c_int),
         "lor_longest_overlap_workspace_size": ([i64], sz),
         "lor_longest_overlap": ([vp, vp, i64, vp, i32, vp, vp, i64, vp, sz, vp], ctypes.c_int),
@@ -95,6 +96,10 @@ def lor_build_sa_workspace_size(n, sigma):
 
 def lor_build_sa(d_text, n, sigma, d_sa, d_ws, ws_bytes, stream):
     return load().lor_build_sa(d_text, n, sigma, d_sa, d_ws, ws_bytes, stream)
+
+
+def lor_build_sa_noalloc(d_text, n, sigma, d_sa, stream):
+    return load().lor_build_sa_noalloc(d_text, n, sigma, d_sa, stream)
 
 
 def lor_lcp(d_text, d_sa, n, d_isa, d_lcp, stream):
