@@ -131,10 +131,13 @@ int lor_build_sa_noalloc(const uint8_t *d_text, int64_t n, int32_t sigma, int32_
  *
  * d_text, n : as for lor_build_sa.   d_sa : device int32[n] suffix array.
  * d_isa     : device int32[n] output.  d_lcp : device int32[n] output.
+ * d_ws      : device workspace of lor_lcp_workspace_size(n) bytes (12 bytes
+ *             per symbol), 256-byte aligned.
  * An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT (and is skipped).
  * ------------------------------------------------------------------------- */
+size_t lor_lcp_workspace_size(int64_t n);
 int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, int32_t *d_isa,
-            int32_t *d_lcp, lor_stream_t stream);
+            int32_t *d_lcp, void *d_ws, size_t ws_bytes, lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * a10. Longest overlap region (Section 3: the longest common prefix between
@@ -161,10 +164,13 @@ int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, int64_t n,
 /* ---------------------------------------------------------------------------
  * a11. Sparse table over the LCP array for range-minimum queries (Section 3:
  * RMQ definition; the LCP of arbitrary suffixes is a range minimum).
- * Layout: level-major int32[levels][n] with levels = floor(log2 n) + 1;
- * table[j*n + i] = min(lcp[i .. min(i + 2^j, n) - 1]).
- * table_elems must be >= lor_rmq_table_elems(n).
+ * Layout: level-major, levels = floor(log2 n) + 1 rows of
+ * stride = lor_rmq_row_stride(n) entries (n rounded up to a multiple of 64);
+ * table[j*stride + i] = min(lcp[i .. min(i + 2^j, n) - 1]) for i < n (the
+ * padding entries are unspecified).  d_table must be 256-byte aligned and
+ * hold at least lor_rmq_table_elems(n) = levels * stride int32 entries.
  * ------------------------------------------------------------------------- */
+int64_t lor_rmq_row_stride(int64_t n);
 int64_t lor_rmq_table_elems(int64_t n);
 int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
                   lor_stream_t stream);

@@ -254,6 +254,7 @@ __global__ void k_rank_scatter(const int32_t *__restrict__ SAR, int64_t m, int32
 
 // Step 2 gather: nonsample positions 3r for every B1 sample r in rank order,
 // keyed by their first symbol (order-preserving compaction by look-back).
+// The value emitted is the group index r (the nonsample position is 3r).
 template <typename CharT>
 __global__ void __launch_bounds__(kScanThreads) k_nonsample(
     const int32_t *__restrict__ SAR, int64_t m, int64_t n0, const CharT *__restrict__ s, int64_t n,
@@ -288,66 +289,110 @@ __global__ void __launch_bounds__(kScanThreads) k_nonsample(
         if (r[i] >= 0 && r[i] < n0) {
             const int64_t q = 3 * int64_t(r[i]);
             keys[o] = q < n ? uint32_t(s[q]) : 0u;
-            vals[o] = uint32_t(q);
+            vals[o] = uint32_t(r[i]);
             ++o;
         }
     }
 }
 
 // ---- Step 3: merge of sample and nonsample suffixes (merge path)
+//
+// Every comparison of Step 3 reads two symbols and one or two ranks next to a
+// position.  For the group of positions 3t, 3t+1, 3t+2 all of them sit in one
+// record: symbols t_3t..t_3t+3 and rank(S_3t+1), rank(S_3t+2), rank(S_3t+4).
+// The records are written by a streaming pass over t, so a merged suffix
+// costs a single gather of its group's record.
+
+template <typename CharT>
+struct GroupRec;
+template <>
+struct __align__(16) GroupRec<uint8_t> {
+    uint32_t c4;  // four symbols, byte k = t_3t+k
+    int32_t r1, r2, r4;
+};
+template <>
+struct __align__(32) GroupRec<int32_t> {
+    int32_t c[4];
+    int32_t r1, r2, r4, pad;
+};
+__device__ __forceinline__ int32_t rec_ch(const GroupRec<uint8_t> &g, int k) {
+    return int32_t((g.c4 >> (8 * k)) & 0xFFu);
+}
+__device__ __forceinline__ int32_t rec_ch(const GroupRec<int32_t> &g, int k) { return g.c[k]; }
+
+// Record of group t: rank(S_x) is rankR[(x-1)/3] for x = 1 mod 3 (the dummy
+// x = n included), rankR[n0 + (x-2)/3] for x = 2 mod 3, and 0 past the end.
+template <typename CharT>
+__global__ void k_group_records(const CharT *__restrict__ s, int64_t n, int64_t n0, int64_t n2,
+                                const int32_t *__restrict__ rankR, GroupRec<CharT> *__restrict__ rec) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= n0) return;
+    const int64_t q = 3 * t;
+    GroupRec<CharT> g;
+    int32_t c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = q + k < n ? int32_t(s[q + k]) : 0;
+    if constexpr (sizeof(CharT) == 1) {
+        g.c4 = uint32_t(c[0]) | (uint32_t(c[1]) << 8) | (uint32_t(c[2]) << 16) | (uint32_t(c[3]) << 24);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g.c[k] = c[k];
+        g.pad = 0;
+    }
+    g.r1 = rankR[t];
+    g.r2 = t < n2 ? rankR[n0 + t] : 0;
+    g.r4 = t + 1 < n0 ? rankR[t + 1] : 0;
+    rec[t] = g;
+}
 
 template <typename CharT>
 struct MergeIn {
-    const CharT *s;
-    int64_t n, n0, n2;
-    const int32_t *rankR;  // rank(S_i) by reduced-string index, 1-based
-    const int32_t *A;      // sample order (reduced-string indices), dummy skipped
+    const GroupRec<CharT> *rec;
+    int32_t n0;
+    const int32_t *A;  // sample order (reduced-string indices), dummy skipped
     int64_t na;
-    const uint32_t *B;     // nonsample order (text positions)
+    const uint32_t *B;  // nonsample order (group indices t; position 3t)
     int64_t nb;
 };
 
-template <typename CharT>
-__device__ __forceinline__ int32_t m_ch(const MergeIn<CharT> &a, int64_t q) {
-    return q < a.n ? int32_t(a.s[q]) : 0;
-}
-// rank(S_x) for a sample position x (the dummy x = n included), 0 beyond.
-template <typename CharT>
-__device__ __forceinline__ int32_t m_rk(const MergeIn<CharT> &a, int64_t x) {
-    const int64_t q = x / 3, rem = x - 3 * q;
-    if (rem == 1) return q < a.n0 ? a.rankR[q] : 0;
-    if (rem == 2) return q < a.n2 ? a.rankR[a.n0 + q] : 0;
-    return 0;
-}
+// Sample suffix p: key (t_p, rank(S_p+1)) for p = 1 mod 3 (marked c1 = -1),
+// (t_p, t_p+1, rank(S_p+2)) for p = 2 mod 3.
+struct ARec { int32_t pos, c0, c1, r; };
+// Nonsample suffix q: t_q, t_q+1, rank(S_q+1), rank(S_q+2).
+struct BRec { int32_t pos, c0, c1, r1, r2; };
 
-struct ARec { int32_t pos, c0, c1, r; };          // sample: r = rank(S_p+1) or rank(S_p+2)
-struct BRec { int32_t pos, c0, c1, r1, r2; };     // nonsample: r1 = rank(S_q+1), r2 = rank(S_q+2)
+__device__ __forceinline__ int32_t a_group(int32_t r, int32_t n0) { return r < n0 ? r : r - n0; }
 
 template <typename CharT>
-__device__ __forceinline__ ARec load_a(const MergeIn<CharT> &a, int64_t i) {
-    const int64_t p = sample_pos(a.A[i], a.n0);
+__device__ __forceinline__ ARec make_a(const GroupRec<CharT> &g, int32_t r, int32_t n0) {
     ARec x;
-    x.pos = int32_t(p);
-    x.c0 = m_ch(a, p);
-    x.c1 = m_ch(a, p + 1);
-    x.r = (p % 3 == 1) ? m_rk(a, p + 1) : m_rk(a, p + 2);
+    if (r < n0) {
+        x.pos = 3 * r + 1;
+        x.c0 = rec_ch(g, 1);
+        x.c1 = -1;
+        x.r = g.r2;
+    } else {
+        x.pos = 3 * (r - n0) + 2;
+        x.c0 = rec_ch(g, 2);
+        x.c1 = rec_ch(g, 3);
+        x.r = g.r4;
+    }
     return x;
 }
 template <typename CharT>
-__device__ __forceinline__ BRec load_b(const MergeIn<CharT> &a, int64_t i) {
-    const int64_t q = a.B[i];
+__device__ __forceinline__ BRec make_b(const GroupRec<CharT> &g, uint32_t t) {
     BRec y;
-    y.pos = int32_t(q);
-    y.c0 = m_ch(a, q);
-    y.c1 = m_ch(a, q + 1);
-    y.r1 = m_rk(a, q + 1);
-    y.r2 = m_rk(a, q + 2);
+    y.pos = int32_t(3 * t);
+    y.c0 = rec_ch(g, 0);
+    y.c1 = rec_ch(g, 1);
+    y.r1 = g.r1;
+    y.r2 = g.r2;
     return y;
 }
 // Is the sample suffix x smaller than the nonsample suffix y?
 __device__ __forceinline__ bool a_less_b(const ARec &x, const BRec &y) {
     if (x.c0 != y.c0) return x.c0 < y.c0;
-    if (x.pos % 3 == 1) return x.r < y.r1;
+    if (x.c1 < 0) return x.r < y.r1;
     if (x.c1 != y.c1) return x.c1 < y.c1;
     return x.r < y.r2;
 }
@@ -363,7 +408,11 @@ __device__ int64_t merge_split(const MergeIn<CharT> &a, int64_t d) {
     int64_t hi = d < a.na ? d : a.na;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (a_less_b(load_a(a, mid), load_b(a, d - 1 - mid))) lo = mid + 1;
+        const int32_t r = a.A[mid];
+        const uint32_t t = a.B[d - 1 - mid];
+        const ARec x = make_a(a.rec[a_group(r, a.n0)], r, a.n0);
+        const BRec y = make_b(a.rec[t], t);
+        if (a_less_b(x, y)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -400,8 +449,26 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeIn<CharT> a,
     a1 = a1c;
     const int64_t b0 = d0 - a0, b1 = d1 - a1;
     const int na = int(a1 - a0), nb = int(b1 - b0), nt = int(d1 - d0);
-    for (int i = threadIdx.x; i < na; i += kMergeThreads) As[i] = load_a(a, a0 + i);
-    for (int i = threadIdx.x; i < nb; i += kMergeThreads) Bs[i] = load_b(a, b0 + i);
+    // Load the tile: all indices first, then all record gathers, so that each
+    // thread keeps kMergeItems independent loads in flight.
+    int32_t idx[kMergeItems];
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k) {
+        const int sl = int(threadIdx.x) + k * kMergeThreads;
+        idx[k] = sl < na ? a.A[a0 + sl] : (sl < nt ? int32_t(a.B[b0 + sl - na]) : 0);
+    }
+    GroupRec<CharT> g[kMergeItems];
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k) {
+        const int sl = int(threadIdx.x) + k * kMergeThreads;
+        if (sl < nt) g[k] = a.rec[sl < na ? a_group(idx[k], a.n0) : idx[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k) {
+        const int sl = int(threadIdx.x) + k * kMergeThreads;
+        if (sl < na) As[sl] = make_a(g[k], idx[k], a.n0);
+        else if (sl < nt) Bs[sl - na] = make_b(g[k], uint32_t(idx[k]));
+    }
     __syncthreads();
     const int dl = min(int(threadIdx.x) * kMergeItems, nt);
     int lo = max(0, dl - nb), hi = min(dl, na);
@@ -573,25 +640,28 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     rc = radix_sort_pairs<uint32_t>(D.rs, k0, D.va, k1, D.vb, z.n0, 0, bits, false, &kr, &vr);
     if (rc) return rc;
 
-    // Step 3: merge (the dummy, when present, is the smallest sample)
+    // Step 3: merge (the dummy, when present, is the smallest sample).  The
+    // key buffers are free now: the group records go there, then the
+    // partition.
+    GroupRec<CharT> *rec = (GroupRec<CharT> *)D.ka;
+    const size_t rec_bytes = align256(sizeof(GroupRec<CharT>) * size_t(z.n0));
+    {
+        ProfScope ps(PK_MERGE, double(z.n0) * (3.0 * sizeof(CharT) + 12 + sizeof(GroupRec<CharT>)), st);
+        k_group_records<CharT><<<grid_for(z.n0, 256), 256, 0, st>>>(s, n, z.n0, z.n2, Rl, rec);
+    }
+    LOR_LAUNCH_CHECK();
     MergeIn<CharT> a;
-    a.s = s;
-    a.n = n;
-    a.n0 = z.n0;
-    a.n2 = z.n2;
-    a.rankR = Rl;
+    a.rec = rec;
+    a.n0 = int32_t(z.n0);
     const int64_t dummy = (z.n0 > z.n1) ? 1 : 0;
     a.A = SAR + dummy;
     a.na = z.n02 - dummy;
     a.B = vr;
     a.nb = z.n0;
     const int64_t ntiles = cdiv(n, kMergeTile);
-    // the merge partition reuses the free key buffer
-    int64_t *split = (int64_t *)(kr == k0 ? (void *)k1 : (void *)k0);
+    int64_t *split = (int64_t *)((char *)D.ka + rec_bytes);
     {
-        ProfScope ps(PK_MERGE, double(n) * (4 + 4) + double(z.n02) * (2 * sizeof(CharT) + 4) +
-                                   double(z.n0) * (2 * sizeof(CharT) + 8),
-                     st);
+        ProfScope ps(PK_MERGE, double(n) * (4 + 4 + sizeof(GroupRec<CharT>)), st);
         k_merge_partition<CharT><<<grid_for(ntiles + 1, 128), 128, 0, st>>>(a, ntiles, split);
         LOR_LAUNCH_CHECK();
         k_merge<CharT><<<unsigned(ntiles), kMergeThreads, 0, st>>>(a, split, out, D.status);

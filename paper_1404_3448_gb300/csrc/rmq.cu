@@ -4,8 +4,15 @@
 //
 // Level j holds the minimum of every window of 2^j entries (clipped at the
 // end of the array): table[j][i] = min(table[j-1][i], table[j-1][i + 2^(j-1)]).
+// Rows are padded to a multiple of 64 entries so that every row starts on a
+// 256-byte boundary.  Levels 0..8 are produced by one kernel that stages a
+// tile plus a 256-entry halo of the LCP array in shared memory and writes the
+// nine rows; every higher level is one streaming pass with 16-byte accesses
+// (the second operand, 2^(j-1) >= 256 entries ahead, is 16-byte aligned too).
 // A query over ranks (r1, r2] reads two overlapping windows of level
 // floor(log2(r2 - r1)).
+#include <climits>
+
 #include "common.cuh"
 
 LOR_DEFINE_TU_STATUS(lor_status_rmq)
@@ -14,23 +21,78 @@ namespace lor {
 namespace {
 
 int levels_for(int64_t n) { return n > 0 ? bit_width_u64(uint64_t(n)) : 1; }
+int64_t row_stride(int64_t n) { return (n + 63) & ~int64_t(63); }
 
-__global__ void k_copy_i32(const int32_t *__restrict__ src, int32_t *__restrict__ dst, int64_t n) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i];
+constexpr int kLowLevels = 8;               // levels 1..8 from shared memory
+constexpr int kLowHalo = 1 << kLowLevels;   // 256 >= 2^8 - 1
+constexpr int kLowTile = 4096;
+constexpr int kLowThreads = 256;
+constexpr int kLowPer = (kLowTile + kLowHalo) / kLowThreads;  // 17
+
+__global__ void __launch_bounds__(kLowThreads) k_rmq_low(const int32_t *__restrict__ lcp, int64_t n,
+                                                         int32_t *__restrict__ table, int64_t stride,
+                                                         int top) {
+    __shared__ int32_t buf[kLowTile + kLowHalo];
+    const int64_t base = int64_t(blockIdx.x) * kLowTile;
+    const int tid = threadIdx.x;
+    int32_t v[kLowPer];
+#pragma unroll
+    for (int k = 0; k < kLowPer; ++k) {
+        const int64_t i = base + tid + k * kLowThreads;
+        v[k] = i < n ? lcp[i] : INT_MAX;  // clipped windows: padding never wins
+        buf[tid + k * kLowThreads] = v[k];
+    }
+    const int out_n = int(min64(int64_t(kLowTile), n - base));
+#pragma unroll
+    for (int k = 0; k < kLowPer; ++k) {
+        const int i = tid + k * kLowThreads;
+        if (i < out_n) table[base + i] = v[k];
+    }
+    for (int j = 1; j <= top; ++j) {
+        const int h = 1 << (j - 1);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kLowPer; ++k) {
+            const int i = tid + k * kLowThreads;
+            if (i + h < kLowTile + kLowHalo) v[k] = min(v[k], buf[i + h]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kLowPer; ++k) buf[tid + k * kLowThreads] = v[k];
+        int32_t *row = table + int64_t(j) * stride + base;
+#pragma unroll
+        for (int k = 0; k < kLowPer; ++k) {
+            const int i = tid + k * kLowThreads;
+            if (i < out_n) row[i] = v[k];
+        }
+    }
 }
 
-__global__ void k_rmq_level(const int32_t *__restrict__ src, int32_t *__restrict__ dst, int64_t n,
-                            int64_t h) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+// One level above the fused ones: four entries per thread, 16-byte accesses.
+__global__ void __launch_bounds__(256) k_rmq_level(const int32_t *__restrict__ src,
+                                                   int32_t *__restrict__ dst, int64_t n, int64_t h) {
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
     if (i >= n) return;
-    const int32_t a = src[i];
-    dst[i] = (i + h < n) ? min(a, src[i + h]) : a;
+    const int4 a = *reinterpret_cast<const int4 *>(src + i);
+    int4 r = a;
+    if (i + h + 3 < n) {
+        const int4 b = *reinterpret_cast<const int4 *>(src + i + h);
+        r.x = min(a.x, b.x);
+        r.y = min(a.y, b.y);
+        r.z = min(a.z, b.z);
+        r.w = min(a.w, b.w);
+    } else {
+        if (i + h + 0 < n) r.x = min(a.x, src[i + h + 0]);
+        if (i + h + 1 < n) r.y = min(a.y, src[i + h + 1]);
+        if (i + h + 2 < n) r.z = min(a.z, src[i + h + 2]);
+    }
+    *reinterpret_cast<int4 *>(dst + i) = r;
 }
 
-__global__ void k_rmq_query(const int32_t *__restrict__ table, const int32_t *__restrict__ isa,
-                            int64_t n, const int32_t *__restrict__ P, const int32_t *__restrict__ Q,
-                            int64_t nq, int32_t *__restrict__ out, int *status) {
+__global__ void k_rmq_query(const int32_t *__restrict__ table, int64_t stride,
+                            const int32_t *__restrict__ isa, int64_t n, const int32_t *__restrict__ P,
+                            const int32_t *__restrict__ Q, int64_t nq, int32_t *__restrict__ out,
+                            int *status) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nq) return;
     const int32_t p = P[i], q = Q[i];
@@ -56,7 +118,7 @@ __global__ void k_rmq_query(const int32_t *__restrict__ table, const int32_t *__
     }
     const int64_t len = int64_t(r2) - r1;  // window (r1, r2] of len entries
     const int j = 63 - __clzll(len);
-    const int32_t *lv = table + int64_t(j) * n;
+    const int32_t *lv = table + int64_t(j) * stride;
     out[i] = min(lv[r1 + 1], lv[r2 - (int64_t(1) << j) + 1]);
 }
 
@@ -65,9 +127,14 @@ __global__ void k_rmq_query(const int32_t *__restrict__ table, const int32_t *__
 
 using namespace lor;
 
+extern "C" int64_t lor_rmq_row_stride(int64_t n) {
+    if (n < 1 || n > LOR_MAX_N) return 0;
+    return row_stride(n);
+}
+
 extern "C" int64_t lor_rmq_table_elems(int64_t n) {
     if (n < 1 || n > LOR_MAX_N) return 0;
-    return int64_t(levels_for(n)) * n;
+    return int64_t(levels_for(n)) * row_stride(n);
 }
 
 extern "C" int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
@@ -75,18 +142,21 @@ extern "C" int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, 
     if (!d_lcp || !d_table || n < 1) return LOR_ERR_INVALID_ARG;
     if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
     if (table_elems < lor_rmq_table_elems(n)) return LOR_ERR_WORKSPACE;
+    if (uintptr_t(d_table) & 255) return LOR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const unsigned grid = unsigned(cdiv(n, 256));
+    const int J = levels_for(n);
+    const int64_t stride = row_stride(n);
+    const int top = J - 1 < kLowLevels ? J - 1 : kLowLevels;
     {
-        ProfScope ps(PK_RMQ_LEVEL, double(n) * 8, s);
-        k_copy_i32<<<grid, 256, 0, s>>>(d_lcp, d_table, n);
+        ProfScope ps(PK_RMQ_LEVEL, double(n) * (4 + 4.0 * (top + 1)), s);
+        k_rmq_low<<<unsigned(cdiv(n, kLowTile)), kLowThreads, 0, s>>>(d_lcp, n, d_table, stride, top);
     }
     LOR_LAUNCH_CHECK();
-    const int J = levels_for(n);
-    for (int j = 1; j < J; ++j) {
+    const unsigned grid = unsigned(cdiv(cdiv(n, 4), 256));
+    for (int j = kLowLevels + 1; j < J; ++j) {
         ProfScope ps(PK_RMQ_LEVEL, double(n) * 8, s);
-        k_rmq_level<<<grid, 256, 0, s>>>(d_table + int64_t(j - 1) * n, d_table + int64_t(j) * n, n,
-                                         int64_t(1) << (j - 1));
+        k_rmq_level<<<grid, 256, 0, s>>>(d_table + int64_t(j - 1) * stride, d_table + int64_t(j) * stride,
+                                         n, int64_t(1) << (j - 1));
         LOR_LAUNCH_CHECK();
     }
     return LOR_OK;
@@ -103,8 +173,8 @@ extern "C" int lor_rmq_query(const int32_t *d_table, const int32_t *d_isa, int64
     if (!status) return LOR_ERR_CUDA;
     {
         ProfScope ps(PK_RMQ_QUERY, double(nq) * (4 + 4 + 4 + 4 + 4 + 4 + 4), s);
-        k_rmq_query<<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(d_table, d_isa, n, d_p, d_q, nq, d_out,
-                                                            status);
+        k_rmq_query<<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(d_table, row_stride(n), d_isa, n, d_p, d_q,
+                                                            nq, d_out, status);
     }
     LOR_LAUNCH_CHECK();
     return LOR_OK;

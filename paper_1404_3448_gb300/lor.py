@@ -58,10 +58,12 @@ def load():
         "lor_build_sa_workspace_size": ([i64, i32], sz),
         "lor_build_sa": ([vp, i64, i32, vp, vp, sz, vp], ctypes.c_int),
         "lor_build_sa_noalloc": ([vp, i64, i32, vp, vp], ctypes.c_int),
-        "lor_lcp": ([vp, vp, i64, vp, vp, vp], ctypes.c_int),
+        "lor_lcp_workspace_size": ([i64], sz),
+        "lor_lcp": ([vp, vp, i64, vp, vp, vp, sz, vp], ctypes.c_int),
         "lor_longest_overlap_workspace_size": ([i64], sz),
         "lor_longest_overlap": ([vp, vp, i64, vp, i32, vp, vp, i64, vp, sz, vp], ctypes.c_int),
         "lor_rmq_table_elems": ([i64], i64),
+        "lor_rmq_row_stride": ([i64], i64),
         "lor_rmq_build": ([vp, i64, vp, i64, vp], ctypes.c_int),
         "lor_rmq_query": ([vp, vp, i64, vp, vp, i64, vp, vp], ctypes.c_int),
         "lor_radix_sort_workspace_size": ([i64], sz),
@@ -102,8 +104,12 @@ def lor_build_sa_noalloc(d_text, n, sigma, d_sa, stream):
     return load().lor_build_sa_noalloc(d_text, n, sigma, d_sa, stream)
 
 
-def lor_lcp(d_text, d_sa, n, d_isa, d_lcp, stream):
-    return load().lor_lcp(d_text, d_sa, n, d_isa, d_lcp, stream)
+def lor_lcp_workspace_size(n):
+    return load().lor_lcp_workspace_size(n)
+
+
+def lor_lcp(d_text, d_sa, n, d_isa, d_lcp, d_ws, ws_bytes, stream):
+    return load().lor_lcp(d_text, d_sa, n, d_isa, d_lcp, d_ws, ws_bytes, stream)
 
 
 def lor_longest_overlap_workspace_size(n):
@@ -118,6 +124,16 @@ def lor_longest_overlap(d_sa, d_lcp, n, d_seq_starts, nseq, d_out, d_pos, pos_ca
 
 def lor_rmq_table_elems(n):
     return load().lor_rmq_table_elems(n)
+
+
+def lor_rmq_row_stride(n):
+    return load().lor_rmq_row_stride(n)
+
+
+def table_view(table: torch.Tensor, n: int) -> torch.Tensor:
+    """(levels, n) view of a sparse table built for n LCP entries."""
+    stride = lor_rmq_row_stride(n)
+    return table.view(-1, stride)[:, :n]
 
 
 def lor_rmq_build(d_lcp, n, d_table, table_elems, stream):
@@ -223,14 +239,18 @@ def build_sa(text: torch.Tensor, sigma: int, sa=None, ws=None, stream=None) -> t
     return sa
 
 
-def lcp(text: torch.Tensor, sa: torch.Tensor, isa=None, lcp_out=None, stream=None):
+def lcp(text: torch.Tensor, sa: torch.Tensor, isa=None, lcp_out=None, ws=None, stream=None):
     n = text.numel()
     if isa is None:
         isa = torch.empty(n, dtype=torch.int32, device=text.device)
     if lcp_out is None:
         lcp_out = torch.empty(n, dtype=torch.int32, device=text.device)
+    need = lor_lcp_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, text.device)
     rc = lor_lcp(_ptr(text, torch.uint8, "text"), _ptr(sa, torch.int32, "sa"), n,
-                 _ptr(isa, torch.int32, "isa"), _ptr(lcp_out, torch.int32, "lcp"), _stream(stream))
+                 _ptr(isa, torch.int32, "isa"), _ptr(lcp_out, torch.int32, "lcp"), ws.data_ptr(),
+                 ws.numel(), _stream(stream))
     _check(rc, "lor_lcp")
     return isa, lcp_out
 
@@ -351,7 +371,7 @@ class Pipeline:
         self.pos_cap = int(pos_cap)
         self.pos = torch.empty(max(self.pos_cap, 1), dtype=torch.int32, device=dev)
         ws_bytes = max(lor_build_sa_workspace_size(n, self.sigma),
-                       lor_longest_overlap_workspace_size(n))
+                       lor_longest_overlap_workspace_size(n), lor_lcp_workspace_size(n))
         self.ws = workspace(ws_bytes, dev)
         self.table = (torch.empty(lor_rmq_table_elems(n), dtype=torch.int32, device=dev)
                       if with_rmq else None)
@@ -364,7 +384,7 @@ class Pipeline:
         _check(lor_build_sa(self.text.data_ptr(), self.n, self.sigma, self.sa.data_ptr(),
                             self.ws.data_ptr(), self.ws.numel(), s), "lor_build_sa")
         _check(lor_lcp(self.text.data_ptr(), self.sa.data_ptr(), self.n, self.isa.data_ptr(),
-                       self.lcp.data_ptr(), s), "lor_lcp")
+                       self.lcp.data_ptr(), self.ws.data_ptr(), self.ws.numel(), s), "lor_lcp")
         _check(lor_longest_overlap(self.sa.data_ptr(), self.lcp.data_ptr(), self.n,
                                    self.starts.data_ptr(), self.nseq, self.out.data_ptr(),
                                    self.pos.data_ptr(), self.pos_cap, self.ws.data_ptr(),

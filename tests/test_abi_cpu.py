@@ -56,8 +56,10 @@ def test_workspace_queries_are_host_only(lib):
     # ~40 bytes per base at scale (sort buffers + per-level arrays)
     assert L.lor_build_sa_workspace_size(10**8, 7) < 48 * 10**8
     assert L.lor_longest_overlap_workspace_size(1000) > 0
-    assert L.lor_rmq_table_elems(1) == 1
-    assert L.lor_rmq_table_elems(8) == 4 * 8
+    assert L.lor_rmq_row_stride(1) == 64 and L.lor_rmq_row_stride(64) == 64
+    assert L.lor_rmq_row_stride(65) == 128
+    assert L.lor_rmq_table_elems(1) == 64
+    assert L.lor_rmq_table_elems(8) == 4 * 64
     assert L.lor_rmq_table_elems(1 << 20) == 21 * (1 << 20)
     assert L.lor_radix_sort_workspace_size(0) > 0
 
@@ -69,13 +71,16 @@ def test_bad_arguments_rejected_on_host(lib):
     assert L.lor_build_sa(1 << 20, 1 << 40, 7, 1 << 20, None, 0, None) == L.LOR_ERR_TOO_LARGE
     assert L.lor_build_sa(1 << 20, 10, 7, 1 << 20, None, 0, None) == L.LOR_ERR_WORKSPACE
     assert L.lor_build_sa(1 << 20, 10, 7, 1 << 20, (1 << 20) + 8, 1 << 30, None) == L.LOR_ERR_WORKSPACE
-    assert L.lor_lcp(None, None, 5, None, None, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_lcp(None, None, 5, None, None, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert L.lor_lcp(256, 256, 5, 256, 256, None, 0, None) == L.LOR_ERR_WORKSPACE
+    assert L.lor_lcp_workspace_size(1000) >= 12 * 1000
     assert L.lor_longest_overlap(1, 1, 5, 1, 0, 1, None, 0, None, 0, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_longest_overlap(1, 1, 5, 1, 251, 1, None, 0, None, 0, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_longest_overlap(256, 256, 5, 256, 2, 256, None, 4, None, 0, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_longest_overlap(256, 256, 5, 256, 2, 256, None, 0, None, 0, None) == L.LOR_ERR_WORKSPACE
     assert L.lor_rmq_build(None, 5, None, 0, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_rmq_build(256, 5, 256, 4, None) == L.LOR_ERR_WORKSPACE
+    assert L.lor_rmq_build(256, 5, 256 + 4, 1 << 10, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_rmq_query(None, None, 5, None, None, 1, None, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_rmq_query(256, 256, 5, None, None, 0, None, None) == L.LOR_OK
     lens = (ctypes.c_int64 * 2)(3, 4)

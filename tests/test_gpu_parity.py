@@ -85,7 +85,8 @@ def assert_full_parity(O, g, e, table=True):
     assert_overlap_equal(g["overlap"], e["overlap"])
     if table and "table" in g:
         st = O.sparse_table(e["lcp"])
-        np.testing.assert_array_equal(g["table"].cpu().numpy().reshape(st.shape), st)
+        from paper_1404_3448_gb300 import lor as C
+        np.testing.assert_array_equal(C.table_view(g["table"], g["n"]).cpu().numpy(), st)
 
 
 # ------------------------------------------------------------------ paper example
