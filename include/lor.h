@@ -114,7 +114,7 @@ int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
  * allocate device memory (the paper has no counterpart; this is a library
  * convenience).  Same result, arguments and errors as lor_build_sa, for
  * n <= LOR_NOALLOC_MAX_N; larger n returns LOR_ERR_TOO_LARGE before touching
- * the device.  The scratch is one 16 MiB array compiled into the library:
+ * the device.  The scratch is one 32 MiB array compiled into the library:
  * every GPU that loads liblor holds it until the process exits.  The first
  * call on a device looks up the array's device address (call it once before
  * any stream capture).  All calls share the array, so calls that can overlap
@@ -208,8 +208,12 @@ uint64_t lor_launch_count(void);
 
 /* Per-level trace of the most recent lor_build_sa call in this process:
  * fills up to cap entries of level length n_l, distinct names found at that
- * level, and key bits sorted; returns the number of levels. */
-int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits, int32_t cap);
+ * level, key bits of the sample keys, how the sample was ordered (0 radix
+ * sort, 1 dense naming table, 2 the parent level's order) and how many
+ * samples shared their first symbol (strategy 2); any pointer may be NULL.
+ * Returns the number of levels. */
+int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits, int32_t *h_strategy,
+                       int64_t *h_dups, int32_t cap);
 
 /* Kernel timing: when enabled, every launch records a CUDA event pair on its
  * stream together with the algorithmic bytes it moves.  lor_profile_read

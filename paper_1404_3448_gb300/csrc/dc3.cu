@@ -49,12 +49,23 @@ constexpr size_t kPad = 4;  // zero symbols kept after every reduced string
 
 struct Dc3Layout {
     size_t ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
-    size_t ka = 0, kb = 0, va = 0, vb = 0;
+    size_t tbl = 0;
+    int64_t tbl_entries = 0;
+    size_t t64[3] = {0, 0, 0};
+    size_t t32[6] = {0, 0, 0, 0, 0, 0};
     int64_t max_m = 0;
     std::vector<int64_t> lev_n;
-    std::vector<size_t> lev_R, lev_SAR;
+    std::vector<size_t> lev_R, lev_SAR, lev_NS;
     size_t total = 0;
 };
+
+// Entries of the dense naming table: enough for 24-bit keys at scale, and
+// never much larger than the sample.
+int64_t dense_entries(int64_t max_m) {
+    int64_t e = int64_t(1) << 16;
+    while (e < (int64_t(1) << 24) && e < 4 * max_m) e <<= 1;
+    return e;
+}
 
 Dc3Layout dc3_layout(int64_t n) {
     Dc3Layout L;
@@ -71,14 +82,16 @@ Dc3Layout dc3_layout(int64_t n) {
     L.offsets = take(sizeof(uint32_t) * kMaxPasses * kRadix);
     L.lookback_bytes = radix_lookback_bytes(L.max_m);
     L.lookback = take(L.lookback_bytes);
-    L.ka = take(sizeof(uint64_t) * size_t(L.max_m));
-    L.kb = take(sizeof(uint64_t) * size_t(L.max_m));
-    L.va = take(sizeof(uint32_t) * size_t(L.max_m));
-    L.vb = take(sizeof(uint32_t) * size_t(L.max_m));
+    L.tbl_entries = dense_entries(L.max_m);
+    L.tbl = take(sizeof(uint32_t) * size_t(L.tbl_entries));
+    // t64[1], t64[2] are adjacent: together they hold the merge records.
+    for (int i = 0; i < 3; ++i) L.t64[i] = take(sizeof(uint64_t) * size_t(L.max_m));
+    for (int i = 0; i < 6; ++i) L.t32[i] = take(sizeof(uint32_t) * size_t(L.max_m));
     for (size_t l = 0; l < L.lev_n.size(); ++l) {
         const int64_t m = level_sizes(L.lev_n[l]).n02;
         L.lev_R.push_back(take(sizeof(int32_t) * (size_t(m) + kPad)));
         L.lev_SAR.push_back(take(sizeof(int32_t) * size_t(m)));
+        L.lev_NS.push_back(take(sizeof(int32_t) * size_t(m)));
     }
     L.total = off;
     return L;
@@ -130,7 +143,7 @@ template <typename KeyT>
 __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ keys,
                                                        const uint32_t *__restrict__ vals, int64_t m,
                                                        int32_t *__restrict__ R, int32_t *__restrict__ SAR,
-                                                       uint32_t *n_names, uint64_t *lb,
+                                                       int32_t *__restrict__ NS, uint32_t *n_names, uint64_t *lb,
                                                        unsigned long long *ctr,
                                                        unsigned long long tile_base, uint32_t epoch,
                                                        int *status) {
@@ -171,6 +184,7 @@ __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ 
             const uint32_t v = vals[j];
             R[v] = int32_t(name);
             SAR[j] = int32_t(v);
+            NS[j] = int32_t(name);
             if (j == m - 1) *n_names = name;
         }
     }
@@ -181,9 +195,9 @@ __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ 
 template <typename CharT>
 __global__ void __launch_bounds__(kScanThreads) k_name_gather(
     const uint32_t *__restrict__ vals, int64_t m, const CharT *__restrict__ s, int64_t n,
-    int64_t n0, int32_t *__restrict__ R, int32_t *__restrict__ SAR, uint32_t *n_names,
-    uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
-    int *status) {
+    int64_t n0, int32_t *__restrict__ R, int32_t *__restrict__ SAR, int32_t *__restrict__ NS,
+    uint32_t *n_names, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base,
+    uint32_t epoch, int *status) {
     __shared__ long long s_tile;
     __shared__ uint32_t scratch[kScanThreads / 32 + 1];
     __shared__ uint32_t s_prefix;
@@ -224,6 +238,7 @@ __global__ void __launch_bounds__(kScanThreads) k_name_gather(
             const uint32_t v = vals[j];
             R[v] = int32_t(name);
             SAR[j] = int32_t(v);
+            NS[j] = int32_t(name);
             if (j == m - 1) *n_names = name;
         }
     }
@@ -489,6 +504,297 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(MergeIn<CharT> a,
     for (int i = threadIdx.x; i < nt; i += kMergeThreads) out[d0 + i] = Os[i];
 }
 
+// ---- generic order-preserving tile compaction and naming (look-back scans)
+
+// Every kernel below handles kScanTile consecutive items per block (blocked:
+// kScanItems per thread), claims its tile from the running counter, scans its
+// predicate and walks back over predecessor tiles for the global offset.
+template <typename Pred, typename Emit>
+__device__ __forceinline__ void tile_compact(int64_t m, Pred pred, Emit emit, uint64_t *lb,
+                                             unsigned long long *ctr, unsigned long long tile_base,
+                                             uint32_t epoch, int *status, uint32_t *count,
+                                             int64_t ntiles) {
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m && pred(j)) {
+            flags |= 1u << i;
+            cnt++;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) {
+            s_prefix = p;
+            if (count && tile == ntiles - 1) *count = p + agg;
+        }
+    }
+    __syncthreads();
+    uint32_t o = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if ((flags >> i) & 1u) emit(base + i, o++);
+}
+
+// name(j) = number of j' <= j where NewName(j') holds (NewName(0) must hold).
+template <typename NewName, typename Emit>
+__device__ __forceinline__ void tile_names(int64_t m, NewName is_new, Emit emit, uint32_t *n_names,
+                                           uint64_t *lb, unsigned long long *ctr,
+                                           unsigned long long tile_base, uint32_t epoch, int *status) {
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m && is_new(j)) {
+            flags |= 1u << i;
+            cnt++;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) s_prefix = p;
+    }
+    __syncthreads();
+    uint32_t name = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m) {
+            name += (flags >> i) & 1u;
+            emit(j, name);
+            if (j == m - 1) *n_names = name;
+        }
+    }
+}
+
+template <typename CharT>
+__device__ __forceinline__ int64_t sym(const CharT *s, int64_t n, int64_t q) {
+    return q < n ? int64_t(s[q]) : 0;
+}
+
+// ---- Step 1 by dense naming: when the key space is small the name of a key
+// is 1 + the number of distinct keys below it, read from a table of present
+// keys; no sort is needed unless the names come out unique.
+
+template <typename CharT, bool kValidate>
+__global__ void k_dense_mark(const CharT *__restrict__ s, int64_t n, int64_t n0, int64_t n02,
+                             int kchars, int bits, int64_t maxc, uint32_t *__restrict__ table,
+                             int *status) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n02) return;
+    const int64_t p = sample_pos(j, n0);
+    uint32_t key = 0;
+    bool bad = false;
+    for (int t = 0; t < kchars; ++t) {
+        int64_t c = sym(s, n, p + t);
+        if (p + t < n && (c < 1 || c > maxc)) {  // keeps the key inside the table
+            bad = true;
+            c = c < 1 ? 1 : maxc;
+        }
+        key = (key << bits) | uint32_t(c);
+    }
+    if (kValidate && j == 0) {
+        const int64_t c = int64_t(s[0]);
+        if (c < 1 || c > maxc) bad = true;
+    }
+    if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
+    table[key] = 1u;
+}
+
+// In place: table[k] = (present ? 1 + number of present keys below k : 0).
+__global__ void __launch_bounds__(kScanThreads) k_dense_scan(uint32_t *__restrict__ table, int64_t m,
+                                                             uint32_t *n_names, uint64_t *lb,
+                                                             unsigned long long *ctr,
+                                                             unsigned long long tile_base,
+                                                             uint32_t epoch, int *status,
+                                                             int64_t ntiles) {
+    tile_compact(
+        m, [&](int64_t k) { return table[k] != 0u; },
+        [&](int64_t k, uint32_t o) { table[k] = o + 1; }, lb, ctr, tile_base, epoch, status, n_names,
+        ntiles);
+}
+
+template <typename CharT>
+__global__ void k_dense_write(const CharT *__restrict__ s, int64_t n, int64_t n0, int64_t n02, int kchars,
+                              int bits, int64_t maxc, const uint32_t *__restrict__ table,
+                              int32_t *__restrict__ R) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n02) return;
+    const int64_t p = sample_pos(j, n0);
+    uint32_t key = 0;
+    for (int t = 0; t < kchars; ++t) {
+        int64_t c = sym(s, n, p + t);
+        if (p + t < n) c = c < 1 ? 1 : (c > maxc ? maxc : c);
+        key = (key << bits) | uint32_t(c);
+    }
+    R[j] = int32_t(table[key]);
+}
+
+// Unique names are ranks: the sorted order is their inverse.
+__global__ void k_dense_sorted(const int32_t *__restrict__ R, int64_t n02, int32_t *__restrict__ SAR,
+                               int32_t *__restrict__ NS, int *status) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n02) return;
+    const int32_t r = R[j];
+    if (r < 1 || r > n02) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        return;
+    }
+    SAR[r - 1] = int32_t(j);
+    NS[r - 1] = r;
+}
+
+// ---- Step 1 from the parent's order: the parent level sorted every position
+// of this level's string by its symbol (its name), so filtering that order to
+// the sample positions sorts the samples by their first symbol; only runs of
+// equal first symbols need their next two symbols.
+
+__global__ void __launch_bounds__(kScanThreads) k_par_samples(
+    const int32_t *__restrict__ PS, const int32_t *__restrict__ NS, int64_t n, int64_t n0, int dummy,
+    uint32_t *__restrict__ SL, uint32_t *__restrict__ PRI, uint64_t *__restrict__ SEC, uint64_t *lb,
+    unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch, int *status) {
+    if (dummy && blockIdx.x == 0 && threadIdx.x == 0) {
+        SL[0] = uint32_t(n0 - 1);  // the dummy position n, key (0,0,0): first
+        PRI[0] = 0;
+        SEC[0] = 0;
+    }
+    tile_compact(
+        n, [&](int64_t j) { return PS[j] % 3 != 0; },
+        [&](int64_t j, uint32_t o) {
+            const int32_t x = PS[j];
+            const int64_t slot = o + dummy;
+            SL[slot] = x % 3 == 1 ? uint32_t((x - 1) / 3) : uint32_t(n0 + (x - 2) / 3);
+            PRI[slot] = uint32_t(NS[j]);
+            SEC[slot] = 0;
+        },
+        lb, ctr, tile_base, epoch, status, nullptr, 0);
+}
+
+__device__ __forceinline__ bool in_dup_run(const uint32_t *PRI, int64_t m, int64_t o) {
+    const uint32_t v = PRI[o];
+    return (o > 0 && PRI[o - 1] == v) || (o + 1 < m && PRI[o + 1] == v);
+}
+
+template <typename CharT>
+__device__ __forceinline__ uint64_t second_third(const CharT *s, int64_t n, int64_t x, int bits) {
+    return (uint64_t(sym(s, n, x + 1)) << bits) | uint64_t(sym(s, n, x + 2));
+}
+
+template <typename CharT>
+__global__ void __launch_bounds__(kScanThreads) k_par_dups(
+    const uint32_t *__restrict__ SL, const uint32_t *__restrict__ PRI, int64_t m, const CharT *__restrict__ s,
+    int64_t n, int64_t n0, int bits, uint32_t *__restrict__ Dslot, uint32_t *__restrict__ Dsl,
+    uint64_t *__restrict__ Dkey, uint32_t *count, uint64_t *lb, unsigned long long *ctr,
+    unsigned long long tile_base, uint32_t epoch, int *status, int64_t ntiles) {
+    tile_compact(
+        m, [&](int64_t o) { return in_dup_run(PRI, m, o); },
+        [&](int64_t o, uint32_t d) {
+            const uint32_t j = SL[o];
+            Dslot[d] = uint32_t(o);
+            Dsl[d] = j;
+            Dkey[d] = second_third(s, n, sample_pos(j, n0), bits);
+        },
+        lb, ctr, tile_base, epoch, status, count, ntiles);
+}
+
+// key32[i] = PRI[slot[v[i]]]: the first symbol of a duplicate, in the order
+// of the previous (secondary) sort.
+__global__ void k_gather_pri(const uint32_t *__restrict__ v, int64_t m, const uint32_t *__restrict__ slot,
+                             const uint32_t *__restrict__ PRI, uint32_t *__restrict__ key32) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < m) key32[i] = PRI[slot[v[i]]];
+}
+
+// The sorted duplicates go back into the duplicate slots in slot order.
+template <typename CharT>
+__global__ void k_par_dup_writeback(const uint32_t *__restrict__ v, int64_t m,
+                                    const uint32_t *__restrict__ Dslot, const uint32_t *__restrict__ Dsl,
+                                    const CharT *__restrict__ s, int64_t n, int64_t n0, int bits,
+                                    uint32_t *__restrict__ SL, uint64_t *__restrict__ SEC) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t d = v[i];
+    const uint32_t o = Dslot[i];
+    const uint32_t j = Dsl[d];
+    SL[o] = j;
+    SEC[o] = second_third(s, n, sample_pos(j, n0), bits);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_par_name(
+    const uint32_t *__restrict__ SL, const uint32_t *__restrict__ PRI, const uint64_t *__restrict__ SEC,
+    int64_t m, int32_t *__restrict__ R, int32_t *__restrict__ SAR, int32_t *__restrict__ NS,
+    uint32_t *n_names, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base,
+    uint32_t epoch, int *status) {
+    tile_names(
+        m, [&](int64_t o) { return o == 0 || PRI[o] != PRI[o - 1] || SEC[o] != SEC[o - 1]; },
+        [&](int64_t o, uint32_t name) {
+            const uint32_t j = SL[o];
+            R[j] = int32_t(name);
+            SAR[o] = int32_t(j);
+            NS[o] = int32_t(name);
+        },
+        n_names, lb, ctr, tile_base, epoch, status);
+}
+
+// ---- Step 2 from the parent's order: nonsample positions 3t sorted by their
+// symbol, then runs of equal symbols refined by rank(S_3t+1).
+
+__global__ void __launch_bounds__(kScanThreads) k_par_nonsamples(
+    const int32_t *__restrict__ PS, const int32_t *__restrict__ NS, int64_t n, uint32_t *__restrict__ T0,
+    uint32_t *__restrict__ P0, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base,
+    uint32_t epoch, int *status) {
+    tile_compact(
+        n, [&](int64_t j) { return PS[j] % 3 == 0; },
+        [&](int64_t j, uint32_t o) {
+            T0[o] = uint32_t(PS[j] / 3);
+            P0[o] = uint32_t(NS[j]);
+        },
+        lb, ctr, tile_base, epoch, status, nullptr, 0);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_par_ns_dups(
+    const uint32_t *__restrict__ T0, const uint32_t *__restrict__ P0, int64_t m,
+    const int32_t *__restrict__ rankR, uint32_t *__restrict__ Dslot, uint32_t *__restrict__ Dt,
+    uint32_t *__restrict__ Dkey, uint32_t *count, uint64_t *lb, unsigned long long *ctr,
+    unsigned long long tile_base, uint32_t epoch, int *status, int64_t ntiles) {
+    tile_compact(
+        m, [&](int64_t o) { return in_dup_run(P0, m, o); },
+        [&](int64_t o, uint32_t d) {
+            const uint32_t t = T0[o];
+            Dslot[d] = uint32_t(o);
+            Dt[d] = t;
+            Dkey[d] = uint32_t(rankR[t]);  // rank(S_3t+1)
+        },
+        lb, ctr, tile_base, epoch, status, count, ntiles);
+}
+
+__global__ void k_par_ns_writeback(const uint32_t *__restrict__ v, int64_t m, const uint32_t *__restrict__ Dslot,
+                                   const uint32_t *__restrict__ Dt, uint32_t *__restrict__ T0) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < m) T0[Dslot[i]] = Dt[v[i]];
+}
+
 // ---------------------------------------------------------------- host driver
 
 struct TraceRow {
@@ -513,19 +819,41 @@ struct Dc3Run {
     char *ws;
     Dc3Layout L;
     RadixScratch rs;
-    uint32_t *d_names;
-    void *ka, *kb;
-    uint32_t *va, *vb;
-    int64_t *split;  // merge partition, carved from the lookback area's tail use
+    uint32_t *d_names;  // count read back after naming
+    uint32_t *d_count;  // count read back after a compaction
+    uint64_t *t64[3];
+    uint32_t *t32[6];
+    uint32_t *tbl;
+    bool force_lsd;
 };
 
 inline unsigned grid_for(int64_t m, int nt) { return unsigned(cdiv(m > 0 ? m : 1, nt)); }
 
+int read_u32(Dc3Run &D, const uint32_t *d, uint32_t *h) {
+    LOR_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, D.s));
+    LOR_CUDA_TRY(cudaStreamSynchronize(D.s));
+    return LOR_OK;
+}
+
+// Launch a tile_compact/tile_names kernel: claims its tiles from the running
+// counter under a fresh look-back epoch.
+#define LOR_TILE_LAUNCH(D, m, kernel, ...)                                                 \
+    do {                                                                                  \
+        const int64_t _nt = cdiv((m) > 0 ? (m) : 1, kScanTile);                           \
+        (D).rs.epoch++;                                                                   \
+        kernel<<<unsigned(_nt), kScanThreads, 0, (D).s>>>(__VA_ARGS__);                   \
+        LOR_LAUNCH_CHECK();                                                               \
+        (D).rs.tile_base += (unsigned long long)_nt;                                      \
+    } while (0)
+
+#define LB_ARGS(D) (D).rs.lookback, (D).rs.tile_ctr, (D).rs.tile_base, (D).rs.epoch, (D).status
+
+// ---- Step 1, strategy "sort": LSD radix sort of the keys, then naming.
 template <typename CharT, typename KeyT>
 int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars,
-                         int bits, int64_t maxc, int32_t *Rl, int32_t *SAR) {
+                         int bits, int64_t maxc, int32_t *Rl, int32_t *SAR, int32_t *NSl) {
     cudaStream_t st = D.s;
-    KeyT *k0 = (KeyT *)D.ka, *k1 = (KeyT *)D.kb;
+    KeyT *k0 = (KeyT *)D.t64[0], *k1 = (KeyT *)D.t64[1];
     {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (sizeof(KeyT) + (lvl == 0 ? 1.0 : 4.0) * kchars / 3.0), st);
         if (lvl == 0)
@@ -538,26 +866,21 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
     LOR_LAUNCH_CHECK();
     KeyT *kr;
     uint32_t *vr;
-    int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.va, k1, D.vb, z.n02, 0, kchars * bits, true, &kr, &vr);
+    int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, kchars * bits, true, &kr, &vr);
     if (rc) return rc;
-    D.rs.epoch++;
     {
-        ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 12), st);
-        k_name<KeyT><<<grid_for(z.n02, kScanTile), kScanThreads, 0, st>>>(
-            kr, vr, z.n02, Rl, SAR, D.d_names, D.rs.lookback, D.rs.tile_ctr, D.rs.tile_base,
-            D.rs.epoch, D.status);
+        ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 16), st);
+        LOR_TILE_LAUNCH(D, z.n02, k_name<KeyT>, kr, vr, z.n02, Rl, SAR, NSl, D.d_names, LB_ARGS(D));
     }
-    LOR_LAUNCH_CHECK();
-    D.rs.tile_base += (unsigned long long)cdiv(z.n02, kScanTile);
     return LOR_OK;
 }
 
 // Triples too wide for 64 bits: stable sort by (t_i+1, t_i+2), then by t_i.
 template <typename CharT>
 int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits, int64_t maxc,
-                              int32_t *Rl, int32_t *SAR) {
+                              int32_t *Rl, int32_t *SAR, int32_t *NSl) {
     cudaStream_t st = D.s;
-    uint64_t *k0 = (uint64_t *)D.ka, *k1 = (uint64_t *)D.kb;
+    uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
     {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (8 + 8), st);
         k_sample_keys<CharT, uint64_t, false><<<grid_for(z.n02, 256), 256, 0, st>>>(
@@ -566,11 +889,11 @@ int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, in
     LOR_LAUNCH_CHECK();
     uint64_t *kr;
     uint32_t *vr;
-    int rc = radix_sort_pairs<uint64_t>(D.rs, k0, D.va, k1, D.vb, z.n02, 0, 2 * bits, true, &kr, &vr);
+    int rc = radix_sort_pairs<uint64_t>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, 2 * bits, true, &kr, &vr);
     if (rc) return rc;
     uint32_t *kx = (uint32_t *)(kr == k0 ? k1 : k0);  // free key buffer
     uint32_t *ky = (uint32_t *)kr;
-    uint32_t *vx = vr, *vy = (vr == D.va ? D.vb : D.va);
+    uint32_t *vx = vr, *vy = (vr == D.t32[0] ? D.t32[1] : D.t32[0]);
     {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (4 + 4 + 4), st);
         k_first_char<CharT><<<grid_for(z.n02, 256), 256, 0, st>>>(vx, z.n02, s, z.n, z.n0, kx);
@@ -579,43 +902,159 @@ int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, in
     uint32_t *kr2, *vr2;
     rc = radix_sort_pairs<uint32_t>(D.rs, kx, vx, ky, vy, z.n02, 0, bits, false, &kr2, &vr2);
     if (rc) return rc;
-    D.rs.epoch++;
     {
-        ProfScope ps(PK_NAMING, double(z.n02) * (4 + 8 + 12 * 2), st);
-        k_name_gather<CharT><<<grid_for(z.n02, kScanTile), kScanThreads, 0, st>>>(
-            vr2, z.n02, s, z.n, z.n0, Rl, SAR, D.d_names, D.rs.lookback, D.rs.tile_ctr,
-            D.rs.tile_base, D.rs.epoch, D.status);
+        ProfScope ps(PK_NAMING, double(z.n02) * (4 + 12 + 12 * 2), st);
+        LOR_TILE_LAUNCH(D, z.n02, k_name_gather<CharT>, vr2, z.n02, s, z.n, z.n0, Rl, SAR, NSl,
+                        D.d_names, LB_ARGS(D));
     }
-    LOR_LAUNCH_CHECK();
-    D.rs.tile_base += (unsigned long long)cdiv(z.n02, kScanTile);
     return LOR_OK;
 }
 
+// ---- Step 1, strategy "dense": names from a table of present keys.
 template <typename CharT>
-int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32_t *out) {
+int sample_dense_names(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars, int bits,
+                       int64_t maxc, int32_t *Rl, int32_t *SAR, int32_t *NSl, uint32_t *names) {
+    cudaStream_t st = D.s;
+    const int64_t T = int64_t(1) << (kchars * bits);
+    LOR_CUDA_TRY(cudaMemsetAsync(D.tbl, 0, sizeof(uint32_t) * size_t(T), st));
+    {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (kchars * sizeof(CharT) / 3.0 + 4), st);
+        if (lvl == 0)
+            k_dense_mark<CharT, true><<<grid_for(z.n02, 256), 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars,
+                                                                            bits, maxc, D.tbl, D.status);
+        else
+            k_dense_mark<CharT, false><<<grid_for(z.n02, 256), 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars,
+                                                                             bits, maxc, D.tbl, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    {
+        ProfScope ps(PK_NAMING, double(T) * 8, st);
+        const int64_t ntiles = cdiv(T, kScanTile);
+        LOR_TILE_LAUNCH(D, T, k_dense_scan, D.tbl, T, D.d_names, LB_ARGS(D), ntiles);
+    }
+    {
+        ProfScope ps(PK_NAMING, double(z.n02) * (kchars * sizeof(CharT) / 3.0 + 8), st);
+        k_dense_write<CharT><<<grid_for(z.n02, 256), 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, bits, maxc,
+                                                                   D.tbl, Rl);
+    }
+    LOR_LAUNCH_CHECK();
+    int rc = read_u32(D, D.d_names, names);
+    if (rc) return rc;
+    if (int64_t(*names) == z.n02) {
+        ProfScope ps(PK_RANK_SCATTER, double(z.n02) * 12, st);
+        k_dense_sorted<<<grid_for(z.n02, 256), 256, 0, st>>>(Rl, z.n02, SAR, NSl, D.status);
+        LOR_LAUNCH_CHECK();
+    }
+    return LOR_OK;
+}
+
+// Sort (key, value) pairs of a duplicate subset: by key (key_bits), then
+// stably by the first symbol PRI[slot[v]] (pri_bits).  Returns the value
+// order in *vout.
+template <typename KeyT>
+int sort_dups_then_by_first(Dc3Run &D, KeyT *keys, int64_t nd, int key_bits, const uint32_t *slot,
+                            const uint32_t *PRI, int pri_bits, uint32_t **vout) {
+    cudaStream_t st = D.s;
+    KeyT *kalt = (KeyT *)D.t64[2];
+    KeyT *kr;
+    uint32_t *vr;
+    int rc = radix_sort_pairs<KeyT>(D.rs, keys, D.t32[4], kalt, D.t32[5], nd, 0, key_bits, true, &kr, &vr);
+    if (rc) return rc;
+    uint32_t *kx = (uint32_t *)(kr == keys ? (void *)kalt : (void *)keys);
+    uint32_t *ky = (uint32_t *)kr;
+    uint32_t *vy = vr == D.t32[4] ? D.t32[5] : D.t32[4];
+    k_gather_pri<<<grid_for(nd, 256), 256, 0, st>>>(vr, nd, slot, PRI, kx);
+    LOR_LAUNCH_CHECK();
+    uint32_t *kr2;
+    rc = radix_sort_pairs<uint32_t>(D.rs, kx, vr, ky, vy, nd, 0, pri_bits, false, &kr2, vout);
+    return rc;
+}
+
+// ---- Step 1, strategy "parent order".
+template <typename CharT>
+int sample_from_parent(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits, const int32_t *PS,
+                       const int32_t *PNS, int32_t *Rl, int32_t *SAR, int32_t *NSl, int64_t *dups) {
+    cudaStream_t st = D.s;
+    const int dummy = (z.n0 > z.n1) ? 1 : 0;
+    uint32_t *SL = D.t32[0], *PRI = D.t32[1], *Dslot = D.t32[2], *Dsl = D.t32[3];
+    uint64_t *SEC = D.t64[0], *Dkey = D.t64[1];
+    {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n) * 8 + double(z.n02) * 16, st);
+        LOR_TILE_LAUNCH(D, z.n, k_par_samples, PS, PNS, z.n, z.n0, dummy, SL, PRI, SEC, LB_ARGS(D));
+    }
+    {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * 8, st);
+        const int64_t ntiles = cdiv(z.n02, kScanTile);
+        LOR_TILE_LAUNCH(D, z.n02, k_par_dups<CharT>, SL, PRI, z.n02, s, z.n, z.n0, bits, Dslot, Dsl, Dkey,
+                        D.d_count, LB_ARGS(D), ntiles);
+    }
+    uint32_t nd = 0;
+    int rc = read_u32(D, D.d_count, &nd);
+    if (rc) return rc;
+    *dups = nd;
+    if (nd > 0) {
+        uint32_t *vord;
+        rc = sort_dups_then_by_first<uint64_t>(D, Dkey, nd, 2 * bits, Dslot, PRI, bits, &vord);
+        if (rc) return rc;
+        k_par_dup_writeback<CharT><<<grid_for(nd, 256), 256, 0, st>>>(vord, nd, Dslot, Dsl, s, z.n, z.n0,
+                                                                      bits, SL, SEC);
+        LOR_LAUNCH_CHECK();
+    }
+    {
+        ProfScope ps(PK_NAMING, double(z.n02) * (4 + 4 + 8 + 4 + 4 + 4), st);
+        LOR_TILE_LAUNCH(D, z.n02, k_par_name, SL, PRI, SEC, z.n02, Rl, SAR, NSl, D.d_names, LB_ARGS(D));
+    }
+    return LOR_OK;
+}
+
+struct TraceExtra {
+    int strategy;  // 0 sort, 1 dense, 2 parent order
+    int64_t dups;
+};
+std::vector<TraceExtra> g_trace_extra;
+
+template <typename CharT>
+int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32_t *out, const int32_t *PS,
+              const int32_t *PNS) {
     cudaStream_t st = D.s;
     if (lvl >= int(D.L.lev_R.size())) return LOR_ERR_WORKSPACE;
     const LevelSizes z = level_sizes(n);
     int32_t *Rl = (int32_t *)(D.ws + D.L.lev_R[lvl]);
     int32_t *SAR = (int32_t *)(D.ws + D.L.lev_SAR[lvl]);
+    int32_t *NSl = (int32_t *)(D.ws + D.L.lev_NS[lvl]);
     const int bits = bit_width_u64(uint64_t(maxc));
     const int kchars = lvl == 0 ? level0_kchars(bits) : 3;
     const int key_bits = kchars * bits;
 
-    // zero padding after R so that level lvl+1 may read past its end
     LOR_CUDA_TRY(cudaMemsetAsync(Rl + z.n02, 0, sizeof(int32_t) * kPad, st));
     int rc;
-    if (key_bits <= 32) rc = sample_sort_and_name<CharT, uint32_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR);
-    else if (key_bits <= 64) rc = sample_sort_and_name<CharT, uint64_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR);
-    else rc = sample_sort_and_name_wide<CharT>(D, s, z, bits, maxc, Rl, SAR);
-    if (rc) return rc;
-
     uint32_t names = 0;
-    LOR_CUDA_TRY(cudaMemcpyAsync(&names, D.d_names, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    LOR_CUDA_TRY(cudaStreamSynchronize(st));
+    int strategy;
+    int64_t dups = 0;
+    bool sorted_list = true;  // SAR / NSl hold the samples in key order
+    if (PS && !D.force_lsd) {
+        strategy = 2;
+        rc = sample_from_parent<CharT>(D, s, z, bits, PS, PNS, Rl, SAR, NSl, &dups);
+        if (rc) return rc;
+        rc = read_u32(D, D.d_names, &names);
+    } else if (!D.force_lsd && key_bits <= 24 && (int64_t(1) << key_bits) <= D.L.tbl_entries) {
+        strategy = 1;
+        rc = sample_dense_names<CharT>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR, NSl, &names);
+        sorted_list = int64_t(names) == z.n02;
+    } else {
+        strategy = 0;
+        if (key_bits <= 32) rc = sample_sort_and_name<CharT, uint32_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR, NSl);
+        else if (key_bits <= 64) rc = sample_sort_and_name<CharT, uint64_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR, NSl);
+        else rc = sample_sort_and_name_wide<CharT>(D, s, z, bits, maxc, Rl, SAR, NSl);
+        if (rc) return rc;
+        rc = read_u32(D, D.d_names, &names);
+    }
+    if (rc) return rc;
     g_trace.push_back(TraceRow{n, int64_t(names), key_bits});
+    g_trace_extra.push_back(TraceExtra{strategy, dups});
     if (int64_t(names) < z.n02) {
-        rc = dc3_level<int32_t>(D, lvl + 1, Rl, z.n02, int64_t(names), SAR);
+        rc = dc3_level<int32_t>(D, lvl + 1, Rl, z.n02, int64_t(names), SAR, sorted_list ? SAR : nullptr,
+                                sorted_list ? NSl : nullptr);
         if (rc) return rc;
         {
             ProfScope ps(PK_RANK_SCATTER, double(z.n02) * 8, st);
@@ -625,25 +1064,48 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     }
     // Rl now holds rank(S_i) by reduced-string index (unique names are ranks).
 
-    // Step 2: nonsample order
-    uint32_t *k0 = (uint32_t *)D.ka, *k1 = (uint32_t *)D.kb;
-    D.rs.epoch++;
-    {
-        ProfScope ps(PK_NONSAMPLE, double(z.n02) * 4 + double(z.n0) * (sizeof(CharT) + 8), st);
-        k_nonsample<CharT><<<grid_for(z.n02, kScanTile), kScanThreads, 0, st>>>(
-            SAR, z.n02, z.n0, s, n, k0, D.va, D.rs.lookback, D.rs.tile_ctr, D.rs.tile_base,
-            D.rs.epoch, D.status);
+    // Step 2: nonsample order, as group indices t (position 3t).
+    const uint32_t *B;
+    if (PS && !D.force_lsd) {
+        uint32_t *T0 = D.t32[0], *P0 = D.t32[1], *Dslot = D.t32[2], *Dt = D.t32[3];
+        uint32_t *Dkey = (uint32_t *)D.t64[1];
+        {
+            ProfScope ps(PK_NONSAMPLE, double(n) * 8 + double(z.n0) * 8, st);
+            LOR_TILE_LAUNCH(D, n, k_par_nonsamples, PS, PNS, n, T0, P0, LB_ARGS(D));
+        }
+        {
+            ProfScope ps(PK_NONSAMPLE, double(z.n0) * 4, st);
+            const int64_t ntiles = cdiv(z.n0, kScanTile);
+            LOR_TILE_LAUNCH(D, z.n0, k_par_ns_dups, T0, P0, z.n0, Rl, Dslot, Dt, Dkey, D.d_count, LB_ARGS(D),
+                            ntiles);
+        }
+        uint32_t nd = 0;
+        rc = read_u32(D, D.d_count, &nd);
+        if (rc) return rc;
+        if (nd > 0) {
+            uint32_t *vord;
+            const int rank_bits = bit_width_u64(uint64_t(z.n02));
+            rc = sort_dups_then_by_first<uint32_t>(D, Dkey, nd, rank_bits, Dslot, P0, bits, &vord);
+            if (rc) return rc;
+            k_par_ns_writeback<<<grid_for(nd, 256), 256, 0, st>>>(vord, nd, Dslot, Dt, T0);
+            LOR_LAUNCH_CHECK();
+        }
+        B = T0;
+    } else {
+        uint32_t *k0 = (uint32_t *)D.t64[1], *k1 = (uint32_t *)D.t64[2];
+        {
+            ProfScope ps(PK_NONSAMPLE, double(z.n02) * 4 + double(z.n0) * (sizeof(CharT) + 8), st);
+            LOR_TILE_LAUNCH(D, z.n02, k_nonsample<CharT>, SAR, z.n02, z.n0, s, n, k0, D.t32[4], LB_ARGS(D));
+        }
+        uint32_t *kr, *vr;
+        rc = radix_sort_pairs<uint32_t>(D.rs, k0, D.t32[4], k1, D.t32[5], z.n0, 0, bits, false, &kr, &vr);
+        if (rc) return rc;
+        B = vr;
     }
-    LOR_LAUNCH_CHECK();
-    D.rs.tile_base += (unsigned long long)cdiv(z.n02, kScanTile);
-    uint32_t *kr, *vr;
-    rc = radix_sort_pairs<uint32_t>(D.rs, k0, D.va, k1, D.vb, z.n0, 0, bits, false, &kr, &vr);
-    if (rc) return rc;
 
     // Step 3: merge (the dummy, when present, is the smallest sample).  The
-    // key buffers are free now: the group records go there, then the
-    // partition.
-    GroupRec<CharT> *rec = (GroupRec<CharT> *)D.ka;
+    // records and the partition go to the two adjacent 64-bit buffers.
+    GroupRec<CharT> *rec = (GroupRec<CharT> *)D.t64[1];
     const size_t rec_bytes = align256(sizeof(GroupRec<CharT>) * size_t(z.n0));
     {
         ProfScope ps(PK_MERGE, double(z.n0) * (3.0 * sizeof(CharT) + 12 + sizeof(GroupRec<CharT>)), st);
@@ -656,10 +1118,10 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     const int64_t dummy = (z.n0 > z.n1) ? 1 : 0;
     a.A = SAR + dummy;
     a.na = z.n02 - dummy;
-    a.B = vr;
+    a.B = B;
     a.nb = z.n0;
     const int64_t ntiles = cdiv(n, kMergeTile);
-    int64_t *split = (int64_t *)((char *)D.ka + rec_bytes);
+    int64_t *split = (int64_t *)((char *)D.t64[1] + rec_bytes);
     {
         ProfScope ps(PK_MERGE, double(n) * (4 + 4 + sizeof(GroupRec<CharT>)), st);
         k_merge_partition<CharT><<<grid_for(ntiles + 1, 128), 128, 0, st>>>(a, ntiles, split);
@@ -700,22 +1162,30 @@ extern "C" int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int
     D.rs.max_tiles = cdiv(D.L.max_m, kSortTile);
     D.rs.status = D.status;
     D.rs.stream = D.s;
-    D.ka = D.ws + D.L.ka;
-    D.kb = D.ws + D.L.kb;
-    D.va = (uint32_t *)(D.ws + D.L.va);
-    D.vb = (uint32_t *)(D.ws + D.L.vb);
+    for (int i = 0; i < 3; ++i) D.t64[i] = (uint64_t *)(D.ws + D.L.t64[i]);
+    for (int i = 0; i < 6; ++i) D.t32[i] = (uint32_t *)(D.ws + D.L.t32[i]);
+    D.tbl = (uint32_t *)(D.ws + D.L.tbl);
+    D.d_count = (uint32_t *)(D.ws + D.L.ctrl + 128);
+    {
+        const char *e = std::getenv("LOR_DC3_STRATEGY");
+        D.force_lsd = e && e[0] == 's';  // "sort": radix-sort every level (test hook)
+    }
     LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.ctrl, 0, 256, D.s));
     LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.lookback, 0, D.L.lookback_bytes, D.s));
     g_trace.clear();
-    return dc3_level<uint8_t>(D, 0, d_text, n, int64_t(sigma - 1), d_sa);
+    g_trace_extra.clear();
+    return dc3_level<uint8_t>(D, 0, d_text, n, int64_t(sigma - 1), d_sa, nullptr, nullptr);
 }
 
-extern "C" int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits, int32_t cap) {
+extern "C" int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits,
+                                  int32_t *h_strategy, int64_t *h_dups, int32_t cap) {
     const int cnt = int(g_trace.size());
     for (int i = 0; i < cnt && i < cap; ++i) {
         if (h_n) h_n[i] = g_trace[i].n;
         if (h_names) h_names[i] = g_trace[i].names;
         if (h_key_bits) h_key_bits[i] = g_trace[i].key_bits;
+        if (h_strategy) h_strategy[i] = g_trace_extra[i].strategy;
+        if (h_dups) h_dups[i] = g_trace_extra[i].dups;
     }
     return cnt;
 }

@@ -1,6 +1,6 @@
 // noalloc.cu -- suffix array for callers that cannot allocate device memory.
 //
-// lor_build_sa needs a caller-provided workspace of about 32 bytes per text
+// lor_build_sa needs a caller-provided workspace of about 60 bytes per text
 // symbol.  Some callers cannot call cudaMalloc (or any allocating routine) at
 // the point where they need a suffix array: a plugin running inside a host
 // application that owns the device memory pool, a callback that must not
@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;

@@ -71,7 +71,7 @@ def load():
         "lor_device_status": ([vp], ctypes.c_int),
         "lor_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lor_launch_count": ([], ctypes.c_uint64),
-        "lor_last_dc3_trace": ([vp, vp, vp, i32], ctypes.c_int),
+        "lor_last_dc3_trace": ([vp, vp, vp, vp, vp, i32], ctypes.c_int),
         "lor_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "lor_profile_reset": ([], ctypes.c_int),
         "lor_profile_kinds": ([], ctypes.c_int),
@@ -323,9 +323,14 @@ def last_dc3_trace():
     n = np.zeros(cap, np.int64)
     names = np.zeros(cap, np.int64)
     bits = np.zeros(cap, np.int32)
-    cnt = load().lor_last_dc3_trace(n.ctypes.data, names.ctypes.data, bits.ctypes.data, cap)
+    strat = np.zeros(cap, np.int32)
+    dups = np.zeros(cap, np.int64)
+    cnt = load().lor_last_dc3_trace(n.ctypes.data, names.ctypes.data, bits.ctypes.data,
+                                    strat.ctypes.data, dups.ctypes.data, cap)
     cnt = min(cnt, cap)
-    return [dict(n=int(n[i]), names=int(names[i]), key_bits=int(bits[i])) for i in range(cnt)]
+    kinds = ("sort", "dense", "parent")
+    return [dict(n=int(n[i]), names=int(names[i]), key_bits=int(bits[i]),
+                 strategy=kinds[int(strat[i])], dups=int(dups[i])) for i in range(cnt)]
 
 
 def profile_enable(on=True):

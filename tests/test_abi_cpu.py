@@ -53,8 +53,8 @@ def test_workspace_queries_are_host_only(lib):
         w = L.lor_build_sa_workspace_size(n, 7)
         assert w >= prev and w % 256 == 0
         prev = w
-    # ~40 bytes per base at scale (sort buffers + per-level arrays)
-    assert L.lor_build_sa_workspace_size(10**8, 7) < 48 * 10**8
+    # under 64 bytes per symbol at scale (sort buffers + per-level arrays)
+    assert L.lor_build_sa_workspace_size(10**8, 7) < 64 * 10**8
     assert L.lor_longest_overlap_workspace_size(1000) > 0
     assert L.lor_rmq_row_stride(1) == 64 and L.lor_rmq_row_stride(64) == 64
     assert L.lor_rmq_row_stride(65) == 128

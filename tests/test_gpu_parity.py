@@ -130,7 +130,10 @@ def test_encode_bad_symbol_reports_status(L):
 
 # ------------------------------------------------------------------ fuzz
 
-def test_fuzz_small_full_path(L, O):
+@pytest.mark.parametrize("strategy", ["auto", "sort"])
+def test_fuzz_small_full_path(L, O, strategy, monkeypatch):
+    if strategy == "sort":
+        monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
     for seed in range(60):
         nseq = [2, 2, 3, 5][seed % 4]
         alpha = [b"ACGT", b"AC", b"A", b"ACGT"][seed % 4 if seed % 7 else 2]
@@ -163,8 +166,11 @@ SIZES = [1, 2, 3, 4, 5, 6, 7, 31, 32, 33, 1023, 1024, 1025, 2047, 2048, 2049, 40
          6143, 6144, 8191, 8193, 12287, 65537, 131071, 300001]
 
 
+@pytest.mark.parametrize("strategy", ["auto", "sort"])
 @pytest.mark.parametrize("alpha", [b"ACGT", b"AC", b"A"])
-def test_sizes_span_tiles(L, O, alpha):
+def test_sizes_span_tiles(L, O, alpha, strategy, monkeypatch):
+    if strategy == "sort":
+        monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
     rng = np.random.default_rng(len(alpha))
     a = np.frombuffer(alpha, np.uint8)
     for total in SIZES:
@@ -177,9 +183,12 @@ def test_sizes_span_tiles(L, O, alpha):
         assert_full_parity(O, g, e, table=total < 5000)
 
 
+@pytest.mark.parametrize("strategy", ["auto", "sort"])
 @pytest.mark.parametrize("k0", ["3", "4", "7", "10", "21"])
-def test_level0_prefix_lengths(L, O, k0, monkeypatch):
+def test_level0_prefix_lengths(L, O, k0, strategy, monkeypatch):
     monkeypatch.setenv("LOR_DC3_K0", k0)
+    if strategy == "sort":
+        monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
     seqs, _ = gen.pair_noncoding(n_each=150_000, seed=31, shared_len=4000, core=900)
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -197,8 +206,10 @@ def test_deep_recursion_single_symbol(L, O):
 
 
 def test_wide_triples_two_stage_sort(L, O, monkeypatch):
-    # level-1 names need > 21 bits, so level-2 triples exceed 64 bits
+    # radix sorts at every level: level-2 names need > 21 bits, so level-3
+    # triples exceed 64 bits
     monkeypatch.setenv("LOR_DC3_K0", "3")
+    monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
     seqs, _ = gen.pair_uniform(n_each=4_500_000, plant_len=700, seed=41)
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -248,7 +259,8 @@ def test_noncoding_workload_2x16M(L, O):
     assert_full_parity(O, g, e, table=False)
     np.testing.assert_array_equal(g["answers"], O.lcp_pairs(e["text"], p, q))
     assert g["overlap"]["length"] >= info["core"]
-    assert any(t["key_bits"] > 64 for t in L.last_dc3_trace())
+    used = {t["strategy"] for t in L.last_dc3_trace()}
+    assert used == {"dense", "sort", "parent"}, L.last_dc3_trace()
 
 
 def test_large_workload_2x128M(L, O):
