@@ -267,6 +267,21 @@ __global__ void k_rank_scatter(const int32_t *__restrict__ SAR, int64_t m, int32
     rankR[r] = int32_t(j + 1);
 }
 
+// rankR[key[i]] = val[i] + 1 after the pairs were bucketed by the top bits of
+// the key: consecutive blocks write into one small window of rankR, so the
+// writes merge in L2 instead of costing a DRAM sector each.
+__global__ void k_scatter_bucketed(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+                                   int64_t m, int32_t *__restrict__ rankR, int *status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t r = key[i];
+    if (r >= uint64_t(m)) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        return;
+    }
+    rankR[r] = int32_t(val[i] + 1);
+}
+
 // Step 2 gather: nonsample positions 3r for every B1 sample r in rank order,
 // keyed by their first symbol (order-preserving compaction by look-back).
 // The value emitted is the group index r (the nonsample position is 3r).
@@ -597,29 +612,45 @@ __device__ __forceinline__ int64_t sym(const CharT *s, int64_t n, int64_t q) {
 // is 1 + the number of distinct keys below it, read from a table of present
 // keys; no sort is needed unless the names come out unique.
 
+// Small tables (level 0) are marked in shared memory first: thousands of
+// blocks storing to the same few table lines would serialise in L2.
+constexpr int kDenseLocal = 4096;
+
 template <typename CharT, bool kValidate>
-__global__ void k_dense_mark(const CharT *__restrict__ s, int64_t n, int64_t n0, int64_t n02,
-                             int kchars, int bits, int64_t maxc, uint32_t *__restrict__ table,
-                             int *status) {
-    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (j >= n02) return;
-    const int64_t p = sample_pos(j, n0);
-    uint32_t key = 0;
+__global__ void __launch_bounds__(256) k_dense_mark(const CharT *__restrict__ s, int64_t n, int64_t n0,
+                                                    int64_t n02, int kchars, int bits, int64_t maxc,
+                                                    int64_t T, uint32_t *__restrict__ table, int *status) {
+    __shared__ uint8_t seen[kDenseLocal];
+    const bool local = T <= kDenseLocal;
+    if (local)
+        for (int i = threadIdx.x; i < T; i += blockDim.x) seen[i] = 0;
+    __syncthreads();
     bool bad = false;
-    for (int t = 0; t < kchars; ++t) {
-        int64_t c = sym(s, n, p + t);
-        if (p + t < n && (c < 1 || c > maxc)) {  // keeps the key inside the table
-            bad = true;
-            c = c < 1 ? 1 : maxc;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n02; j += stride) {
+        const int64_t p = sample_pos(j, n0);
+        uint32_t key = 0;
+        for (int t = 0; t < kchars; ++t) {
+            int64_t c = sym(s, n, p + t);
+            if (p + t < n && (c < 1 || c > maxc)) {  // keeps the key inside the table
+                bad = true;
+                c = c < 1 ? 1 : maxc;
+            }
+            key = (key << bits) | uint32_t(c);
         }
-        key = (key << bits) | uint32_t(c);
+        if (local) seen[key] = 1;
+        else if (table[key] == 0u) table[key] = 1u;
     }
-    if (kValidate && j == 0) {
+    if (kValidate && blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t c = int64_t(s[0]);
         if (c < 1 || c > maxc) bad = true;
     }
     if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
-    table[key] = 1u;
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < T; i += blockDim.x)
+            if (seen[i]) table[i] = 1u;
+    }
 }
 
 // In place: table[k] = (present ? 1 + number of present keys below k : 0).
@@ -919,12 +950,13 @@ int sample_dense_names(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, 
     LOR_CUDA_TRY(cudaMemsetAsync(D.tbl, 0, sizeof(uint32_t) * size_t(T), st));
     {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (kchars * sizeof(CharT) / 3.0 + 4), st);
+        const unsigned grid = unsigned(min64(cdiv(z.n02, 256), 152 * 8));
         if (lvl == 0)
-            k_dense_mark<CharT, true><<<grid_for(z.n02, 256), 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars,
-                                                                            bits, maxc, D.tbl, D.status);
+            k_dense_mark<CharT, true><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, bits, maxc, T,
+                                                             D.tbl, D.status);
         else
-            k_dense_mark<CharT, false><<<grid_for(z.n02, 256), 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars,
-                                                                             bits, maxc, D.tbl, D.status);
+            k_dense_mark<CharT, false><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, bits, maxc, T,
+                                                              D.tbl, D.status);
     }
     LOR_LAUNCH_CHECK();
     {
@@ -1007,6 +1039,30 @@ int sample_from_parent(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits,
     return LOR_OK;
 }
 
+// rankR[SAR[j]] = j + 1.  Large inputs: one radix pass buckets the pairs by
+// the top 8 bits of SAR[j], then a streaming pass writes each bucket into its
+// window; small inputs scatter directly.
+int rank_scatter(Dc3Run &D, const int32_t *SAR, int64_t m, int32_t *Rl) {
+    cudaStream_t st = D.s;
+    const int top = bit_width_u64(uint64_t(m > 1 ? m - 1 : 1));
+    if (m < (int64_t(1) << 22) || D.force_lsd) {
+        ProfScope ps(PK_RANK_SCATTER, double(m) * 8, st);
+        k_rank_scatter<<<grid_for(m, 256), 256, 0, st>>>(SAR, m, Rl, D.status);
+        LOR_LAUNCH_CHECK();
+        return LOR_OK;
+    }
+    uint32_t *kr, *vr;
+    int rc = radix_sort_pairs<uint32_t>(D.rs, (uint32_t *)const_cast<int32_t *>(SAR), D.t32[0],
+                                        (uint32_t *)D.t64[0], D.t32[1], m, top - 8, top, true, &kr, &vr);
+    if (rc) return rc;
+    {
+        ProfScope ps(PK_RANK_SCATTER, double(m) * 12, st);
+        k_scatter_bucketed<<<grid_for(m, 256), 256, 0, st>>>(kr, vr, m, Rl, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
 struct TraceExtra {
     int strategy;  // 0 sort, 1 dense, 2 parent order
     int64_t dups;
@@ -1056,11 +1112,8 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
         rc = dc3_level<int32_t>(D, lvl + 1, Rl, z.n02, int64_t(names), SAR, sorted_list ? SAR : nullptr,
                                 sorted_list ? NSl : nullptr);
         if (rc) return rc;
-        {
-            ProfScope ps(PK_RANK_SCATTER, double(z.n02) * 8, st);
-            k_rank_scatter<<<grid_for(z.n02, 256), 256, 0, st>>>(SAR, z.n02, Rl, D.status);
-        }
-        LOR_LAUNCH_CHECK();
+        rc = rank_scatter(D, SAR, z.n02, Rl);
+        if (rc) return rc;
     }
     // Rl now holds rank(S_i) by reduced-string index (unique names are ranks).
 
