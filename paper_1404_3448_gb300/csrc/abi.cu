@@ -195,7 +195,7 @@ extern "C" int lor_radix_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t 
     rs.offsets = (uint32_t *)(ws + L.offsets);
     rs.lookback = (uint64_t *)(ws + L.lookback);
     rs.tile_ctr = (unsigned long long *)(ws + L.ctrl);
-    rs.max_tiles = cdiv(m, kSortTile);
+    rs.max_tiles = cdiv(m, kMinSortTile);
     rs.status = status;
     rs.stream = s;
     LOR_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, 256, s));

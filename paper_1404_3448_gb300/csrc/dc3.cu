@@ -1212,7 +1212,7 @@ extern "C" int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int
     D.rs.offsets = (uint32_t *)(D.ws + D.L.offsets);
     D.rs.lookback = (uint64_t *)(D.ws + D.L.lookback);
     D.rs.tile_ctr = (unsigned long long *)(D.ws + D.L.ctrl + 64);
-    D.rs.max_tiles = cdiv(D.L.max_m, kSortTile);
+    D.rs.max_tiles = cdiv(D.L.max_m, kMinSortTile);
     D.rs.status = D.status;
     D.rs.stream = D.s;
     for (int i = 0; i < 3; ++i) D.t64[i] = (uint64_t *)(D.ws + D.L.t64[i]);

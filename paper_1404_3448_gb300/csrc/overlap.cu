@@ -269,7 +269,7 @@ extern "C" int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, in
     rs.offsets = (uint32_t *)(ws + L.offsets);
     rs.lookback = (uint64_t *)(ws + L.lookback);
     rs.tile_ctr = (unsigned long long *)(ws + L.ctrl + 64);
-    rs.max_tiles = cdiv(n, kSortTile);
+    rs.max_tiles = cdiv(n, kMinSortTile);
     rs.status = status;
     rs.stream = s;
     int32_t *run_id = (int32_t *)(ws + L.run_id);

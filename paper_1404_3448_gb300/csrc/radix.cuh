@@ -18,9 +18,15 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 256;
 constexpr int kSortThreads = 256;  // == kRadix: one thread per digit in the look-back
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
-constexpr int kMaxPasses = 8;                         // 64-bit keys
+constexpr int kMaxPasses = 8;  // 64-bit keys
+
+// Keys per thread: sized so that three 256-thread blocks fit an SM (at most
+// 85 registers per thread, under 76 KB of shared memory per block).
+template <typename KeyT>
+__host__ __device__ constexpr int sort_items() { return sizeof(KeyT) == 8 ? 12 : 16; }
+template <typename KeyT>
+__host__ __device__ constexpr int sort_tile() { return kSortThreads * sort_items<KeyT>(); }
+constexpr int kMinSortTile = kSortThreads * 12;
 
 template <typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask = 0xFFu) {
@@ -32,7 +38,9 @@ __host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int end_bit) 
     return (1u << w) - 1u;
 }
 
-// Digit histograms of every pass in one read of the keys.
+// Digit histograms of every pass in one read of the keys.  Counts go to
+// shared-memory atomics; when all 32 lanes of a warp hold the same digit (low
+// entropy passes) one lane adds 32 instead.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_radix_hist(const KeyT *__restrict__ keys, int64_t m,
                                                     int begin_bit, int end_bit, int npasses,
@@ -40,16 +48,32 @@ __global__ void __launch_bounds__(256) k_radix_hist(const KeyT *__restrict__ key
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     for (int i = threadIdx.x; i < npasses * kRadix; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < m; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < m;
-        const KeyT k = valid ? keys[i] : KeyT(0);
+    const int lane = threadIdx.x & 31;
+    constexpr int kPer = 4;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x * kPer;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x * kPer; base < m; base += stride) {
+        KeyT k[kPer];
+        bool valid[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int64_t i = base + u * int64_t(blockDim.x) + threadIdx.x;
+            valid[u] = i < m;
+            k[u] = valid[u] ? keys[i] : KeyT(0);
+        }
         for (int p = 0; p < npasses; ++p) {
             const int sft = begin_bit + p * kRadixBits;
-            const uint32_t d = valid ? digit_of(k, sft, digit_mask(sft, end_bit)) : 0x100u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&sh[p * kRadix + d], __popc(peers));
+            const uint32_t dm = digit_mask(sft, end_bit);
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const uint32_t d = digit_of(k[u], sft, dm);
+                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+                const bool all_valid = __all_sync(0xffffffffu, valid[u]);
+                if (all_valid && __all_sync(0xffffffffu, d == d0)) {
+                    if (lane == 0) atomicAdd(&sh[p * kRadix + d0], 32u);
+                } else if (valid[u]) {
+                    atomicAdd(&sh[p * kRadix + d], 1u);
+                }
+            }
         }
     }
     __syncthreads();
@@ -69,8 +93,8 @@ static __global__ void __launch_bounds__(256) k_radix_offsets(const uint32_t *__
 
 template <typename KeyT>
 struct OnesweepSmem {
-    KeyT keys[kSortTile];
-    uint32_t vals[kSortTile];
+    KeyT keys[sort_tile<KeyT>()];
+    uint32_t vals[sort_tile<KeyT>()];
     uint32_t warp_hist[kSortWarps][kRadix];
     uint32_t local_start[kRadix];
     long long gbase[kRadix];
@@ -82,12 +106,14 @@ struct OnesweepSmem {
 // order from a running counter, so every predecessor a block waits on is
 // already resident; each wait is still bounded by kSpinLimitNs.
 template <typename KeyT, bool kIotaVals>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
     const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int shift, uint32_t dmask,
     const uint32_t *__restrict__ offsets,
     uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
     uint32_t epoch, int *status) {
+    constexpr int kItems = sort_items<KeyT>();
+    constexpr int kTile = sort_tile<KeyT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem<KeyT> &S = *reinterpret_cast<OnesweepSmem<KeyT> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -95,30 +121,31 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t tile = S.tile;
-    const int64_t base = tile * kSortTile;
-    const int64_t wbase = base + int64_t(warp) * (kSortItems * 32);
+    const int64_t base = tile * kTile;
+    const int64_t wbase = base + int64_t(warp) * (kItems * 32);
 
-    KeyT k[kSortItems];
-    uint32_t v[kSortItems], d[kSortItems], r[kSortItems];
+    KeyT k[kItems];
+    uint32_t v[kItems], r[kItems];
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
+    for (int i = 0; i < kItems; ++i) {
         const int64_t idx = wbase + i * 32 + lane;
         const bool valid = idx < m;
         k[i] = valid ? kin[idx] : KeyT(0);
-        if (kIotaVals) v[i] = uint32_t(idx);
-        else v[i] = valid ? vin[idx] : 0u;
-        d[i] = valid ? digit_of(k[i], shift, dmask) : 0x100u;
+        if (!kIotaVals) v[i] = valid ? vin[idx] : 0u;
     }
-    // Stable rank inside the warp: items in order, lanes in order.
+    // Stable rank inside the warp: items in order, lanes in order.  Slots
+    // past the end of the input use digit 256 and are never counted.
     uint32_t *wh = S.warp_hist[warp];
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t peers = __match_any_sync(0xffffffffu, d[i]);
+    for (int i = 0; i < kItems; ++i) {
+        const bool valid = wbase + i * 32 + lane < m;
+        const uint32_t d = valid ? digit_of(k[i], shift, dmask) : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t lt = __popc(peers & lanemask_lt());
-        const uint32_t cnt = d[i] < 256 ? wh[d[i]] : 0u;
+        const uint32_t cnt = valid ? wh[d] : 0u;
         r[i] = cnt + lt;
         __syncwarp();
-        if (d[i] < 256 && lt == 0) wh[d[i]] = cnt + __popc(peers);
+        if (valid && lt == 0) wh[d] = cnt + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -161,15 +188,17 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        if (d[i] < 256) {
-            const uint32_t pos = S.local_start[d[i]] + S.warp_hist[warp][d[i]] + r[i];
+    for (int i = 0; i < kItems; ++i) {
+        const int64_t idx = wbase + i * 32 + lane;
+        if (idx < m) {
+            const uint32_t d = digit_of(k[i], shift, dmask);
+            const uint32_t pos = S.local_start[d] + S.warp_hist[warp][d] + r[i];
             S.keys[pos] = k[i];
-            S.vals[pos] = v[i];
+            S.vals[pos] = kIotaVals ? uint32_t(idx) : v[i];
         }
     }
     __syncthreads();
-    const int cnt_tile = int(min(int64_t(kSortTile), m - base));
+    const int cnt_tile = int(min64(int64_t(kTile), m - base));
     for (int i = tid; i < cnt_tile; i += kSortThreads) {
         const KeyT kk = S.keys[i];
         const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
@@ -197,7 +226,7 @@ struct RadixScratch {
 };
 
 inline size_t radix_lookback_bytes(int64_t max_m) {
-    return size_t(cdiv(max_m > 0 ? max_m : 1, kSortTile)) * kRadix * sizeof(uint64_t);
+    return size_t(cdiv(max_m > 0 ? max_m : 1, kMinSortTile)) * kRadix * sizeof(uint64_t);
 }
 
 // Sort m pairs by bits [begin_bit, end_bit) of the keys.  (k0, v0) hold the
@@ -215,13 +244,13 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
     if (begin_bit < 0 || end_bit < begin_bit || end_bit > int(8 * sizeof(KeyT)) ||
         npasses > kMaxPasses)
         return LOR_ERR_INVALID_ARG;
-    if (cdiv(m, kSortTile) > rs.max_tiles) return LOR_ERR_WORKSPACE;
+    if (cdiv(m, sort_tile<KeyT>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
     uint32_t hh[kMaxPasses * kRadix];
     if (npasses > 0) {
         LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * npasses * kRadix, s));
         {
             ProfScope ps(PK_RADIX_HIST, double(m) * sizeof(KeyT), s);
-            const int grid = int(min64(cdiv(m, 256), 152 * 8));
+            const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
             k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, begin_bit, end_bit, npasses, rs.hist);
         }
         LOR_LAUNCH_CHECK();
@@ -239,7 +268,7 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
     KeyT *ki = k0, *ko = k1;
     uint32_t *vi = v0, *vo = v1;
     bool vals_ready = !iota_vals;
-    const int64_t ntiles = cdiv(m, kSortTile);
+    const int64_t ntiles = cdiv(m, sort_tile<KeyT>());
     for (int p = 0; p < npasses; ++p) {
         bool trivial = false;
         for (int dgt = 0; dgt < kRadix; ++dgt)
