@@ -427,8 +427,10 @@ __device__ __forceinline__ bool a_less_b(const ARec &x, const BRec &y) {
     return x.r < y.r2;
 }
 
-constexpr int kMergeThreads = 128;
-constexpr int kMergeItems = 8;
+// 512 threads x 2 outputs: the record gathers are latency bound, and wide
+// blocks with few items each keep the most of them in flight per SM.
+constexpr int kMergeThreads = 512;
+constexpr int kMergeItems = 2;
 constexpr int kMergeTile = kMergeThreads * kMergeItems;
 
 // Number of sample suffixes among the first d merged suffixes.
