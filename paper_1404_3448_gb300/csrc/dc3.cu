@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ 
         if (j < m) {
             name += (flags >> i) & 1u;
             const uint32_t v = vals[j];
-            R[v] = int32_t(name);
+            if (R) R[v] = int32_t(name);
             SAR[j] = int32_t(v);
             NS[j] = int32_t(name);
             if (j == m - 1) *n_names = name;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kScanThreads) k_name_gather(
         if (j < m) {
             name += (flags >> i) & 1u;
             const uint32_t v = vals[j];
-            R[v] = int32_t(name);
+            if (R) R[v] = int32_t(name);
             SAR[j] = int32_t(v);
             NS[j] = int32_t(name);
             if (j == m - 1) *n_names = name;
@@ -265,21 +265,6 @@ __global__ void k_rank_scatter(const int32_t *__restrict__ SAR, int64_t m, int32
         return;
     }
     rankR[r] = int32_t(j + 1);
-}
-
-// rankR[key[i]] = val[i] + 1 after the pairs were bucketed by the top bits of
-// the key: consecutive blocks write into one small window of rankR, so the
-// writes merge in L2 instead of costing a DRAM sector each.
-__global__ void k_scatter_bucketed(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
-                                   int64_t m, int32_t *__restrict__ rankR, int *status) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const uint32_t r = key[i];
-    if (r >= uint64_t(m)) {
-        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
-        return;
-    }
-    rankR[r] = int32_t(val[i] + 1);
 }
 
 // Step 2 gather: nonsample positions 3r for every B1 sample r in rank order,
@@ -783,7 +768,7 @@ __global__ void __launch_bounds__(kScanThreads) k_par_name(
         m, [&](int64_t o) { return o == 0 || PRI[o] != PRI[o - 1] || SEC[o] != SEC[o - 1]; },
         [&](int64_t o, uint32_t name) {
             const uint32_t j = SL[o];
-            R[j] = int32_t(name);
+            if (R) R[j] = int32_t(name);
             SAR[o] = int32_t(j);
             NS[o] = int32_t(name);
         },
@@ -881,6 +866,30 @@ int read_u32(Dc3Run &D, const uint32_t *d, uint32_t *h) {
 
 #define LB_ARGS(D) (D).rs.lookback, (D).rs.tile_ctr, (D).rs.tile_base, (D).rs.epoch, (D).status
 
+// Inputs of at least this many entries scatter through bucketing.
+constexpr int64_t kBucketMin = int64_t(1) << 22;
+
+// rankR[SAR[j]] = j + 1 (the inverse of the level below's suffix array).
+int rank_scatter(Dc3Run &D, const int32_t *SAR, int64_t m, int32_t *Rl) {
+    if (m < kBucketMin || D.force_lsd) {
+        ProfScope ps(PK_RANK_SCATTER, double(m) * 8, D.s);
+        k_rank_scatter<<<grid_for(m, 256), 256, 0, D.s>>>(SAR, m, Rl, D.status);
+        LOR_LAUNCH_CHECK();
+        return LOR_OK;
+    }
+    return bucketed_scatter(D.rs, (const uint32_t *)SAR, nullptr, m, m, (uint32_t *)D.t64[0], D.t32[0],
+                            D.t32[1], Rl, 1);
+}
+
+inline bool bucket_names(const Dc3Run &D, const LevelSizes &z) { return z.n02 >= kBucketMin && !D.force_lsd; }
+
+// R[SAR[j]] = NS[j]: the names in reduced-string order, for naming kernels
+// that left R unwritten (large levels).
+int names_scatter(Dc3Run &D, const int32_t *SAR, const int32_t *NSl, int64_t m, int32_t *Rl) {
+    return bucketed_scatter(D.rs, (const uint32_t *)SAR, (const uint32_t *)NSl, m, m, D.t32[2], D.t32[3],
+                            D.t32[4], Rl, 0);
+}
+
 // ---- Step 1, strategy "sort": LSD radix sort of the keys, then naming.
 template <typename CharT, typename KeyT>
 int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars,
@@ -903,9 +912,10 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
     if (rc) return rc;
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 16), st);
-        LOR_TILE_LAUNCH(D, z.n02, k_name<KeyT>, kr, vr, z.n02, Rl, SAR, NSl, D.d_names, LB_ARGS(D));
+        LOR_TILE_LAUNCH(D, z.n02, k_name<KeyT>, kr, vr, z.n02, bucket_names(D, z) ? nullptr : Rl, SAR, NSl,
+                        D.d_names, LB_ARGS(D));
     }
-    return LOR_OK;
+    return bucket_names(D, z) ? names_scatter(D, SAR, NSl, z.n02, Rl) : LOR_OK;
 }
 
 // Triples too wide for 64 bits: stable sort by (t_i+1, t_i+2), then by t_i.
@@ -937,10 +947,10 @@ int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, in
     if (rc) return rc;
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (4 + 12 + 12 * 2), st);
-        LOR_TILE_LAUNCH(D, z.n02, k_name_gather<CharT>, vr2, z.n02, s, z.n, z.n0, Rl, SAR, NSl,
-                        D.d_names, LB_ARGS(D));
+        LOR_TILE_LAUNCH(D, z.n02, k_name_gather<CharT>, vr2, z.n02, s, z.n, z.n0,
+                        bucket_names(D, z) ? nullptr : Rl, SAR, NSl, D.d_names, LB_ARGS(D));
     }
-    return LOR_OK;
+    return bucket_names(D, z) ? names_scatter(D, SAR, NSl, z.n02, Rl) : LOR_OK;
 }
 
 // ---- Step 1, strategy "dense": names from a table of present keys.
@@ -1036,33 +1046,10 @@ int sample_from_parent(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits,
     }
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (4 + 4 + 8 + 4 + 4 + 4), st);
-        LOR_TILE_LAUNCH(D, z.n02, k_par_name, SL, PRI, SEC, z.n02, Rl, SAR, NSl, D.d_names, LB_ARGS(D));
+        LOR_TILE_LAUNCH(D, z.n02, k_par_name, SL, PRI, SEC, z.n02, bucket_names(D, z) ? nullptr : Rl, SAR,
+                        NSl, D.d_names, LB_ARGS(D));
     }
-    return LOR_OK;
-}
-
-// rankR[SAR[j]] = j + 1.  Large inputs: one radix pass buckets the pairs by
-// the top 8 bits of SAR[j], then a streaming pass writes each bucket into its
-// window; small inputs scatter directly.
-int rank_scatter(Dc3Run &D, const int32_t *SAR, int64_t m, int32_t *Rl) {
-    cudaStream_t st = D.s;
-    const int top = bit_width_u64(uint64_t(m > 1 ? m - 1 : 1));
-    if (m < (int64_t(1) << 22) || D.force_lsd) {
-        ProfScope ps(PK_RANK_SCATTER, double(m) * 8, st);
-        k_rank_scatter<<<grid_for(m, 256), 256, 0, st>>>(SAR, m, Rl, D.status);
-        LOR_LAUNCH_CHECK();
-        return LOR_OK;
-    }
-    uint32_t *kr, *vr;
-    int rc = radix_sort_pairs<uint32_t>(D.rs, (uint32_t *)const_cast<int32_t *>(SAR), D.t32[0],
-                                        (uint32_t *)D.t64[0], D.t32[1], m, top - 8, top, true, &kr, &vr);
-    if (rc) return rc;
-    {
-        ProfScope ps(PK_RANK_SCATTER, double(m) * 12, st);
-        k_scatter_bucketed<<<grid_for(m, 256), 256, 0, st>>>(kr, vr, m, Rl, D.status);
-    }
-    LOR_LAUNCH_CHECK();
-    return LOR_OK;
+    return bucket_names(D, z) ? names_scatter(D, SAR, NSl, z.n02, Rl) : LOR_OK;
 }
 
 struct TraceExtra {

@@ -302,4 +302,46 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
     return LOR_OK;
 }
 
+// ---- bucketed scatter: dst[key[i]] = val[i] + add for distinct keys in
+// [0, bound).  A random 4-byte store costs a DRAM sector; here one radix pass
+// on the top 8 bits of the keys groups the pairs by destination window
+// (bound / 256 entries), and a streaming pass then writes them: consecutive
+// blocks write into the same small window, so the stores combine in L2.
+
+static __global__ void k_scatter_pairs(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+                                       int64_t m, int32_t *__restrict__ dst, int32_t add, int64_t bound,
+                                       int *status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t r = key[i];
+    if (int64_t(r) >= bound) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        return;
+    }
+    dst[r] = int32_t(val[i]) + add;
+}
+
+// keys/vals: inputs (vals == nullptr means 0..m-1).  kbuf, vbuf0, vbuf1:
+// caller scratch of m entries each (vbuf0 receives the input values when they
+// are generated).  The caller accounts the scatter kernel's launch.
+inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32_t *vals, int64_t m,
+                            int64_t bound, uint32_t *kbuf, uint32_t *vbuf0, uint32_t *vbuf1,
+                            int32_t *dst, int32_t add) {
+    if (m <= 0) return LOR_OK;
+    const int top = bit_width_u64(uint64_t(bound > 1 ? bound - 1 : 1));
+    const int lo = top > kRadixBits ? top - kRadixBits : 0;
+    uint32_t *kr, *vr;
+    const bool iota = vals == nullptr;
+    const int rc = radix_sort_pairs<uint32_t>(rs, const_cast<uint32_t *>(keys),
+                                              iota ? vbuf0 : const_cast<uint32_t *>(vals), kbuf,
+                                              iota ? vbuf1 : vbuf0, m, lo, top, iota, &kr, &vr);
+    if (rc) return rc;
+    {
+        ProfScope ps(PK_RANK_SCATTER, double(m) * 12, rs.stream);
+        k_scatter_pairs<<<unsigned(cdiv(m, 256)), 256, 0, rs.stream>>>(kr, vr, m, dst, add, bound, rs.status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
 }  // namespace lor
