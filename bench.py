@@ -49,6 +49,33 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(vals, device=None):
+    """Element-wise maximum of a list of floats over all ranks (identity on
+    one process).  Used for the timed region: the job is as slow as its
+    slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job units per second: every rank processed units_per_rank in at
+    most ms milliseconds."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
+def percentile(vals, q):
+    v = sorted(vals)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[k]
+
+
 def make_inputs(name):
     import lor_inputs as gen
     kw, nq, desc = WORKLOADS[name]
@@ -190,7 +217,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    n_each = 1 << 21
+    n_each = args.ref_bases // 2
     for i in range(args.warmup):
         cpu_sample_run(n_each, 1000 + i, 20000)
     total_t, total_b = 0.0, 0
@@ -264,16 +291,16 @@ def run_lor(args):
     barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clocks:
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for i in range(args.steps):
             step()
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize(dev)
     barrier()
     launches = C.lor_launch_count() - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    ms = evs[0].elapsed_time(evs[-1]) / args.steps
     prof = lor.profile_read()
     lor.profile_enable(False)
     lor.check_device(where="timed")
@@ -300,17 +327,12 @@ def run_lor(args):
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
-    ms_all = ms
-    e2e_all = e2e_ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all, e2e_all = float(t[0]), float(t[1])
+    ms_all, e2e_all, p50, p99 = max_over_ranks(
+        [ms, e2e_ms, percentile(step_ms, 50), percentile(step_ms, 99)], device=dev)
 
     if rank == 0:
-        value = world * n_bases / (ms_all / 1000.0)
-        e2e_value = world * n_bases / (e2e_all / 1000.0)
+        value = job_throughput(n_bases, world, ms_all)
+        e2e_value = job_throughput(n_bases, world, e2e_all)
         h2d = host_ascii.numel() + 4 * (host_p.numel() + host_q.numel())
         d2h = 32 + 4 * host_ans.numel() + 4 * npos
         stage_ms = {k: v["ms"] / args.steps for k, v in prof.items()}
@@ -341,6 +363,7 @@ def run_lor(args):
             "path_model_bytes_per_step": path_bytes,
             "path_model_gbs": path_bytes / (ms / 1000.0) / 1e9,
             "stage_ms": stage_ms,
+            "step_latency_ms": {"p50": p50, "p99": p99, "mean": ms_all, "steps": args.steps},
             "overlap": {"length": int(host_out[0]), "n_pos": int(host_out[6])},
             "dc3_levels": len(lor.last_dc3_trace()),
             "clocks": clocks.summary(),
@@ -366,6 +389,8 @@ def main():
     ap.add_argument("--impl", default="lor", choices=["lor", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-bases", type=int, default=1 << 22,
+                    help="bases per step of the reference (oracle) arm")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
