@@ -240,6 +240,95 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- batched
+
+def batch_vs_plain(npairs, steps, warmup, dev, seed=140434484):
+    """The same npairs sequence pairs (per-sequence lengths log-uniform in
+    [1k, 1M], noncoding-like) through lor_batch_overlap, and one pair per
+    call through encode + SA + LCP + overlap.  Returns a dict of throughputs
+    and per-pair latencies of the plain path."""
+    import torch
+    import lor_inputs as gen
+    import paper_1404_3448_gb300 as lor
+    from paper_1404_3448_gb300 import lor as C
+
+    pairs = gen.pair_batch(npairs=npairs, seed=seed)
+    flat = [x for pr in pairs for x in pr]
+    lens = np.array([len(x) for x in flat], dtype=np.int64)
+    n_bases = int(lens.sum())
+    ascii_dev = torch.from_numpy(np.concatenate(flat)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    b = lor.lor.Batch(lens, device=dev, pos_cap=1 << 24)
+    for _ in range(warmup):
+        b.run(ascii_dev)
+    torch.cuda.synchronize(dev)
+    lor.check_device(where="batch warmup")
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for i in range(steps):
+        b.run(ascii_dev)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    batch_ms = evs[0].elapsed_time(evs[-1]) / steps
+    batch_steps = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+
+    # plain: one pair per call, buffers sized for the largest pair
+    nmax = int(max(lens[0::2] + lens[1::2])) + 2
+    text = torch.empty(nmax, dtype=torch.uint8, device=dev)
+    starts = torch.empty(3, dtype=torch.int32, device=dev)
+    sa = torch.empty(nmax, dtype=torch.int32, device=dev)
+    isa = torch.empty(nmax, dtype=torch.int32, device=dev)
+    lcp = torch.empty(nmax, dtype=torch.int32, device=dev)
+    out = torch.empty(8, dtype=torch.int32, device=dev)
+    pos = torch.empty(1 << 20, dtype=torch.int32, device=dev)
+    ws = lor.workspace(max(C.lor_build_sa_workspace_size(nmax, 7), C.lor_lcp_workspace_size(nmax),
+                           C.lor_longest_overlap_workspace_size(nmax)), dev)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    s = int(stream.cuda_stream)
+
+    def plain_pair(p):
+        l2 = lens[2 * p:2 * p + 2].copy()
+        n = int(l2.sum()) + 2
+        a = ascii_dev[int(offs[2 * p]):int(offs[2 * p + 2])]
+        C._check(C.lor_encode_concat(a.data_ptr() if a.numel() else None, l2.ctypes.data, 2,
+                                     text.data_ptr(), starts.data_ptr(), s), "encode")
+        C._check(C.lor_build_sa(text.data_ptr(), n, 7, sa.data_ptr(), ws.data_ptr(), ws.numel(), s),
+                 "build_sa")
+        C._check(C.lor_lcp(text.data_ptr(), sa.data_ptr(), n, isa.data_ptr(), lcp.data_ptr(),
+                           ws.data_ptr(), ws.numel(), s), "lcp")
+        C._check(C.lor_longest_overlap(sa.data_ptr(), lcp.data_ptr(), n, starts.data_ptr(), 2,
+                                       out.data_ptr(), pos.data_ptr(), pos.numel(), ws.data_ptr(),
+                                       ws.numel(), s), "overlap")
+
+    for p in range(min(npairs, 16)):
+        plain_pair(p)
+    torch.cuda.synchronize(dev)
+    pe = [torch.cuda.Event(enable_timing=True) for _ in range(npairs + 1)]
+    pe[0].record(stream)
+    for p in range(npairs):
+        plain_pair(p)
+        pe[p + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    lor.check_device(where="plain pairs")
+    plain_ms = pe[0].elapsed_time(pe[-1])
+    per_pair = [pe[i].elapsed_time(pe[i + 1]) for i in range(npairs)]
+    batch_value = n_bases / (batch_ms / 1000.0)
+    plain_value = n_bases / (plain_ms / 1000.0)
+    return {
+        "workload": f"{npairs} noncoding-like pairs, per-sequence lengths log-uniform in [1k, 1M], "
+                    f"one shared plant of 50-5000 bases per pair ({n_bases} bases)",
+        "pairs": npairs, "input_bases": n_bases,
+        "batched": {"value": batch_value, "unit": UNIT, "ms_per_step": batch_ms,
+                    "step_latency_ms": {"p50": percentile(batch_steps, 50),
+                                        "p99": percentile(batch_steps, 99)}, "steps": steps},
+        "plain": {"value": plain_value, "unit": UNIT, "ms_all_pairs": plain_ms,
+                  "pair_latency_ms": {"p50": percentile(per_pair, 50), "p99": percentile(per_pair, 99),
+                                      "max": max(per_pair)}},
+        "batched_over_plain": batch_value / plain_value,
+    }
+
+
 # --------------------------------------------------------------------------- GPU
 
 def run_lor(args):
@@ -374,6 +463,10 @@ def run_lor(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        if args.batch_pairs > 0:
+            del pipe
+            torch.cuda.empty_cache()
+            line["batch_vs_plain"] = batch_vs_plain(args.batch_pairs, 3, 1, dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -389,6 +482,8 @@ def main():
     ap.add_argument("--impl", default="lor", choices=["lor", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=1024,
+                    help="pairs of the batched-vs-plain sub-measurement (0 skips it)")
     ap.add_argument("--ref-bases", type=int, default=1 << 22,
                     help="bases per step of the reference (oracle) arm")
     args = ap.parse_args()

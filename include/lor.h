@@ -162,6 +162,32 @@ int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, int64_t n,
                         lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Longest overlap region of many sequence pairs (Section 3's problem, one
+ * answer per pair; the batching is this library's).
+ *
+ * d_ascii   : device, the 2*npairs sequences' ASCII bytes back to back, pair
+ *             p being sequences 2p and 2p+1.
+ * h_lens    : host, 2*npairs lengths.
+ * d_out     : device lor_overlap[npairs]: for every pair the record that
+ *             lor_longest_overlap returns for that pair alone (sequence ids 0
+ *             and 1, offsets inside the pair's sequences, rank inside the
+ *             pair's own suffix array).
+ * d_pos_off : device int64[npairs + 1]: pair p's positions occupy
+ *             d_pos[d_pos_off[p] .. d_pos_off[p+1]), each an offset inside
+ *             the pair's own text S1#S2$, ascending.
+ * d_pos     : device int32[pos_cap]; positions beyond pos_cap are dropped
+ *             (the offsets still count them).
+ * d_ws      : lor_batch_workspace_size(h_lens, npairs) bytes, 256-byte aligned.
+ * Pairs are processed in groups of up to 125 pairs (250 sequences) and at
+ * most 2^28 symbols; one DC3 suffix array per group is split into per-pair
+ * blocks.  Synchronises `stream` a few times per group.
+ * ------------------------------------------------------------------------- */
+size_t lor_batch_workspace_size(const int64_t *h_lens, int32_t npairs);
+int lor_batch_overlap(const uint8_t *d_ascii, const int64_t *h_lens, int32_t npairs,
+                      lor_overlap *d_out, int64_t *d_pos_off, int32_t *d_pos, int64_t pos_cap,
+                      void *d_ws, size_t ws_bytes, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * a11. Sparse table over the LCP array for range-minimum queries (Section 3:
  * RMQ definition; the LCP of arbitrary suffixes is a range minimum).
  * Layout: level-major, levels = floor(log2 n) + 1 rows of

@@ -236,3 +236,4 @@ int lor_status_lcp(cudaStream_t s, int clear);
 int lor_status_overlap(cudaStream_t s, int clear);
 int lor_status_rmq(cudaStream_t s, int clear);
 int lor_status_abi(cudaStream_t s, int clear);
+int lor_status_batch(cudaStream_t s, int clear);

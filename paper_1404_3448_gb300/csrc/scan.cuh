@@ -1,0 +1,98 @@
+// scan.cuh -- order-preserving tile compaction and naming by single-pass
+// decoupled look-back scans (bounded waits), shared by the DC3 levels and the
+// batched pipeline.
+#pragma once
+
+#include "common.cuh"
+
+namespace lor {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// ---- generic order-preserving tile compaction and naming (look-back scans)
+
+// Every kernel below handles kScanTile consecutive items per block (blocked:
+// kScanItems per thread), claims its tile from the running counter, scans its
+// predicate and walks back over predecessor tiles for the global offset.
+template <typename Pred, typename Emit>
+__device__ __forceinline__ void tile_compact(int64_t m, Pred pred, Emit emit, uint64_t *lb,
+                                             unsigned long long *ctr, unsigned long long tile_base,
+                                             uint32_t epoch, int *status, uint32_t *count,
+                                             int64_t ntiles) {
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m && pred(j)) {
+            flags |= 1u << i;
+            cnt++;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) {
+            s_prefix = p;
+            if (count && tile == ntiles - 1) *count = p + agg;
+        }
+    }
+    __syncthreads();
+    uint32_t o = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if ((flags >> i) & 1u) emit(base + i, o++);
+}
+
+// name(j) = number of j' <= j where NewName(j') holds (NewName(0) must hold).
+template <typename NewName, typename Emit>
+__device__ __forceinline__ void tile_names(int64_t m, NewName is_new, Emit emit, uint32_t *n_names,
+                                           uint64_t *lb, unsigned long long *ctr,
+                                           unsigned long long tile_base, uint32_t epoch, int *status) {
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m && is_new(j)) {
+            flags |= 1u << i;
+            cnt++;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) s_prefix = p;
+    }
+    __syncthreads();
+    uint32_t name = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < m) {
+            name += (flags >> i) & 1u;
+            emit(j, name);
+            if (j == m - 1) *n_names = name;
+        }
+    }
+}
+
+}  // namespace lor

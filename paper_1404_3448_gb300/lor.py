@@ -62,6 +62,8 @@ def load():
         "lor_lcp": ([vp, vp, i64, vp, vp, vp, sz, vp], ctypes.c_int),
         "lor_longest_overlap_workspace_size": ([i64], sz),
         "lor_longest_overlap": ([vp, vp, i64, vp, i32, vp, vp, i64, vp, sz, vp], ctypes.c_int),
+        "lor_batch_workspace_size": ([vp, i32], sz),
+        "lor_batch_overlap": ([vp, vp, i32, vp, vp, vp, i64, vp, sz, vp], ctypes.c_int),
         "lor_rmq_table_elems": ([i64], i64),
         "lor_rmq_row_stride": ([i64], i64),
         "lor_rmq_build": ([vp, i64, vp, i64, vp], ctypes.c_int),
@@ -120,6 +122,15 @@ def lor_longest_overlap(d_sa, d_lcp, n, d_seq_starts, nseq, d_out, d_pos, pos_ca
                         stream):
     return load().lor_longest_overlap(d_sa, d_lcp, n, d_seq_starts, nseq, d_out, d_pos, pos_cap,
                                       d_ws, ws_bytes, stream)
+
+
+def lor_batch_workspace_size(h_lens, npairs):
+    return load().lor_batch_workspace_size(h_lens, npairs)
+
+
+def lor_batch_overlap(d_ascii, h_lens, npairs, d_out, d_pos_off, d_pos, pos_cap, d_ws, ws_bytes, stream):
+    return load().lor_batch_overlap(d_ascii, h_lens, npairs, d_out, d_pos_off, d_pos, pos_cap, d_ws,
+                                    ws_bytes, stream)
 
 
 def lor_rmq_table_elems(n):
@@ -273,6 +284,46 @@ def longest_overlap(sa, lcp_arr, seq_starts, nseq, pos_cap=1 << 16, out=None, po
                              int(pos_cap), ws.data_ptr(), ws.numel(), _stream(stream))
     _check(rc, "lor_longest_overlap")
     return out, pos
+
+
+class Batch:
+    """Buffers for lor_batch_overlap over a fixed list of pair lengths."""
+
+    def __init__(self, lens, device="cuda", pos_cap=1 << 20):
+        self.lens = np.ascontiguousarray(np.asarray(lens, dtype=np.int64))
+        if self.lens.size % 2:
+            raise ValueError("lens must hold two lengths per pair")
+        self.npairs = int(self.lens.size // 2)
+        dev = torch.device(device)
+        self.out = torch.empty((self.npairs, 8), dtype=torch.int32, device=dev)
+        self.pos_off = torch.empty(self.npairs + 1, dtype=torch.int64, device=dev)
+        self.pos_cap = int(pos_cap)
+        self.pos = torch.empty(max(self.pos_cap, 1), dtype=torch.int32, device=dev)
+        need = lor_batch_workspace_size(self.lens.ctypes.data, self.npairs)
+        if need == 0:
+            raise ValueError("bad pair lengths")
+        self.ws = workspace(need, dev)
+
+    def run(self, ascii_dev, stream=None):
+        ptr = _ptr(ascii_dev, torch.uint8, "ascii") if ascii_dev.numel() else None
+        _check(lor_batch_overlap(ptr, self.lens.ctypes.data, self.npairs, self.out.data_ptr(),
+                                 self.pos_off.data_ptr(), self.pos.data_ptr(), self.pos_cap,
+                                 self.ws.data_ptr(), self.ws.numel(), _stream(stream)),
+               "lor_batch_overlap")
+        return self.out, self.pos_off, self.pos
+
+    def results(self):
+        """List of per-pair dicts (like overlap_dict) on the host."""
+        out = self.out.cpu().numpy()
+        off = self.pos_off.cpu().numpy()
+        pos = self.pos.cpu().numpy()
+        res = []
+        for p in range(self.npairs):
+            d = dict(zip(OVERLAP_FIELDS, out[p].tolist()))
+            a, b = int(off[p]), int(off[p + 1])
+            d["positions"] = pos[a:min(b, self.pos_cap)].astype(np.int64)
+            res.append(d)
+        return res
 
 
 def overlap_dict(out: torch.Tensor, pos: torch.Tensor, seq_starts=None) -> dict:

@@ -1,0 +1,95 @@
+"""lor_batch_overlap against the oracle, pair by pair.
+
+Every pair's record and position list must equal what the oracle computes for
+that pair alone (its own text S1#S2$): batching is an implementation detail
+that changes no result.  Batches here span several groups (125 pairs each),
+hold empty sequences, degenerate pairs and uneven lengths.
+"""
+import numpy as np
+import pytest
+
+import lor_inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3448_gb300 as lor
+    lor.load()
+    return lor
+
+
+def run_batch(L, pairs, pos_cap=1 << 22):
+    flat = [s for pr in pairs for s in pr]
+    lens = [len(s) for s in flat]
+    ascii_dev = torch.from_numpy(np.concatenate(flat) if sum(lens) else np.zeros(0, np.uint8)).cuda()
+    b = L.lor.Batch(lens, pos_cap=pos_cap)
+    b.run(ascii_dev)
+    L.check_device(where="batch")
+    return b.results()
+
+
+def expect_pair(O, a, b):
+    text, starts, _ = O.encode_concat([a, b])
+    sa = O.suffix_array(text)
+    lcp = O.lcp_array(text, sa)
+    return O.longest_overlap(text, sa, lcp, starts)
+
+
+def assert_same(got, exp, p):
+    for k in ("length", "rank", "seq_a", "pos_a", "seq_b", "pos_b"):
+        assert got[k] == exp[k], (p, k, got[k], exp[k])
+    assert got["n_pos"] == len(exp["positions"]), p
+    np.testing.assert_array_equal(got["positions"], exp["positions"], err_msg=str(p))
+
+
+def test_batch_small_random_pairs_over_three_groups(L, oracle_mod):
+    rng = np.random.default_rng(11)
+    pairs = []
+    for i in range(300):
+        alpha = [b"ACGT", b"AC", b"A"][i % 3]
+        a, b = gen.fuzz_sequences(7000 + i, nseq=2, max_len=[5, 60, 400][i % 3], alphabet=alpha)
+        if i % 17 == 0:
+            a = a[:0]  # empty first sequence
+        if i % 23 == 0:
+            b = b[:0]
+        pairs.append([a, b])
+    res = run_batch(L, pairs)
+    assert len(res) == len(pairs)
+    for p, (a, b) in enumerate(pairs):
+        assert_same(res[p], expect_pair(oracle_mod, a, b), p)
+
+
+def test_batch_degenerate_pairs(L, oracle_mod):
+    cases = [v for v in gen.degenerate_cases().values() if len(v) == 2]
+    res = run_batch(L, cases)
+    for p, (a, b) in enumerate(cases):
+        assert_same(res[p], expect_pair(oracle_mod, a, b), p)
+
+
+def test_batch_noncoding_pairs_of_uneven_length(L, oracle_mod):
+    pairs = gen.pair_batch(npairs=160, lo=1_000, hi=60_000, seed=140434490)
+    res = run_batch(L, pairs)
+    for p, (a, b) in enumerate(pairs):
+        assert_same(res[p], expect_pair(oracle_mod, a, b), p)
+
+
+def test_batch_single_pair_equals_plain_path(L, oracle_mod):
+    seqs, _ = gen.pair_uniform(n_each=50_000, plant_len=300, seed=5)
+    res = run_batch(L, [seqs])
+    assert_same(res[0], expect_pair(oracle_mod, *seqs), 0)
+
+
+def test_batch_positions_capacity(L, oracle_mod):
+    pairs = [[np.frombuffer(b"A" * 10, np.uint8), np.frombuffer(b"CAC", np.uint8)]] * 3
+    res = run_batch(L, pairs, pos_cap=5)
+    exp = expect_pair(oracle_mod, *pairs[0])
+    assert res[0]["n_pos"] == len(exp["positions"])
+    np.testing.assert_array_equal(res[0]["positions"], exp["positions"][:5])
