@@ -89,6 +89,42 @@ __global__ void __launch_bounds__(256) k_rmq_level(const int32_t *__restrict__ s
     *reinterpret_cast<int4 *>(dst + i) = r;
 }
 
+// Two levels per pass: dst1 = level j (windows of 2h, h = 2^(j-1)) and
+// dst2 = level j+1 (windows of 4h) from level j-1, reading src once from
+// DRAM (the operands h, 2h and 3h ahead were read by earlier blocks and are
+// mostly served by L2).
+__global__ void __launch_bounds__(256) k_rmq_level2(const int32_t *__restrict__ src,
+                                                    int32_t *__restrict__ dst1, int32_t *__restrict__ dst2,
+                                                    int64_t n, int64_t h) {
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
+    if (i >= n) return;
+    int4 a = *reinterpret_cast<const int4 *>(src + i);
+    int v[4] = {a.x, a.y, a.z, a.w};
+    int w[4];
+    // level j: min(src[i], src[i+h]); level j+1: min of src at i, i+h, i+2h, i+3h
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = v[u];
+#pragma unroll
+    for (int q = 1; q <= 3; ++q) {
+        const int64_t o = i + q * h;
+        int x[4];
+        if (o + 3 < n) {
+            const int4 b = *reinterpret_cast<const int4 *>(src + o);
+            x[0] = b.x; x[1] = b.y; x[2] = b.z; x[3] = b.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = o + u < n ? src[o + u] : INT_MAX;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (q == 1) v[u] = min(v[u], x[u]);
+            w[u] = min(w[u], x[u]);
+        }
+    }
+    *reinterpret_cast<int4 *>(dst1 + i) = make_int4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<int4 *>(dst2 + i) = make_int4(w[0], w[1], w[2], w[3]);
+}
+
 __global__ void k_rmq_query(const int32_t *__restrict__ table, int64_t stride,
                             const int32_t *__restrict__ isa, int64_t n, const int32_t *__restrict__ P,
                             const int32_t *__restrict__ Q, int64_t nq, int32_t *__restrict__ out,
@@ -153,7 +189,14 @@ extern "C" int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, 
     }
     LOR_LAUNCH_CHECK();
     const unsigned grid = unsigned(cdiv(cdiv(n, 4), 256));
-    for (int j = kLowLevels + 1; j < J; ++j) {
+    int j = kLowLevels + 1;
+    for (; j + 1 < J; j += 2) {
+        ProfScope ps(PK_RMQ_LEVEL, double(n) * 12, s);
+        k_rmq_level2<<<grid, 256, 0, s>>>(d_table + int64_t(j - 1) * stride, d_table + int64_t(j) * stride,
+                                          d_table + int64_t(j + 1) * stride, n, int64_t(1) << (j - 1));
+        LOR_LAUNCH_CHECK();
+    }
+    for (; j < J; ++j) {
         ProfScope ps(PK_RMQ_LEVEL, double(n) * 8, s);
         k_rmq_level<<<grid, 256, 0, s>>>(d_table + int64_t(j - 1) * stride, d_table + int64_t(j) * stride,
                                          n, int64_t(1) << (j - 1));
