@@ -131,8 +131,8 @@ int lor_build_sa_noalloc(const uint8_t *d_text, int64_t n, int32_t sigma, int32_
  *
  * d_text, n : as for lor_build_sa.   d_sa : device int32[n] suffix array.
  * d_isa     : device int32[n] output.  d_lcp : device int32[n] output.
- * d_ws      : device workspace of lor_lcp_workspace_size(n) bytes (12 bytes
- *             per symbol), 256-byte aligned.
+ * d_ws      : device workspace of lor_lcp_workspace_size(n) bytes (about 25
+ *             bytes per symbol), 256-byte aligned.
  * An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT (and is skipped).
  * ------------------------------------------------------------------------- */
 size_t lor_lcp_workspace_size(int64_t n);

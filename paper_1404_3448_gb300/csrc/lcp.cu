@@ -11,20 +11,47 @@
 //      PLCP[i] and ISA[i] are written in text order;
 //   3. LCP[k] = PLCP[SA[k]] is gathered in rank order.
 #include "lcp_kernels.cuh"
+#include "radix.cuh"
 
 LOR_DEFINE_TU_STATUS(lor_status_lcp)
 
 namespace lor {
 namespace {
 
+// Inputs of at least this many symbols scatter through bucketing (one radix
+// pass on the destination's top bits, then writes that combine in L2).
+constexpr int64_t kBucketMin = int64_t(1) << 22;
+
+__global__ void k_lcp_scatter_direct(const int32_t *__restrict__ isa, int64_t n,
+                                     const int32_t *__restrict__ plcp, int32_t *__restrict__ lcp) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t r = isa[i];
+    if (r >= 0 && r < n) lcp[r] = plcp[i];
+}
+
 struct LcpLayout {
-    size_t ip = 0, plcp = 0, total = 0;
+    size_t ip = 0, plcp = 0, ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
+    size_t kbuf = 0, vbuf = 0, total = 0;
 };
 LcpLayout lcp_layout(int64_t n) {
     LcpLayout L;
-    L.ip = 0;
-    L.plcp = align256(sizeof(int2) * size_t(n));
-    L.total = L.plcp + align256(sizeof(int32_t) * size_t(n));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.ip = take(sizeof(int2) * size_t(n));
+    L.plcp = take(sizeof(int32_t) * size_t(n));
+    L.ctrl = take(256);
+    L.hist = take(sizeof(uint32_t) * kMaxPasses * kRadix);
+    L.offsets = take(sizeof(uint32_t) * kMaxPasses * kRadix);
+    L.lookback_bytes = radix_lookback_bytes(n);
+    L.lookback = take(L.lookback_bytes);
+    L.kbuf = take(sizeof(uint32_t) * size_t(n));
+    L.vbuf = take(sizeof(uint64_t) * size_t(n));
+    L.total = off;
     return L;
 }
 
@@ -47,14 +74,31 @@ extern "C" int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, in
     cudaStream_t s = (cudaStream_t)stream;
     int *status = tu_status_ptr();
     if (!status) return LOR_ERR_CUDA;
-    int2 *ip = (int2 *)((char *)d_ws + L.ip);
-    int32_t *plcp = (int32_t *)((char *)d_ws + L.plcp);
-    {
+    char *ws = (char *)d_ws;
+    int2 *ip = (int2 *)(ws + L.ip);
+    int32_t *plcp = (int32_t *)(ws + L.plcp);
+    uint32_t *kbuf = (uint32_t *)(ws + L.kbuf);
+    uint64_t *vbuf = (uint64_t *)(ws + L.vbuf);
+    const bool bucket = n >= kBucketMin;
+    RadixScratch rs;
+    rs.hist = (uint32_t *)(ws + L.hist);
+    rs.offsets = (uint32_t *)(ws + L.offsets);
+    rs.lookback = (uint64_t *)(ws + L.lookback);
+    rs.tile_ctr = (unsigned long long *)(ws + L.ctrl);
+    rs.max_tiles = cdiv(n, kMinSortTile);
+    rs.status = status;
+    rs.stream = s;
+    if (bucket) {
+        LOR_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, 256, s));
+        LOR_CUDA_TRY(cudaMemsetAsync(ws + L.lookback, 0, L.lookback_bytes, s));
+        const int rc = bucketed_isa_phi(rs, d_sa, n, n, kbuf, vbuf, ip);
+        if (rc) return rc;
+    } else {
         // SA read (4 + 4 neighbour), 8-byte scatter
         ProfScope ps(PK_ISA_SCATTER, double(n) * 12, s);
         k_isa_phi<<<unsigned(cdiv(n, 256)), 256, 0, s>>>(d_sa, n, nullptr, ip, status);
+        LOR_LAUNCH_CHECK();
     }
-    LOR_LAUNCH_CHECK();
     {
         // {ISA, PHI} read, ISA + PLCP written, two text reads per position
         ProfScope ps(PK_KASAI, double(n) * (8 + 4 + 4 + 2), s);
@@ -63,10 +107,16 @@ extern "C" int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, in
                                                                      status);
     }
     LOR_LAUNCH_CHECK();
-    {
+    // LCP[ISA[i]] = PLCP[i]
+    if (bucket) {
+        uint32_t *vb0 = reinterpret_cast<uint32_t *>(vbuf);
+        const int rc = bucketed_scatter(rs, (const uint32_t *)d_isa, (const uint32_t *)plcp, n, n, kbuf, vb0,
+                                        vb0 + n, d_lcp, 0);
+        if (rc) return rc;
+    } else {
         ProfScope ps(PK_KASAI, double(n) * 12, s);
-        k_lcp_gather<<<unsigned(cdiv(n, 256)), 256, 0, s>>>(d_sa, n, plcp, d_lcp);
+        k_lcp_scatter_direct<<<unsigned(cdiv(n, 256)), 256, 0, s>>>(d_isa, n, plcp, d_lcp);
+        LOR_LAUNCH_CHECK();
     }
-    LOR_LAUNCH_CHECK();
     return LOR_OK;
 }

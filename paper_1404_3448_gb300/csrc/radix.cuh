@@ -22,10 +22,17 @@ constexpr int kMaxPasses = 8;  // 64-bit keys
 
 // Keys per thread: sized so that three 256-thread blocks fit an SM (at most
 // 85 registers per thread, under 76 KB of shared memory per block).
-template <typename KeyT>
-__host__ __device__ constexpr int sort_items() { return sizeof(KeyT) == 8 ? 12 : 16; }
-template <typename KeyT>
-__host__ __device__ constexpr int sort_tile() { return kSortThreads * sort_items<KeyT>(); }
+template <typename KeyT, typename ValT = uint32_t>
+__host__ __device__ constexpr int sort_items() { return sizeof(KeyT) + sizeof(ValT) > 8 ? 12 : 16; }
+template <typename KeyT, typename ValT = uint32_t>
+__host__ __device__ constexpr int sort_tile() { return kSortThreads * sort_items<KeyT, ValT>(); }
+
+// Where a pass takes its values from.
+enum ValMode {
+    VM_LOAD = 0,      // vin[idx]
+    VM_IOTA = 1,      // idx (32-bit values)
+    VM_IDX_PREV = 2,  // 64-bit values: low word idx, high word the previous key (kin[idx-1], or ~0)
+};
 constexpr int kMinSortTile = kSortThreads * 12;
 
 template <typename KeyT>
@@ -91,10 +98,10 @@ static __global__ void __launch_bounds__(256) k_radix_offsets(const uint32_t *__
     offsets[p * kRadix + threadIdx.x] = block_excl_scan<kRadix>(v, scratch, &total);
 }
 
-template <typename KeyT>
+template <typename KeyT, typename ValT>
 struct OnesweepSmem {
-    KeyT keys[sort_tile<KeyT>()];
-    uint32_t vals[sort_tile<KeyT>()];
+    KeyT keys[sort_tile<KeyT, ValT>()];
+    ValT vals[sort_tile<KeyT, ValT>()];
     uint32_t warp_hist[kSortWarps][kRadix];
     uint32_t local_start[kRadix];
     long long gbase[kRadix];
@@ -105,17 +112,17 @@ struct OnesweepSmem {
 // One LSD pass over digit (shift .. shift+7).  Tiles are claimed in launch
 // order from a running counter, so every predecessor a block waits on is
 // already resident; each wait is still bounded by kSpinLimitNs.
-template <typename KeyT, bool kIotaVals>
+template <typename KeyT, typename ValT, int kVMode>
 __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
-    const KeyT *__restrict__ kin, const uint32_t *__restrict__ vin, KeyT *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t m, int shift, uint32_t dmask,
+    const KeyT *__restrict__ kin, const ValT *__restrict__ vin, KeyT *__restrict__ kout,
+    ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask,
     const uint32_t *__restrict__ offsets,
     uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
     uint32_t epoch, int *status) {
-    constexpr int kItems = sort_items<KeyT>();
-    constexpr int kTile = sort_tile<KeyT>();
+    constexpr int kItems = sort_items<KeyT, ValT>();
+    constexpr int kTile = sort_tile<KeyT, ValT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    OnesweepSmem<KeyT> &S = *reinterpret_cast<OnesweepSmem<KeyT> *>(smem_raw);
+    OnesweepSmem<KeyT, ValT> &S = *reinterpret_cast<OnesweepSmem<KeyT, ValT> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
     for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
@@ -125,13 +132,17 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
     const int64_t wbase = base + int64_t(warp) * (kItems * 32);
 
     KeyT k[kItems];
-    uint32_t v[kItems], r[kItems];
+    ValT v[kItems];
+    uint32_t r[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         const int64_t idx = wbase + i * 32 + lane;
         const bool valid = idx < m;
         k[i] = valid ? kin[idx] : KeyT(0);
-        if (!kIotaVals) v[i] = valid ? vin[idx] : 0u;
+        if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[idx] : ValT(0);
+        if constexpr (kVMode == VM_IDX_PREV)
+            v[i] = uint64_t(uint32_t(idx)) |
+                   (uint64_t(valid && idx > 0 ? uint32_t(kin[idx - 1]) : 0xFFFFFFFFu) << 32);
     }
     // Stable rank inside the warp: items in order, lanes in order.  Slots
     // past the end of the input use digit 256 and are never counted.
@@ -194,7 +205,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
             const uint32_t d = digit_of(k[i], shift, dmask);
             const uint32_t pos = S.local_start[d] + S.warp_hist[warp][d] + r[i];
             S.keys[pos] = k[i];
-            S.vals[pos] = kIotaVals ? uint32_t(idx) : v[i];
+            S.vals[pos] = kVMode == VM_IOTA ? ValT(uint32_t(idx)) : v[i];
         }
     }
     __syncthreads();
@@ -244,7 +255,7 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
     if (begin_bit < 0 || end_bit < begin_bit || end_bit > int(8 * sizeof(KeyT)) ||
         npasses > kMaxPasses)
         return LOR_ERR_INVALID_ARG;
-    if (cdiv(m, sort_tile<KeyT>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
+    if (cdiv(m, sort_tile<KeyT, uint32_t>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
     uint32_t hh[kMaxPasses * kRadix];
     if (npasses > 0) {
         LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * npasses * kRadix, s));
@@ -260,15 +271,15 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
                                      cudaMemcpyDeviceToHost, s));
         LOR_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    const size_t smem = sizeof(OnesweepSmem<KeyT>);
-    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, true>,
+    const size_t smem = sizeof(OnesweepSmem<KeyT, uint32_t>);
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, uint32_t, VM_IOTA>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, false>,
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, uint32_t, VM_LOAD>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     KeyT *ki = k0, *ko = k1;
     uint32_t *vi = v0, *vo = v1;
     bool vals_ready = !iota_vals;
-    const int64_t ntiles = cdiv(m, sort_tile<KeyT>());
+    const int64_t ntiles = cdiv(m, sort_tile<KeyT, uint32_t>());
     for (int p = 0; p < npasses; ++p) {
         bool trivial = false;
         for (int dgt = 0; dgt < kRadix; ++dgt)
@@ -279,11 +290,11 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
         {
             ProfScope ps(PK_RADIX_PASS, double(m) * 2.0 * (sizeof(KeyT) + 4), s);
             if (vals_ready)
-                k_onesweep<KeyT, false><<<unsigned(ntiles), kSortThreads, smem, s>>>(
+                k_onesweep<KeyT, uint32_t, VM_LOAD><<<unsigned(ntiles), kSortThreads, smem, s>>>(
                     ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
                     rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status);
             else
-                k_onesweep<KeyT, true><<<unsigned(ntiles), kSortThreads, smem, s>>>(
+                k_onesweep<KeyT, uint32_t, VM_IOTA><<<unsigned(ntiles), kSortThreads, smem, s>>>(
                     ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
                     rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status);
         }
@@ -339,6 +350,63 @@ inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32
     {
         ProfScope ps(PK_RANK_SCATTER, double(m) * 12, rs.stream);
         k_scatter_pairs<<<unsigned(cdiv(m, 256)), 256, 0, rs.stream>>>(kr, vr, m, dst, add, bound, rs.status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
+// ---- the same bucketing for {ISA, PHI}: ip[SA[k]] = {k, SA[k-1]}.  One
+// radix pass on the top 8 bits of SA[k] whose 64-bit values are generated in
+// the pass (k and the previous key), then a streaming 8-byte scatter.
+
+static __global__ void k_scatter_isa_phi(const uint32_t *__restrict__ key, const uint64_t *__restrict__ val,
+                                         int64_t m, int2 *__restrict__ ip, int64_t bound, int *status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t r = key[i];
+    if (int64_t(r) >= bound) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        return;
+    }
+    const uint64_t v = val[i];
+    ip[r] = make_int2(int32_t(uint32_t(v)), int32_t(uint32_t(v >> 32)));
+}
+
+// sa: m entries (a permutation of [0, bound)); kbuf: m uint32 scratch; vbuf:
+// m uint64 scratch.
+inline int bucketed_isa_phi(RadixScratch &rs, const int32_t *sa, int64_t m, int64_t bound, uint32_t *kbuf,
+                            uint64_t *vbuf, int2 *ip) {
+    cudaStream_t s = rs.stream;
+    if (m <= 0) return LOR_OK;
+    const int top = bit_width_u64(uint64_t(bound > 1 ? bound - 1 : 1));
+    const int lo = top > kRadixBits ? top - kRadixBits : 0;
+    if (cdiv(m, sort_tile<uint32_t, uint64_t>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
+    const uint32_t *keys = reinterpret_cast<const uint32_t *>(sa);
+    LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * kRadix, s));
+    {
+        ProfScope ps(PK_RADIX_HIST, double(m) * 4, s);
+        const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
+        k_radix_hist<uint32_t><<<grid, 256, 0, s>>>(keys, m, lo, top, 1, rs.hist);
+    }
+    LOR_LAUNCH_CHECK();
+    k_radix_offsets<<<1, kRadix, 0, s>>>(rs.hist, rs.offsets);
+    LOR_LAUNCH_CHECK();
+    const size_t smem = sizeof(OnesweepSmem<uint32_t, uint64_t>);
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<uint32_t, uint64_t, VM_IDX_PREV>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    const int64_t ntiles = cdiv(m, sort_tile<uint32_t, uint64_t>());
+    rs.epoch++;
+    {
+        ProfScope ps(PK_RADIX_PASS, double(m) * (4 + 4 + 12), s);
+        k_onesweep<uint32_t, uint64_t, VM_IDX_PREV><<<unsigned(ntiles), kSortThreads, smem, s>>>(
+            keys, nullptr, kbuf, vbuf, m, lo, digit_mask(lo, top), rs.offsets, rs.lookback, rs.tile_ctr,
+            rs.tile_base, rs.epoch, rs.status);
+    }
+    LOR_LAUNCH_CHECK();
+    rs.tile_base += (unsigned long long)ntiles;
+    {
+        ProfScope ps(PK_ISA_SCATTER, double(m) * 20, s);
+        k_scatter_isa_phi<<<unsigned(cdiv(m, 256)), 256, 0, s>>>(kbuf, vbuf, m, ip, bound, rs.status);
     }
     LOR_LAUNCH_CHECK();
     return LOR_OK;

@@ -73,7 +73,7 @@ def test_bad_arguments_rejected_on_host(lib):
     assert L.lor_build_sa(1 << 20, 10, 7, 1 << 20, (1 << 20) + 8, 1 << 30, None) == L.LOR_ERR_WORKSPACE
     assert L.lor_lcp(None, None, 5, None, None, None, 0, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_lcp(256, 256, 5, 256, 256, None, 0, None) == L.LOR_ERR_WORKSPACE
-    assert L.lor_lcp_workspace_size(1000) >= 12 * 1000
+    assert L.lor_lcp_workspace_size(1000) >= 24 * 1000
     assert L.lor_longest_overlap(1, 1, 5, 1, 0, 1, None, 0, None, 0, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_longest_overlap(1, 1, 5, 1, 251, 1, None, 0, None, 0, None) == L.LOR_ERR_INVALID_ARG
     assert L.lor_longest_overlap(256, 256, 5, 256, 2, 256, None, 4, None, 0, None) == L.LOR_ERR_INVALID_ARG
