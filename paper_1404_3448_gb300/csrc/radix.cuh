@@ -218,6 +218,91 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
     }
 }
 
+// One non-stable partition pass (for the bucketed scatters, where the order
+// inside a bucket does not matter): an element's place inside its tile's
+// digit run comes from a shared-memory atomic instead of the stable warp
+// ranking; the look-back and the staged write are those of k_onesweep.
+template <typename ValT, int kVMode>
+__global__ void __launch_bounds__(kSortThreads, 3) k_partition(
+    const uint32_t *__restrict__ kin, const ValT *__restrict__ vin, uint32_t *__restrict__ kout,
+    ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask, const uint32_t *__restrict__ offsets,
+    uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
+    uint32_t epoch, int *status) {
+    constexpr int kItems = sort_items<uint32_t, ValT>();
+    constexpr int kTile = sort_tile<uint32_t, ValT>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnesweepSmem<uint32_t, ValT> &S = *reinterpret_cast<OnesweepSmem<uint32_t, ValT> *>(smem_raw);
+    uint32_t *cnt = S.warp_hist[0];
+    const int tid = threadIdx.x;
+    if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+    cnt[tid] = 0;
+    __syncthreads();
+    const int64_t tile = S.tile;
+    const int64_t base = tile * kTile;
+    uint32_t k[kItems], r[kItems];
+    ValT v[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const int64_t idx = base + i * kSortThreads + tid;
+        const bool valid = idx < m;
+        k[i] = valid ? kin[idx] : 0u;
+        if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[idx] : ValT(0);
+        if constexpr (kVMode == VM_IOTA) v[i] = ValT(uint32_t(idx));
+        if constexpr (kVMode == VM_IDX_PREV)
+            v[i] = uint64_t(uint32_t(idx)) |
+                   (uint64_t(valid && idx > 0 ? kin[idx - 1] : 0xFFFFFFFFu) << 32);
+        r[i] = valid ? atomicAdd(&cnt[digit_of(k[i], shift, dmask)], 1u) : 0u;
+    }
+    __syncthreads();
+    const int dg = tid;
+    const uint32_t total = cnt[dg];
+    uint32_t tile_total;
+    const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
+    S.local_start[dg] = lstart;
+    uint32_t excl = 0;
+    uint64_t *lb = lookback;
+    if (tile == 0) {
+        st_volatile_u64(&lb[dg], lb_pack(epoch, kFlagIncl, total));
+    } else {
+        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
+        int64_t j = tile - 1;
+        const uint64_t t0 = global_ns();
+        while (j >= 0) {
+            const uint64_t w = ld_volatile_u64(&lb[j * kRadix + dg]);
+            if (lb_epoch(w) != epoch || lb_flag(w) == 0) {
+                if (global_ns() - t0 > kSpinLimitNs) {
+                    atomicCAS(status, 0, LOR_ERR_TIMEOUT);
+                    break;
+                }
+                continue;
+            }
+            excl += lb_value(w);
+            if (lb_flag(w) == kFlagIncl) break;
+            --j;
+        }
+        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
+    }
+    S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const int64_t idx = base + i * kSortThreads + tid;
+        if (idx < m) {
+            const uint32_t pos = S.local_start[digit_of(k[i], shift, dmask)] + r[i];
+            S.keys[pos] = k[i];
+            S.vals[pos] = v[i];
+        }
+    }
+    __syncthreads();
+    const int cnt_tile = int(min64(int64_t(kTile), m - base));
+    for (int i = tid; i < cnt_tile; i += kSortThreads) {
+        const uint32_t kk = S.keys[i];
+        const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
+        kout[o] = kk;
+        vout[o] = S.vals[i];
+    }
+}
+
 static __global__ void k_iota_u32(uint32_t *__restrict__ v, int64_t m) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < m) v[i] = uint32_t(i);
@@ -335,29 +420,61 @@ static __global__ void k_scatter_pairs(const uint32_t *__restrict__ key, const u
 // keys/vals: inputs (vals == nullptr means 0..m-1).  kbuf, vbuf0, vbuf1:
 // caller scratch of m entries each (vbuf0 receives the input values when they
 // are generated).  The caller accounts the scatter kernel's launch.
+// One partition pass of m keys by bits [lo, top) (top - lo <= 8): histogram,
+// offsets and k_partition.  No host synchronisation.
+template <typename ValT, int kVMode>
+int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int64_t m, int lo, int top,
+                   uint32_t *kout, ValT *vout) {
+    cudaStream_t s = rs.stream;
+    if (cdiv(m, sort_tile<uint32_t, ValT>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
+    LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * kRadix, s));
+    {
+        ProfScope ps(PK_RADIX_HIST, double(m) * 4, s);
+        const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
+        k_radix_hist<uint32_t><<<grid, 256, 0, s>>>(keys, m, lo, top, 1, rs.hist);
+    }
+    LOR_LAUNCH_CHECK();
+    k_radix_offsets<<<1, kRadix, 0, s>>>(rs.hist, rs.offsets);
+    LOR_LAUNCH_CHECK();
+    const size_t smem = sizeof(OnesweepSmem<uint32_t, ValT>);
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_partition<ValT, kVMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(smem)));
+    const int64_t ntiles = cdiv(m, sort_tile<uint32_t, ValT>());
+    rs.epoch++;
+    {
+        ProfScope ps(PK_RADIX_PASS, double(m) * (4 + (kVMode == VM_LOAD ? sizeof(ValT) : 0) + 4 + sizeof(ValT)),
+                     s);
+        k_partition<ValT, kVMode><<<unsigned(ntiles), kSortThreads, smem, s>>>(
+            keys, vals, kout, vout, m, lo, digit_mask(lo, top), rs.offsets, rs.lookback, rs.tile_ctr,
+            rs.tile_base, rs.epoch, rs.status);
+    }
+    LOR_LAUNCH_CHECK();
+    rs.tile_base += (unsigned long long)ntiles;
+    return LOR_OK;
+}
+
 inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32_t *vals, int64_t m,
                             int64_t bound, uint32_t *kbuf, uint32_t *vbuf0, uint32_t *vbuf1,
                             int32_t *dst, int32_t add) {
+    (void)vbuf1;
     if (m <= 0) return LOR_OK;
     const int top = bit_width_u64(uint64_t(bound > 1 ? bound - 1 : 1));
     const int lo = top > kRadixBits ? top - kRadixBits : 0;
-    uint32_t *kr, *vr;
-    const bool iota = vals == nullptr;
-    const int rc = radix_sort_pairs<uint32_t>(rs, const_cast<uint32_t *>(keys),
-                                              iota ? vbuf0 : const_cast<uint32_t *>(vals), kbuf,
-                                              iota ? vbuf1 : vbuf0, m, lo, top, iota, &kr, &vr);
+    const int rc = vals ? partition_pass<uint32_t, VM_LOAD>(rs, keys, vals, m, lo, top, kbuf, vbuf0)
+                        : partition_pass<uint32_t, VM_IOTA>(rs, keys, nullptr, m, lo, top, kbuf, vbuf0);
     if (rc) return rc;
     {
         ProfScope ps(PK_RANK_SCATTER, double(m) * 12, rs.stream);
-        k_scatter_pairs<<<unsigned(cdiv(m, 256)), 256, 0, rs.stream>>>(kr, vr, m, dst, add, bound, rs.status);
+        k_scatter_pairs<<<unsigned(cdiv(m, 256)), 256, 0, rs.stream>>>(kbuf, vbuf0, m, dst, add, bound,
+                                                                      rs.status);
     }
     LOR_LAUNCH_CHECK();
     return LOR_OK;
 }
 
 // ---- the same bucketing for {ISA, PHI}: ip[SA[k]] = {k, SA[k-1]}.  One
-// radix pass on the top 8 bits of SA[k] whose 64-bit values are generated in
-// the pass (k and the previous key), then a streaming 8-byte scatter.
+// partition pass on the top 8 bits of SA[k] whose 64-bit values are generated
+// in the pass (k and the previous key), then a streaming 8-byte scatter.
 
 static __global__ void k_scatter_isa_phi(const uint32_t *__restrict__ key, const uint64_t *__restrict__ val,
                                          int64_t m, int2 *__restrict__ ip, int64_t bound, int *status) {
@@ -376,37 +493,15 @@ static __global__ void k_scatter_isa_phi(const uint32_t *__restrict__ key, const
 // m uint64 scratch.
 inline int bucketed_isa_phi(RadixScratch &rs, const int32_t *sa, int64_t m, int64_t bound, uint32_t *kbuf,
                             uint64_t *vbuf, int2 *ip) {
-    cudaStream_t s = rs.stream;
     if (m <= 0) return LOR_OK;
     const int top = bit_width_u64(uint64_t(bound > 1 ? bound - 1 : 1));
     const int lo = top > kRadixBits ? top - kRadixBits : 0;
-    if (cdiv(m, sort_tile<uint32_t, uint64_t>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
-    const uint32_t *keys = reinterpret_cast<const uint32_t *>(sa);
-    LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * kRadix, s));
+    const int rc = partition_pass<uint64_t, VM_IDX_PREV>(rs, reinterpret_cast<const uint32_t *>(sa), nullptr, m,
+                                                          lo, top, kbuf, vbuf);
+    if (rc) return rc;
     {
-        ProfScope ps(PK_RADIX_HIST, double(m) * 4, s);
-        const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
-        k_radix_hist<uint32_t><<<grid, 256, 0, s>>>(keys, m, lo, top, 1, rs.hist);
-    }
-    LOR_LAUNCH_CHECK();
-    k_radix_offsets<<<1, kRadix, 0, s>>>(rs.hist, rs.offsets);
-    LOR_LAUNCH_CHECK();
-    const size_t smem = sizeof(OnesweepSmem<uint32_t, uint64_t>);
-    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<uint32_t, uint64_t, VM_IDX_PREV>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    const int64_t ntiles = cdiv(m, sort_tile<uint32_t, uint64_t>());
-    rs.epoch++;
-    {
-        ProfScope ps(PK_RADIX_PASS, double(m) * (4 + 4 + 12), s);
-        k_onesweep<uint32_t, uint64_t, VM_IDX_PREV><<<unsigned(ntiles), kSortThreads, smem, s>>>(
-            keys, nullptr, kbuf, vbuf, m, lo, digit_mask(lo, top), rs.offsets, rs.lookback, rs.tile_ctr,
-            rs.tile_base, rs.epoch, rs.status);
-    }
-    LOR_LAUNCH_CHECK();
-    rs.tile_base += (unsigned long long)ntiles;
-    {
-        ProfScope ps(PK_ISA_SCATTER, double(m) * 20, s);
-        k_scatter_isa_phi<<<unsigned(cdiv(m, 256)), 256, 0, s>>>(kbuf, vbuf, m, ip, bound, rs.status);
+        ProfScope ps(PK_ISA_SCATTER, double(m) * 20, rs.stream);
+        k_scatter_isa_phi<<<unsigned(cdiv(m, 256)), 256, 0, rs.stream>>>(kbuf, vbuf, m, ip, bound, rs.status);
     }
     LOR_LAUNCH_CHECK();
     return LOR_OK;
