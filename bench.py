@@ -329,6 +329,113 @@ def batch_vs_plain(npairs, steps, warmup, dev, seed=140434484):
     }
 
 
+# --------------------------------------------------------------------------- served
+
+def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed=140434485):
+    """Requests arrive as a Poisson process (``rate`` per second for
+    ``seconds``), each asking for one pair of a pool of noncoding-like pairs
+    (per-sequence lengths log-uniform in [1k, 4M]) held in pinned host memory.
+    A submitter thread submits on the arrival clock to a lor_server with a
+    ``budget_gb`` device reservation; the main thread polls results, asks the
+    request's ``queries`` follow-up LCP queries on its resident state and
+    releases it.  Reports sustained input bases/s and latency percentiles."""
+    import threading
+    import torch
+    import lor_inputs as gen
+    import paper_1404_3448_gb300 as lor
+
+    pool = gen.pair_batch(npairs=pool_pairs, lo=1_000, hi=4_000_000, seed=seed)
+    lens = [(len(a), len(b)) for a, b in pool]
+    total = sum(a + b for a, b in lens)
+    host = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    hv = host.numpy()
+    ptrs, off = [], 0
+    for a, b in pool:
+        hv[off:off + len(a)] = a
+        hv[off + len(a):off + len(a) + len(b)] = b
+        ptrs.append((host.data_ptr() + off, host.data_ptr() + off + len(a)))
+        off += len(a) + len(b)
+    arrivals = gen.poisson_arrivals(rate, seconds, seed=seed + 1)
+    choice, P, Q = gen.request_stream(len(arrivals), lens, queries=queries, seed=seed + 2)
+    nreq = len(arrivals)
+
+    srv = lor.Server(int(budget_gb * (1 << 30)), workers=workers, max_batch_pairs=125)
+    try:
+        # warm-up: every pool pair once, so first-launch setup is not timed
+        for k in range(pool_pairs):
+            srv.submit_ptr(ptrs[k][0], lens[k][0], ptrs[k][1], lens[k][1], tag=k)
+        got = 0
+        while got < pool_pairs:
+            for r in srv.poll(timeout_ms=100):
+                if r["status"] != 0:
+                    raise RuntimeError(f"warm-up request failed: {lor.lor.status_string(r['status'])}")
+                srv.release(r["id"])
+                got += 1
+        first = {}
+        lat, qlat, sub_t, done_t = [], [], [], []
+        errors = []
+        t0 = srv.now() + 0.05
+
+        def submitter():
+            try:
+                for k in range(nreq):
+                    while True:
+                        wait = t0 + arrivals[k] - srv.now()
+                        if wait <= 0:
+                            break
+                        time.sleep(min(wait, 0.001))
+                    c = int(choice[k])
+                    srv.submit_ptr(ptrs[c][0], lens[c][0], ptrs[c][1], lens[c][1], tag=k)
+            except Exception as e:  # surfaced by the main thread
+                errors.append(e)
+
+        th = threading.Thread(target=submitter, daemon=True)
+        th.start()
+        done = 0
+        consistent = True
+        while done < nreq and not errors:
+            for r in srv.poll(timeout_ms=20):
+                k = int(r["tag"])
+                if r["status"] != 0:
+                    raise RuntimeError(f"request {k} failed: {lor.lor.status_string(r['status'])}")
+                q0 = time.perf_counter()
+                ans = srv.query(r["id"], P[k], Q[k])
+                qlat.append((time.perf_counter() - q0) * 1000.0)
+                c = int(choice[k])
+                rec = (r["length"], r["rank"], r["pos_a"], r["pos_b"], r["n_pos"])
+                if first.setdefault(c, rec) != rec:
+                    consistent = False
+                if ans.min() < 0:
+                    consistent = False
+                srv.release(r["id"])
+                lat.append((r["t_done"] - r["t_submit"]) * 1000.0)
+                sub_t.append(r["t_submit"])
+                done_t.append(r["t_done"])
+                done += 1
+        th.join()
+        if errors:
+            raise errors[0]
+        st = srv.stats()
+    finally:
+        srv.close()
+    bases = int(sum(lens[int(c)][0] + lens[int(c)][1] for c in choice))
+    span = max(done_t) - min(sub_t)
+    return {
+        "workload": f"Poisson arrivals at {rate:g} pair requests/s for {seconds:g} s; pairs drawn uniformly "
+                    f"from a pool of {pool_pairs} noncoding-like pairs (per-sequence lengths log-uniform in "
+                    f"[1k, 4M]) in pinned host memory; {queries} follow-up LCP queries per pair on resident "
+                    f"state; {budget_gb:g} GB device budget; {workers} workers",
+        "requests": nreq, "input_bases": bases,
+        "offered_bases_per_s": bases / float(arrivals[-1]) if nreq else 0.0,
+        "value": bases / span, "unit": UNIT,
+        "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "max": max(lat)},
+        "query_call_ms": {"p50": percentile(qlat, 50), "p99": percentile(qlat, 99)},
+        "batches": st["batches"], "mean_batch_pairs": st["pairs"] / max(st["batches"], 1),
+        "admission_waits": st["admission_waits"], "peak_reserved_gb": st["peak_bytes"] / 2**30,
+        "results_consistent": consistent,
+    }
+
+
 # --------------------------------------------------------------------------- GPU
 
 def run_lor(args):
@@ -467,6 +574,10 @@ def run_lor(args):
             del pipe
             torch.cuda.empty_cache()
             line["batch_vs_plain"] = batch_vs_plain(args.batch_pairs, 3, 1, dev)
+        if args.serve_seconds > 0:
+            torch.cuda.empty_cache()
+            line["serving"] = serving(args.serve_seconds, args.serve_rate, args.serve_pool, args.serve_workers,
+                                      args.serve_budget_gb, dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -484,6 +595,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=1024,
                     help="pairs of the batched-vs-plain sub-measurement (0 skips it)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="seconds of Poisson arrivals of the served sub-measurement (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="pair requests per second")
+    ap.add_argument("--serve-pool", type=int, default=256, help="distinct pairs the requests draw from")
+    ap.add_argument("--serve-workers", type=int, default=2)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--ref-bases", type=int, default=1 << 22,
                     help="bases per step of the reference (oracle) arm")
     args = ap.parse_args()

@@ -45,6 +45,7 @@ typedef struct CUstream_st *lor_stream_t; /* same type as cudaStream_t */
 #define LOR_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define LOR_ERR_TIMEOUT (-6)     /* a bounded inter-block wait ran out on the device */
 #define LOR_ERR_BAD_INPUT (-7)   /* an input array holds an out-of-range index (SA, ISA, query) */
+#define LOR_ERR_CANCELLED (-8)   /* server shut down before the request ran */
 
 /* Largest supported text length (int32 indices with head-room for DC3's
  * dummy sample and padding). */
@@ -212,6 +213,93 @@ int lor_rmq_query(const int32_t *d_table, const int32_t *d_isa, int64_t n, const
                   const int32_t *d_q, int64_t nq, int32_t *d_out, lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Request server: pair requests arrive one by one; each gets the longest
+ * overlap region of its pair (Section 3's problem) and then answers LCP
+ * queries between arbitrary suffixes of its own text S1#S2$ (Section 3: the
+ * LCP of two suffixes through the RMQ over the LCP array) while its state
+ * stays resident.  The serving loop has no counterpart in the paper.
+ *
+ * lor_server_create reserves hbm_budget_bytes of device memory on the current
+ * device (one allocation; the server allocates nothing else on the device
+ * afterwards except its small query buffers) and starts `workers` threads,
+ * each with its own non-blocking stream.  A free worker takes the oldest
+ * waiting requests (at most max_batch_pairs pairs and max_batch_symbols text
+ * symbols) as one batch, admits it when the batch's workspace and resident
+ * state fit in the reserved memory (otherwise it waits until a batch finishes
+ * or a request is released; requests are admitted in arrival order), copies
+ * the pairs to the device and runs the grouped pipeline of lor_batch_overlap
+ * on them.  Batches of different workers run on the device at once.  After a
+ * batch, its workspace is returned to the reservation; the batch's ISA and a
+ * sparse table over its LCP array stay resident until every request of the
+ * batch has been released.
+ *
+ * Results do not depend on how requests are batched: a request's record,
+ * positions and query answers equal those of lor_longest_overlap and
+ * lor_rmq_query run on its pair alone.
+ *
+ * Ownership: the host sequences passed to lor_server_submit must stay valid
+ * and unchanged until the request's result has been returned by
+ * lor_server_poll (pinned memory makes the copies faster).  The positions
+ * pointer of a result is owned by the server and valid until
+ * lor_server_release.  Times are seconds on a monotonic clock whose zero is
+ * the server's creation.  All functions are thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct lor_server lor_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;   /* device memory reserved for batches and resident state */
+    int32_t workers;           /* concurrent batches, 1 .. 8 */
+    int32_t max_batch_pairs;   /* 1 .. 125 */
+    int64_t max_batch_symbols; /* text symbols per batch, 1 .. 2^28 (a single larger pair still runs alone) */
+} lor_server_config;
+
+typedef struct {
+    int64_t id;          /* returned by lor_server_submit */
+    uint64_t tag;        /* caller's tag, passed through */
+    int32_t status;      /* LOR_OK, or the error that ended the request's batch */
+    int32_t batch_pairs; /* pairs in the batch the request ran in */
+    lor_overlap ov;      /* as lor_longest_overlap on the pair alone */
+    const int32_t *positions; /* ov.n_pos offsets in S1#S2$, ascending (server-owned) */
+    double t_submit, t_admit, t_done; /* submit, batch admitted, result ready */
+} lor_served;
+
+typedef struct {
+    int64_t submitted, completed, released, batches, pairs, bases;
+    int64_t admission_waits;   /* times a free worker waited for reserved memory */
+    int64_t queries;           /* LCP queries answered */
+    size_t reserved_bytes, in_use_bytes, peak_bytes;
+    int32_t pending, in_flight;
+} lor_server_stats;
+
+/* Device bytes one batch of the given pairs takes from the reservation while
+ * it runs (the first value) and afterwards until released (*h_resident). */
+size_t lor_server_batch_bytes(const int64_t *h_lens, int32_t npairs, size_t *h_resident);
+int lor_server_create(const lor_server_config *cfg, lor_server **out);
+/* Queues one pair; *out_id receives its id.  LOR_ERR_TOO_LARGE if the pair
+ * alone cannot fit in the reservation; LOR_ERR_INVALID_ARG for null pointers
+ * with nonzero length or negative lengths. */
+int lor_server_submit(lor_server *srv, const uint8_t *h_a, int64_t len_a, const uint8_t *h_b,
+                      int64_t len_b, uint64_t tag, int64_t *out_id);
+/* Moves up to cap finished requests into out[], waiting up to timeout_ms for
+ * the first; returns how many (or a negative status). */
+int lor_server_poll(lor_server *srv, lor_served *out, int32_t cap, int32_t timeout_ms);
+/* LCP of suffixes h_p[i] and h_q[i] of request id's text S1#S2$ (as
+ * lor_rmq_query on the pair alone), for a request whose result was polled
+ * and not yet released.  Host arrays of nq entries; synchronous.
+ * LOR_ERR_INVALID_ARG for an unknown id or a suffix outside the text. */
+int lor_server_query(lor_server *srv, int64_t id, const int32_t *h_p, const int32_t *h_q, int32_t nq,
+                     int32_t *h_out);
+/* Drops a polled request's result and resident state. */
+int lor_server_release(lor_server *srv, int64_t id);
+int lor_server_stats_get(lor_server *srv, lor_server_stats *out);
+/* Seconds on the server's clock (the clock of the t_* fields). */
+double lor_server_now(lor_server *srv);
+/* Stops the workers after their current batches, drops waiting and unreleased
+ * requests and frees everything (result pointers become invalid).  Submits
+ * racing with it return LOR_ERR_CANCELLED. */
+int lor_server_destroy(lor_server *srv);
+
+/* ---------------------------------------------------------------------------
  * The radix sort of Section 4 (Algorithm 1) as a standalone primitive:
  * stable LSD sort of m (key, value) pairs by the low key_bits bits of the
  * keys, in place.  d_keys uint64[m], d_vals uint32[m]; d_ws of
@@ -232,7 +320,7 @@ const char *lor_status_string(int status);
 /* Number of kernels this library has launched in this process. */
 uint64_t lor_launch_count(void);
 
-/* Per-level trace of the most recent lor_build_sa call in this process:
+/* Per-level trace of the most recent lor_build_sa call on the calling thread:
  * fills up to cap entries of level length n_l, distinct names found at that
  * level, key bits of the sample keys, how the sample was ordered (0 radix
  * sort, 1 dense naming table, 2 the parent level's order) and how many

@@ -15,6 +15,9 @@ for them with the shapes the workloads name:
   and one shared 10 kb region with 1 % mutations around an exact 2 kb core;
 * ``pair_batch``       -- many pairs of uneven, log-uniform length;
 * ``random_queries``   -- uniform (p, q) suffix pairs for LCP queries;
+* ``poisson_arrivals`` -- request arrival times of a Poisson process, and
+  ``request_stream``   -- which pool pair each arrival asks for and its
+  follow-up LCP queries (the served workload);
 * ``fuzz_pair``        -- small random/degenerate cases for parity tests.
 
 Seeds: workload c (1-based) uses seed 140434480 + c unless given another.
@@ -154,6 +157,28 @@ def pair_batch(npairs=4096, lo=1_000, hi=1_000_000, seed=SEED_BASE + 4):
         s2, _ = noncoding_sequence(rng, l2, consensi, shared, core=plen)
         pairs.append([s1, s2])
     return pairs
+
+
+def poisson_arrivals(rate, seconds, seed=SEED_BASE + 5):
+    """Arrival times (seconds, ascending) of a Poisson process of ``rate``
+    requests per second over [0, seconds): exponential gaps of mean 1/rate."""
+    rng = _rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=int(rate * seconds * 1.5) + 64)
+    t = np.cumsum(gaps)
+    return t[t < seconds]
+
+
+def request_stream(count, pool_pair_lens, queries=16, seed=SEED_BASE + 6):
+    """For ``count`` requests: the pool pair each one asks for (uniform over
+    the pool) and ``queries`` follow-up (p, q) suffix pairs uniform over that
+    pair's text of len1 + len2 + 2 symbols.  Returns (choice, P, Q) with P, Q
+    int32 arrays of shape (count, queries)."""
+    rng = _rng(seed)
+    choice = rng.integers(0, len(pool_pair_lens), size=count)
+    n = np.asarray([a + b + 2 for a, b in pool_pair_lens], dtype=np.int64)[choice]
+    P = (rng.random((count, queries)) * n[:, None]).astype(np.int64).astype(np.int32)
+    Q = (rng.random((count, queries)) * n[:, None]).astype(np.int64).astype(np.int32)
+    return choice, P, Q
 
 
 def fuzz_sequences(seed, nseq=2, max_len=64, alphabet=b"ACGT"):

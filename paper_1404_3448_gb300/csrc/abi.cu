@@ -126,7 +126,7 @@ extern "C" int lor_device_status(lor_stream_t stream) {
     int first = LOR_OK;
     int (*fns[])(cudaStream_t, int) = {lor_status_encode, lor_status_dc3, lor_status_lcp,
                                        lor_status_overlap, lor_status_rmq, lor_status_abi,
-                                       lor_status_batch};
+                                       lor_status_batch, lor_status_serve};
     for (auto f : fns) {
         const int v = f(s, 1);
         if (v != LOR_OK && first == LOR_OK) first = v;
@@ -144,6 +144,7 @@ extern "C" const char *lor_status_string(int status) {
         case LOR_ERR_CUDA: return "CUDA runtime error";
         case LOR_ERR_TIMEOUT: return "bounded device wait expired";
         case LOR_ERR_BAD_INPUT: return "input array holds an out-of-range index";
+        case LOR_ERR_CANCELLED: return "server shut down before the request ran";
         default: return "unknown status";
     }
 }

@@ -15,6 +15,7 @@
 // run on that pair alone.
 #include <vector>
 
+#include "batch.cuh"
 #include "lcp_kernels.cuh"
 #include "radix.cuh"
 #include "scan.cuh"
@@ -23,9 +24,6 @@ LOR_DEFINE_TU_STATUS(lor_status_batch)
 
 namespace lor {
 namespace {
-
-constexpr int kPairsPerGroup = LOR_MAX_SEQ / 2;
-constexpr int64_t kGroupSymbolCap = int64_t(1) << 28;
 
 __device__ __forceinline__ int bseq(const int32_t *st, int nseq, int32_t p) {
     int lo = 0, hi = nseq - 1;
@@ -231,13 +229,7 @@ std::vector<Group> make_groups(const int64_t *lens, int npairs) {
     return g;
 }
 
-struct BatchLayout {
-    size_t text = 0, starts = 0, sa = 0, region = 0, total = 0;
-    // inside region, after the suffix array is built
-    size_t ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
-    size_t pk = 0, pk2 = 0, sa2 = 0, ip = 0, isa = 0, plcp = 0, lcp = 0, run_id = 0, qual = 0;
-    size_t mem = 0, kb = 0, va = 0, vb = 0, bstart = 0, best = 0, cnt = 0, post = 0;
-};
+}  // namespace
 
 BatchLayout batch_layout(int64_t nmax) {
     BatchLayout L;
@@ -285,9 +277,129 @@ BatchLayout batch_layout(int64_t nmax) {
     return L;
 }
 
+namespace {
 unsigned gridn(int64_t m, int nt) { return unsigned(cdiv(m > 0 ? m : 1, nt)); }
-
 }  // namespace
+
+int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n, char *ws, size_t ws_bytes,
+                const BatchLayout &L, int64_t nmax, const GroupOutputs &o, int64_t *h_found, cudaStream_t s) {
+    const int nseq = 2 * np;
+    lor_stream_t stream = (lor_stream_t)s;
+    int *status = tu_status_ptr();
+    if (!status) return LOR_ERR_CUDA;
+    uint8_t *text = (uint8_t *)(ws + L.text);
+    int32_t *starts = (int32_t *)(ws + L.starts);
+    int32_t *sa = (int32_t *)(ws + L.sa);
+    int rc = lor_encode_concat(d_ascii, h_lens, nseq, text, starts, stream);
+    if (rc) return rc;
+    rc = lor_build_sa(text, n, nseq + 5, sa, ws + L.region, ws_bytes - L.region, stream);
+    if (rc) return rc;
+    // The suffix-array workspace is free again: carve the group buffers.
+    RadixScratch rs;
+    rs.hist = (uint32_t *)(ws + L.hist);
+    rs.offsets = (uint32_t *)(ws + L.offsets);
+    rs.lookback = (uint64_t *)(ws + L.lookback);
+    rs.tile_ctr = (unsigned long long *)(ws + L.ctrl);
+    rs.max_tiles = cdiv(nmax, kMinSortTile);
+    rs.status = status;
+    rs.stream = s;
+    uint32_t *pk = (uint32_t *)(ws + L.pk), *pk2 = (uint32_t *)(ws + L.pk2);
+    int32_t *sa2 = (int32_t *)(ws + L.sa2), *isa = (int32_t *)(ws + L.isa);
+    int32_t *plcp = (int32_t *)(ws + L.plcp), *lcp = (int32_t *)(ws + L.lcp);
+    int32_t *run_id = (int32_t *)(ws + L.run_id), *bstart = (int32_t *)(ws + L.bstart);
+    int32_t *cnt = (int32_t *)(ws + L.cnt);
+    uint8_t *qual = (uint8_t *)(ws + L.qual);
+    uint32_t *mem = (uint32_t *)(ws + L.mem), *kb = (uint32_t *)(ws + L.kb);
+    uint32_t *va = (uint32_t *)(ws + L.va), *vb = (uint32_t *)(ws + L.vb);
+    unsigned long long *best = (unsigned long long *)(ws + L.best);
+    uint32_t *d_count = (uint32_t *)(ws + L.ctrl + 128);
+    uint32_t *d_runs = (uint32_t *)(ws + L.ctrl + 192);
+    int2 *ip = (int2 *)(ws + L.ip);
+    LOR_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, 256, s));
+    LOR_CUDA_TRY(cudaMemsetAsync(ws + L.lookback, 0, L.lookback_bytes, s));
+    LOR_CUDA_TRY(cudaMemsetAsync(best, 0, sizeof(unsigned long long) * kPairsPerGroup, s));
+    LOR_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * kPairsPerGroup, s));
+    LOR_CUDA_TRY(cudaMemsetAsync(qual, 0, size_t(n), s));
+
+    // Per-pair blocks of the suffix array (stable by pair id).
+    k_pair_keys<<<gridn(n, 256), 256, 0, s>>>(sa, n, starts, nseq, pk);
+    LOR_LAUNCH_CHECK();
+    uint32_t *kr, *vr;
+    rc = radix_sort_pairs<uint32_t>(rs, pk, (uint32_t *)sa, pk2, (uint32_t *)sa2, n, 0,
+                                    bit_width_u64(uint64_t(np - 1)), false, &kr, &vr);
+    if (rc) return rc;
+    const uint32_t *PK = kr;
+    const int32_t *SA = (const int32_t *)vr;
+    k_block_starts<<<gridn(n, 256), 256, 0, s>>>(PK, n, bstart);
+    LOR_LAUNCH_CHECK();
+
+    // LCP inside the blocks.
+    {
+        ProfScope ps(PK_ISA_SCATTER, double(n) * 16, s);
+        k_isa_phi<<<gridn(n, 256), 256, 0, s>>>(SA, n, PK, ip, status);
+    }
+    LOR_LAUNCH_CHECK();
+    {
+        ProfScope ps(PK_KASAI, double(n) * 18, s);
+        k_plcp<<<gridn(n, kPlcpTile), kPlcpThreads, 0, s>>>(text, n, ip, isa, plcp,
+                                                           (uintptr_t(text) & 3) == 0, status);
+    }
+    LOR_LAUNCH_CHECK();
+    {
+        ProfScope ps(PK_KASAI, double(n) * 12, s);
+        k_lcp_gather<<<gridn(n, 256), 256, 0, s>>>(SA, n, plcp, lcp);
+    }
+    LOR_LAUNCH_CHECK();
+
+    // Segmented overlap.
+    {
+        ProfScope ps(PK_OVERLAP_SCAN, double(n) * 16, s);
+        const unsigned grid = unsigned(min64(cdiv(n, 256), 152 * 16));
+        k_seg_argmax<<<grid, 256, 0, s>>>(SA, lcp, PK, n, bstart, starts, nseq, best);
+    }
+    LOR_LAUNCH_CHECK();
+    const int64_t ntiles = cdiv(n, kScanTile);
+    {
+        ProfScope ps(PK_OVERLAP_COLLECT, double(n) * 16, s);
+        rs.epoch++;
+        k_seg_runs<<<unsigned(ntiles), kScanThreads, 0, s>>>(PK, bstart, lcp, best, n, run_id, d_runs,
+                                                            rs.lookback, rs.tile_ctr, rs.tile_base,
+                                                            rs.epoch, status);
+        LOR_LAUNCH_CHECK();
+        rs.tile_base += (unsigned long long)ntiles;
+        k_seg_qual<<<gridn(n, 256), 256, 0, s>>>(SA, PK, bstart, lcp, best, n, starts, nseq, run_id, qual);
+        LOR_LAUNCH_CHECK();
+        rs.epoch++;
+        k_seg_members<<<unsigned(ntiles), kScanThreads, 0, s>>>(SA, n, run_id, qual, mem, d_count,
+                                                               rs.lookback, rs.tile_ctr, rs.tile_base,
+                                                               rs.epoch, status, ntiles);
+        LOR_LAUNCH_CHECK();
+        rs.tile_base += (unsigned long long)ntiles;
+    }
+    uint32_t h_count = 0;
+    LOR_CUDA_TRY(cudaMemcpyAsync(&h_count, d_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LOR_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t m = h_count;
+    uint32_t *mr = mem, *mv;
+    if (m > 1) {
+        rc = radix_sort_pairs<uint32_t>(rs, mem, va, kb, vb, m, 0, bit_width_u64(uint64_t(n - 1)), true, &mr,
+                                        &mv);
+        if (rc) return rc;
+    }
+    if (m > 0) {
+        k_pair_count<<<gridn(m, 256), 256, 0, s>>>(mr, m, starts, nseq, cnt);
+        LOR_LAUNCH_CHECK();
+    }
+    k_group_finish<<<1, 128, 0, s>>>(SA, bstart, best, cnt, starts, nseq, np, o.pos_base, o.out, o.pos_off);
+    LOR_LAUNCH_CHECK();
+    if (m > 0 && o.pos_base < o.pos_cap) {
+        k_group_positions<<<gridn(m, 256), 256, 0, s>>>(mr, m, starts, nseq, o.pos_base, o.pos, o.pos_cap);
+        LOR_LAUNCH_CHECK();
+    }
+    *h_found = m;
+    return LOR_OK;
+}
+
 }  // namespace lor
 
 using namespace lor;
@@ -316,124 +428,14 @@ extern "C" int lor_batch_overlap(const uint8_t *d_ascii, const int64_t *h_lens, 
     const BatchLayout L = batch_layout(nmax);
     if (!d_ws || ws_bytes < L.total || (uintptr_t(d_ws) & 255)) return LOR_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    int *status = tu_status_ptr();
-    if (!status) return LOR_ERR_CUDA;
     char *ws = (char *)d_ws;
-    uint8_t *text = (uint8_t *)(ws + L.text);
-    int32_t *starts = (int32_t *)(ws + L.starts);
-    int32_t *sa = (int32_t *)(ws + L.sa);
     int64_t pos_base = 0;
     for (const Group &g : groups) {
-        const int nseq = 2 * g.np;
-        const int64_t n = g.n;
-        int rc = lor_encode_concat(d_ascii ? d_ascii + g.in0 : nullptr, h_lens + 2 * g.p0, nseq, text, starts,
-                                   stream);
+        const GroupOutputs o{d_out + g.p0, d_pos_off + g.p0, d_pos, pos_cap, pos_base};
+        int64_t m = 0;
+        const int rc = batch_group(d_ascii ? d_ascii + g.in0 : nullptr, h_lens + 2 * g.p0, g.np, g.n, ws,
+                                   ws_bytes, L, nmax, o, &m, s);
         if (rc) return rc;
-        rc = lor_build_sa(text, n, nseq + 5, sa, ws + L.region, ws_bytes - L.region, stream);
-        if (rc) return rc;
-        // The suffix-array workspace is free again: carve the group buffers.
-        RadixScratch rs;
-        rs.hist = (uint32_t *)(ws + L.hist);
-        rs.offsets = (uint32_t *)(ws + L.offsets);
-        rs.lookback = (uint64_t *)(ws + L.lookback);
-        rs.tile_ctr = (unsigned long long *)(ws + L.ctrl);
-        rs.max_tiles = cdiv(nmax, kMinSortTile);
-        rs.status = status;
-        rs.stream = s;
-        uint32_t *pk = (uint32_t *)(ws + L.pk), *pk2 = (uint32_t *)(ws + L.pk2);
-        int32_t *sa2 = (int32_t *)(ws + L.sa2), *isa = (int32_t *)(ws + L.isa);
-        int32_t *plcp = (int32_t *)(ws + L.plcp), *lcp = (int32_t *)(ws + L.lcp);
-        int32_t *run_id = (int32_t *)(ws + L.run_id), *bstart = (int32_t *)(ws + L.bstart);
-        int32_t *cnt = (int32_t *)(ws + L.cnt);
-        uint8_t *qual = (uint8_t *)(ws + L.qual);
-        uint32_t *mem = (uint32_t *)(ws + L.mem), *kb = (uint32_t *)(ws + L.kb);
-        uint32_t *va = (uint32_t *)(ws + L.va), *vb = (uint32_t *)(ws + L.vb);
-        unsigned long long *best = (unsigned long long *)(ws + L.best);
-        uint32_t *d_count = (uint32_t *)(ws + L.ctrl + 128);
-        uint32_t *d_runs = (uint32_t *)(ws + L.ctrl + 192);
-        int2 *ip = (int2 *)(ws + L.ip);
-        LOR_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, 256, s));
-        LOR_CUDA_TRY(cudaMemsetAsync(ws + L.lookback, 0, L.lookback_bytes, s));
-        LOR_CUDA_TRY(cudaMemsetAsync(best, 0, sizeof(unsigned long long) * kPairsPerGroup, s));
-        LOR_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * kPairsPerGroup, s));
-        LOR_CUDA_TRY(cudaMemsetAsync(qual, 0, size_t(n), s));
-
-        // Per-pair blocks of the suffix array (stable by pair id).
-        k_pair_keys<<<gridn(n, 256), 256, 0, s>>>(sa, n, starts, nseq, pk);
-        LOR_LAUNCH_CHECK();
-        uint32_t *kr, *vr;
-        rc = radix_sort_pairs<uint32_t>(rs, pk, (uint32_t *)sa, pk2, (uint32_t *)sa2, n, 0,
-                                        bit_width_u64(uint64_t(g.np - 1)), false, &kr, &vr);
-        if (rc) return rc;
-        const uint32_t *PK = kr;
-        const int32_t *SA = (const int32_t *)vr;
-        k_block_starts<<<gridn(n, 256), 256, 0, s>>>(PK, n, bstart);
-        LOR_LAUNCH_CHECK();
-
-        // LCP inside the blocks.
-        {
-            ProfScope ps(PK_ISA_SCATTER, double(n) * 16, s);
-            k_isa_phi<<<gridn(n, 256), 256, 0, s>>>(SA, n, PK, ip, status);
-        }
-        LOR_LAUNCH_CHECK();
-        {
-            ProfScope ps(PK_KASAI, double(n) * 18, s);
-            k_plcp<<<gridn(n, kPlcpTile), kPlcpThreads, 0, s>>>(text, n, ip, isa, plcp,
-                                                               (uintptr_t(text) & 3) == 0, status);
-        }
-        LOR_LAUNCH_CHECK();
-        {
-            ProfScope ps(PK_KASAI, double(n) * 12, s);
-            k_lcp_gather<<<gridn(n, 256), 256, 0, s>>>(SA, n, plcp, lcp);
-        }
-        LOR_LAUNCH_CHECK();
-
-        // Segmented overlap.
-        {
-            ProfScope ps(PK_OVERLAP_SCAN, double(n) * 16, s);
-            const unsigned grid = unsigned(min64(cdiv(n, 256), 152 * 16));
-            k_seg_argmax<<<grid, 256, 0, s>>>(SA, lcp, PK, n, bstart, starts, nseq, best);
-        }
-        LOR_LAUNCH_CHECK();
-        const int64_t ntiles = cdiv(n, kScanTile);
-        {
-            ProfScope ps(PK_OVERLAP_COLLECT, double(n) * 16, s);
-            rs.epoch++;
-            k_seg_runs<<<unsigned(ntiles), kScanThreads, 0, s>>>(PK, bstart, lcp, best, n, run_id, d_runs,
-                                                                rs.lookback, rs.tile_ctr, rs.tile_base,
-                                                                rs.epoch, status);
-            LOR_LAUNCH_CHECK();
-            rs.tile_base += (unsigned long long)ntiles;
-            k_seg_qual<<<gridn(n, 256), 256, 0, s>>>(SA, PK, bstart, lcp, best, n, starts, nseq, run_id, qual);
-            LOR_LAUNCH_CHECK();
-            rs.epoch++;
-            k_seg_members<<<unsigned(ntiles), kScanThreads, 0, s>>>(SA, n, run_id, qual, mem, d_count,
-                                                                   rs.lookback, rs.tile_ctr, rs.tile_base,
-                                                                   rs.epoch, status, ntiles);
-            LOR_LAUNCH_CHECK();
-            rs.tile_base += (unsigned long long)ntiles;
-        }
-        uint32_t h_count = 0;
-        LOR_CUDA_TRY(cudaMemcpyAsync(&h_count, d_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        LOR_CUDA_TRY(cudaStreamSynchronize(s));
-        const int64_t m = h_count;
-        uint32_t *mr = mem, *mv;
-        if (m > 1) {
-            rc = radix_sort_pairs<uint32_t>(rs, mem, va, kb, vb, m, 0, bit_width_u64(uint64_t(n - 1)), true, &mr,
-                                            &mv);
-            if (rc) return rc;
-        }
-        if (m > 0) {
-            k_pair_count<<<gridn(m, 256), 256, 0, s>>>(mr, m, starts, nseq, cnt);
-            LOR_LAUNCH_CHECK();
-        }
-        k_group_finish<<<1, 128, 0, s>>>(SA, bstart, best, cnt, starts, nseq, g.np, pos_base, d_out + g.p0,
-                                         d_pos_off + g.p0);
-        LOR_LAUNCH_CHECK();
-        if (m > 0 && pos_base < pos_cap) {
-            k_group_positions<<<gridn(m, 256), 256, 0, s>>>(mr, m, starts, nseq, pos_base, d_pos, pos_cap);
-            LOR_LAUNCH_CHECK();
-        }
         pos_base += m;
     }
     return LOR_OK;

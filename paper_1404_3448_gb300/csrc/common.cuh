@@ -216,8 +216,8 @@ __device__ __forceinline__ uint32_t warp_lookback(uint64_t *lb, int64_t tile, ui
         return h;                                                                     \
     }                                                                                 \
     static int *tu_status_ptr() {                                                     \
-        static int *p = nullptr;                                                      \
-        static int dev = -1;                                                          \
+        static thread_local int *p = nullptr;                                         \
+        static thread_local int dev = -1;                                             \
         int cur = -1;                                                                 \
         cudaGetDevice(&cur);                                                          \
         if (p == nullptr || dev != cur) {                                             \
@@ -237,3 +237,10 @@ int lor_status_overlap(cudaStream_t s, int clear);
 int lor_status_rmq(cudaStream_t s, int clear);
 int lor_status_abi(cudaStream_t s, int clear);
 int lor_status_batch(cudaStream_t s, int clear);
+int lor_status_serve(cudaStream_t s, int clear);
+
+namespace lor {
+// Sparse-table rows 0..levels-1 over lcp[0..n) (rmq.cu); rows are
+// row_stride(n) = n rounded up to 64 entries apart, table 256-byte aligned.
+int rmq_build_levels(const int32_t *d_lcp, int64_t n, int levels, int32_t *d_table, cudaStream_t s);
+}  // namespace lor

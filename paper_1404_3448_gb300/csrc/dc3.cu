@@ -732,7 +732,7 @@ struct TraceRow {
     int64_t n, names;
     int32_t key_bits;
 };
-std::vector<TraceRow> g_trace;
+thread_local std::vector<TraceRow> g_trace;
 
 int level0_kchars(int bits) {
     int k = 3;
@@ -969,7 +969,7 @@ struct TraceExtra {
     int strategy;  // 0 sort, 1 dense, 2 parent order
     int64_t dups;
 };
-std::vector<TraceExtra> g_trace_extra;
+thread_local std::vector<TraceExtra> g_trace_extra;
 
 template <typename CharT>
 int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32_t *out, const int32_t *PS,

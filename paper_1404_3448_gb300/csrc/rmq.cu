@@ -173,14 +173,8 @@ extern "C" int64_t lor_rmq_table_elems(int64_t n) {
     return int64_t(levels_for(n)) * row_stride(n);
 }
 
-extern "C" int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
-                             lor_stream_t stream) {
-    if (!d_lcp || !d_table || n < 1) return LOR_ERR_INVALID_ARG;
-    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
-    if (table_elems < lor_rmq_table_elems(n)) return LOR_ERR_WORKSPACE;
-    if (uintptr_t(d_table) & 255) return LOR_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int J = levels_for(n);
+int lor::rmq_build_levels(const int32_t *d_lcp, int64_t n, int J, int32_t *d_table, cudaStream_t s) {
+    if (J < 1 || J > levels_for(n)) return LOR_ERR_INVALID_ARG;
     const int64_t stride = row_stride(n);
     const int top = J - 1 < kLowLevels ? J - 1 : kLowLevels;
     {
@@ -203,6 +197,15 @@ extern "C" int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, 
         LOR_LAUNCH_CHECK();
     }
     return LOR_OK;
+}
+
+extern "C" int lor_rmq_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
+                             lor_stream_t stream) {
+    if (!d_lcp || !d_table || n < 1) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    if (table_elems < lor_rmq_table_elems(n)) return LOR_ERR_WORKSPACE;
+    if (uintptr_t(d_table) & 255) return LOR_ERR_INVALID_ARG;
+    return rmq_build_levels(d_lcp, n, levels_for(n), d_table, (cudaStream_t)stream);
 }
 
 extern "C" int lor_rmq_query(const int32_t *d_table, const int32_t *d_isa, int64_t n, const int32_t *d_p,

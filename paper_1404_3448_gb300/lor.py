@@ -26,6 +26,7 @@ LOR_ERR_WORKSPACE = -4
 LOR_ERR_CUDA = -5
 LOR_ERR_TIMEOUT = -6
 LOR_ERR_BAD_INPUT = -7
+LOR_ERR_CANCELLED = -8
 LOR_MAX_SEQ = 250
 
 OVERLAP_FIELDS = ("length", "rank", "seq_a", "pos_a", "seq_b", "pos_b", "n_pos", "reserved")
@@ -79,6 +80,15 @@ def load():
         "lor_profile_kinds": ([], ctypes.c_int),
         "lor_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
         "lor_profile_read": ([ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "lor_server_batch_bytes": ([vp, i32, vp], sz),
+        "lor_server_create": ([vp, vp], ctypes.c_int),
+        "lor_server_submit": ([vp, vp, i64, vp, i64, ctypes.c_uint64, vp], ctypes.c_int),
+        "lor_server_poll": ([vp, vp, i32, i32], ctypes.c_int),
+        "lor_server_query": ([vp, i64, vp, vp, i32, vp], ctypes.c_int),
+        "lor_server_release": ([vp, i64], ctypes.c_int),
+        "lor_server_stats_get": ([vp, vp], ctypes.c_int),
+        "lor_server_now": ([vp], ctypes.c_double),
+        "lor_server_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -324,6 +334,123 @@ class Batch:
             d["positions"] = pos[a:min(b, self.pos_cap)].astype(np.int64)
             res.append(d)
         return res
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("workers", ctypes.c_int32),
+                ("max_batch_pairs", ctypes.c_int32), ("max_batch_symbols", ctypes.c_int64)]
+
+
+class Overlap(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in OVERLAP_FIELDS]
+
+
+class Served(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("batch_pairs", ctypes.c_int32), ("ov", Overlap),
+                ("positions", ctypes.POINTER(ctypes.c_int32)), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "released", "batches", "pairs",
+                                              "bases", "admission_waits", "queries")] + \
+               [(f, ctypes.c_size_t) for f in ("reserved_bytes", "in_use_bytes", "peak_bytes")] + \
+               [("pending", ctypes.c_int32), ("in_flight", ctypes.c_int32)]
+
+
+def server_batch_bytes(lens):
+    """(workspace bytes, resident bytes) one batch of these pair lengths takes."""
+    lens = np.ascontiguousarray(np.asarray(lens, dtype=np.int64))
+    res = ctypes.c_size_t(0)
+    work = load().lor_server_batch_bytes(lens.ctypes.data, int(lens.size // 2), ctypes.byref(res))
+    return int(work), int(res.value)
+
+
+class Server:
+    """Request server of liblor (lor_server_*): submit pairs, poll results,
+    ask LCP queries on a polled request, release it."""
+
+    def __init__(self, budget_bytes, workers=2, max_batch_pairs=125, max_batch_symbols=1 << 28):
+        L = load()
+        cfg = ServerConfig(int(budget_bytes), int(workers), int(max_batch_pairs), int(max_batch_symbols))
+        h = ctypes.c_void_p()
+        _check(L.lor_server_create(ctypes.byref(cfg), ctypes.byref(h)), "lor_server_create")
+        self._L, self._h = L, h
+        self._keep = {}
+        self._buf = (Served * 256)()
+
+    def submit_ptr(self, ptr_a, len_a, ptr_b, len_b, tag=0) -> int:
+        """Queue a pair given host pointers that stay valid until polled."""
+        rid = ctypes.c_int64(0)
+        _check(self._L.lor_server_submit(self._h, ptr_a or None, int(len_a), ptr_b or None, int(len_b),
+                                         int(tag), ctypes.byref(rid)), "lor_server_submit")
+        return int(rid.value)
+
+    def submit(self, a, b, tag=0) -> int:
+        """Queue a pair of host uint8 arrays (kept alive until polled)."""
+        a = np.ascontiguousarray(a, dtype=np.uint8)
+        b = np.ascontiguousarray(b, dtype=np.uint8)
+        rid = self.submit_ptr(a.ctypes.data if a.size else None, a.size,
+                              b.ctypes.data if b.size else None, b.size, tag)
+        self._keep[rid] = (a, b)
+        return rid
+
+    def poll(self, timeout_ms=10, cap=256) -> list:
+        k = self._L.lor_server_poll(self._h, self._buf, min(cap, len(self._buf)), int(timeout_ms))
+        if k < 0:
+            raise LorError(k, "lor_server_poll")
+        out = []
+        for i in range(k):
+            r = self._buf[i]
+            d = {f: getattr(r.ov, f) for f in OVERLAP_FIELDS}
+            n = d["n_pos"] if r.status == LOR_OK else 0
+            d["positions"] = (np.ctypeslib.as_array(r.positions, shape=(n,)).astype(np.int64)
+                              if n else np.zeros(0, np.int64))
+            d.update(id=r.id, tag=r.tag, status=r.status, batch_pairs=r.batch_pairs,
+                     t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done)
+            self._keep.pop(r.id, None)
+            out.append(d)
+        return out
+
+    def query(self, rid, p, q) -> np.ndarray:
+        p = np.ascontiguousarray(p, dtype=np.int32)
+        q = np.ascontiguousarray(q, dtype=np.int32)
+        if p.shape != q.shape:
+            raise ValueError("p and q differ in length")
+        out = np.empty(p.size, dtype=np.int32)
+        _check(self._L.lor_server_query(self._h, int(rid), p.ctypes.data, q.ctypes.data, p.size,
+                                        out.ctypes.data), "lor_server_query")
+        return out
+
+    def release(self, rid):
+        _check(self._L.lor_server_release(self._h, int(rid)), "lor_server_release")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._L.lor_server_stats_get(self._h, ctypes.byref(st)), "lor_server_stats_get")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def now(self) -> float:
+        return float(self._L.lor_server_now(self._h))
+
+    def close(self):
+        if self._h:
+            self._L.lor_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def overlap_dict(out: torch.Tensor, pos: torch.Tensor, seq_starts=None) -> dict:

@@ -3,6 +3,8 @@ header declares, and rejects bad arguments before touching a device."""
 import ctypes
 import re
 
+import numpy as np
+
 import pytest
 
 import __graft_entry__
@@ -40,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for code in [0, -1, -2, -3, -4, -5, -6, -7]:
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8]:
         s = L.lor_status_string(code)
         assert s and s != "unknown status"
     assert L.lor_status_string(-99) == "unknown status"
@@ -102,3 +104,46 @@ def test_no_oracle_in_product_path():
                 txt = open(os.path.join(root, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "lor_oracle" not in txt, f
+
+
+def test_server_batch_bytes_host_only(lib):
+    work1, res1 = L.server_batch_bytes([1000, 2000])
+    assert work1 > 0 and res1 > 0
+    # one pair: workspace covers the grouped pipeline (text 3002 symbols) plus
+    # input, records and positions; resident = ISA + 12 table rows (3002 < 2^12)
+    n = 3002
+    assert res1 >= 4 * n + 4 * 12 * n
+    assert work1 >= L.lor_batch_workspace_size(np.array([1000, 2000], np.int64).ctypes.data, 1)
+    work2, res2 = L.server_batch_bytes([1000, 2000, 5, 7])
+    assert work2 >= work1 and res2 >= res1
+    # more pairs than one group holds, negative lengths: rejected
+    assert L.server_batch_bytes([10] * 252) == (0, 0)
+    assert L.server_batch_bytes([10, -1]) == (0, 0)
+
+
+def test_server_config_validation_is_host_only(lib):
+    bad = [
+        L.ServerConfig(1 << 30, 0, 8, 1 << 20),    # no workers
+        L.ServerConfig(1 << 30, 9, 8, 1 << 20),    # too many workers
+        L.ServerConfig(1 << 30, 2, 126, 1 << 20),  # more pairs than one group holds
+        L.ServerConfig(1 << 30, 2, 8, 0),
+        L.ServerConfig(1 << 30, 2, 8, (1 << 28) + 1),
+        L.ServerConfig(1000, 2, 8, 1 << 20),       # below one granule
+    ]
+    for cfg in bad:
+        h = ctypes.c_void_p()
+        assert lib.lor_server_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LOR_ERR_INVALID_ARG
+        assert not h.value
+    assert lib.lor_server_create(None, None) == L.LOR_ERR_INVALID_ARG
+    for fn, args in [("lor_server_poll", (None, None, 1, 0)), ("lor_server_release", (None, 1)),
+                     ("lor_server_stats_get", (None, None)), ("lor_server_destroy", (None,)),
+                     ("lor_server_query", (None, 1, None, None, 1, None))]:
+        assert getattr(lib, fn)(*args) == L.LOR_ERR_INVALID_ARG
+
+
+@pytest.mark.skipif(L.torch.cuda.is_available(), reason="checks the no-device path")
+def test_server_create_without_device_fails_cleanly(lib):
+    cfg = L.ServerConfig(1 << 26, 1, 8, 1 << 20)
+    h = ctypes.c_void_p()
+    assert lib.lor_server_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LOR_ERR_CUDA
+    assert not h.value
