@@ -323,8 +323,10 @@ uint64_t lor_launch_count(void);
 /* Per-level trace of the most recent lor_build_sa call on the calling thread:
  * fills up to cap entries of level length n_l, distinct names found at that
  * level, key bits of the sample keys, how the sample was ordered (0 radix
- * sort, 1 dense naming table, 2 the parent level's order) and how many
- * samples shared their first symbol (strategy 2); any pointer may be NULL.
+ * sort, 1 dense naming table, 2 the parent level's order, 3 prefix doubling
+ * of the reduced string in place of a DC3 level) and how many samples shared
+ * their first symbol (strategy 2) or their name (strategy 3); any pointer
+ * may be NULL.
  * Returns the number of levels. */
 int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits, int32_t *h_strategy,
                        int64_t *h_dups, int32_t cap);

@@ -728,6 +728,91 @@ __global__ void k_par_ns_writeback(const uint32_t *__restrict__ v, int64_t m, co
 
 // ---------------------------------------------------------------- host driver
 
+// ---- Prefix doubling on a reduced string whose names are almost unique
+//
+// When a level's names leave only a few samples sharing a name, the suffix
+// array of its reduced string R follows from the name order by prefix
+// doubling over the groups of equal names instead of one more DC3 level (the
+// result is the same suffix array of R).  The rank of an R-suffix is one
+// plus the index of the first element of its group in the current order.
+// The pass with step h orders every unresolved group by (rank(j),
+// rank(j + h)), rank 0 past the end of R, after which the order is by the
+// first 2h symbols of R; a group of one is final.
+
+// headof[v] = 1 + index of the first sample named v in name order.
+__global__ void k_dbl_headof(const int32_t *__restrict__ NS, int64_t m, int32_t *__restrict__ headof) {
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k < m && (k == 0 || NS[k] != NS[k - 1])) headof[NS[k]] = int32_t(k + 1);
+}
+
+// R[j] = rank of R-suffix j by its first symbol.
+__global__ void k_dbl_init(int32_t *__restrict__ R, int64_t m, const int32_t *__restrict__ headof) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j < m) R[j] = headof[R[j]];
+}
+
+// Positions (in name order) of samples that share their name.
+__global__ void __launch_bounds__(kScanThreads) k_dbl_unresolved(
+    const int32_t *__restrict__ NS, int64_t m, uint32_t *__restrict__ ul, uint32_t *count, uint64_t *lb,
+    unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch, int *status, int64_t ntiles) {
+    tile_compact(
+        m,
+        [&](int64_t k) {
+            const int32_t v = NS[k];
+            return (k > 0 && NS[k - 1] == v) || (k + 1 < m && NS[k + 1] == v);
+        },
+        [&](int64_t k, uint32_t d) { ul[d] = uint32_t(k); }, lb, ctr, tile_base, epoch, status, count, ntiles);
+}
+
+__global__ void k_dbl_keys(const uint32_t *__restrict__ ul, int64_t U, const int32_t *__restrict__ SAR,
+                           const int32_t *__restrict__ R, int64_t m, int64_t h, int shift,
+                           uint64_t *__restrict__ key, uint32_t *__restrict__ val) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= U) return;
+    const int32_t j = SAR[ul[i]];
+    const uint32_t r2 = j + h < m ? uint32_t(R[j + h]) : 0u;
+    key[i] = (uint64_t(uint32_t(R[j])) << shift) | r2;
+    val[i] = uint32_t(j);
+}
+
+// Sorted unresolved samples go back to their slots; run ids and run starts
+// of the refined groups.
+__global__ void __launch_bounds__(kScanThreads) k_dbl_runs(
+    const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, const uint32_t *__restrict__ ul,
+    int64_t U, int32_t *__restrict__ SAR, uint32_t *__restrict__ runid, uint32_t *__restrict__ rstart,
+    uint32_t *n_runs, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
+    int *status) {
+    tile_names(
+        U, [&](int64_t i) { return i == 0 || key[i] != key[i - 1]; },
+        [&](int64_t i, uint32_t r) {
+            SAR[ul[i]] = int32_t(val[i]);
+            runid[i] = r;
+            if (i == 0 || key[i] != key[i - 1]) rstart[r - 1] = uint32_t(i);
+        },
+        n_runs, lb, ctr, tile_base, epoch, status);
+}
+
+__global__ void k_dbl_rank(const uint32_t *__restrict__ val, const uint32_t *__restrict__ runid,
+                           const uint32_t *__restrict__ rstart, const uint32_t *__restrict__ ul, int64_t U,
+                           int32_t *__restrict__ R) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < U) R[val[i]] = int32_t(ul[rstart[runid[i] - 1]] + 1);
+}
+
+// Samples whose refined group still holds more than one.
+__global__ void __launch_bounds__(kScanThreads) k_dbl_next(
+    const uint32_t *__restrict__ runid, const uint32_t *__restrict__ ul, int64_t U, uint32_t *__restrict__ ul2,
+    uint32_t *count, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
+    int *status, int64_t ntiles) {
+    tile_compact(
+        U,
+        [&](int64_t i) {
+            const uint32_t r = runid[i];
+            return (i > 0 && runid[i - 1] == r) || (i + 1 < U && runid[i + 1] == r);
+        },
+        [&](int64_t i, uint32_t d) { ul2[d] = ul[i]; }, lb, ctr, tile_base, epoch, status, count, ntiles);
+}
+
 struct TraceRow {
     int64_t n, names;
     int32_t key_bits;
@@ -750,6 +835,7 @@ struct Dc3Run {
     char *ws;
     Dc3Layout L;
     RadixScratch rs;
+    int doubling;       // 0 never, 1 when names are almost unique, 2 whenever names repeat
     uint32_t *d_names;  // count read back after naming
     uint32_t *d_count;  // count read back after a compaction
     uint64_t *t64[3];
@@ -966,10 +1052,68 @@ int sample_from_parent(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits,
 }
 
 struct TraceExtra {
-    int strategy;  // 0 sort, 1 dense, 2 parent order
+    int strategy;  // 0 sort, 1 dense, 2 parent order, 3 prefix doubling
     int64_t dups;
 };
 thread_local std::vector<TraceExtra> g_trace_extra;
+
+// Suffix array of the reduced string R (length m, names in R order in Rl,
+// samples in name order in SAR with their names in NSl) by prefix doubling;
+// leaves SA_R in SAR and rank(R-suffix) in Rl, like a returned recursion
+// followed by the rank scatter.  *U0 receives the initial unresolved count.
+int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_t *NSl, int64_t *U0) {
+    cudaStream_t st = D.s;
+    int32_t *headof = (int32_t *)D.t32[0];
+    uint32_t *ul = D.t32[1], *ul2 = D.t32[2], *runid = D.t32[3], *val = D.t32[4], *rstart = D.t32[5];
+    uint32_t *valt = D.t32[0];  // headof is dead once the ranks are initialised
+    uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
+    {
+        ProfScope ps(PK_NAMING, double(m) * 16, st);
+        k_dbl_headof<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof);
+        LOR_LAUNCH_CHECK();
+        k_dbl_init<<<grid_for(m, 256), 256, 0, st>>>(Rl, m, headof);
+        LOR_LAUNCH_CHECK();
+        const int64_t ntiles = cdiv(m, kScanTile);
+        LOR_TILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, D.d_count, LB_ARGS(D), ntiles);
+    }
+    uint32_t hU = 0;
+    int rc = read_u32(D, D.d_count, &hU);
+    if (rc) return rc;
+    *U0 = hU;
+    const int shift = bit_width_u64(uint64_t(m));
+    for (int64_t h = 1; hU > 0; h *= 2) {
+        if (h >= m) return LOR_ERR_BAD_INPUT;  // cannot happen for a valid R
+        const int64_t U = hU;
+        {
+            ProfScope ps(PK_SAMPLE_KEYS, double(U) * 24, st);
+            k_dbl_keys<<<grid_for(U, 256), 256, 0, st>>>(ul, U, SAR, Rl, m, h, shift, k0, val);
+            LOR_LAUNCH_CHECK();
+        }
+        uint64_t *kr;
+        uint32_t *vr;
+        rc = radix_sort_pairs<uint64_t>(D.rs, k0, val, k1, valt, U, 0, 2 * shift, false, &kr, &vr);
+        if (rc) return rc;
+        {
+            ProfScope ps(PK_NAMING, double(U) * 32, st);
+            LOR_TILE_LAUNCH(D, U, k_dbl_runs, kr, vr, ul, U, SAR, runid, rstart, D.d_names, LB_ARGS(D));
+            k_dbl_rank<<<grid_for(U, 256), 256, 0, st>>>(vr, runid, rstart, ul, U, Rl);
+            LOR_LAUNCH_CHECK();
+            const int64_t ntiles = cdiv(U, kScanTile);
+            LOR_TILE_LAUNCH(D, U, k_dbl_next, runid, ul, U, ul2, D.d_count, LB_ARGS(D), ntiles);
+        }
+        rc = read_u32(D, D.d_count, &hU);
+        if (rc) return rc;
+        uint32_t *t = ul;
+        ul = ul2;
+        ul2 = t;
+    }
+    return LOR_OK;
+}
+
+// Doubling replaces the next level when at most 1/kDoublingShare of the
+// samples lost their name to a duplicate (LOR_DC3_DOUBLING: "0" never,
+// "force" whenever names repeat; a test hook).
+constexpr int64_t kDoublingShare = 16;
 
 template <typename CharT>
 int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32_t *out, const int32_t *PS,
@@ -1010,7 +1154,15 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     if (rc) return rc;
     g_trace.push_back(TraceRow{n, int64_t(names), key_bits});
     g_trace_extra.push_back(TraceExtra{strategy, dups});
-    if (int64_t(names) < z.n02) {
+    const int64_t lost = z.n02 - int64_t(names);
+    if (lost > 0 && sorted_list &&
+        (D.doubling == 2 || (D.doubling == 1 && lost * kDoublingShare <= z.n02))) {
+        int64_t u0 = 0;
+        rc = sa_by_doubling(D, Rl, z.n02, SAR, NSl, &u0);
+        if (rc) return rc;
+        g_trace.push_back(TraceRow{z.n02, z.n02, 0});
+        g_trace_extra.push_back(TraceExtra{3, u0});
+    } else if (lost > 0) {
         rc = dc3_level<int32_t>(D, lvl + 1, Rl, z.n02, int64_t(names), SAR, sorted_list ? SAR : nullptr,
                                 sorted_list ? NSl : nullptr);
         if (rc) return rc;
@@ -1124,6 +1276,8 @@ extern "C" int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int
     {
         const char *e = std::getenv("LOR_DC3_STRATEGY");
         D.force_lsd = e && e[0] == 's';  // "sort": radix-sort every level (test hook)
+        const char *d = std::getenv("LOR_DC3_DOUBLING");
+        D.doubling = !d ? 1 : (d[0] == '0' ? 0 : (d[0] == 'f' ? 2 : 1));
     }
     LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.ctrl, 0, 256, D.s));
     LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.lookback, 0, D.L.lookback_bytes, D.s));

@@ -506,7 +506,7 @@ def last_dc3_trace():
     cnt = load().lor_last_dc3_trace(n.ctypes.data, names.ctypes.data, bits.ctypes.data,
                                     strat.ctypes.data, dups.ctypes.data, cap)
     cnt = min(cnt, cap)
-    kinds = ("sort", "dense", "parent")
+    kinds = ("sort", "dense", "parent", "doubling")
     return [dict(n=int(n[i]), names=int(names[i]), key_bits=int(bits[i]),
                  strategy=kinds[int(strat[i])], dups=int(dups[i])) for i in range(cnt)]
 

@@ -130,10 +130,26 @@ def test_encode_bad_symbol_reports_status(L):
 
 # ------------------------------------------------------------------ fuzz
 
-@pytest.mark.parametrize("strategy", ["auto", "sort"])
-def test_fuzz_small_full_path(L, O, strategy, monkeypatch):
+# How DC3 orders each level: "auto" (the library's choice), "sort" (radix
+# sort at every level and full recursion), "dbl" (prefix doubling of the
+# reduced string whenever a sorted level's names repeat).
+STRATEGIES = ["auto", "sort", "dbl"]
+
+
+def set_strategy(monkeypatch, strategy):
     if strategy == "sort":
         monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
+        monkeypatch.setenv("LOR_DC3_DOUBLING", "0")
+    elif strategy == "dbl":
+        monkeypatch.setenv("LOR_DC3_DOUBLING", "force")
+    elif strategy == "nodbl":
+        monkeypatch.setenv("LOR_DC3_DOUBLING", "0")
+
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_fuzz_small_full_path(L, O, strategy, monkeypatch):
+    set_strategy(monkeypatch, strategy)
     for seed in range(60):
         nseq = [2, 2, 3, 5][seed % 4]
         alpha = [b"ACGT", b"AC", b"A", b"ACGT"][seed % 4 if seed % 7 else 2]
@@ -166,11 +182,10 @@ SIZES = [1, 2, 3, 4, 5, 6, 7, 31, 32, 33, 1023, 1024, 1025, 2047, 2048, 2049, 40
          6143, 6144, 8191, 8193, 12287, 65537, 131071, 300001]
 
 
-@pytest.mark.parametrize("strategy", ["auto", "sort"])
+@pytest.mark.parametrize("strategy", STRATEGIES)
 @pytest.mark.parametrize("alpha", [b"ACGT", b"AC", b"A"])
 def test_sizes_span_tiles(L, O, alpha, strategy, monkeypatch):
-    if strategy == "sort":
-        monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
+    set_strategy(monkeypatch, strategy)
     rng = np.random.default_rng(len(alpha))
     a = np.frombuffer(alpha, np.uint8)
     for total in SIZES:
@@ -183,12 +198,11 @@ def test_sizes_span_tiles(L, O, alpha, strategy, monkeypatch):
         assert_full_parity(O, g, e, table=total < 5000)
 
 
-@pytest.mark.parametrize("strategy", ["auto", "sort"])
+@pytest.mark.parametrize("strategy", STRATEGIES + ["nodbl"])
 @pytest.mark.parametrize("k0", ["3", "4", "7", "10", "21"])
 def test_level0_prefix_lengths(L, O, k0, strategy, monkeypatch):
     monkeypatch.setenv("LOR_DC3_K0", k0)
-    if strategy == "sort":
-        monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
+    set_strategy(monkeypatch, strategy)
     seqs, _ = gen.pair_noncoding(n_each=150_000, seed=31, shared_len=4000, core=900)
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -196,6 +210,7 @@ def test_level0_prefix_lengths(L, O, k0, strategy, monkeypatch):
 
 
 def test_deep_recursion_single_symbol(L, O):
+    # names stay few at every level, so no level is replaced by doubling
     seqs = [np.full(20000, ord("A"), np.uint8), np.full(15001, ord("A"), np.uint8)]
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -203,13 +218,27 @@ def test_deep_recursion_single_symbol(L, O):
     trace = L.last_dc3_trace()
     last = trace[-1]
     assert len(trace) >= 8 and last["names"] == (last["n"] + 2) // 3 + last["n"] // 3
+    assert "doubling" not in {t["strategy"] for t in trace}
+
+
+@pytest.mark.parametrize("seqlen", [35001, 4096])
+def test_doubling_on_one_symbol_runs(L, O, seqlen, monkeypatch):
+    # forced doubling from level 0: every group splits by one suffix per pass
+    set_strategy(monkeypatch, "dbl")
+    monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
+    seqs = [np.full(seqlen, ord("A"), np.uint8), np.full(seqlen // 2, ord("A"), np.uint8)]
+    e = oracle_path(O, seqs, nthreads=NCPU)
+    g = gpu_path(L, seqs, rmq=False)
+    assert_full_parity(O, g, e, table=False)
+    trace = L.last_dc3_trace()
+    assert [t["strategy"] for t in trace] == ["sort", "doubling"], trace
 
 
 def test_wide_triples_two_stage_sort(L, O, monkeypatch):
     # radix sorts at every level: level-2 names need > 21 bits, so level-3
     # triples exceed 64 bits
     monkeypatch.setenv("LOR_DC3_K0", "3")
-    monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
+    set_strategy(monkeypatch, "sort")
     seqs, _ = gen.pair_uniform(n_each=4_500_000, plant_len=700, seed=41)
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -251,16 +280,27 @@ def test_tiny_workload_2x100k(L, O):
     assert g["overlap"]["length"] >= info["plant_len"]
 
 
-def test_noncoding_workload_2x16M(L, O):
+@pytest.fixture(scope="module")
+def noncoding_16M(O):
     seqs, info = gen.pair_noncoding()
     e = oracle_path(O, seqs, nthreads=NCPU)
     p, q = gen.random_queries(len(e["text"]), count=200_000, seed=2)
+    return seqs, info, e, p, q, O.lcp_pairs(e["text"], p, q)
+
+
+@pytest.mark.parametrize("strategy", ["auto", "nodbl"])
+def test_noncoding_workload_2x16M(L, O, noncoding_16M, strategy, monkeypatch):
+    set_strategy(monkeypatch, strategy)
+    seqs, info, e, p, q, answers = noncoding_16M
     g = gpu_path(L, seqs, (p, q), rmq=True)
     assert_full_parity(O, g, e, table=False)
-    np.testing.assert_array_equal(g["answers"], O.lcp_pairs(e["text"], p, q))
+    np.testing.assert_array_equal(g["answers"], answers)
     assert g["overlap"]["length"] >= info["core"]
-    used = {t["strategy"] for t in L.last_dc3_trace()}
-    assert used == {"dense", "sort", "parent"}, L.last_dc3_trace()
+    used = [t["strategy"] for t in L.last_dc3_trace()]
+    if strategy == "nodbl":
+        assert set(used) == {"dense", "sort", "parent"}, L.last_dc3_trace()
+    else:
+        assert used[-1] == "doubling" and "sort" in used, L.last_dc3_trace()
 
 
 def test_large_workload_2x128M(L, O):
@@ -272,6 +312,7 @@ def test_large_workload_2x128M(L, O):
     text, starts, _ = O.encode_concat(seqs)
     p, q = gen.random_queries(len(text), count=1_000_000)
     g = gpu_path(L, seqs, (p, q), pos_cap=1 << 16, rmq=True)
+    assert L.last_dc3_trace()[-1]["strategy"] == "doubling", L.last_dc3_trace()
     del g["table"]
     np.testing.assert_array_equal(g["text"], text)
     assert O.check_suffix_array(text, g["sa"], nthreads=NCPU) == -1
