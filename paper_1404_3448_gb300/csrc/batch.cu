@@ -268,6 +268,7 @@ BatchLayout batch_layout(int64_t nmax) {
     L.kb = rtake(n4);
     L.va = rtake(n4);
     L.vb = rtake(n4);
+    L.packed = rtake(packed_text_bytes(nmax));
     L.bstart = rtake(sizeof(int32_t) * kPairsPerGroup);
     L.best = rtake(sizeof(unsigned long long) * kPairsPerGroup);
     L.cnt = rtake(sizeof(int32_t) * kPairsPerGroup);
@@ -339,10 +340,15 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
         k_isa_phi<<<gridn(n, 256), 256, 0, s>>>(SA, n, PK, ip, status);
     }
     LOR_LAUNCH_CHECK();
+    const PackedText T = packed_text_at(ws + L.packed, n);
+    {
+        ProfScope ps(PK_KASAI, double(n) * (2 + 0.375), s);
+        rc = pack_text(text, n, T, s);
+        if (rc) return rc;
+    }
     {
         ProfScope ps(PK_KASAI, double(n) * 18, s);
-        k_plcp<<<gridn(n, kPlcpTile), kPlcpThreads, 0, s>>>(text, n, ip, isa, plcp,
-                                                           (uintptr_t(text) & 3) == 0, status);
+        k_plcp_packed<<<gridn(n, kPlcpTile), kPlcpThreads, 0, s>>>(text, T, n, ip, isa, plcp, status);
     }
     LOR_LAUNCH_CHECK();
     {

@@ -18,7 +18,7 @@ struct BatchLayout {
     size_t text = 0, starts = 0, sa = 0, region = 0, total = 0;
     size_t ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
     size_t pk = 0, pk2 = 0, sa2 = 0, ip = 0, isa = 0, plcp = 0, lcp = 0, run_id = 0, qual = 0;
-    size_t mem = 0, kb = 0, va = 0, vb = 0, bstart = 0, best = 0, cnt = 0, post = 0;
+    size_t mem = 0, kb = 0, va = 0, vb = 0, packed = 0, bstart = 0, best = 0, cnt = 0, post = 0;
 };
 
 BatchLayout batch_layout(int64_t nmax);

@@ -745,6 +745,14 @@ __global__ void k_dbl_headof(const int32_t *__restrict__ NS, int64_t m, int32_t 
     if (k < m && (k == 0 || NS[k] != NS[k - 1])) headof[NS[k]] = int32_t(k + 1);
 }
 
+// H[k] = headof[NS[k]]: the rank of every sample in name order (NS is sorted,
+// so the table reads are monotone).
+__global__ void k_dbl_heads(const int32_t *__restrict__ NS, int64_t m, const int32_t *__restrict__ headof,
+                            uint32_t *__restrict__ H) {
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k < m) H[k] = uint32_t(headof[NS[k]]);
+}
+
 // R[j] = rank of R-suffix j by its first symbol.
 __global__ void k_dbl_init(int32_t *__restrict__ R, int64_t m, const int32_t *__restrict__ headof) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -914,7 +922,7 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
         LOR_TILE_LAUNCH(D, z.n02, k_name<KeyT>, kr, vr, z.n02, bucket_names(D, z) ? nullptr : Rl, SAR, NSl,
                         D.d_names, LB_ARGS(D));
     }
-    return bucket_names(D, z) ? names_scatter(D, SAR, NSl, z.n02, Rl) : LOR_OK;
+    return LOR_OK;  // large levels: R is written by dc3_level once it knows how to continue
 }
 
 // Triples too wide for 64 bits: stable sort by (t_i+1, t_i+2), then by t_i.
@@ -949,7 +957,7 @@ int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, in
         LOR_TILE_LAUNCH(D, z.n02, k_name_gather<CharT>, vr2, z.n02, s, z.n, z.n0,
                         bucket_names(D, z) ? nullptr : Rl, SAR, NSl, D.d_names, LB_ARGS(D));
     }
-    return bucket_names(D, z) ? names_scatter(D, SAR, NSl, z.n02, Rl) : LOR_OK;
+    return LOR_OK;  // large levels: R is written by dc3_level once it knows how to continue
 }
 
 // ---- Step 1, strategy "dense": names from a table of present keys.
@@ -1048,7 +1056,7 @@ int sample_from_parent(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits,
         LOR_TILE_LAUNCH(D, z.n02, k_par_name, SL, PRI, SEC, z.n02, bucket_names(D, z) ? nullptr : Rl, SAR,
                         NSl, D.d_names, LB_ARGS(D));
     }
-    return bucket_names(D, z) ? names_scatter(D, SAR, NSl, z.n02, Rl) : LOR_OK;
+    return LOR_OK;  // large levels: R is written by dc3_level once it knows how to continue
 }
 
 struct TraceExtra {
@@ -1061,18 +1069,35 @@ thread_local std::vector<TraceExtra> g_trace_extra;
 // samples in name order in SAR with their names in NSl) by prefix doubling;
 // leaves SA_R in SAR and rank(R-suffix) in Rl, like a returned recursion
 // followed by the rank scatter.  *U0 receives the initial unresolved count.
-int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_t *NSl, int64_t *U0) {
+int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_t *NSl, bool r_unwritten,
+                   int64_t *U0) {
     cudaStream_t st = D.s;
     int32_t *headof = (int32_t *)D.t32[0];
     uint32_t *ul = D.t32[1], *ul2 = D.t32[2], *runid = D.t32[3], *val = D.t32[4], *rstart = D.t32[5];
     uint32_t *valt = D.t32[0];  // headof is dead once the ranks are initialised
     uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
     {
-        ProfScope ps(PK_NAMING, double(m) * 16, st);
+        ProfScope ps(PK_NAMING, double(m) * 8, st);
         k_dbl_headof<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof);
         LOR_LAUNCH_CHECK();
+    }
+    if (r_unwritten) {
+        // Large levels left R unwritten: scatter the ranks instead of the names.
+        uint32_t *H = D.t32[1];
+        {
+            ProfScope ps(PK_NAMING, double(m) * 12, st);
+            k_dbl_heads<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof, H);
+            LOR_LAUNCH_CHECK();
+        }
+        int rc = bucketed_scatter(D.rs, (const uint32_t *)SAR, H, m, m, D.t32[2], D.t32[3], D.t32[4], Rl, 0);
+        if (rc) return rc;
+    } else {
+        ProfScope ps(PK_NAMING, double(m) * 12, st);
         k_dbl_init<<<grid_for(m, 256), 256, 0, st>>>(Rl, m, headof);
         LOR_LAUNCH_CHECK();
+    }
+    {
+        ProfScope ps(PK_NAMING, double(m) * 8, st);
         const int64_t ntiles = cdiv(m, kScanTile);
         LOR_TILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, D.d_count, LB_ARGS(D), ntiles);
     }
@@ -1155,10 +1180,17 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     g_trace.push_back(TraceRow{n, int64_t(names), key_bits});
     g_trace_extra.push_back(TraceExtra{strategy, dups});
     const int64_t lost = z.n02 - int64_t(names);
-    if (lost > 0 && sorted_list &&
-        (D.doubling == 2 || (D.doubling == 1 && lost * kDoublingShare <= z.n02))) {
+    const bool doubling = lost > 0 && sorted_list &&
+                          (D.doubling == 2 || (D.doubling == 1 && lost * kDoublingShare <= z.n02));
+    // Sorted large levels left R unwritten; doubling writes ranks there itself.
+    const bool r_unwritten = strategy != 1 && bucket_names(D, z);
+    if (r_unwritten && !doubling) {
+        rc = names_scatter(D, SAR, NSl, z.n02, Rl);
+        if (rc) return rc;
+    }
+    if (doubling) {
         int64_t u0 = 0;
-        rc = sa_by_doubling(D, Rl, z.n02, SAR, NSl, &u0);
+        rc = sa_by_doubling(D, Rl, z.n02, SAR, NSl, r_unwritten, &u0);
         if (rc) return rc;
         g_trace.push_back(TraceRow{z.n02, z.n02, 0});
         g_trace_extra.push_back(TraceExtra{3, u0});

@@ -7,8 +7,9 @@
 //   1. one scatter per rank k writes {ISA, PHI} = {k, SA[k-1]} at position
 //      SA[k] (one 8-byte write instead of separate ISA / predecessor lookups);
 //   2. text positions are walked in order in chunks (h carried within a
-//      chunk), comparing T[i+h..] with T[PHI[i]+h..] four bytes at a time, and
-//      PLCP[i] and ISA[i] are written in text order;
+//      chunk), comparing T[i+h..] with T[PHI[i]+h..] 32 symbols at a time on a
+//      2-bit copy of the text (which stays in L2 for DNA), and PLCP[i] and
+//      ISA[i] are written in text order;
 //   3. LCP[k] = PLCP[SA[k]] is gathered in rank order.
 #include "lcp_kernels.cuh"
 #include "radix.cuh"
@@ -32,7 +33,7 @@ __global__ void k_lcp_scatter_direct(const int32_t *__restrict__ isa, int64_t n,
 
 struct LcpLayout {
     size_t ip = 0, plcp = 0, ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
-    size_t kbuf = 0, vbuf = 0, total = 0;
+    size_t kbuf = 0, vbuf = 0, packed = 0, total = 0;
 };
 LcpLayout lcp_layout(int64_t n) {
     LcpLayout L;
@@ -51,6 +52,7 @@ LcpLayout lcp_layout(int64_t n) {
     L.lookback = take(L.lookback_bytes);
     L.kbuf = take(sizeof(uint32_t) * size_t(n));
     L.vbuf = take(sizeof(uint64_t) * size_t(n));
+    L.packed = take(packed_text_bytes(n));
     L.total = off;
     return L;
 }
@@ -99,12 +101,17 @@ extern "C" int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, in
         k_isa_phi<<<unsigned(cdiv(n, 256)), 256, 0, s>>>(d_sa, n, nullptr, ip, status);
         LOR_LAUNCH_CHECK();
     }
+    const PackedText T = packed_text_at(ws + L.packed, n);
     {
-        // {ISA, PHI} read, ISA + PLCP written, two text reads per position
+        // text read twice, 2-bit copy and exception bitmap written
+        ProfScope ps(PK_KASAI, double(n) * (2 + 0.375), s);
+        const int rc = pack_text(d_text, n, T, s);
+        if (rc) return rc;
+    }
+    {
+        // {ISA, PHI} read, ISA + PLCP written, two text windows per position
         ProfScope ps(PK_KASAI, double(n) * (8 + 4 + 4 + 2), s);
-        const int aligned = (uintptr_t(d_text) & 3) == 0;
-        k_plcp<<<unsigned(cdiv(n, kPlcpTile)), kPlcpThreads, 0, s>>>(d_text, n, ip, d_isa, plcp, aligned,
-                                                                     status);
+        k_plcp_packed<<<unsigned(cdiv(n, kPlcpTile)), kPlcpThreads, 0, s>>>(d_text, T, n, ip, d_isa, plcp, status);
     }
     LOR_LAUNCH_CHECK();
     // LCP[ISA[i]] = PLCP[i]

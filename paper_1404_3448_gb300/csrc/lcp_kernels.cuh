@@ -1,11 +1,18 @@
-// lcp_kernels.cuh -- the three LCP kernels (Section 3, LCP table; Kasai et
+// lcp_kernels.cuh -- the LCP kernels (Section 3, LCP table; Kasai et
 // al., cited there), shared by lor_lcp and the batched pipeline:
 //   k_isa_phi   {ISA, PHI} = {k, SA[k-1]} scattered to position SA[k];
-//   k_plcp      text positions in order (h carried within a chunk), comparing
-//               T[i+h..] with T[PHI[i]+h..] four bytes at a time: ISA and PLCP
-//               in text order;
+//   k_text_max, k_pack_text: a 2-bit copy of the text (the four largest
+//               codes; smaller codes such as terminators are flagged in an
+//               exception bitmap and compared as bytes).  For DNA the copy is
+//               a quarter of the text and stays in L2, where the random
+//               PHI-side reads of the next kernel land;
+//   k_plcp_packed text positions in order (h carried within a chunk),
+//               comparing T[i+h..] with T[PHI[i]+h..] 32 symbols at a time:
+//               ISA and PLCP in text order;
 //   k_lcp_gather LCP[k] = PLCP[SA[k]].
 #pragma once
+
+#include <climits>
 
 #include "common.cuh"
 
@@ -27,63 +34,273 @@ __global__ void k_isa_phi(const int32_t *__restrict__ sa, int64_t n, const uint3
     ip[p] = make_int2(int32_t(k), head ? -1 : sa[k - 1]);
 }
 
-// Four text bytes starting at byte offset a (little-endian), from two aligned
-// words; the caller guarantees a + 8 <= n.
-__device__ __forceinline__ uint32_t load4(const uint8_t *t, int64_t a) {
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(t + (a & ~int64_t(3)));
-    return __funnelshift_r(w[0], w[1], uint32_t(a & 3) * 8u);
-}
-
 constexpr int kPlcpThreads = 256;
 constexpr int kPlcpPer = 16;  // text positions per thread
 constexpr int kPlcpTile = kPlcpThreads * kPlcpPer;
 
-__global__ void __launch_bounds__(kPlcpThreads) k_plcp(const uint8_t *__restrict__ t, int64_t n,
-                                                       const int2 *__restrict__ ip,
-                                                       int32_t *__restrict__ isa, int32_t *__restrict__ plcp,
-                                                       int aligned, int *status) {
-    __shared__ int2 s_ip[kPlcpTile];
-    __shared__ int32_t s_out[kPlcpTile];
+// ---- packed text
+
+constexpr int kPackThreads = 256;
+constexpr int kPackPer = 32;  // symbols per thread: one 64-bit word, one 32-bit exception word
+constexpr int kPackTile = kPackThreads * kPackPer;
+constexpr int kExcCap = 4096;    // exceptions kept as a sorted list (else the bitmap is used)
+constexpr int kExcShared = 512;  // listed exceptions the LCP kernel keeps in shared memory
+
+// Words of the 2-bit copy and of the exception bitmap for n symbols (enough
+// for 16-byte loads of the chunk holding any symbol, and for two-word
+// windows at any position).
+__host__ __device__ inline int64_t packed_words(int64_t n) { return n / 32 + 4; }
+
+// The 2-bit copy of a text: P (16-byte aligned), the exception bitmap E,
+// the sorted exception list (when it has at most kExcCap entries), and two
+// control words: ctl[0] = largest code, ctl[1] = number of exceptions.
+struct PackedText {
+    uint64_t *P;
+    uint32_t *E;
+    int32_t *list;
+    int *ctl;
+};
+
+inline size_t packed_text_bytes(int64_t n) {
+    return align256(sizeof(uint64_t) * size_t(packed_words(n))) +
+           align256(sizeof(uint32_t) * size_t(packed_words(n))) + align256(sizeof(int32_t) * kExcCap) + 256;
+}
+inline PackedText packed_text_at(char *mem, int64_t n) {
+    PackedText T;
+    size_t off = 0;
+    T.P = (uint64_t *)(mem + off);
+    off += align256(sizeof(uint64_t) * size_t(packed_words(n)));
+    T.E = (uint32_t *)(mem + off);
+    off += align256(sizeof(uint32_t) * size_t(packed_words(n)));
+    T.list = (int32_t *)(mem + off);
+    off += align256(sizeof(int32_t) * kExcCap);
+    T.ctl = (int *)(mem + off);
+    return T;
+}
+
+// ctl[0] = largest code in the text (the caller zeroes it first).
+__global__ void k_text_max(const uint8_t *__restrict__ t, int64_t n, int *mx) {
+    uint32_t m = 0;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
+    int64_t head = 0;
+    if ((uintptr_t(t) & 15) == 0) {
+        // 16 bytes per load; per-byte maximum of four packed bytes via __vmaxu4
+        const int64_t nv = n / 16;
+        const uint4 *v = reinterpret_cast<const uint4 *>(t);
+        uint32_t acc = 0;
+        for (int64_t i = tid; i < nv; i += nth) {
+            const uint4 x = v[i];
+            acc = __vmaxu4(acc, __vmaxu4(__vmaxu4(x.x, x.y), __vmaxu4(x.z, x.w)));
+        }
+        m = max(max(acc & 0xFFu, (acc >> 8) & 0xFFu), max((acc >> 16) & 0xFFu, acc >> 24));
+        head = nv * 16;
+    }
+    for (int64_t i = head + tid; i < n; i += nth) m = max(m, uint32_t(t[i]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, int(m));
+}
+
+// Code c in [mx-3, mx] -> c - (mx - 3) in two bits (symbol k of a word in
+// bits 2k, 2k+1); any smaller code -> 0 with its exception bit set and its
+// position appended to the (unordered) exception list.
+__global__ void __launch_bounds__(kPackThreads) k_pack_text(const uint8_t *__restrict__ t, int64_t n,
+                                                            PackedText T) {
+    __shared__ uint8_t st[kPackTile];
+    const int64_t base = int64_t(blockIdx.x) * kPackTile;
+    const int cnt = int(min64(int64_t(kPackTile), n - base));
+    for (int i = threadIdx.x; i < cnt; i += kPackThreads) st[i] = t[base + i];
+    __syncthreads();
+    const int lo = T.ctl[0] - 3;
+    uint64_t w = 0;
+    uint32_t e = 0;
+    const int l0 = int(threadIdx.x) * kPackPer;
+#pragma unroll 8
+    for (int k = 0; k < kPackPer; ++k) {
+        const int l = l0 + k;
+        if (l >= cnt) break;
+        const int c = int(st[l]) - lo;
+        if (c >= 0) w |= uint64_t(c & 3) << (2 * k);
+        else e |= 1u << k;
+    }
+    const int64_t wi = int64_t(blockIdx.x) * kPackThreads + threadIdx.x;
+    if (l0 < cnt) {
+        T.P[wi] = w;
+        T.E[wi] = e;
+    }
+    if (e) {
+        int slot = atomicAdd(&T.ctl[1], __popc(e));
+        for (; e && slot < kExcCap; e &= e - 1, ++slot) T.list[slot] = int32_t(base + l0 + __ffs(int(e)) - 1);
+    }
+}
+
+// Sorts the exception list in place when it is short enough to be used.
+__global__ void __launch_bounds__(1024) k_sort_exc(PackedText T) {
+    __shared__ int32_t v[kExcCap];
+    const int cnt = T.ctl[1];
+    if (cnt <= 1 || cnt > kExcCap) return;
+    int m = 1;
+    while (m < cnt) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = i < cnt ? T.list[i] : INT_MAX;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    if ((v[i] > v[l]) == up) {
+                        const int32_t x = v[i];
+                        v[i] = v[l];
+                        v[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) T.list[i] = v[i];
+}
+
+// Enqueues the 2-bit copy of t[0..n) (the buffers of T come from
+// packed_text_at) on stream s.
+inline int pack_text(const uint8_t *t, int64_t n, const PackedText &T, cudaStream_t s) {
+    const int64_t w0 = n / 32;
+    LOR_CUDA_TRY(cudaMemsetAsync(T.P + w0, 0, sizeof(uint64_t) * size_t(packed_words(n) - w0), s));
+    LOR_CUDA_TRY(cudaMemsetAsync(T.E + w0, 0, sizeof(uint32_t) * size_t(packed_words(n) - w0), s));
+    LOR_CUDA_TRY(cudaMemsetAsync(T.ctl, 0, 2 * sizeof(int), s));
+    k_text_max<<<unsigned(min64(cdiv(n, 256), 152 * 8)), 256, 0, s>>>(t, n, T.ctl);
+    LOR_LAUNCH_CHECK();
+    k_pack_text<<<unsigned(cdiv(n, kPackTile)), kPackThreads, 0, s>>>(t, n, T);
+    LOR_LAUNCH_CHECK();
+    k_sort_exc<<<1, 1024, 0, s>>>(T);
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
+// Symbols p .. p+31 of the 2-bit copy (p + 32 <= n) and their exception bits.
+__device__ __forceinline__ uint64_t window2(const uint64_t *__restrict__ P, int64_t p) {
+    const int64_t w = p >> 5;
+    const int sft = int(p & 31) * 2;
+    const uint64_t a = P[w];
+    return sft ? (a >> sft) | (P[w + 1] << (64 - sft)) : a;
+}
+__device__ __forceinline__ uint32_t window_exc(const uint32_t *__restrict__ E, int64_t p) {
+    const int64_t w = p >> 5;
+    return __funnelshift_r(E[w], E[w + 1], uint32_t(p & 31));
+}
+
+// Symbols from p on out of the 16-byte chunk holding p: 32 of them when p
+// sits in the chunk's first half, else the 64 - (p mod 64) up to its end.
+__device__ __forceinline__ uint64_t window_chunk(const uint64_t *__restrict__ P, int64_t p, int &avail) {
+    const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(P)[p >> 6];
+    const int off = int(p & 63);
+    if (off < 32) {
+        avail = 32;
+        return off ? (v.x >> (2 * off)) | (v.y << (64 - 2 * off)) : v.x;
+    }
+    avail = 64 - off;
+    return v.y >> (2 * (off - 32));
+}
+
+// First exception at or after p (n if none), from the sorted list.
+__device__ __forceinline__ int64_t next_exc(const int32_t *__restrict__ lst, int cnt, int64_t p, int64_t n) {
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (lst[mid] < p) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < cnt ? int64_t(lst[lo]) : n;
+}
+
+// Shared-memory index of position l of a tile: one pad word per 16, so that
+// the 16-position chunks of a warp's threads fall in different banks.
+__device__ __forceinline__ int chunk_slot(int l) { return l + (l >> 4); }
+
+__global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__restrict__ t, PackedText T,
+                                                              int64_t n, const int2 *__restrict__ ip,
+                                                              int32_t *__restrict__ isa,
+                                                              int32_t *__restrict__ plcp, int *status) {
+    __shared__ int32_t s_out[kPlcpTile + kPlcpTile / 16];
+    __shared__ int32_t s_exc[kExcShared];
     const int64_t base = int64_t(blockIdx.x) * kPlcpTile;
     const int cnt = int(min64(int64_t(kPlcpTile), n - base));
-    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) {
-        const int2 v = ip[base + i];
-        s_ip[i] = v;
-        isa[base + i] = v.x;
-    }
+    const int nexc = T.ctl[1];
+    const bool listed = nexc <= kExcCap;
+    const int32_t *lst = nexc <= kExcShared ? s_exc : T.list;
+    if (nexc <= kExcShared)
+        for (int i = threadIdx.x; i < nexc; i += kPlcpThreads) s_exc[i] = T.list[i];
+    // ISA in text order (coalesced); the PHI reads below hit the same lines.
+    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) isa[base + i] = ip[base + i].x;
     __syncthreads();
+    const uint64_t *__restrict__ P = T.P;
     int64_t h = 0;
     bool bad = false;
     const int l0 = int(threadIdx.x) * kPlcpPer;
     for (int l = l0; l < l0 + kPlcpPer && l < cnt; ++l) {
         const int64_t i = base + l;
-        const int64_t j = s_ip[l].y;
+        const int64_t j = ip[i].y;
         if (j < 0 || j >= n) {
             if (j != -1) bad = true;
             h = 0;
-            s_out[l] = 0;
+            s_out[chunk_slot(l)] = 0;
             continue;
         }
-        bool found = false;
-        if (aligned) {
-            while (i + h + 8 <= n && j + h + 8 <= n) {
-                const uint32_t x = load4(t, i + h) ^ load4(t, j + h);
-                if (x) {
-                    h += (__ffs(x) - 1) >> 3;  // equal low-order (leading) bytes
-                    found = true;
-                    break;
+        if (listed) {
+            // Compare packed symbols up to the next exception (or the end) on
+            // either side; there compare the bytes and go on if they match.
+            for (;;) {
+                const int64_t a = i + h, b = j + h;
+                const int64_t lim = min64(min64(next_exc(lst, nexc, a, n) - a, next_exc(lst, nexc, b, n) - b),
+                                          min64(n - a, n - b));
+                int64_t k = 0;
+                bool mism = false;
+                while (k < lim) {
+                    int aa, ab;
+                    const uint64_t wa = window_chunk(P, a + k, aa);
+                    const uint64_t wb = window_chunk(P, b + k, ab);
+                    int len = aa < ab ? aa : ab;
+                    if (lim - k < len) len = int(lim - k);
+                    uint64_t d = wa ^ wb;
+                    if (len < 32) d &= (uint64_t(1) << (2 * len)) - 1;
+                    if (d) {
+                        k += (__ffsll((long long)d) - 1) >> 1;
+                        mism = true;
+                        break;
+                    }
+                    k += len;
                 }
-                h += 4;
+                h += k;
+                if (mism || i + h >= n || j + h >= n || t[i + h] != t[j + h]) break;
+                ++h;
             }
+        } else {
+            bool done = false;
+            while (!done && i + h + 32 <= n && j + h + 32 <= n) {
+                const uint64_t d = window2(P, i + h) ^ window2(P, j + h);
+                const uint32_t e = window_exc(T.E, i + h) | window_exc(T.E, j + h);
+                const int dpos = d ? (__ffsll((long long)d) - 1) >> 1 : 32;
+                const int epos = e ? __ffs(int(e)) - 1 : 32;
+                if (dpos < epos) {
+                    h += dpos;
+                    done = true;
+                } else if (epos < 32) {
+                    h += epos;
+                    if (t[i + h] != t[j + h]) done = true;
+                    else ++h;
+                } else {
+                    h += 32;
+                }
+            }
+            if (!done)
+                while (i + h < n && j + h < n && t[i + h] == t[j + h]) ++h;
         }
-        if (!found)
-            while (i + h < n && j + h < n && t[i + h] == t[j + h]) ++h;
-        s_out[l] = int32_t(h);
+        s_out[chunk_slot(l)] = int32_t(h);
         if (h > 0) --h;
     }
     if (bad) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) plcp[base + i] = s_out[i];
+    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) plcp[base + i] = s_out[chunk_slot(i)];
 }
 
 // LCP[k] = PLCP[SA[k]] (a position without predecessor has PLCP 0).

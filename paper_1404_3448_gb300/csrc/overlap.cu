@@ -5,20 +5,20 @@
 //   1. argmax: L = max LCP[k] over rank-adjacent suffixes from different
 //      sequences, smallest such k; a warp-shuffle max of the packed key
 //      (LCP << 32 | ~k), a block max and one 64-bit atomicMax per block.
-//   2. positions: rank runs with adjacent LCP >= L (run ids by a look-back
-//      scan), a run qualifies when it holds a cross-sequence adjacent pair,
-//      every member of a qualifying run is compacted out, and the list is
-//      radix sorted ascending.
+//   2. positions: the ranks k with LCP[k] >= L ("hits") are compacted in
+//      rank order; consecutive hits k_a .. k_b form one run of ranks
+//      k_a - 1 .. k_b (all suffixes sharing the length-L prefix); a run
+//      qualifies when one of its adjacent pairs comes from two sequences,
+//      every member of a qualifying run is emitted, and the list is radix
+//      sorted ascending.  Only the hits (usually a handful) are touched after
+//      the compaction.
 #include "radix.cuh"
+#include "scan.cuh"
 
 LOR_DEFINE_TU_STATUS(lor_status_overlap)
 
 namespace lor {
 namespace {
-
-constexpr int kOvThreads = 256;
-constexpr int kOvItems = 8;
-constexpr int kOvTile = kOvThreads * kOvItems;
 
 struct OvLayout {
     size_t ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
@@ -59,24 +59,44 @@ __device__ __forceinline__ int seq_of(const int32_t *starts, int nseq, int32_t p
     return lo;
 }
 
+// Candidate rank k of the argmax: keeps the larger packed key.
+__device__ __forceinline__ void ov_consider(unsigned long long &my, const int32_t *sst, int nseq, int32_t a,
+                                           int32_t b, int32_t l, int64_t k) {
+    if (uint32_t(l) < uint32_t(my >> 32)) return;  // cannot win: skip the sequence lookups
+    if (seq_of(sst, nseq, a) != seq_of(sst, nseq, b)) {
+        const unsigned long long key =
+            (static_cast<unsigned long long>(uint32_t(l)) << 32) | (0xFFFFFFFFull - uint64_t(k));
+        my = key > my ? key : my;
+    }
+}
+
+// vec: SA and LCP are 16-byte aligned, so four ranks are read per load.
 __global__ void __launch_bounds__(256) k_ov_argmax(const int32_t *__restrict__ sa,
                                                    const int32_t *__restrict__ lcp, int64_t n,
-                                                   const int32_t *__restrict__ starts, int nseq,
+                                                   const int32_t *__restrict__ starts, int nseq, int vec,
                                                    unsigned long long *best) {
     __shared__ int32_t sst[LOR_MAX_SEQ + 1];
     __shared__ unsigned long long wbest[8];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
     unsigned long long my = 0;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t k = 1 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const int32_t a = sa[k - 1], b = sa[k];
-        if (seq_of(sst, nseq, a) != seq_of(sst, nseq, b)) {
-            const unsigned long long key =
-                (static_cast<unsigned long long>(uint32_t(lcp[k])) << 32) | (0xFFFFFFFFull - uint64_t(k));
-            my = key > my ? key : my;
+    int64_t k0 = 1;
+    if (vec) {
+        const int64_t nv = n / 4;
+        for (int64_t v = tid; v < nv; v += stride) {
+            const int4 s4 = reinterpret_cast<const int4 *>(sa)[v];
+            const int4 l4 = reinterpret_cast<const int4 *>(lcp)[v];
+            const int64_t k = 4 * v;
+            if (k > 0) ov_consider(my, sst, nseq, sa[k - 1], s4.x, l4.x, k);
+            ov_consider(my, sst, nseq, s4.x, s4.y, l4.y, k + 1);
+            ov_consider(my, sst, nseq, s4.y, s4.z, l4.z, k + 2);
+            ov_consider(my, sst, nseq, s4.z, s4.w, l4.w, k + 3);
         }
+        k0 = nv * 4 > 1 ? nv * 4 : 1;
     }
+    for (int64_t k = k0 + tid; k < n; k += stride) ov_consider(my, sst, nseq, sa[k - 1], sa[k], lcp[k], k);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         const unsigned long long o = __shfl_xor_sync(0xffffffffu, my, d);
@@ -95,96 +115,105 @@ __device__ __forceinline__ int32_t best_len(const unsigned long long *best) {
     return int32_t(*best >> 32);
 }
 
-// run_id[k] = number of run starts in [0, k] minus one; a run starts at k = 0
-// and wherever LCP[k] < L.
-__global__ void __launch_bounds__(kOvThreads) k_ov_runs(const int32_t *__restrict__ lcp, int64_t n,
-                                                        const unsigned long long *best,
-                                                        int32_t *__restrict__ run_id, uint64_t *lb,
-                                                        unsigned long long *ctr,
-                                                        unsigned long long tile_base, uint32_t epoch,
-                                                        int *status) {
-    __shared__ long long s_tile;
-    __shared__ uint32_t scratch[kOvThreads / 32 + 1];
-    __shared__ uint32_t s_prefix;
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
-    __syncthreads();
+// Hits: ranks k >= 1 with LCP[k] >= L, appended in any order (a warp
+// reserves its slots with one atomic); they are sorted afterwards.
+__device__ __forceinline__ void ov_append(bool hit, uint32_t k, uint32_t *hits, uint32_t *count) {
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(int(mask)) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, uint32_t(__popc(mask)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (hit) hits[base + __popc(mask & ((1u << lane) - 1u))] = k;
+}
+
+__global__ void __launch_bounds__(256) k_ov_hits(const int32_t *__restrict__ lcp, int64_t n, int vec,
+                                                 const unsigned long long *best, uint32_t *__restrict__ hits,
+                                                 uint32_t *count) {
     const int32_t L = best_len(best);
     if (L <= 0) return;
-    const int64_t tile = s_tile;
-    const int64_t base = tile * kOvTile + int64_t(tid) * kOvItems;
-    uint32_t flags = 0, cnt = 0;
-#pragma unroll
-    for (int i = 0; i < kOvItems; ++i) {
-        const int64_t k = base + i;
-        if (k < n) {
-            const uint32_t f = (k == 0 || lcp[k] < L) ? 1u : 0u;
-            flags |= f << i;
-            cnt += f;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t k0 = 0;
+    if (vec) {
+        const int64_t nv = n / 4;
+        const int64_t nvr = (nv + 31) & ~int64_t(31);  // whole warps iterate together
+        for (int64_t v = tid; v < nvr; v += stride) {
+            int4 l4 = make_int4(0, 0, 0, 0);
+            if (v < nv) l4 = reinterpret_cast<const int4 *>(lcp)[v];
+            const uint32_t k = uint32_t(4 * v);
+            ov_append(v < nv && k > 0 && l4.x >= L, k, hits, count);
+            ov_append(v < nv && l4.y >= L, k + 1, hits, count);
+            ov_append(v < nv && l4.z >= L, k + 2, hits, count);
+            ov_append(v < nv && l4.w >= L, k + 3, hits, count);
         }
+        k0 = nv * 4;
     }
-    uint32_t agg;
-    const uint32_t excl = block_excl_scan<kOvThreads>(cnt, scratch, &agg);
-    if (tid < 32) {
-        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
-        if (tid == 0) s_prefix = p;
-    }
-    __syncthreads();
-    uint32_t id = s_prefix + excl;
-#pragma unroll
-    for (int i = 0; i < kOvItems; ++i) {
-        const int64_t k = base + i;
-        if (k < n) {
-            id += (flags >> i) & 1u;
-            run_id[k] = int32_t(id) - 1;
-        }
+    const int64_t rest = n - k0;
+    const int64_t restr = (rest + 31) & ~int64_t(31);
+    for (int64_t x = tid; x < restr; x += stride) {
+        const int64_t k = k0 + x;
+        ov_append(x < rest && k > 0 && lcp[k] >= L, uint32_t(k), hits, count);
     }
 }
 
-// A run qualifies when it holds an adjacent pair from different sequences.
-__global__ void k_ov_qual(const int32_t *__restrict__ sa, const int32_t *__restrict__ lcp, int64_t n,
-                          const int32_t *__restrict__ starts, int nseq,
-                          const unsigned long long *best, const int32_t *__restrict__ run_id,
-                          uint8_t *__restrict__ qual) {
+__device__ __forceinline__ bool hit_starts_run(const uint32_t *hits, int64_t i) {
+    return i == 0 || hits[i] != hits[i - 1] + 1;
+}
+
+// Run ids of the hits; a run qualifies when one of its hits pairs suffixes
+// of two sequences.
+__global__ void __launch_bounds__(kScanThreads) k_ov_hit_runs(
+    const int32_t *__restrict__ sa, const uint32_t *__restrict__ hits, int64_t c,
+    const int32_t *__restrict__ starts, int nseq, uint32_t *__restrict__ run, uint8_t *__restrict__ qual,
+    uint32_t *n_runs, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
+    int *status) {
     __shared__ int32_t sst[LOR_MAX_SEQ + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
-    const int32_t L = best_len(best);
-    if (L <= 0) return;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t k = 1 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
-        if (lcp[k] >= L && seq_of(sst, nseq, sa[k - 1]) != seq_of(sst, nseq, sa[k]))
-            qual[run_id[k]] = 1;
-    }
+    tile_names(
+        c, [&](int64_t i) { return hit_starts_run(hits, i); },
+        [&](int64_t i, uint32_t r) {
+            run[i] = r - 1;
+            const uint32_t k = hits[i];
+            if (seq_of(sst, nseq, sa[k - 1]) != seq_of(sst, nseq, sa[k])) qual[r - 1] = 1;
+        },
+        n_runs, lb, ctr, tile_base, epoch, status);
 }
 
-// Members of qualifying runs, compacted in rank order.
-__global__ void __launch_bounds__(kOvThreads) k_ov_members(
-    const int32_t *__restrict__ sa, int64_t n, const unsigned long long *best,
-    const int32_t *__restrict__ run_id, const uint8_t *__restrict__ qual, uint32_t *__restrict__ out,
-    uint32_t *count, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base,
-    int64_t ntiles, uint32_t epoch, int *status) {
+// Members of qualifying runs in rank order: a run's first hit k adds SA[k-1]
+// and SA[k], every other hit adds SA[k].
+__global__ void __launch_bounds__(kScanThreads) k_ov_hit_members(
+    const int32_t *__restrict__ sa, const uint32_t *__restrict__ hits, int64_t c,
+    const uint32_t *__restrict__ run, const uint8_t *__restrict__ qual, uint32_t *__restrict__ out,
+    uint32_t *count, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
+    int *status, int64_t ntiles) {
     __shared__ long long s_tile;
-    __shared__ uint32_t scratch[kOvThreads / 32 + 1];
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
     __shared__ uint32_t s_prefix;
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
     __syncthreads();
-    const int32_t L = best_len(best);
-    if (L <= 0) return;
     const int64_t tile = s_tile;
-    const int64_t base = tile * kOvTile + int64_t(tid) * kOvItems;
-    uint32_t flags = 0, cnt = 0;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    uint32_t cnt = 0;
+    uint32_t two = 0, one = 0;
 #pragma unroll
-    for (int i = 0; i < kOvItems; ++i) {
-        const int64_t k = base + i;
-        if (k < n && qual[run_id[k]]) {
-            flags |= 1u << i;
-            cnt++;
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t x = base + i;
+        if (x < c && qual[run[x]]) {
+            if (hit_starts_run(hits, x)) {
+                two |= 1u << i;
+                cnt += 2;
+            } else {
+                one |= 1u << i;
+                cnt += 1;
+            }
         }
     }
     uint32_t agg;
-    const uint32_t excl = block_excl_scan<kOvThreads>(cnt, scratch, &agg);
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
     if (tid < 32) {
         const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
         if (tid == 0) {
@@ -195,8 +224,10 @@ __global__ void __launch_bounds__(kOvThreads) k_ov_members(
     __syncthreads();
     uint32_t o = s_prefix + excl;
 #pragma unroll
-    for (int i = 0; i < kOvItems; ++i) {
-        if ((flags >> i) & 1u) out[o++] = uint32_t(sa[base + i]);
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t x = base + i;
+        if ((two >> i) & 1u) out[o++] = uint32_t(sa[hits[x] - 1]);
+        if (((two | one) >> i) & 1u) out[o++] = uint32_t(sa[hits[x]]);
     }
 }
 
@@ -277,42 +308,59 @@ extern "C" int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, in
     uint32_t *ka = (uint32_t *)(ws + L.ka), *kb = (uint32_t *)(ws + L.kb);
     uint32_t *va = (uint32_t *)(ws + L.va), *vb = (uint32_t *)(ws + L.vb);
 
+    uint32_t *hits = (uint32_t *)run_id, *run = kb;
+    uint32_t *n_runs = (uint32_t *)(ws + L.ctrl + 16);
     LOR_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, 256, s));
     LOR_CUDA_TRY(cudaMemsetAsync(ws + L.lookback, 0, L.lookback_bytes, s));
-    LOR_CUDA_TRY(cudaMemsetAsync(qual, 0, size_t(n), s));
     {
         ProfScope ps(PK_OVERLAP_SCAN, double(n) * 8, s);
-        const unsigned grid = unsigned(min64(cdiv(n, 256), 152 * 16));
-        k_ov_argmax<<<grid, 256, 0, s>>>(d_sa, d_lcp, n, d_seq_starts, nseq, best);
-    }
-    LOR_LAUNCH_CHECK();
-    const int64_t ntiles = cdiv(n, kOvTile);
-    {
-        ProfScope ps(PK_OVERLAP_COLLECT, double(n) * 8, s);
-        rs.epoch++;
-        k_ov_runs<<<unsigned(ntiles), kOvThreads, 0, s>>>(d_lcp, n, best, run_id, rs.lookback,
-                                                         rs.tile_ctr, rs.tile_base, rs.epoch, status);
-    }
-    LOR_LAUNCH_CHECK();
-    rs.tile_base += (unsigned long long)ntiles;
-    {
-        ProfScope ps(PK_OVERLAP_COLLECT, double(n) * 12, s);
-        const unsigned grid = unsigned(min64(cdiv(n, 256), 152 * 16));
-        k_ov_qual<<<grid, 256, 0, s>>>(d_sa, d_lcp, n, d_seq_starts, nseq, best, run_id, qual);
+        const unsigned grid = unsigned(min64(cdiv(n, 1024), 152 * 16));
+        const int vec = ((uintptr_t(d_sa) | uintptr_t(d_lcp)) & 15) == 0;
+        k_ov_argmax<<<grid, 256, 0, s>>>(d_sa, d_lcp, n, d_seq_starts, nseq, vec, best);
     }
     LOR_LAUNCH_CHECK();
     {
-        ProfScope ps(PK_OVERLAP_COLLECT, double(n) * 5, s);
-        rs.epoch++;
-        k_ov_members<<<unsigned(ntiles), kOvThreads, 0, s>>>(d_sa, n, best, run_id, qual, ka, count,
-                                                            rs.lookback, rs.tile_ctr, rs.tile_base,
-                                                            ntiles, rs.epoch, status);
+        ProfScope ps(PK_OVERLAP_COLLECT, double(n) * 4, s);
+        const int vec = (uintptr_t(d_lcp) & 15) == 0;
+        k_ov_hits<<<unsigned(min64(cdiv(n, 1024), 152 * 16)), 256, 0, s>>>(d_lcp, n, vec, best, hits, count);
     }
     LOR_LAUNCH_CHECK();
-    rs.tile_base += (unsigned long long)ntiles;
-    uint32_t h_count = 0;
-    LOR_CUDA_TRY(cudaMemcpyAsync(&h_count, count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    uint32_t h_hits = 0;
+    LOR_CUDA_TRY(cudaMemcpyAsync(&h_hits, count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     LOR_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t c = int64_t(h_hits);
+    uint32_t h_count = 0;
+    if (c > 1) {
+        uint32_t *hr, *hv;
+        const int rc = radix_sort_pairs<uint32_t>(rs, hits, va, kb, vb, c, 0, bit_width_u64(uint64_t(n - 1)), true,
+                                                  &hr, &hv);
+        if (rc) return rc;
+        if (hr != hits)
+            LOR_CUDA_TRY(cudaMemcpyAsync(hits, hr, sizeof(uint32_t) * size_t(c), cudaMemcpyDeviceToDevice, s));
+    }
+    if (c > 0) {
+        const int64_t ct = cdiv(c, kScanTile);
+        LOR_CUDA_TRY(cudaMemsetAsync(qual, 0, size_t(c), s));
+        {
+            ProfScope ps(PK_OVERLAP_COLLECT, double(c) * 21, s);
+            rs.epoch++;
+            k_ov_hit_runs<<<unsigned(ct), kScanThreads, 0, s>>>(d_sa, hits, c, d_seq_starts, nseq, run, qual,
+                                                               n_runs, rs.lookback, rs.tile_ctr, rs.tile_base,
+                                                               rs.epoch, status);
+            LOR_LAUNCH_CHECK();
+            rs.tile_base += (unsigned long long)ct;
+            rs.epoch++;
+            k_ov_hit_members<<<unsigned(ct), kScanThreads, 0, s>>>(d_sa, hits, c, run, qual, ka, count,
+                                                                  rs.lookback, rs.tile_ctr, rs.tile_base,
+                                                                  rs.epoch, status, ct);
+            LOR_LAUNCH_CHECK();
+            rs.tile_base += (unsigned long long)ct;
+        }
+        LOR_CUDA_TRY(cudaMemcpyAsync(&h_count, count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        LOR_CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+        LOR_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(uint32_t), s));
+    }
     const int64_t m = int64_t(h_count);
     uint32_t *kr = ka, *vr = va;
     if (m > 1) {
