@@ -110,7 +110,7 @@ __device__ __forceinline__ int64_t sample_pos(int64_t j, int64_t n0) {
 template <typename CharT, typename KeyT, bool kValidate>
 __global__ void __launch_bounds__(256) k_sample_keys(const CharT *__restrict__ s, int64_t n,
                                                      int64_t n0, int64_t n02, int first, int kchars,
-                                                     int bits, int64_t maxc, KeyT *__restrict__ keys,
+                                                     uint64_t radix, int64_t maxc, KeyT *__restrict__ keys,
                                                      int *status) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n02) return;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_sample_keys(const CharT *__restrict__ s
             bad = true;
             c = c < 1 ? 1 : maxc;
         }
-        key = (key << bits) | KeyT(c);
+        key = key * KeyT(radix) + KeyT(c);
     }
     if (kValidate && j == 0 && n > 0) {
         const int64_t c = int64_t(s[0]);
@@ -518,7 +518,7 @@ constexpr int kDenseLocal = 4096;
 
 template <typename CharT, bool kValidate>
 __global__ void __launch_bounds__(256) k_dense_mark(const CharT *__restrict__ s, int64_t n, int64_t n0,
-                                                    int64_t n02, int kchars, int bits, int64_t maxc,
+                                                    int64_t n02, int kchars, uint32_t radix, int64_t maxc,
                                                     int64_t T, uint32_t *__restrict__ table, int *status) {
     __shared__ uint8_t seen[kDenseLocal];
     const bool local = T <= kDenseLocal;
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(256) k_dense_mark(const CharT *__restrict__ s,
                 bad = true;
                 c = c < 1 ? 1 : maxc;
             }
-            key = (key << bits) | uint32_t(c);
+            key = key * radix + uint32_t(c);
         }
         if (local) seen[key] = 1;
         else if (table[key] == 0u) table[key] = 1u;
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(kScanThreads) k_dense_scan(uint32_t *__restric
 
 template <typename CharT>
 __global__ void k_dense_write(const CharT *__restrict__ s, int64_t n, int64_t n0, int64_t n02, int kchars,
-                              int bits, int64_t maxc, const uint32_t *__restrict__ table,
+                              uint32_t radix, int64_t maxc, const uint32_t *__restrict__ table,
                               int32_t *__restrict__ R) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n02) return;
@@ -577,7 +577,7 @@ __global__ void k_dense_write(const CharT *__restrict__ s, int64_t n, int64_t n0
     for (int t = 0; t < kchars; ++t) {
         int64_t c = sym(s, n, p + t);
         if (p + t < n) c = c < 1 ? 1 : (c > maxc ? maxc : c);
-        key = (key << bits) | uint32_t(c);
+        key = key * radix + uint32_t(c);
     }
     R[j] = int32_t(table[key]);
 }
@@ -900,22 +900,23 @@ int names_scatter(Dc3Run &D, const int32_t *SAR, const int32_t *NSl, int64_t m, 
 // ---- Step 1, strategy "sort": LSD radix sort of the keys, then naming.
 template <typename CharT, typename KeyT>
 int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars,
-                         int bits, int64_t maxc, int32_t *Rl, int32_t *SAR, int32_t *NSl) {
+                         int key_bits, int64_t maxc, int32_t *Rl, int32_t *SAR, int32_t *NSl) {
+    const uint64_t radix = uint64_t(maxc) + 1;
     cudaStream_t st = D.s;
     KeyT *k0 = (KeyT *)D.t64[0], *k1 = (KeyT *)D.t64[1];
     {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (sizeof(KeyT) + (lvl == 0 ? 1.0 : 4.0) * kchars / 3.0), st);
         if (lvl == 0)
             k_sample_keys<CharT, KeyT, true><<<grid_for(z.n02, 256), 256, 0, st>>>(
-                s, z.n, z.n0, z.n02, 0, kchars, bits, maxc, k0, D.status);
+                s, z.n, z.n0, z.n02, 0, kchars, radix, maxc, k0, D.status);
         else
             k_sample_keys<CharT, KeyT, false><<<grid_for(z.n02, 256), 256, 0, st>>>(
-                s, z.n, z.n0, z.n02, 0, kchars, bits, maxc, k0, D.status);
+                s, z.n, z.n0, z.n02, 0, kchars, radix, maxc, k0, D.status);
     }
     LOR_LAUNCH_CHECK();
     KeyT *kr;
     uint32_t *vr;
-    int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, kchars * bits, true, &kr, &vr);
+    int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, key_bits, true, &kr, &vr);
     if (rc) return rc;
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 16), st);
@@ -934,12 +935,13 @@ int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, in
     {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (8 + 8), st);
         k_sample_keys<CharT, uint64_t, false><<<grid_for(z.n02, 256), 256, 0, st>>>(
-            s, z.n, z.n0, z.n02, 1, 3, bits, maxc, k0, D.status);
+            s, z.n, z.n0, z.n02, 1, 3, uint64_t(maxc) + 1, maxc, k0, D.status);
     }
     LOR_LAUNCH_CHECK();
     uint64_t *kr;
     uint32_t *vr;
-    int rc = radix_sort_pairs<uint64_t>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, 2 * bits, true, &kr, &vr);
+    const int pair_bits = bit_width_u64((uint64_t(maxc) + 1) * (uint64_t(maxc) + 1) - 1);
+    int rc = radix_sort_pairs<uint64_t>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, pair_bits, true, &kr, &vr);
     if (rc) return rc;
     uint32_t *kx = (uint32_t *)(kr == k0 ? k1 : k0);  // free key buffer
     uint32_t *ky = (uint32_t *)kr;
@@ -962,19 +964,19 @@ int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, in
 
 // ---- Step 1, strategy "dense": names from a table of present keys.
 template <typename CharT>
-int sample_dense_names(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars, int bits,
+int sample_dense_names(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars, int64_t T,
                        int64_t maxc, int32_t *Rl, int32_t *SAR, int32_t *NSl, uint32_t *names) {
     cudaStream_t st = D.s;
-    const int64_t T = int64_t(1) << (kchars * bits);
+    const uint32_t radix = uint32_t(maxc + 1);
     LOR_CUDA_TRY(cudaMemsetAsync(D.tbl, 0, sizeof(uint32_t) * size_t(T), st));
     {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (kchars * sizeof(CharT) / 3.0 + 4), st);
         const unsigned grid = unsigned(min64(cdiv(z.n02, 256), 152 * 8));
         if (lvl == 0)
-            k_dense_mark<CharT, true><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, bits, maxc, T,
+            k_dense_mark<CharT, true><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, radix, maxc, T,
                                                              D.tbl, D.status);
         else
-            k_dense_mark<CharT, false><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, bits, maxc, T,
+            k_dense_mark<CharT, false><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, radix, maxc, T,
                                                               D.tbl, D.status);
     }
     LOR_LAUNCH_CHECK();
@@ -985,7 +987,7 @@ int sample_dense_names(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, 
     }
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (kchars * sizeof(CharT) / 3.0 + 8), st);
-        k_dense_write<CharT><<<grid_for(z.n02, 256), 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, bits, maxc,
+        k_dense_write<CharT><<<grid_for(z.n02, 256), 256, 0, st>>>(s, z.n, z.n0, z.n02, kchars, radix, maxc,
                                                                    D.tbl, Rl);
     }
     LOR_LAUNCH_CHECK();
@@ -1151,7 +1153,12 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     int32_t *NSl = (int32_t *)(D.ws + D.L.lev_NS[lvl]);
     const int bits = bit_width_u64(uint64_t(maxc));
     const int kchars = lvl == 0 ? level0_kchars(bits) : 3;
-    const int key_bits = kchars * bits;
+    // Keys are the kchars symbols as digits of base maxc + 1 (most significant
+    // first): T = (maxc + 1)^kchars distinct keys, 0 when that overflows 64 bits.
+    uint64_t T = 1;
+    for (int t = 0; t < kchars && T; ++t)
+        T = T > ~uint64_t(0) / (uint64_t(maxc) + 1) ? 0 : T * (uint64_t(maxc) + 1);
+    const int key_bits = T ? bit_width_u64(T - 1) : kchars * bits;
 
     LOR_CUDA_TRY(cudaMemsetAsync(Rl + z.n02, 0, sizeof(int32_t) * kPad, st));
     int rc;
@@ -1164,14 +1171,16 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
         rc = sample_from_parent<CharT>(D, s, z, bits, PS, PNS, Rl, SAR, NSl, &dups);
         if (rc) return rc;
         rc = read_u32(D, D.d_names, &names);
-    } else if (!D.force_lsd && key_bits <= 24 && (int64_t(1) << key_bits) <= D.L.tbl_entries) {
+    } else if (!D.force_lsd && T && T <= uint64_t(D.L.tbl_entries)) {
         strategy = 1;
-        rc = sample_dense_names<CharT>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR, NSl, &names);
+        rc = sample_dense_names<CharT>(D, lvl, s, z, kchars, int64_t(T), maxc, Rl, SAR, NSl, &names);
         sorted_list = int64_t(names) == z.n02;
     } else {
         strategy = 0;
-        if (key_bits <= 32) rc = sample_sort_and_name<CharT, uint32_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR, NSl);
-        else if (key_bits <= 64) rc = sample_sort_and_name<CharT, uint64_t>(D, lvl, s, z, kchars, bits, maxc, Rl, SAR, NSl);
+        if (T && key_bits <= 32)
+            rc = sample_sort_and_name<CharT, uint32_t>(D, lvl, s, z, kchars, key_bits, maxc, Rl, SAR, NSl);
+        else if (T)
+            rc = sample_sort_and_name<CharT, uint64_t>(D, lvl, s, z, kchars, key_bits, maxc, Rl, SAR, NSl);
         else rc = sample_sort_and_name_wide<CharT>(D, s, z, bits, maxc, Rl, SAR, NSl);
         if (rc) return rc;
         rc = read_u32(D, D.d_names, &names);
