@@ -359,7 +359,7 @@ def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed
     choice, P, Q = gen.request_stream(len(arrivals), lens, queries=queries, seed=seed + 2)
     nreq = len(arrivals)
 
-    srv = lor.Server(int(budget_gb * (1 << 30)), workers=workers, max_batch_pairs=125)
+    srv = lor.Server(int(budget_gb * (1 << 30)), workers=workers, max_batch_pairs=512)
     try:
         # warm-up: every pool pair once, so first-launch setup is not timed
         for k in range(pool_pairs):

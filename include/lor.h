@@ -179,9 +179,10 @@ int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, int64_t n,
  * d_pos     : device int32[pos_cap]; positions beyond pos_cap are dropped
  *             (the offsets still count them).
  * d_ws      : lor_batch_workspace_size(h_lens, npairs) bytes, 256-byte aligned.
- * Pairs are processed in groups of up to 125 pairs (250 sequences) and at
- * most 2^28 symbols; one DC3 suffix array per group is split into per-pair
- * blocks.  Synchronises `stream` a few times per group.
+ * Pairs are processed in groups of up to 512 pairs and at most 2^28 symbols
+ * (a single larger pair forms its own group); one DC3 suffix array over the
+ * concatenated pair texts of a group is split into per-pair blocks.  A symbol
+ * outside ACGT/acgt sets LOR_ERR_BAD_SYMBOL in the status word.  Synchronises `stream` a few times per group.
  * ------------------------------------------------------------------------- */
 size_t lor_batch_workspace_size(const int64_t *h_lens, int32_t npairs);
 int lor_batch_overlap(const uint8_t *d_ascii, const int64_t *h_lens, int32_t npairs,
@@ -249,7 +250,7 @@ typedef struct lor_server lor_server;
 typedef struct {
     size_t hbm_budget_bytes;   /* device memory reserved for batches and resident state */
     int32_t workers;           /* concurrent batches, 1 .. 8 */
-    int32_t max_batch_pairs;   /* 1 .. 125 */
+    int32_t max_batch_pairs;   /* 1 .. 512 */
     int64_t max_batch_symbols; /* text symbols per batch, 1 .. 2^28 (a single larger pair still runs alone) */
 } lor_server_config;
 

@@ -1,13 +1,16 @@
 // batch.cu -- longest overlap region of many sequence pairs at once.
 //
-// Pairs are processed in groups of up to 125 (250 sequences, so that every
-// terminator keeps its own byte code).  For one group a single suffix array is
-// built over the concatenation of all its sequences (each followed by its
-// terminator) with the DC3 of lor_build_sa; a stable one-pass radix sort on
-// the pair id then splits it into one block per pair.  The two terminators of
-// pair p keep their relative order and sort below every base, so block p is
-// exactly the suffix array of the pair's own text S1#S2$ (shifted by the
-// pair's offset in the group text).  The LCP inside the blocks comes from the
+// Pairs are processed in groups of up to 512 pairs and 2^28 symbols.  The
+// group text is the concatenation of every pair's own text S1#S2$ with the
+// codes of a two-sequence text ($ = 1 < # = 2 < A < C < G < T), so the
+// terminator codes repeat from pair to pair.  One suffix array is built over
+// the group text with the DC3 of lor_build_sa; a stable radix sort on the
+// pair id then splits it into one block per pair.  Two suffixes of the same
+// pair are decided at the latest where the first of them reaches its own
+// terminator: at that offset the other holds a base or the other terminator,
+// exactly as in the pair's own text, so the order never depends on what
+// follows a terminator and block p is the suffix array of pair p's S1#S2$
+// (shifted by the pair's offset in the group text).  The LCP inside the blocks comes from the
 // Kasai kernels with the predecessor of every block head cleared, and the
 // overlap is the segmented form of lor_longest_overlap (Section 3): one
 // argmax per block, runs with LCP >= L_p inside blocks, members compacted and
@@ -37,11 +40,11 @@ __device__ __forceinline__ int bseq(const int32_t *st, int nseq, int32_t p) {
 
 __global__ void k_pair_keys(const int32_t *__restrict__ sa, int64_t n, const int32_t *__restrict__ starts,
                             int nseq, uint32_t *__restrict__ key) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ int32_t sst[kGroupSeqs + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
-    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (k < n) key[k] = uint32_t(bseq(sst, nseq, sa[k]) >> 1);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        key[k] = uint32_t(bseq(sst, nseq, sa[k]) >> 1);
 }
 
 __global__ void k_block_starts(const uint32_t *__restrict__ pk, int64_t n, int32_t *__restrict__ bstart) {
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(256) k_seg_argmax(const int32_t *__restrict__ 
                                                     const int32_t *__restrict__ bstart,
                                                     const int32_t *__restrict__ starts, int nseq,
                                                     unsigned long long *best) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ int32_t sst[kGroupSeqs + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -113,12 +116,13 @@ __global__ void k_seg_qual(const int32_t *__restrict__ sa, const uint32_t *__res
                            const unsigned long long *__restrict__ best, int64_t n,
                            const int32_t *__restrict__ starts, int nseq, const int32_t *__restrict__ run_id,
                            uint8_t *__restrict__ qual) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ int32_t sst[kGroupSeqs + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
-    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (k >= n || seg_run_start(k, pk, bstart, lcp, best)) return;
-    if (bseq(sst, nseq, sa[k - 1]) != bseq(sst, nseq, sa[k])) qual[run_id[k]] = 1;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        if (seg_run_start(k, pk, bstart, lcp, best)) continue;
+        if (bseq(sst, nseq, sa[k - 1]) != bseq(sst, nseq, sa[k])) qual[run_id[k]] = 1;
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_seg_members(
@@ -133,11 +137,11 @@ __global__ void __launch_bounds__(kScanThreads) k_seg_members(
 
 __global__ void k_pair_count(const uint32_t *__restrict__ pos, int64_t m, const int32_t *__restrict__ starts,
                              int nseq, int32_t *__restrict__ cnt) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ int32_t sst[kGroupSeqs + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < m) atomicAdd(&cnt[bseq(sst, nseq, int32_t(pos[i])) >> 1], 1);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&cnt[bseq(sst, nseq, int32_t(pos[i])) >> 1], 1);
 }
 
 // One block: records and position offsets of the group's pairs.
@@ -145,7 +149,7 @@ __global__ void k_group_finish(const int32_t *__restrict__ sa, const int32_t *__
                                const unsigned long long *__restrict__ best, const int32_t *__restrict__ cnt,
                                const int32_t *__restrict__ starts, int nseq, int npairs, int64_t pos_base,
                                lor_overlap *__restrict__ out, int64_t *__restrict__ pos_off) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ int32_t sst[kGroupSeqs + 1];
     __shared__ int64_t soff[kPairsPerGroup + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     if (threadIdx.x == 0) {
@@ -194,14 +198,48 @@ __global__ void k_group_finish(const int32_t *__restrict__ sa, const int32_t *__
 __global__ void k_group_positions(const uint32_t *__restrict__ pos, int64_t m,
                                   const int32_t *__restrict__ starts, int nseq, int64_t pos_base,
                                   int32_t *__restrict__ dst, int64_t cap) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ int32_t sst[kGroupSeqs + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= m || pos_base + i >= cap) return;
-    const int32_t x = int32_t(pos[i]);
-    const int pair = bseq(sst, nseq, x) >> 1;
-    dst[pos_base + i] = x - sst[2 * pair];
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m && pos_base + i < cap;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t x = int32_t(pos[i]);
+        const int pair = bseq(sst, nseq, x) >> 1;
+        dst[pos_base + i] = x - sst[2 * pair];
+    }
+}
+
+// Group text: sequence q's bases (ASCII ACGT/acgt -> 3..6) followed by its
+// terminator (# = 2 after the first sequence of a pair, $ = 1 after the
+// second).  starts[q] is where sequence q begins in the text; its ASCII bytes
+// begin at starts[q] - q.  Each thread writes 16 consecutive symbols.
+__global__ void k_encode_group(const uint8_t *__restrict__ ascii, const int32_t *__restrict__ starts, int nseq,
+                               int64_t n, uint8_t *__restrict__ text, int *status) {
+    __shared__ int32_t sst[kGroupSeqs + 1];
+    for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
+    __syncthreads();
+    bool bad = false;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x * 16;
+    for (int64_t x0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 16; x0 < n; x0 += stride) {
+        int q = bseq(sst, nseq, int32_t(x0));
+        for (int64_t x = x0; x < x0 + 16 && x < n; ++x) {
+            while (q + 1 < nseq && x >= sst[q + 1]) ++q;
+            uint8_t c;
+            if (x == sst[q + 1] - 1) {
+                c = (q & 1) ? 1 : 2;
+            } else {
+                switch (ascii[x - q]) {
+                    case 'A': case 'a': c = 3; break;
+                    case 'C': case 'c': c = 4; break;
+                    case 'G': case 'g': c = 5; break;
+                    case 'T': case 't': c = 6; break;
+                    default: c = 3; bad = true;
+                }
+            }
+            text[x] = c;
+        }
+    }
+    if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
 }
 
 struct Group {
@@ -240,7 +278,7 @@ BatchLayout batch_layout(int64_t nmax) {
         return o;
     };
     L.text = take(size_t(nmax));
-    L.starts = take(sizeof(int32_t) * (LOR_MAX_SEQ + 1));
+    L.starts = take(sizeof(int32_t) * (kGroupSeqs + 1));
     L.sa = take(sizeof(int32_t) * size_t(nmax));
     L.region = off;
     size_t r = 0;
@@ -273,13 +311,16 @@ BatchLayout batch_layout(int64_t nmax) {
     L.best = rtake(sizeof(unsigned long long) * kPairsPerGroup);
     L.cnt = rtake(sizeof(int32_t) * kPairsPerGroup);
     L.post = r;
-    const size_t sa_ws = lor_build_sa_workspace_size(nmax, LOR_MAX_SEQ + 5);
+    const size_t sa_ws = lor_build_sa_workspace_size(nmax, 7);
     L.total = L.region + (sa_ws > L.post ? sa_ws : L.post);
     return L;
 }
 
 namespace {
 unsigned gridn(int64_t m, int nt) { return unsigned(cdiv(m > 0 ? m : 1, nt)); }
+// Grid of the grid-stride kernels that stage the group's starts in shared
+// memory first (a few blocks per SM, not one per 256 items).
+unsigned gridc(int64_t m) { return unsigned(min64(cdiv(m > 0 ? m : 1, 256), 152 * 8)); }
 }  // namespace
 
 int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n, char *ws, size_t ws_bytes,
@@ -291,9 +332,25 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
     uint8_t *text = (uint8_t *)(ws + L.text);
     int32_t *starts = (int32_t *)(ws + L.starts);
     int32_t *sa = (int32_t *)(ws + L.sa);
-    int rc = lor_encode_concat(d_ascii, h_lens, nseq, text, starts, stream);
-    if (rc) return rc;
-    rc = lor_build_sa(text, n, nseq + 5, sa, ws + L.region, ws_bytes - L.region, stream);
+    if (np < 1 || np > kPairsPerGroup) return LOR_ERR_INVALID_ARG;
+    {
+        std::vector<int32_t> hst(size_t(nseq) + 1);
+        int64_t x = 0;
+        for (int q = 0; q < nseq; ++q) {
+            hst[q] = int32_t(x);
+            x += h_lens[q] + 1;
+        }
+        hst[nseq] = int32_t(x);
+        if (x != n) return LOR_ERR_INVALID_ARG;
+        // pageable source: the copy has left hst when the call returns
+        LOR_CUDA_TRY(cudaMemcpyAsync(starts, hst.data(), sizeof(int32_t) * hst.size(), cudaMemcpyHostToDevice, s));
+    }
+    {
+        ProfScope ps(PK_ENCODE, double(n) * 2, s);
+        k_encode_group<<<gridc(cdiv(n, 16)), 256, 0, s>>>(d_ascii, starts, nseq, n, text, status);
+    }
+    LOR_LAUNCH_CHECK();
+    int rc = lor_build_sa(text, n, 7, sa, ws + L.region, ws_bytes - L.region, stream);
     if (rc) return rc;
     // The suffix-array workspace is free again: carve the group buffers.
     RadixScratch rs;
@@ -323,7 +380,7 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
     LOR_CUDA_TRY(cudaMemsetAsync(qual, 0, size_t(n), s));
 
     // Per-pair blocks of the suffix array (stable by pair id).
-    k_pair_keys<<<gridn(n, 256), 256, 0, s>>>(sa, n, starts, nseq, pk);
+    k_pair_keys<<<gridc(n), 256, 0, s>>>(sa, n, starts, nseq, pk);
     LOR_LAUNCH_CHECK();
     uint32_t *kr, *vr;
     rc = radix_sort_pairs<uint32_t>(rs, pk, (uint32_t *)sa, pk2, (uint32_t *)sa2, n, 0,
@@ -373,7 +430,7 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
                                                             rs.epoch, status);
         LOR_LAUNCH_CHECK();
         rs.tile_base += (unsigned long long)ntiles;
-        k_seg_qual<<<gridn(n, 256), 256, 0, s>>>(SA, PK, bstart, lcp, best, n, starts, nseq, run_id, qual);
+        k_seg_qual<<<gridc(n), 256, 0, s>>>(SA, PK, bstart, lcp, best, n, starts, nseq, run_id, qual);
         LOR_LAUNCH_CHECK();
         rs.epoch++;
         k_seg_members<<<unsigned(ntiles), kScanThreads, 0, s>>>(SA, n, run_id, qual, mem, d_count,
@@ -393,13 +450,13 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
         if (rc) return rc;
     }
     if (m > 0) {
-        k_pair_count<<<gridn(m, 256), 256, 0, s>>>(mr, m, starts, nseq, cnt);
+        k_pair_count<<<gridc(m), 256, 0, s>>>(mr, m, starts, nseq, cnt);
         LOR_LAUNCH_CHECK();
     }
     k_group_finish<<<1, 128, 0, s>>>(SA, bstart, best, cnt, starts, nseq, np, o.pos_base, o.out, o.pos_off);
     LOR_LAUNCH_CHECK();
     if (m > 0 && o.pos_base < o.pos_cap) {
-        k_group_positions<<<gridn(m, 256), 256, 0, s>>>(mr, m, starts, nseq, o.pos_base, o.pos, o.pos_cap);
+        k_group_positions<<<gridc(m), 256, 0, s>>>(mr, m, starts, nseq, o.pos_base, o.pos, o.pos_cap);
         LOR_LAUNCH_CHECK();
     }
     *h_found = m;

@@ -7,8 +7,11 @@
 
 namespace lor {
 
-// 125 pairs = 250 sequences, the most that keep one byte code per terminator.
-constexpr int kPairsPerGroup = LOR_MAX_SEQ / 2;
+// Pairs per group and their sequences.  Every pair's text inside a group is
+// its own S1#S2$ (the terminator codes are shared by all pairs of the group),
+// so the group size is not bound by the number of terminator codes.
+constexpr int kPairsPerGroup = 512;
+constexpr int kGroupSeqs = 2 * kPairsPerGroup;
 constexpr int64_t kGroupSymbolCap = int64_t(1) << 28;
 
 // Offsets (bytes from the workspace start) of one group's buffers.  The text,

@@ -371,7 +371,7 @@ class Server:
     """Request server of liblor (lor_server_*): submit pairs, poll results,
     ask LCP queries on a polled request, release it."""
 
-    def __init__(self, budget_bytes, workers=2, max_batch_pairs=125, max_batch_symbols=1 << 28):
+    def __init__(self, budget_bytes, workers=2, max_batch_pairs=512, max_batch_symbols=1 << 28):
         L = load()
         cfg = ServerConfig(int(budget_bytes), int(workers), int(max_batch_pairs), int(max_batch_symbols))
         h = ctypes.c_void_p()

@@ -117,7 +117,7 @@ def test_server_batch_bytes_host_only(lib):
     work2, res2 = L.server_batch_bytes([1000, 2000, 5, 7])
     assert work2 >= work1 and res2 >= res1
     # more pairs than one group holds, negative lengths: rejected
-    assert L.server_batch_bytes([10] * 252) == (0, 0)
+    assert L.server_batch_bytes([10] * 1026) == (0, 0)
     assert L.server_batch_bytes([10, -1]) == (0, 0)
 
 
@@ -125,7 +125,7 @@ def test_server_config_validation_is_host_only(lib):
     bad = [
         L.ServerConfig(1 << 30, 0, 8, 1 << 20),    # no workers
         L.ServerConfig(1 << 30, 9, 8, 1 << 20),    # too many workers
-        L.ServerConfig(1 << 30, 2, 126, 1 << 20),  # more pairs than one group holds
+        L.ServerConfig(1 << 30, 2, 513, 1 << 20),  # more pairs than one group holds
         L.ServerConfig(1 << 30, 2, 8, 0),
         L.ServerConfig(1 << 30, 2, 8, (1 << 28) + 1),
         L.ServerConfig(1000, 2, 8, 1 << 20),       # below one granule

@@ -2,8 +2,8 @@
 
 Every pair's record and position list must equal what the oracle computes for
 that pair alone (its own text S1#S2$): batching is an implementation detail
-that changes no result.  Batches here span several groups (125 pairs each),
-hold empty sequences, degenerate pairs and uneven lengths.
+that changes no result.  Batches here span several groups (up to 512 pairs
+each), hold empty sequences, degenerate pairs and uneven lengths.
 """
 import numpy as np
 import pytest
@@ -51,9 +51,8 @@ def assert_same(got, exp, p):
 
 
 def test_batch_small_random_pairs_over_three_groups(L, oracle_mod):
-    rng = np.random.default_rng(11)
     pairs = []
-    for i in range(300):
+    for i in range(1100):
         alpha = [b"ACGT", b"AC", b"A"][i % 3]
         a, b = gen.fuzz_sequences(7000 + i, nseq=2, max_len=[5, 60, 400][i % 3], alphabet=alpha)
         if i % 17 == 0:
@@ -93,3 +92,16 @@ def test_batch_positions_capacity(L, oracle_mod):
     exp = expect_pair(oracle_mod, *pairs[0])
     assert res[0]["n_pos"] == len(exp["positions"])
     np.testing.assert_array_equal(res[0]["positions"], exp["positions"][:5])
+
+
+def test_batch_repeated_pair_many_copies(L, oracle_mod):
+    """300 copies of one pair in one group: the group text is one long
+    repeat (pair texts share their terminator codes), yet every block must
+    still be the pair's own suffix array."""
+    seqs, _ = gen.pair_uniform(n_each=1500, plant_len=120, seed=77)
+    pairs = [seqs] * 300 + [[seqs[1], seqs[0]]]
+    res = run_batch(L, pairs)
+    exp = expect_pair(oracle_mod, *seqs)
+    for p in range(300):
+        assert_same(res[p], exp, p)
+    assert_same(res[300], expect_pair(oracle_mod, seqs[1], seqs[0]), 300)

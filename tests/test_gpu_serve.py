@@ -172,7 +172,7 @@ def test_serve_rejections(L):
 
 def test_serve_many_small_requests_match_batched_path(L):
     pairs = [list(gen.fuzz_sequences(9000 + i, nseq=2, max_len=[8, 300, 3000][i % 3])) for i in range(300)]
-    mix = serve_mix(L, pairs, workers=3, max_pairs=125, gap_s=0)
+    mix = serve_mix(L, pairs, workers=3, max_pairs=512, gap_s=0)
     lens = [len(s) for pr in pairs for s in pr]
     b = L.lor.Batch(lens, pos_cap=1 << 22)
     b.run(torch.from_numpy(np.concatenate([s for pr in pairs for s in pr])).cuda())
