@@ -17,6 +17,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -161,21 +162,32 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
+TRAFFIC_PROFILES = {"large": "dram_by_kind_2x134217728.md"}
+
+
 def ncu_traffic(kind, workload):
-    """DRAM bytes per launch of `kind` from a committed ncu summary, only when
-    it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """DRAM bytes per launch of `kind` from the committed ncu summary of this
+    workload (profiles/, written by paper_1404_3448_gb300.ncu_summary), only
+    when it was taken on the current kernel sources."""
+    name = TRAFFIC_PROFILES.get(workload)
+    if not name:
+        return None
     try:
-        with open(path) as fh:
-            rec = json.load(fh)
-    except (OSError, ValueError):
+        with open(os.path.join(ROOT, "profiles", name)) as fh:
+            text = fh.read()
+    except OSError:
         return None
-    if rec.get("source_hash") != kernel_source_hash():
+    m = re.search(r"source hash: `([0-9a-f]+)`", text)
+    if not m or m.group(1) != kernel_source_hash():
         return None
-    ent = rec.get("kernels", {}).get(kind)
-    if not ent or ent.get("workload") != workload:
-        return None
-    return ent.get("dram_bytes_per_launch")
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) == 6 and cells[0] == kind:
+            try:
+                return float(cells[5])
+            except ValueError:
+                return None
+    return None
 
 
 # --------------------------------------------------------------------------- CPU (oracle)
