@@ -20,8 +20,9 @@ constexpr int kSortThreads = 256;  // == kRadix: one thread per digit in the loo
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kMaxPasses = 8;  // 64-bit keys
 
-// Keys per thread: sized so that three 256-thread blocks fit an SM (at most
-// 85 registers per thread, under 76 KB of shared memory per block).
+// Keys per thread: sized so that four 256-thread blocks fit an SM (64
+// registers per thread, under 57 KB of shared memory per block; the few
+// spilled registers cost less than the occupancy they buy).
 template <typename KeyT, typename ValT = uint32_t>
 __host__ __device__ constexpr int sort_items() { return sizeof(KeyT) + sizeof(ValT) > 8 ? 12 : 16; }
 template <typename KeyT, typename ValT = uint32_t>
@@ -113,7 +114,7 @@ struct OnesweepSmem {
 // order from a running counter, so every predecessor a block waits on is
 // already resident; each wait is still bounded by kSpinLimitNs.
 template <typename KeyT, typename ValT, int kVMode>
-__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const KeyT *__restrict__ kin, const ValT *__restrict__ vin, KeyT *__restrict__ kout,
     ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask,
     const uint32_t *__restrict__ offsets,
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(
 // digit run comes from a shared-memory atomic instead of the stable warp
 // ranking; the look-back and the staged write are those of k_onesweep.
 template <typename ValT, int kVMode>
-__global__ void __launch_bounds__(kSortThreads, 3) k_partition(
+__global__ void __launch_bounds__(kSortThreads, 4) k_partition(
     const uint32_t *__restrict__ kin, const ValT *__restrict__ vin, uint32_t *__restrict__ kout,
     ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask, const uint32_t *__restrict__ offsets,
     uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
