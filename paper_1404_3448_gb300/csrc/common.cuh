@@ -72,6 +72,25 @@ struct ProfScope {
 
 // ---------------------------------------------------------------- device side
 
+// Asks the L2 to fetch [p, p + bytes) ahead of its use (p 16-byte aligned,
+// bytes a multiple of 16): a hint with no effect on results.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Tiles a radix pass asks the L2 to fetch ahead of the one it works on: about
+// the number of tiles resident at once (four 256-thread blocks per SM), so
+// that the data of the tile an SM takes next is already in L2.  0 when a
+// buffer is not 16-byte aligned.
+inline int64_t prefetch_ahead(const void *a, const void *b) {
+    if ((uintptr_t(a) | uintptr_t(b)) & 15) return 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return int64_t(4) * sms;
+}
+
 // Monotonic nanosecond clock shared by all SMs.
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;

@@ -119,13 +119,25 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask,
     const uint32_t *__restrict__ offsets,
     uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
-    uint32_t epoch, int *status) {
+    uint32_t epoch, int *status, int64_t ahead) {
     constexpr int kItems = sort_items<KeyT, ValT>();
     constexpr int kTile = sort_tile<KeyT, ValT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem<KeyT, ValT> &S = *reinterpret_cast<OnesweepSmem<KeyT, ValT> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+    if (tid == 0) {
+        S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+        const int64_t b2 = (S.tile + ahead) * kTile;
+        if (ahead > 0 && b2 < m) {
+            const int64_t c2 = min64(int64_t(kTile), m - b2);
+            const uint32_t kb = uint32_t(c2 * int64_t(sizeof(KeyT))) & ~15u;
+            if (kb) prefetch_l2_bulk(kin + b2, kb);
+            if (kVMode == VM_LOAD) {
+                const uint32_t vb = uint32_t(c2 * int64_t(sizeof(ValT))) & ~15u;
+                if (vb) prefetch_l2_bulk(vin + b2, vb);
+            }
+        }
+    }
     for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t tile = S.tile;
@@ -228,14 +240,26 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
     const uint32_t *__restrict__ kin, const ValT *__restrict__ vin, uint32_t *__restrict__ kout,
     ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask, const uint32_t *__restrict__ offsets,
     uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
-    uint32_t epoch, int *status) {
+    uint32_t epoch, int *status, int64_t ahead) {
     constexpr int kItems = sort_items<uint32_t, ValT>();
     constexpr int kTile = sort_tile<uint32_t, ValT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem<uint32_t, ValT> &S = *reinterpret_cast<OnesweepSmem<uint32_t, ValT> *>(smem_raw);
     uint32_t *cnt = S.warp_hist[0];
     const int tid = threadIdx.x;
-    if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+    if (tid == 0) {
+        S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+        const int64_t b2 = (S.tile + ahead) * kTile;
+        if (ahead > 0 && b2 < m) {
+            const int64_t c2 = min64(int64_t(kTile), m - b2);
+            const uint32_t kb = uint32_t(c2 * 4) & ~15u;
+            if (kb) prefetch_l2_bulk(kin + b2, kb);
+            if (kVMode == VM_LOAD) {
+                const uint32_t vb = uint32_t(c2 * int64_t(sizeof(ValT))) & ~15u;
+                if (vb) prefetch_l2_bulk(vin + b2, vb);
+            }
+        }
+    }
     cnt[tid] = 0;
     __syncthreads();
     const int64_t tile = S.tile;
@@ -378,11 +402,11 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
             if (vals_ready)
                 k_onesweep<KeyT, uint32_t, VM_LOAD><<<unsigned(ntiles), kSortThreads, smem, s>>>(
                     ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
-                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status);
+                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status, prefetch_ahead(ki, vi));
             else
                 k_onesweep<KeyT, uint32_t, VM_IOTA><<<unsigned(ntiles), kSortThreads, smem, s>>>(
                     ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
-                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status);
+                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status, prefetch_ahead(ki, ki));
         }
         LOR_LAUNCH_CHECK();
         rs.tile_base += (unsigned long long)ntiles;
@@ -447,7 +471,7 @@ int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int
                      s);
         k_partition<ValT, kVMode><<<unsigned(ntiles), kSortThreads, smem, s>>>(
             keys, vals, kout, vout, m, lo, digit_mask(lo, top), rs.offsets, rs.lookback, rs.tile_ctr,
-            rs.tile_base, rs.epoch, rs.status);
+            rs.tile_base, rs.epoch, rs.status, prefetch_ahead(keys, kVMode == VM_LOAD ? (const void *)vals : keys));
     }
     LOR_LAUNCH_CHECK();
     rs.tile_base += (unsigned long long)ntiles;
