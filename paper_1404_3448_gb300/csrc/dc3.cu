@@ -52,6 +52,7 @@ struct Dc3Layout {
     size_t ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
     size_t tbl = 0;
     int64_t tbl_entries = 0;
+    size_t split = 0;  // merge-path partition of the largest level
     size_t t64[3] = {0, 0, 0};
     size_t t32[6] = {0, 0, 0, 0, 0, 0};
     int64_t max_m = 0;
@@ -87,6 +88,7 @@ Dc3Layout dc3_layout(int64_t n) {
     L.tbl = take(sizeof(uint32_t) * size_t(L.tbl_entries));
     // t64[1], t64[2] are adjacent: together they hold the merge records.
     for (int i = 0; i < 3; ++i) L.t64[i] = take(sizeof(uint64_t) * size_t(L.max_m));
+    L.split = take(sizeof(int64_t) * size_t(cdiv(n, 1024) + 2));
     for (int i = 0; i < 6; ++i) L.t32[i] = take(sizeof(uint32_t) * size_t(L.max_m));
     for (size_t l = 0; l < L.lev_n.size(); ++l) {
         const int64_t m = level_sizes(L.lev_n[l]).n02;
@@ -134,6 +136,69 @@ __global__ void __launch_bounds__(256) k_sample_keys(const CharT *__restrict__ s
     keys[j] = key;
 }
 
+// Level-0 keys staged through shared memory.  Block (x, c) makes the keys of
+// kKeyTile consecutive samples of one class: c = 0 positions 3j+1 (j < n0,
+// stored at j), c = 1 positions 3j+2 (j < n2, stored at n0 + j).  The text
+// bytes the tile needs are read once, coalesced, and validated (codes must
+// lie in [1, maxc]); every radix pass's digit histogram is counted on the
+// way, so the sort needs no separate histogram read of the keys.
+constexpr int kKeyTile = 2048;
+constexpr int kKeyMaxChars = 64;
+
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_sample_keys0(const uint8_t *__restrict__ s, int64_t n, int64_t n0,
+                                                      int64_t n2, int kchars, uint32_t radix, int64_t maxc,
+                                                      KeyT *__restrict__ keys, int npasses, int end_bit,
+                                                      uint32_t *__restrict__ hist, int *status) {
+    __shared__ uint8_t txt[3 * kKeyTile + kKeyMaxChars];
+    __shared__ uint32_t sh[kMaxPasses * kRadix];
+    const int tid = threadIdx.x;
+    const int cls = int(blockIdx.y);
+    const int64_t ncls = cls == 0 ? n0 : n2;
+    const int64_t j0 = int64_t(blockIdx.x) * kKeyTile;
+    if (j0 >= ncls) return;  // uniform over the block
+    const int nj = int(min64(int64_t(kKeyTile), ncls - j0));
+    const int64_t p0 = 3 * j0 + 1 + cls;
+    const int span = 3 * (nj - 1) + kchars;
+    bool bad = false;
+    for (int i = tid; i < span; i += 256) {
+        const int64_t q = p0 + i;
+        uint32_t c = 0;
+        if (q < n) {
+            c = s[q];
+            if (c < 1 || c > uint32_t(maxc)) {  // keeps the key inside its range
+                bad = true;
+                c = c < 1 ? 1u : uint32_t(maxc);
+            }
+        }
+        txt[i] = uint8_t(c);
+    }
+    for (int i = tid; i < npasses * kRadix; i += 256) sh[i] = 0;
+    if (blockIdx.x == 0 && cls == 0 && tid == 0 && n > 0) {
+        const uint32_t c = s[0];
+        if (c < 1 || c > uint32_t(maxc)) bad = true;
+    }
+    __syncthreads();
+    KeyT *out = keys + (cls == 0 ? 0 : n0) + j0;
+    for (int k = tid; k < nj; k += 256) {
+        const uint8_t *w = txt + 3 * k;
+        KeyT key = 0;
+        for (int t = 0; t < kchars; ++t) key = key * KeyT(radix) + KeyT(w[t]);
+        out[k] = key;
+        if (hist)
+            for (int p = 0; p < npasses; ++p) {
+                const int sft = p * kRadixBits;
+                atomicAdd(&sh[p * kRadix + digit_of(key, sft, digit_mask(sft, end_bit))], 1u);
+            }
+    }
+    if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
+    if (hist) {
+        __syncthreads();
+        for (int i = tid; i < npasses * kRadix; i += 256)
+            if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    }
+}
+
 // Step 1 naming: name(j) = 1 + number of key changes in sorted[0..j].
 // Writes R[val] = name, SA_R[j] = val, and the name count.
 template <typename KeyT>
@@ -153,18 +218,21 @@ __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ 
     const int64_t tile = s_tile;
     const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
     KeyT prev = (base > 0 && base - 1 < m) ? keys[base - 1] : KeyT(0);
+    KeyT kk[kScanItems];
+    load_run<KeyT, kScanItems>(keys, base, m, KeyT(0), kk);
     uint32_t flags = 0, cnt = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t j = base + i;
         if (j < m) {
-            const KeyT k = keys[j];
-            const uint32_t f = (j == 0 || k != prev) ? 1u : 0u;
+            const uint32_t f = (j == 0 || kk[i] != prev) ? 1u : 0u;
             flags |= f << i;
             cnt += f;
-            prev = k;
+            prev = kk[i];
         }
     }
+    uint32_t vv[kScanItems];
+    load_run<uint32_t, kScanItems>(vals, base, m, 0u, vv);
     uint32_t agg;
     const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
     if (tid < 32) {
@@ -173,18 +241,19 @@ __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ 
     }
     __syncthreads();
     uint32_t name = s_prefix + excl;
+    int32_t nm[kScanItems];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
+        name += (flags >> i) & 1u;
+        nm[i] = int32_t(name);
         const int64_t j = base + i;
         if (j < m) {
-            name += (flags >> i) & 1u;
-            const uint32_t v = vals[j];
-            if (R) R[v] = int32_t(name);
-            SAR[j] = int32_t(v);
-            NS[j] = int32_t(name);
+            if (R) R[vv[i]] = int32_t(name);
             if (j == m - 1) *n_names = name;
         }
     }
+    store_run<int32_t, kScanItems>(SAR, base, m, reinterpret_cast<const int32_t(&)[kScanItems]>(vv));
+    store_run<int32_t, kScanItems>(NS, base, m, nm);
 }
 
 // Naming after a two-stage sort: equality of triples is checked on the
@@ -414,6 +483,7 @@ __device__ __forceinline__ bool a_less_b(const ARec &x, const BRec &y) {
 constexpr int kMergeThreads = 512;
 constexpr int kMergeItems = 2;
 constexpr int kMergeTile = kMergeThreads * kMergeItems;
+static_assert(kMergeTile >= 1024, "the workspace holds a partition entry per 1024 merged suffixes");
 
 // Number of sample suffixes among the first d merged suffixes.
 template <typename CharT>
@@ -821,14 +891,147 @@ __global__ void __launch_bounds__(kScanThreads) k_dbl_next(
         [&](int64_t i, uint32_t d) { ul2[d] = ul[i]; }, lb, ctr, tile_base, epoch, status, count, ntiles);
 }
 
+// The rest of the doubling in one block once few samples are unresolved:
+// every pass of the loop above (keys, sort, run ranks, next unresolved set)
+// on a shared-memory copy of the unresolved list, sorted by a block bitonic
+// sort, until no group holds more than one sample.  Keys of a pass are all
+// read before any rank of that pass is written, as in the multi-kernel loop.
+constexpr int kDblSmall = 4096;
+constexpr int kDblSmallThreads = 1024;
+constexpr int kDblSmallRounds = 40;
+
+struct DblSmallSmem {
+    uint64_t key[kDblSmall];
+    uint32_t val[kDblSmall];
+    uint32_t ul[kDblSmall];
+    uint32_t run[kDblSmall];    // run id (1-based) of each sorted element
+    uint32_t rstart[kDblSmall];  // first element of each run
+    uint32_t scratch[kDblSmallThreads / 32 + 1];
+    uint32_t count;
+};
+
+__global__ void __launch_bounds__(kDblSmallThreads) k_dbl_small(const uint32_t *__restrict__ ul_in,
+                                                                const uint32_t *U_in, int64_t m, int64_t h0,
+                                                                int shift, int32_t *__restrict__ SAR,
+                                                                int32_t *__restrict__ R, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DblSmallSmem &S = *reinterpret_cast<DblSmallSmem *>(smem_raw);
+    const int tid = threadIdx.x;
+    constexpr int kPer = kDblSmall / kDblSmallThreads;
+    int U = int(*U_in);
+    if (U > kDblSmall) {
+        if (tid == 0) atomicCAS(status, 0, LOR_ERR_INVALID_ARG);
+        return;
+    }
+    for (int i = tid; i < U; i += kDblSmallThreads) S.ul[i] = ul_in[i];
+    __syncthreads();
+    int64_t h = h0;
+    for (int round = 0; U > 0; ++round, h *= 2) {
+        if (h >= m || round >= kDblSmallRounds) {  // cannot happen for a valid R
+            if (tid == 0) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+            return;
+        }
+        int P = 1;
+        while (P < U) P <<= 1;
+        for (int i = tid; i < P; i += kDblSmallThreads) {
+            if (i < U) {
+                const int32_t j = SAR[S.ul[i]];
+                const uint32_t r2 = j + h < m ? uint32_t(R[j + h]) : 0u;
+                S.key[i] = (uint64_t(uint32_t(R[j])) << shift) | r2;
+                S.val[i] = uint32_t(j);
+            } else {
+                S.key[i] = ~uint64_t(0);
+                S.val[i] = 0;
+            }
+        }
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = tid; i < P; i += kDblSmallThreads) {
+                    const int l = i ^ jj;
+                    if (l > i) {
+                        const bool up = (i & k) == 0;
+                        const uint64_t a = S.key[i], b = S.key[l];
+                        if ((a > b) == up) {
+                            S.key[i] = b;
+                            S.key[l] = a;
+                            const uint32_t t = S.val[i];
+                            S.val[i] = S.val[l];
+                            S.val[l] = t;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // Run ids: blocked kPer items per thread, block scan of the run starts.
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int i = tid * kPer + q;
+            if (i < U && (i == 0 || S.key[i] != S.key[i - 1])) cnt++;
+        }
+        uint32_t total;
+        uint32_t r = block_excl_scan<kDblSmallThreads>(cnt, S.scratch, &total);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int i = tid * kPer + q;
+            if (i < U) {
+                if (i == 0 || S.key[i] != S.key[i - 1]) {
+                    ++r;
+                    S.rstart[r - 1] = uint32_t(i);
+                }
+                S.run[i] = r;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < U; i += kDblSmallThreads) {
+            SAR[S.ul[i]] = int32_t(S.val[i]);
+            R[S.val[i]] = int32_t(S.ul[S.rstart[S.run[i] - 1]] + 1);
+        }
+        // Next unresolved set: members of runs with more than one element.
+        cnt = 0;
+        bool keep[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int i = tid * kPer + q;
+            keep[q] = i < U && ((i > 0 && S.run[i - 1] == S.run[i]) || (i + 1 < U && S.run[i + 1] == S.run[i]));
+            cnt += keep[q] ? 1u : 0u;
+        }
+        uint32_t o = block_excl_scan<kDblSmallThreads>(cnt, S.scratch, &total);
+        uint32_t nxt[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) nxt[q] = keep[q] ? S.ul[tid * kPer + q] : 0u;
+        __syncthreads();  // every old list entry is read before the list is rewritten
+#pragma unroll
+        for (int q = 0; q < kPer; ++q)
+            if (keep[q]) S.ul[o++] = nxt[q];
+        U = int(total);
+        __syncthreads();
+    }
+}
+
 struct TraceRow {
     int64_t n, names;
     int32_t key_bits;
 };
 thread_local std::vector<TraceRow> g_trace;
 
-int level0_kchars(int bits) {
-    int k = 3;
+// Symbols named at level 0: by default the longest prefix whose key, in base
+// maxc + 1, fits 48 bits (six 8-bit radix passes; 17 symbols for a DNA pair),
+// so that on text without long repeats the names come out almost unique and
+// the reduced string is finished by prefix doubling.  Naming by any prefix of
+// at least 3 symbols keeps the order of the reduced string's suffixes equal
+// to the order of the sample suffixes.  LOR_DC3_K0 overrides it (a test hook).
+constexpr int kLevel0KeyBits = 48;
+
+int level0_kchars(int bits, int64_t maxc) {
+    int k = 0;
+    for (unsigned __int128 T = 1; k < kKeyMaxChars; ++k) {
+        T *= uint64_t(maxc) + 1;
+        if (T > (unsigned __int128)1 << kLevel0KeyBits) break;
+    }
+    if (k < 3) k = 3;
     if (const char *e = std::getenv("LOR_DC3_K0")) {
         const int v = std::atoi(e);
         if (v >= 3) k = v;
@@ -904,19 +1107,27 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
     const uint64_t radix = uint64_t(maxc) + 1;
     cudaStream_t st = D.s;
     KeyT *k0 = (KeyT *)D.t64[0], *k1 = (KeyT *)D.t64[1];
-    {
-        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (sizeof(KeyT) + (lvl == 0 ? 1.0 : 4.0) * kchars / 3.0), st);
-        if (lvl == 0)
-            k_sample_keys<CharT, KeyT, true><<<grid_for(z.n02, 256), 256, 0, st>>>(
-                s, z.n, z.n0, z.n02, 0, kchars, radix, maxc, k0, D.status);
-        else
-            k_sample_keys<CharT, KeyT, false><<<grid_for(z.n02, 256), 256, 0, st>>>(
-                s, z.n, z.n0, z.n02, 0, kchars, radix, maxc, k0, D.status);
+    bool hist_ready = false;
+    if constexpr (sizeof(CharT) == 1) {
+        // Level 0: staged keys with the digit histograms counted on the way.
+        const int npasses = int(cdiv(key_bits, kRadixBits));
+        if (kchars > kKeyMaxChars || npasses > kMaxPasses) return LOR_ERR_INVALID_ARG;
+        LOR_CUDA_TRY(cudaMemsetAsync(D.rs.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, st));
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * sizeof(KeyT) + double(z.n), st);
+        const dim3 grid(unsigned(cdiv(max64(z.n0, z.n2), kKeyTile)), 2);
+        k_sample_keys0<KeyT><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n2, kchars, uint32_t(radix), maxc, k0,
+                                                   npasses, key_bits, D.rs.hist, D.status);
+        hist_ready = true;
+    } else {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (sizeof(KeyT) + 4.0 * kchars / 3.0), st);
+        k_sample_keys<CharT, KeyT, false><<<grid_for(z.n02, 256), 256, 0, st>>>(
+            s, z.n, z.n0, z.n02, 0, kchars, radix, maxc, k0, D.status);
     }
     LOR_LAUNCH_CHECK();
     KeyT *kr;
     uint32_t *vr;
-    int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, key_bits, true, &kr, &vr);
+    int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, key_bits, true, &kr, &vr,
+                                    hist_ready);
     if (rc) return rc;
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 16), st);
@@ -1111,6 +1322,14 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
     for (int64_t h = 1; hU > 0; h *= 2) {
         if (h >= m) return LOR_ERR_BAD_INPUT;  // cannot happen for a valid R
         const int64_t U = hU;
+        if (U <= kDblSmall) {
+            ProfScope ps(PK_NAMING, double(U) * 48, st);
+            const size_t smem = sizeof(DblSmallSmem);
+            LOR_CUDA_TRY(cudaFuncSetAttribute(k_dbl_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            k_dbl_small<<<1, kDblSmallThreads, smem, st>>>(ul, D.d_count, m, h, shift, SAR, Rl, D.status);
+            LOR_LAUNCH_CHECK();
+            break;
+        }
         {
             ProfScope ps(PK_SAMPLE_KEYS, double(U) * 24, st);
             k_dbl_keys<<<grid_for(U, 256), 256, 0, st>>>(ul, U, SAR, Rl, m, h, shift, k0, val);
@@ -1152,7 +1371,7 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     int32_t *SAR = (int32_t *)(D.ws + D.L.lev_SAR[lvl]);
     int32_t *NSl = (int32_t *)(D.ws + D.L.lev_NS[lvl]);
     const int bits = bit_width_u64(uint64_t(maxc));
-    const int kchars = lvl == 0 ? level0_kchars(bits) : 3;
+    const int kchars = lvl == 0 ? level0_kchars(bits, maxc) : 3;
     // Keys are the kchars symbols as digits of base maxc + 1 (most significant
     // first): T = (maxc + 1)^kchars distinct keys, 0 when that overflows 64 bits.
     uint64_t T = 1;
@@ -1269,7 +1488,10 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     a.B = B;
     a.nb = z.n0;
     const int64_t ntiles = cdiv(n, kMergeTile);
-    int64_t *split = (int64_t *)((char *)D.t64[1] + rec_bytes);
+    // The records fill at most t64[1..2] (16 bytes per position at level 0,
+    // 32 per group of three below); the partition has a region of its own.
+    if (rec_bytes > size_t((char *)D.t64[2] - (char *)D.t64[1]) * 2) return LOR_ERR_WORKSPACE;
+    int64_t *split = (int64_t *)(D.ws + D.L.split);
     {
         ProfScope ps(PK_MERGE, double(n) * (4 + 4 + sizeof(GroupRec<CharT>)), st);
         k_merge_partition<CharT><<<grid_for(ntiles + 1, 128), 128, 0, st>>>(a, ntiles, split);

@@ -354,9 +354,12 @@ inline size_t radix_lookback_bytes(int64_t max_m) {
 // input; (k1, v1) are same-sized buffers.  On return *kres / *vres point at
 // whichever pair holds the sorted result.  When iota_vals is set the values
 // are taken to be 0..m-1 and v0 is not read.
+// When hist_ready is set the caller has already counted every pass's digits
+// into rs.hist (zeroed first), e.g. in the kernel that made the keys.
 template <typename KeyT>
 int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v1, int64_t m,
-                     int begin_bit, int end_bit, bool iota_vals, KeyT **kres, uint32_t **vres) {
+                     int begin_bit, int end_bit, bool iota_vals, KeyT **kres, uint32_t **vres,
+                     bool hist_ready = false) {
     cudaStream_t s = rs.stream;
     *kres = k0;
     *vres = v0;
@@ -368,13 +371,15 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
     if (cdiv(m, sort_tile<KeyT, uint32_t>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
     uint32_t hh[kMaxPasses * kRadix];
     if (npasses > 0) {
-        LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * npasses * kRadix, s));
-        {
-            ProfScope ps(PK_RADIX_HIST, double(m) * sizeof(KeyT), s);
-            const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
-            k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, begin_bit, end_bit, npasses, rs.hist);
+        if (!hist_ready) {
+            LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * npasses * kRadix, s));
+            {
+                ProfScope ps(PK_RADIX_HIST, double(m) * sizeof(KeyT), s);
+                const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
+                k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, begin_bit, end_bit, npasses, rs.hist);
+            }
+            LOR_LAUNCH_CHECK();
         }
-        LOR_LAUNCH_CHECK();
         k_radix_offsets<<<npasses, kRadix, 0, s>>>(rs.hist, rs.offsets);
         LOR_LAUNCH_CHECK();
         LOR_CUDA_TRY(cudaMemcpyAsync(hh, rs.hist, sizeof(uint32_t) * npasses * kRadix,

@@ -11,6 +11,38 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Loads the N consecutive items p[base .. base+N) of one thread (entries at
+// or past m read as `fill`): 16-byte loads when the run is whole and aligned.
+template <typename T, int N>
+__device__ __forceinline__ void load_run(const T *__restrict__ p, int64_t base, int64_t m, T fill, T (&out)[N]) {
+    static_assert((N * sizeof(T)) % 16 == 0, "run must be whole 16-byte chunks");
+    if (base + N <= m && ((uintptr_t)(p + base) & 15) == 0) {
+        const int4 *q = reinterpret_cast<const int4 *>(p + base);
+        int4 *o = reinterpret_cast<int4 *>(out);
+#pragma unroll
+        for (int c = 0; c < int(N * sizeof(T) / 16); ++c) o[c] = q[c];
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = base + i < m ? p[base + i] : fill;
+    }
+}
+
+// Stores the N consecutive items of one thread at p[base ..], those below m.
+template <typename T, int N>
+__device__ __forceinline__ void store_run(T *__restrict__ p, int64_t base, int64_t m, const T (&v)[N]) {
+    static_assert((N * sizeof(T)) % 16 == 0, "run must be whole 16-byte chunks");
+    if (base + N <= m && ((uintptr_t)(p + base) & 15) == 0) {
+        int4 *q = reinterpret_cast<int4 *>(p + base);
+        const int4 *o = reinterpret_cast<const int4 *>(v);
+#pragma unroll
+        for (int c = 0; c < int(N * sizeof(T) / 16); ++c) q[c] = o[c];
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (base + i < m) p[base + i] = v[i];
+    }
+}
+
 // ---- generic order-preserving tile compaction and naming (look-back scans)
 
 // Every kernel below handles kScanTile consecutive items per block (blocked:

@@ -288,17 +288,21 @@ def noncoding_16M(O):
     return seqs, info, e, p, q, O.lcp_pairs(e["text"], p, q)
 
 
-@pytest.mark.parametrize("strategy", ["auto", "nodbl"])
+@pytest.mark.parametrize("strategy", ["auto", "nodbl", "k3nodbl"])
 def test_noncoding_workload_2x16M(L, O, noncoding_16M, strategy, monkeypatch):
-    set_strategy(monkeypatch, strategy)
+    if strategy == "k3nodbl":  # level 0 named by triples: a dense level, then sorted and parent levels
+        monkeypatch.setenv("LOR_DC3_K0", "3")
+    set_strategy(monkeypatch, "nodbl" if strategy == "k3nodbl" else strategy)
     seqs, info, e, p, q, answers = noncoding_16M
     g = gpu_path(L, seqs, (p, q), rmq=True)
     assert_full_parity(O, g, e, table=False)
     np.testing.assert_array_equal(g["answers"], answers)
     assert g["overlap"]["length"] >= info["core"]
     used = [t["strategy"] for t in L.last_dc3_trace()]
-    if strategy == "nodbl":
+    if strategy == "k3nodbl":
         assert set(used) == {"dense", "sort", "parent"}, L.last_dc3_trace()
+    elif strategy == "nodbl":
+        assert used[0] == "sort" and "parent" in used and "doubling" not in used, L.last_dc3_trace()
     else:
         assert used[-1] == "doubling" and "sort" in used, L.last_dc3_trace()
 
