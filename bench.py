@@ -284,6 +284,31 @@ def batch_vs_plain(npairs, steps, warmup, dev, seed=140434484):
     torch.cuda.synchronize(dev)
     batch_ms = evs[0].elapsed_time(evs[-1]) / steps
     batch_steps = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    eager_out = b.out.clone()
+    del b
+    torch.cuda.empty_cache()
+
+    # the same pipeline captured once into a CUDA graph and replayed
+    t0 = time.perf_counter()
+    gb = lor.lor.BatchGraph(lens, ascii_dev, device=dev, pos_cap=1 << 24)
+    capture_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        gb.run()
+    torch.cuda.synchronize(dev)
+    lor.check_device(where="batch graph warmup")
+    graph_same = bool(torch.equal(gb.out, eager_out))
+    gev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    gev[0].record(stream)
+    for i in range(steps):
+        gb.run()
+        gev[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = gev[0].elapsed_time(gev[-1]) / steps
+    graph_steps = [gev[i].elapsed_time(gev[i + 1]) for i in range(steps)]
+    graph_kernels = gb.kernels
+    gb.close()
+    del gb
+    torch.cuda.empty_cache()
 
     # plain: one pair per call, buffers sized for the largest pair
     nmax = int(max(lens[0::2] + lens[1::2])) + 2
@@ -326,6 +351,7 @@ def batch_vs_plain(npairs, steps, warmup, dev, seed=140434484):
     plain_ms = pe[0].elapsed_time(pe[-1])
     per_pair = [pe[i].elapsed_time(pe[i + 1]) for i in range(npairs)]
     batch_value = n_bases / (batch_ms / 1000.0)
+    graph_value = n_bases / (graph_ms / 1000.0)
     plain_value = n_bases / (plain_ms / 1000.0)
     return {
         "workload": f"{npairs} noncoding-like pairs, per-sequence lengths log-uniform in [1k, 1M], "
@@ -334,10 +360,16 @@ def batch_vs_plain(npairs, steps, warmup, dev, seed=140434484):
         "batched": {"value": batch_value, "unit": UNIT, "ms_per_step": batch_ms,
                     "step_latency_ms": {"p50": percentile(batch_steps, 50),
                                         "p99": percentile(batch_steps, 99)}, "steps": steps},
+        "batched_graph": {"value": graph_value, "unit": UNIT, "ms_per_step": graph_ms,
+                          "step_latency_ms": {"p50": percentile(graph_steps, 50),
+                                              "p99": percentile(graph_steps, 99)}, "steps": steps,
+                          "capture_s": capture_s, "kernels_per_replay": graph_kernels,
+                          "records_equal_eager": graph_same},
         "plain": {"value": plain_value, "unit": UNIT, "ms_all_pairs": plain_ms,
                   "pair_latency_ms": {"p50": percentile(per_pair, 50), "p99": percentile(per_pair, 99),
                                       "max": max(per_pair)}},
         "batched_over_plain": batch_value / plain_value,
+        "graph_over_plain": graph_value / plain_value,
     }
 
 
@@ -535,6 +567,37 @@ def run_lor(args):
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
+    # ---- linear-space RMQ on the same LCP array and queries (a side measurement)
+    rmq_linear = None
+    try:
+        btab = lor.rmq_block_build(pipe.lcp)
+        bans = torch.empty_like(p_dev)
+        torch.cuda.synchronize(dev)
+        r0, r1, r2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        reps = 5
+        r0.record(stream)
+        for _ in range(reps):
+            lor.rmq_block_build(pipe.lcp, table=btab)
+        r1.record(stream)
+        for _ in range(reps):
+            lor.rmq_block_query(btab, pipe.lcp, pipe.isa, p_dev, q_dev, out=bans)
+        r2.record(stream)
+        torch.cuda.synchronize(dev)
+        lor.check_device(where="block rmq")
+        pipe.run(ascii_dev, p_dev, q_dev, ans_dev)
+        torch.cuda.synchronize(dev)
+        rmq_linear = {
+            "table_bytes": int(btab.numel()) * 4,
+            "sparse_table_bytes": int(pipe.table.numel()) * 4,
+            "build_ms": r0.elapsed_time(r1) / reps,
+            "query_ms": r1.elapsed_time(r2) / reps,
+            "queries": int(p_np.size),
+            "answers_equal_sparse_table": bool(torch.equal(bans, ans_dev)),
+        }
+        del btab, bans
+    except Exception as exc:  # reported, not hidden
+        rmq_linear = {"error": str(exc)}
+
     ms_all, e2e_all, p50, p99 = max_over_ranks(
         [ms, e2e_ms, percentile(step_ms, 50), percentile(step_ms, 99)], device=dev)
 
@@ -577,6 +640,7 @@ def run_lor(args):
             "clocks": clocks.summary(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
+            "rmq_linear": rmq_linear,
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
         }
@@ -605,7 +669,7 @@ def main():
     ap.add_argument("--impl", default="lor", choices=["lor", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch-pairs", type=int, default=1024,
+    ap.add_argument("--batch-pairs", type=int, default=4096,
                     help="pairs of the batched-vs-plain sub-measurement (0 skips it)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson arrivals of the served sub-measurement (0 skips it)")

@@ -190,6 +190,103 @@ int lor_batch_overlap(const uint8_t *d_ascii, const int64_t *h_lens, int32_t npa
                       void *d_ws, size_t ws_bytes, lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched longest overlap replayed from one CUDA graph (no counterpart in
+ * the paper; the batched pipeline of lor_batch_overlap captured once and
+ * launched any number of times).
+ *
+ * lor_batch_graph_create captures the whole grouped pipeline for a fixed list
+ * of pair lengths and fixed device buffers (d_ascii, d_out, d_pos_off, d_pos,
+ * d_ws, the same meaning and layout as for lor_batch_overlap) into a CUDA
+ * graph, without any host round trip inside: the suffix array of each group
+ * sorts the level-0 sample by its 48-bit prefix and finishes the reduced
+ * string by prefix doubling with every round enqueued up front (rounds whose
+ * unresolved count, held on the device, is 0 do nothing); counts of later
+ * stages stay on the device too.  Nothing runs on the device at creation.
+ * lor_batch_graph_launch enqueues one replay on `stream`: it reads whatever
+ * bases d_ascii holds at that time and writes every pair's record and
+ * positions exactly as lor_batch_overlap does for them.
+ * d_ws: lor_batch_graph_workspace_size(h_lens, npairs) bytes, 256-byte
+ * aligned, used by nothing else while the graph exists.  Replays of one graph
+ * must not overlap on the device (they share d_ws).  The graph owns a little
+ * pinned host memory, freed by lor_batch_graph_destroy.
+ * Returns LOR_ERR_CUDA when capture or instantiation fails.
+ * ------------------------------------------------------------------------- */
+typedef struct lor_batch_graph lor_batch_graph;
+size_t lor_batch_graph_workspace_size(const int64_t *h_lens, int32_t npairs);
+int lor_batch_graph_create(const uint8_t *d_ascii, const int64_t *h_lens, int32_t npairs,
+                           lor_overlap *d_out, int64_t *d_pos_off, int32_t *d_pos, int64_t pos_cap,
+                           void *d_ws, size_t ws_bytes, lor_batch_graph **out);
+int lor_batch_graph_launch(lor_batch_graph *g, lor_stream_t stream);
+/* Kernels one replay launches (for launch accounting). */
+int64_t lor_batch_graph_kernels(const lor_batch_graph *g);
+int lor_batch_graph_destroy(lor_batch_graph *g);
+
+/* ---------------------------------------------------------------------------
+ * a11/a12 in linear space (Section 3: the same range minimum, stored in
+ * O(n) words; the paper's own linear-space RMQ is a +-1 RMQ over a Cartesian
+ * tree, this is a block decomposition).
+ * The LCP array is cut into blocks of 32 entries; the table is a sparse
+ * table over the block minima: levels = floor(log2 nb) + 1 rows of
+ * stride = nb rounded up to 64 entries, nb = ceil(n / 32), with
+ * table[j*stride + b] = min(blockmin[b .. min(b + 2^j, nb) - 1]) and
+ * blockmin[b] = min(lcp[32b .. min(32b + 32, n) - 1]).  d_table must be
+ * 256-byte aligned and hold lor_rmq_block_table_elems(n) int32 entries
+ * (n / 32 * (log2 n - 4) words, under a tenth of the sparse table at any n
+ * above 2^16).
+ * lor_rmq_block_query answers exactly what lor_rmq_query answers (same
+ * arguments, same errors) and also reads d_lcp: the partial blocks at both
+ * ends of a rank range are scanned in the LCP array, the whole blocks between
+ * them read from the table.
+ * ------------------------------------------------------------------------- */
+int64_t lor_rmq_block_table_elems(int64_t n);
+int lor_rmq_block_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
+                        lor_stream_t stream);
+int lor_rmq_block_query(const int32_t *d_table, const int32_t *d_lcp, const int32_t *d_isa, int64_t n,
+                        const int32_t *d_p, const int32_t *d_q, int64_t nq, int32_t *d_out,
+                        lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch parameters and their autotuner (no counterpart in the paper).
+ *
+ * Every value gives the same results; only the speed differs.  The
+ * configuration is process-wide: set it before work is enqueued from other
+ * threads.  A call reads it when it starts; a CUDA graph keeps the values it
+ * was captured with.
+ *   digit_bits      radix digit width of every sort pass, 5..8 (default 8)
+ *   level0_key_bits width of the level-0 sample keys, 24..60 (default 48): DC3
+ *                   level 0 names the longest prefix whose key in base
+ *                   (largest code + 1) fits it, so wider keys cost radix passes
+ *                   and leave fewer repeated names for the later rounds
+ *   sort_items_64   keys per thread of a sort pass over 64-bit keys: 8 or 12 (12)
+ *   sort_items_32   keys per thread over 32-bit keys: 12 or 16 (16)
+ *   merge_items     merged suffixes per thread of the Step-3 merge: 2 (512-thread
+ *                   blocks) or 4 (256-thread blocks); default 2
+ * lor_tune_set returns LOR_ERR_INVALID_ARG for a value out of range (and
+ * changes nothing).
+ *
+ * lor_autotune_batch times lor_batch_overlap on the caller's pairs (the same
+ * arguments, buffers and workspace as lor_batch_overlap) for candidate values,
+ * one parameter at a time in the order above, starting from the current
+ * configuration and keeping a change only when it is faster: every candidate
+ * runs once untimed and then `reps` times (1..100) between CUDA events on
+ * `stream`.  On return the fastest configuration found is set and copied to
+ * *best, and *best_ms holds its time per run.  Synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t digit_bits;
+    int32_t level0_key_bits;
+    int32_t sort_items_64;
+    int32_t sort_items_32;
+    int32_t merge_items;
+} lor_tune;
+void lor_tune_default(lor_tune *cfg);
+int lor_tune_get(lor_tune *cfg);
+int lor_tune_set(const lor_tune *cfg);
+int lor_autotune_batch(const uint8_t *d_ascii, const int64_t *h_lens, int32_t npairs, lor_overlap *d_out,
+                       int64_t *d_pos_off, int32_t *d_pos, int64_t pos_cap, void *d_ws, size_t ws_bytes,
+                       int32_t reps, lor_stream_t stream, lor_tune *best, double *best_ms);
+
+/* ---------------------------------------------------------------------------
  * a11. Sparse table over the LCP array for range-minimum queries (Section 3:
  * RMQ definition; the LCP of arbitrary suffixes is a range minimum).
  * Layout: level-major, levels = floor(log2 n) + 1 rows of

@@ -327,6 +327,20 @@ def sparse_table(lcp) -> np.ndarray:
     return st
 
 
+def block_minima(lcp, block: int = 32) -> np.ndarray:
+    """min(lcp[b*block : min((b+1)*block, n)]) for every block b (the blocks
+    of the linear-space range-minimum structure; Section 3 RMQ)."""
+    lcp = np.asarray(lcp, dtype=np.int32)
+    n = lcp.size
+    nb = -(-n // block)
+    return np.array([lcp[b * block:min((b + 1) * block, n)].min() for b in range(nb)], dtype=np.int32)
+
+
+def block_sparse_table(lcp, block: int = 32) -> np.ndarray:
+    """The sparse table over the block minima (rows as in sparse_table)."""
+    return sparse_table(block_minima(lcp, block))
+
+
 def lcp_pairs(text, p, q) -> np.ndarray:
     """LCP of suffixes p[i] and q[i] by direct symbol comparison; the LCP of a
     suffix with itself is its length (Section 3, lcp of arbitrary suffixes)."""

@@ -11,7 +11,23 @@ LOR_DEFINE_TU_STATUS(lor_status_abi)
 namespace lor {
 
 static std::atomic<unsigned long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// While a thread captures work into a CUDA graph its launches are counted
+// apart (they run when the graph is launched, as often as it is launched).
+static thread_local bool t_capturing = false;
+static thread_local unsigned long long t_captured = 0;
+void note_launch() {
+    if (t_capturing) ++t_captured;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void capture_begin() {
+    t_capturing = true;
+    t_captured = 0;
+}
+unsigned long long capture_end() {
+    t_capturing = false;
+    return t_captured;
+}
+void note_graph_launches(unsigned long long kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- timing
 
@@ -45,8 +61,26 @@ const char *kKindNames[PK_COUNT] = {
 
 bool prof_enabled() { return g_prof_on; }
 
+// ---------------------------------------------------------------- launch parameters
+
+namespace {
+std::mutex g_tune_mu;
+TuneConfig g_tune;
+}  // namespace
+
+TuneConfig tune_config() {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_tune;
+}
+
+static bool tune_valid(const lor_tune &c) {
+    return c.digit_bits >= 5 && c.digit_bits <= 8 && c.level0_key_bits >= 24 && c.level0_key_bits <= 60 &&
+           (c.sort_items_64 == 8 || c.sort_items_64 == 12) && (c.sort_items_32 == 12 || c.sort_items_32 == 16) &&
+           (c.merge_items == 2 || c.merge_items == 4);
+}
+
 ProfScope::ProfScope(int kind, double bytes, cudaStream_t s) : stream(s) {
-    if (!g_prof_on) return;
+    if (!g_prof_on || t_capturing) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     ProfRec r;
     r.kind = kind;
@@ -212,5 +246,37 @@ extern "C" int lor_radix_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t 
         LOR_CUDA_TRY(cudaMemcpyAsync(d_keys, kr, sizeof(uint64_t) * size_t(m), cudaMemcpyDeviceToDevice, s));
         LOR_CUDA_TRY(cudaMemcpyAsync(d_vals, vr, sizeof(uint32_t) * size_t(m), cudaMemcpyDeviceToDevice, s));
     }
+    return LOR_OK;
+}
+
+extern "C" void lor_tune_default(lor_tune *cfg) {
+    if (!cfg) return;
+    const TuneConfig d;
+    cfg->digit_bits = d.digit_bits;
+    cfg->level0_key_bits = d.level0_key_bits;
+    cfg->sort_items_64 = d.sort_items_64;
+    cfg->sort_items_32 = d.sort_items_32;
+    cfg->merge_items = d.merge_items;
+}
+
+extern "C" int lor_tune_get(lor_tune *cfg) {
+    if (!cfg) return LOR_ERR_INVALID_ARG;
+    const TuneConfig c = tune_config();
+    cfg->digit_bits = c.digit_bits;
+    cfg->level0_key_bits = c.level0_key_bits;
+    cfg->sort_items_64 = c.sort_items_64;
+    cfg->sort_items_32 = c.sort_items_32;
+    cfg->merge_items = c.merge_items;
+    return LOR_OK;
+}
+
+extern "C" int lor_tune_set(const lor_tune *cfg) {
+    if (!cfg || !tune_valid(*cfg)) return LOR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune.digit_bits = cfg->digit_bits;
+    g_tune.level0_key_bits = cfg->level0_key_bits;
+    g_tune.sort_items_64 = cfg->sort_items_64;
+    g_tune.sort_items_32 = cfg->sort_items_32;
+    g_tune.merge_items = cfg->merge_items;
     return LOR_OK;
 }

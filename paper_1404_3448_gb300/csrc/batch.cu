@@ -16,6 +16,7 @@
 // argmax per block, runs with LCP >= L_p inside blocks, members compacted and
 // sorted.  Every pair's record and positions equal those of lor_longest_overlap
 // run on that pair alone.
+#include <algorithm>
 #include <vector>
 
 #include "batch.cuh"
@@ -135,9 +136,11 @@ __global__ void __launch_bounds__(kScanThreads) k_seg_members(
         ntiles);
 }
 
-__global__ void k_pair_count(const uint32_t *__restrict__ pos, int64_t m, const int32_t *__restrict__ starts,
-                             int nseq, int32_t *__restrict__ cnt) {
+// m_dev (when given) holds the member count on the device.
+__global__ void k_pair_count(const uint32_t *__restrict__ pos, int64_t m, const uint32_t *m_dev,
+                             const int32_t *__restrict__ starts, int nseq, int32_t *__restrict__ cnt) {
     __shared__ int32_t sst[kGroupSeqs + 1];
+    if (m_dev) m = int64_t(*m_dev);
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += int64_t(gridDim.x) * blockDim.x)
@@ -145,12 +148,16 @@ __global__ void k_pair_count(const uint32_t *__restrict__ pos, int64_t m, const 
 }
 
 // One block: records and position offsets of the group's pairs.
+// pos_base_dev (when given) holds the group's first position slot on the
+// device.
 __global__ void k_group_finish(const int32_t *__restrict__ sa, const int32_t *__restrict__ bstart,
                                const unsigned long long *__restrict__ best, const int32_t *__restrict__ cnt,
                                const int32_t *__restrict__ starts, int nseq, int npairs, int64_t pos_base,
-                               lor_overlap *__restrict__ out, int64_t *__restrict__ pos_off) {
+                               const int64_t *pos_base_dev, lor_overlap *__restrict__ out,
+                               int64_t *__restrict__ pos_off) {
     __shared__ int32_t sst[kGroupSeqs + 1];
     __shared__ int64_t soff[kPairsPerGroup + 1];
+    if (pos_base_dev) pos_base = *pos_base_dev;
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     if (threadIdx.x == 0) {
         int64_t acc = 0;
@@ -195,10 +202,12 @@ __global__ void k_group_finish(const int32_t *__restrict__ sa, const int32_t *__
 
 // Positions sorted by text position are grouped by pair, in pair order: the
 // i-th goes to slot pos_base + i, as an offset inside its pair's own text.
-__global__ void k_group_positions(const uint32_t *__restrict__ pos, int64_t m,
+__global__ void k_group_positions(const uint32_t *__restrict__ pos, int64_t m, const uint32_t *m_dev,
                                   const int32_t *__restrict__ starts, int nseq, int64_t pos_base,
-                                  int32_t *__restrict__ dst, int64_t cap) {
+                                  const int64_t *pos_base_dev, int32_t *__restrict__ dst, int64_t cap) {
     __shared__ int32_t sst[kGroupSeqs + 1];
+    if (m_dev) m = int64_t(*m_dev);
+    if (pos_base_dev) pos_base = *pos_base_dev;
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m && pos_base + i < cap;
@@ -207,6 +216,11 @@ __global__ void k_group_positions(const uint32_t *__restrict__ pos, int64_t m,
         const int pair = bseq(sst, nseq, x) >> 1;
         dst[pos_base + i] = x - sst[2 * pair];
     }
+}
+
+// The next group's first position slot: this group's plus its count.
+__global__ void k_group_pos_advance(int64_t *pos_base_dev, const uint32_t *m_dev) {
+    if (threadIdx.x == 0) *pos_base_dev += int64_t(*m_dev);
 }
 
 // Group text: sequence q's bases (ASCII ACGT/acgt -> 3..6) followed by its
@@ -324,9 +338,9 @@ unsigned gridc(int64_t m) { return unsigned(min64(cdiv(m > 0 ? m : 1, 256), 152 
 }  // namespace
 
 int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n, char *ws, size_t ws_bytes,
-                const BatchLayout &L, int64_t nmax, const GroupOutputs &o, int64_t *h_found, cudaStream_t s) {
+                const BatchLayout &L, int64_t nmax, const GroupOutputs &o, int64_t *h_found, cudaStream_t s,
+                const GroupGraph *g) {
     const int nseq = 2 * np;
-    lor_stream_t stream = (lor_stream_t)s;
     int *status = tu_status_ptr();
     if (!status) return LOR_ERR_CUDA;
     uint8_t *text = (uint8_t *)(ws + L.text);
@@ -342,15 +356,22 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
         }
         hst[nseq] = int32_t(x);
         if (x != n) return LOR_ERR_INVALID_ARG;
-        // pageable source: the copy has left hst when the call returns
-        LOR_CUDA_TRY(cudaMemcpyAsync(starts, hst.data(), sizeof(int32_t) * hst.size(), cudaMemcpyHostToDevice, s));
+        if (g) {
+            // captured copy: the source must outlive the graph (pinned, owned by it)
+            std::copy(hst.begin(), hst.end(), g->h_starts);
+            LOR_CUDA_TRY(cudaMemcpyAsync(starts, g->h_starts, sizeof(int32_t) * hst.size(), cudaMemcpyHostToDevice, s));
+        } else {
+            // pageable source: the copy has left hst when the call returns
+            LOR_CUDA_TRY(cudaMemcpyAsync(starts, hst.data(), sizeof(int32_t) * hst.size(), cudaMemcpyHostToDevice, s));
+        }
     }
     {
         ProfScope ps(PK_ENCODE, double(n) * 2, s);
         k_encode_group<<<gridc(cdiv(n, 16)), 256, 0, s>>>(d_ascii, starts, nseq, n, text, status);
     }
     LOR_LAUNCH_CHECK();
-    int rc = lor_build_sa(text, n, 7, sa, ws + L.region, ws_bytes - L.region, stream);
+    int rc = build_sa_impl(text, n, 7, sa, ws + L.region, ws_bytes - L.region, s, g ? g->sa_pool : nullptr,
+                           g ? g->sa_pool_size : 0);
     if (rc) return rc;
     // The suffix-array workspace is free again: carve the group buffers.
     RadixScratch rs;
@@ -361,6 +382,12 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
     rs.max_tiles = cdiv(nmax, kMinSortTile);
     rs.status = status;
     rs.stream = s;
+    if (g) {
+        rs.graph = true;
+        rs.ctr_pool = g->post_pool;
+        rs.ctr_pool_size = g->post_pool_size;
+        LOR_CUDA_TRY(cudaMemsetAsync(g->post_pool, 0, sizeof(unsigned long long) * size_t(g->post_pool_size), s));
+    }
     uint32_t *pk = (uint32_t *)(ws + L.pk), *pk2 = (uint32_t *)(ws + L.pk2);
     int32_t *sa2 = (int32_t *)(ws + L.sa2), *isa = (int32_t *)(ws + L.isa);
     int32_t *plcp = (int32_t *)(ws + L.plcp), *lcp = (int32_t *)(ws + L.lcp);
@@ -439,6 +466,24 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
         LOR_LAUNCH_CHECK();
         rs.tile_base += (unsigned long long)ntiles;
     }
+    if (g) {
+        // The member count stays on the device: everything below is sized by
+        // its bound n and reads the count itself.
+        uint32_t *mr, *mv;
+        rc = radix_sort_pairs<uint32_t>(rs, mem, va, kb, vb, n, 0, bit_width_u64(uint64_t(n - 1)), true, &mr, &mv,
+                                        false, d_count);
+        if (rc) return rc;
+        k_pair_count<<<gridc(n), 256, 0, s>>>(mr, n, d_count, starts, nseq, cnt);
+        LOR_LAUNCH_CHECK();
+        k_group_finish<<<1, 128, 0, s>>>(SA, bstart, best, cnt, starts, nseq, np, 0, g->pos_base, o.out, o.pos_off);
+        LOR_LAUNCH_CHECK();
+        k_group_positions<<<gridc(n), 256, 0, s>>>(mr, n, d_count, starts, nseq, 0, g->pos_base, o.pos, o.pos_cap);
+        LOR_LAUNCH_CHECK();
+        k_group_pos_advance<<<1, 32, 0, s>>>(g->pos_base, d_count);
+        LOR_LAUNCH_CHECK();
+        *h_found = 0;
+        return LOR_OK;
+    }
     uint32_t h_count = 0;
     LOR_CUDA_TRY(cudaMemcpyAsync(&h_count, d_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     LOR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -450,13 +495,15 @@ int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n
         if (rc) return rc;
     }
     if (m > 0) {
-        k_pair_count<<<gridc(m), 256, 0, s>>>(mr, m, starts, nseq, cnt);
+        k_pair_count<<<gridc(m), 256, 0, s>>>(mr, m, nullptr, starts, nseq, cnt);
         LOR_LAUNCH_CHECK();
     }
-    k_group_finish<<<1, 128, 0, s>>>(SA, bstart, best, cnt, starts, nseq, np, o.pos_base, o.out, o.pos_off);
+    k_group_finish<<<1, 128, 0, s>>>(SA, bstart, best, cnt, starts, nseq, np, o.pos_base, nullptr, o.out,
+                                     o.pos_off);
     LOR_LAUNCH_CHECK();
     if (m > 0 && o.pos_base < o.pos_cap) {
-        k_group_positions<<<gridc(m), 256, 0, s>>>(mr, m, starts, nseq, o.pos_base, o.pos, o.pos_cap);
+        k_group_positions<<<gridc(m), 256, 0, s>>>(mr, m, nullptr, starts, nseq, o.pos_base, nullptr, o.pos,
+                                                   o.pos_cap);
         LOR_LAUNCH_CHECK();
     }
     *h_found = m;
@@ -497,9 +544,131 @@ extern "C" int lor_batch_overlap(const uint8_t *d_ascii, const int64_t *h_lens, 
         const GroupOutputs o{d_out + g.p0, d_pos_off + g.p0, d_pos, pos_cap, pos_base};
         int64_t m = 0;
         const int rc = batch_group(d_ascii ? d_ascii + g.in0 : nullptr, h_lens + 2 * g.p0, g.np, g.n, ws,
-                                   ws_bytes, L, nmax, o, &m, s);
+                                   ws_bytes, L, nmax, o, &m, s, nullptr);
         if (rc) return rc;
         pos_base += m;
     }
+    return LOR_OK;
+}
+
+// ---------------------------------------------------------------- CUDA graph
+
+namespace lor {
+namespace {
+constexpr int kGraphSaPool = 1024;   // tile counters of device-sized launches, per group
+constexpr int kGraphPostPool = 64;
+
+struct GraphExtra {
+    size_t sa_pool, post_pool, pos_base, total;
+};
+GraphExtra graph_extra(size_t base) {
+    GraphExtra E;
+    E.sa_pool = align256(base);
+    E.post_pool = align256(E.sa_pool + sizeof(unsigned long long) * kGraphSaPool);
+    E.pos_base = align256(E.post_pool + sizeof(unsigned long long) * kGraphPostPool);
+    E.total = align256(E.pos_base + sizeof(int64_t));
+    return E;
+}
+}  // namespace
+}  // namespace lor
+
+struct lor_batch_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t *h_starts = nullptr;  // pinned: the captured copies read it at every replay
+    unsigned long long kernels = 0;
+};
+
+extern "C" size_t lor_batch_graph_workspace_size(const int64_t *h_lens, int32_t npairs) {
+    const size_t base = lor_batch_workspace_size(h_lens, npairs);
+    return base ? graph_extra(base).total : 0;
+}
+
+extern "C" int lor_batch_graph_create(const uint8_t *d_ascii, const int64_t *h_lens, int32_t npairs,
+                                      lor_overlap *d_out, int64_t *d_pos_off, int32_t *d_pos, int64_t pos_cap,
+                                      void *d_ws, size_t ws_bytes, lor_batch_graph **out) {
+    if (!out || !h_lens || npairs < 1 || !d_out || !d_pos_off || pos_cap < 0) return LOR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (pos_cap > 0 && !d_pos) return LOR_ERR_INVALID_ARG;
+    for (int i = 0; i < 2 * npairs; ++i)
+        if (h_lens[i] < 0) return LOR_ERR_INVALID_ARG;
+    const std::vector<Group> groups = make_groups(h_lens, npairs);
+    int64_t nmax = 1, total_in = 0;
+    for (const Group &g : groups) nmax = g.n > nmax ? g.n : nmax;
+    for (int i = 0; i < 2 * npairs; ++i) total_in += h_lens[i];
+    if (nmax > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    if (total_in > 0 && !d_ascii) return LOR_ERR_INVALID_ARG;
+    const BatchLayout L = batch_layout(nmax);
+    const GraphExtra E = graph_extra(L.total);
+    if (!d_ws || ws_bytes < E.total || (uintptr_t(d_ws) & 255)) return LOR_ERR_WORKSPACE;
+    char *ws = (char *)d_ws;
+
+    lor_batch_graph *G = new lor_batch_graph();
+    size_t nst = 0;
+    for (const Group &g : groups) nst += size_t(2 * g.np + 1);
+    if (cudaMallocHost(&G->h_starts, sizeof(int32_t) * nst) != cudaSuccess) {
+        delete G;
+        return LOR_ERR_CUDA;
+    }
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFreeHost(G->h_starts);
+        delete G;
+        return LOR_ERR_CUDA;
+    }
+    int rc = LOR_OK;
+    capture_begin();
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LOR_ERR_CUDA;
+    if (rc == LOR_OK) {
+        int64_t *pos_base = (int64_t *)(ws + E.pos_base);
+        if (cudaMemsetAsync(pos_base, 0, sizeof(int64_t), cs) != cudaSuccess) rc = LOR_ERR_CUDA;
+        size_t st = 0;
+        for (size_t gi = 0; gi < groups.size() && rc == LOR_OK; ++gi) {
+            const Group &g = groups[gi];
+            GroupGraph gg;
+            gg.sa_pool = (unsigned long long *)(ws + E.sa_pool);
+            gg.sa_pool_size = kGraphSaPool;
+            gg.post_pool = (unsigned long long *)(ws + E.post_pool);
+            gg.post_pool_size = kGraphPostPool;
+            gg.pos_base = pos_base;
+            gg.h_starts = G->h_starts + st;
+            st += size_t(2 * g.np + 1);
+            const GroupOutputs o{d_out + g.p0, d_pos_off + g.p0, d_pos, pos_cap, 0};
+            int64_t found = 0;
+            rc = batch_group(d_ascii ? d_ascii + g.in0 : nullptr, h_lens + 2 * g.p0, g.np, g.n, ws, L.total, L,
+                             nmax, o, &found, cs, &gg);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (rc == LOR_OK && (e != cudaSuccess || !graph)) rc = LOR_ERR_CUDA;
+        G->graph = graph;
+    }
+    G->kernels = capture_end();
+    cudaStreamDestroy(cs);
+    if (rc == LOR_OK && cudaGraphInstantiate(&G->exec, G->graph, 0) != cudaSuccess) rc = LOR_ERR_CUDA;
+    if (rc != LOR_OK) {
+        cudaGetLastError();
+        lor_batch_graph_destroy(G);
+        return rc;
+    }
+    *out = G;
+    return LOR_OK;
+}
+
+extern "C" int lor_batch_graph_launch(lor_batch_graph *g, lor_stream_t stream) {
+    if (!g || !g->exec) return LOR_ERR_INVALID_ARG;
+    if (cudaGraphLaunch(g->exec, (cudaStream_t)stream) != cudaSuccess) return LOR_ERR_CUDA;
+    note_graph_launches(g->kernels);
+    return LOR_OK;
+}
+
+extern "C" int64_t lor_batch_graph_kernels(const lor_batch_graph *g) { return g ? int64_t(g->kernels) : 0; }
+
+extern "C" int lor_batch_graph_destroy(lor_batch_graph *g) {
+    if (!g) return LOR_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->h_starts) cudaFreeHost(g->h_starts);
+    delete g;
     return LOR_OK;
 }

@@ -26,6 +26,13 @@ struct BatchLayout {
 
 BatchLayout batch_layout(int64_t nmax);
 
+// lor_build_sa with, when graph_ctr_pool is given, no host round trip at all
+// (for stream capture): level 0 and then enqueued doubling rounds, with the
+// tile counters of device-sized launches taken from the pool (graph_pool_size
+// zeroed counters; the call zeroes them itself first).
+int build_sa_impl(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa, void *d_ws, size_t ws_bytes,
+                  cudaStream_t stream, unsigned long long *graph_ctr_pool, int graph_pool_size);
+
 // Where one group writes its results: np overlap records, np + 1 position
 // offsets (starting at pos_base) and its positions at pos[pos_base ...]
 // (positions at or beyond pos_cap are counted but not stored).
@@ -37,6 +44,19 @@ struct GroupOutputs {
     int64_t pos_base;
 };
 
+// Graph mode of batch_group (work captured into a CUDA graph): the counter
+// pools of the suffix array and of the rest, the device-held first position
+// slot of the group (advanced by the group's count), and pinned host memory
+// for the group's sequence starts that lives as long as the graph.
+struct GroupGraph {
+    unsigned long long *sa_pool;
+    int sa_pool_size;
+    unsigned long long *post_pool;
+    int post_pool_size;
+    int64_t *pos_base;
+    int32_t *h_starts;
+};
+
 // Runs one group of np pairs (ASCII bases of all 2*np sequences back to back
 // at d_ascii, lengths h_lens[0 .. 2*np), text length n = sum + 2*np) on
 // stream s.  On return (LOR_OK) the group's results are enqueued, *h_found
@@ -44,6 +64,7 @@ struct GroupOutputs {
 // terminator starts, per-pair ISA (ws + L.isa: rank of every text position in
 // the blocked suffix array) and LCP (ws + L.lcp, 0 at every block head).
 int batch_group(const uint8_t *d_ascii, const int64_t *h_lens, int np, int64_t n, char *ws, size_t ws_bytes,
-                const BatchLayout &L, int64_t nmax, const GroupOutputs &o, int64_t *h_found, cudaStream_t s);
+                const BatchLayout &L, int64_t nmax, const GroupOutputs &o, int64_t *h_found, cudaStream_t s,
+                const GroupGraph *g = nullptr);
 
 }  // namespace lor

@@ -29,6 +29,10 @@ inline int bit_width_u64(uint64_t v) {  // number of bits needed to hold v
 
 // Launch accounting and kernel timing (defined in abi.cu).
 void note_launch();
+// Stream capture on this thread: launches are counted for the graph, not run.
+void capture_begin();
+unsigned long long capture_end();  // kernels captured since capture_begin
+void note_graph_launches(unsigned long long kernels);
 enum ProfKind {
     PK_ENCODE = 0,
     PK_SAMPLE_KEYS,
@@ -48,6 +52,19 @@ enum ProfKind {
     PK_COUNT
 };
 bool prof_enabled();
+
+// Launch parameters picked by the autotuner (lor_autotune_batch) or set with
+// lor_tune_set; every value gives the same results, only the speed differs.
+// A call reads the configuration once when it starts (a CUDA graph keeps the
+// one it was captured with).
+struct TuneConfig {
+    int digit_bits = 8;        // radix digit width of the sorts, 5..8 bits
+    int level0_key_bits = 48;  // width of the level-0 sample keys (the symbols named at level 0)
+    int sort_items_64 = 12;    // keys per thread of a sort pass over 64-bit keys: 8 or 12
+    int sort_items_32 = 16;    // ... over 32-bit keys: 12 or 16
+    int merge_items = 2;       // merged suffixes per thread of the Step-3 merge: 2 (512 threads) or 4 (256)
+};
+TuneConfig tune_config();
 // Records an event pair around one launch when profiling is on.
 struct ProfScope {
     int slot = -1;
@@ -78,17 +95,57 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Tiles a radix pass asks the L2 to fetch ahead of the one it works on: about
-// the number of tiles resident at once (four 256-thread blocks per SM), so
-// that the data of the tile an SM takes next is already in L2.  0 when a
-// buffer is not 16-byte aligned.
-inline int64_t prefetch_ahead(const void *a, const void *b) {
+// Tiles a radix pass asks the L2 to fetch ahead of the one it works on: the
+// number of tiles resident at once (four 256-thread blocks per SM, or the
+// grid of a persistent pass), so that the data of the tile a block takes next
+// is already in L2.  0 when a buffer is not 16-byte aligned.
+inline int64_t prefetch_ahead(const void *a, const void *b, int64_t resident = 0) {
     if ((uintptr_t(a) | uintptr_t(b)) & 15) return 0;
+    if (resident > 0) return resident;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
     return int64_t(4) * sms;
+}
+
+// ---- mbarrier + bulk (TMA) copies into shared memory
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return uint32_t(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Makes initialised barriers visible to the async proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later bulk
+// copies into shared memory (generic -> async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
 // Monotonic nanosecond clock shared by all SMs.
@@ -100,6 +157,15 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Every inter-block wait gives up after this long and reports LOR_ERR_TIMEOUT.
 constexpr uint64_t kSpinLimitNs = 2000000000ull;  // 2 s
+
+// Waits for phase `parity` of a barrier, at most kSpinLimitNs; false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kSpinLimitNs) return false;
+    return true;
+}
 
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
     uint64_t v;

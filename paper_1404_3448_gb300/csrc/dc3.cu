@@ -18,6 +18,7 @@
 #include <cstdlib>
 #include <vector>
 
+#include "batch.cuh"
 #include "radix.cuh"
 #include "scan.cuh"
 
@@ -149,7 +150,7 @@ template <typename KeyT>
 __global__ void __launch_bounds__(256) k_sample_keys0(const uint8_t *__restrict__ s, int64_t n, int64_t n0,
                                                       int64_t n2, int kchars, uint32_t radix, int64_t maxc,
                                                       KeyT *__restrict__ keys, int npasses, int end_bit,
-                                                      uint32_t *__restrict__ hist, int *status) {
+                                                      int dbits, uint32_t *__restrict__ hist, int *status) {
     __shared__ uint8_t txt[3 * kKeyTile + kKeyMaxChars];
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     const int tid = threadIdx.x;
@@ -187,8 +188,8 @@ __global__ void __launch_bounds__(256) k_sample_keys0(const uint8_t *__restrict_
         out[k] = key;
         if (hist)
             for (int p = 0; p < npasses; ++p) {
-                const int sft = p * kRadixBits;
-                atomicAdd(&sh[p * kRadix + digit_of(key, sft, digit_mask(sft, end_bit))], 1u);
+                const int sft = p * dbits;
+                atomicAdd(&sh[p * kRadix + digit_of(key, sft, digit_mask(sft, end_bit, dbits))], 1u);
             }
     }
     if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
@@ -478,11 +479,10 @@ __device__ __forceinline__ bool a_less_b(const ARec &x, const BRec &y) {
     return x.r < y.r2;
 }
 
-// 512 threads x 2 outputs: the record gathers are latency bound, and wide
-// blocks with few items each keep the most of them in flight per SM.
-constexpr int kMergeThreads = 512;
-constexpr int kMergeItems = 2;
-constexpr int kMergeTile = kMergeThreads * kMergeItems;
+// A merge tile is 1024 outputs: 512 threads x 2 (the default: the record
+// gathers are latency bound, and wide blocks with few items each keep the most
+// of them in flight per SM) or 256 threads x 4 (tune_config().merge_items).
+constexpr int kMergeTile = 1024;
 static_assert(kMergeTile >= 1024, "the workspace holds a partition entry per 1024 merged suffixes");
 
 // Number of sample suffixes among the first d merged suffixes.
@@ -511,10 +511,11 @@ __global__ void k_merge_partition(MergeIn<CharT> a, int64_t ntiles, int64_t *__r
     split[t] = merge_split(a, d);
 }
 
-template <typename CharT>
-__global__ void __launch_bounds__(kMergeThreads) k_merge(MergeIn<CharT> a,
-                                                         const int64_t *__restrict__ split,
-                                                         int32_t *__restrict__ out, int *status) {
+template <typename CharT, int kMergeItems>
+__global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge(MergeIn<CharT> a,
+                                                                    const int64_t *__restrict__ split,
+                                                                    int32_t *__restrict__ out, int *status) {
+    constexpr int kMergeThreads = kMergeTile / kMergeItems;
     __shared__ ARec As[kMergeTile];
     __shared__ BRec Bs[kMergeTile];
     __shared__ int32_t Os[kMergeTile];
@@ -910,19 +911,23 @@ struct DblSmallSmem {
     uint32_t count;
 };
 
+// When skip_big is set an unresolved set larger than kDblSmall is left for
+// the multi-kernel rounds (no error); a finished set zeroes *U_in.
 __global__ void __launch_bounds__(kDblSmallThreads) k_dbl_small(const uint32_t *__restrict__ ul_in,
-                                                                const uint32_t *U_in, int64_t m, int64_t h0,
+                                                                uint32_t *U_in, int64_t m, int64_t h0,
                                                                 int shift, int32_t *__restrict__ SAR,
-                                                                int32_t *__restrict__ R, int *status) {
+                                                                int32_t *__restrict__ R, int *status,
+                                                                int skip_big) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DblSmallSmem &S = *reinterpret_cast<DblSmallSmem *>(smem_raw);
     const int tid = threadIdx.x;
     constexpr int kPer = kDblSmall / kDblSmallThreads;
     int U = int(*U_in);
     if (U > kDblSmall) {
-        if (tid == 0) atomicCAS(status, 0, LOR_ERR_INVALID_ARG);
+        if (tid == 0 && !skip_big) atomicCAS(status, 0, LOR_ERR_INVALID_ARG);
         return;
     }
+    if (U == 0) return;
     for (int i = tid; i < U; i += kDblSmallThreads) S.ul[i] = ul_in[i];
     __syncthreads();
     int64_t h = h0;
@@ -1009,6 +1014,62 @@ __global__ void __launch_bounds__(kDblSmallThreads) k_dbl_small(const uint32_t *
         U = int(total);
         __syncthreads();
     }
+    if (tid == 0) *U_in = 0;
+}
+
+// The doubling round kernels over a device-held unresolved count (graph
+// mode): grid-stride or resident-block forms of the kernels above.
+__global__ void k_dbl_keys_dev(const uint32_t *__restrict__ ul, const uint32_t *U_dev,
+                               const int32_t *__restrict__ SAR, const int32_t *__restrict__ R, int64_t m,
+                               int64_t h, int shift, uint64_t *__restrict__ key, uint32_t *__restrict__ val) {
+    const int64_t U = int64_t(*U_dev);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < U; i += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t j = SAR[ul[i]];
+        const uint32_t r2 = j + h < m ? uint32_t(R[j + h]) : 0u;
+        key[i] = (uint64_t(uint32_t(R[j])) << shift) | r2;
+        val[i] = uint32_t(j);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_dbl_runs_dev(
+    const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, const uint32_t *__restrict__ ul,
+    const uint32_t *U_dev, int32_t *__restrict__ SAR, uint32_t *__restrict__ runid,
+    uint32_t *__restrict__ rstart, uint64_t *lb, unsigned long long *ctr, uint32_t epoch, int *status) {
+    tile_names_dyn(
+        U_dev, [&](int64_t i) { return i == 0 || key[i] != key[i - 1]; },
+        [&](int64_t i, uint32_t r) {
+            SAR[ul[i]] = int32_t(val[i]);
+            runid[i] = r;
+            if (i == 0 || key[i] != key[i - 1]) rstart[r - 1] = uint32_t(i);
+        },
+        lb, ctr, epoch, status);
+}
+
+__global__ void k_dbl_rank_dev(const uint32_t *__restrict__ val, const uint32_t *__restrict__ runid,
+                               const uint32_t *__restrict__ rstart, const uint32_t *__restrict__ ul,
+                               const uint32_t *U_dev, int32_t *__restrict__ R) {
+    const int64_t U = int64_t(*U_dev);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < U; i += int64_t(gridDim.x) * blockDim.x)
+        R[val[i]] = int32_t(ul[rstart[runid[i] - 1]] + 1);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_dbl_next_dev(
+    const uint32_t *__restrict__ runid, const uint32_t *__restrict__ ul, const uint32_t *U_dev,
+    uint32_t *__restrict__ ul2, uint32_t *count, uint64_t *lb, unsigned long long *ctr, uint32_t epoch,
+    int *status) {
+    const int64_t U = int64_t(*U_dev);
+    tile_compact_dyn(
+        U_dev,
+        [&](int64_t i) {
+            const uint32_t r = runid[i];
+            return (i > 0 && runid[i - 1] == r) || (i + 1 < U && runid[i + 1] == r);
+        },
+        [&](int64_t i, uint32_t d) { ul2[d] = ul[i]; }, lb, ctr, epoch, status, count);
+}
+
+// After the last enqueued round nothing may be left unresolved.
+__global__ void k_dbl_check_done(const uint32_t *U_dev, int *status) {
+    if (threadIdx.x == 0 && *U_dev != 0) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
 }
 
 struct TraceRow {
@@ -1017,19 +1078,19 @@ struct TraceRow {
 };
 thread_local std::vector<TraceRow> g_trace;
 
-// Symbols named at level 0: by default the longest prefix whose key, in base
-// maxc + 1, fits 48 bits (six 8-bit radix passes; 17 symbols for a DNA pair),
+// Symbols named at level 0: the longest prefix whose key, in base maxc + 1,
+// fits the configured key width (48 bits by default: six 8-bit radix passes,
+// 17 symbols for a DNA pair),
 // so that on text without long repeats the names come out almost unique and
 // the reduced string is finished by prefix doubling.  Naming by any prefix of
 // at least 3 symbols keeps the order of the reduced string's suffixes equal
 // to the order of the sample suffixes.  LOR_DC3_K0 overrides it (a test hook).
-constexpr int kLevel0KeyBits = 48;
-
 int level0_kchars(int bits, int64_t maxc) {
+    const int budget = tune_config().level0_key_bits;
     int k = 0;
     for (unsigned __int128 T = 1; k < kKeyMaxChars; ++k) {
         T *= uint64_t(maxc) + 1;
-        if (T > (unsigned __int128)1 << kLevel0KeyBits) break;
+        if (T > (unsigned __int128)1 << budget) break;
     }
     if (k < 3) k = 3;
     if (const char *e = std::getenv("LOR_DC3_K0")) {
@@ -1110,13 +1171,14 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
     bool hist_ready = false;
     if constexpr (sizeof(CharT) == 1) {
         // Level 0: staged keys with the digit histograms counted on the way.
-        const int npasses = int(cdiv(key_bits, kRadixBits));
+        const int dbits = tune_config().digit_bits;
+        const int npasses = int(cdiv(key_bits, dbits));
         if (kchars > kKeyMaxChars || npasses > kMaxPasses) return LOR_ERR_INVALID_ARG;
         LOR_CUDA_TRY(cudaMemsetAsync(D.rs.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, st));
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * sizeof(KeyT) + double(z.n), st);
         const dim3 grid(unsigned(cdiv(max64(z.n0, z.n2), kKeyTile)), 2);
         k_sample_keys0<KeyT><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n2, kchars, uint32_t(radix), maxc, k0,
-                                                   npasses, key_bits, D.rs.hist, D.status);
+                                                   npasses, key_bits, dbits, D.rs.hist, D.status);
         hist_ready = true;
     } else {
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * (sizeof(KeyT) + 4.0 * kchars / 3.0), st);
@@ -1326,7 +1388,7 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
             ProfScope ps(PK_NAMING, double(U) * 48, st);
             const size_t smem = sizeof(DblSmallSmem);
             LOR_CUDA_TRY(cudaFuncSetAttribute(k_dbl_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-            k_dbl_small<<<1, kDblSmallThreads, smem, st>>>(ul, D.d_count, m, h, shift, SAR, Rl, D.status);
+            k_dbl_small<<<1, kDblSmallThreads, smem, st>>>(ul, D.d_count, m, h, shift, SAR, Rl, D.status, 0);
             LOR_LAUNCH_CHECK();
             break;
         }
@@ -1356,10 +1418,176 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
     return LOR_OK;
 }
 
+// Step 2 by sorting: nonsample positions 3r for every B1 sample r in rank
+// order, keyed by their first symbol, then one stable radix sort by it.
+template <typename CharT>
+int nonsample_by_sort(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits, const int32_t *SAR,
+                      const uint32_t **B) {
+    cudaStream_t st = D.s;
+    uint32_t *k0 = (uint32_t *)D.t64[1], *k1 = (uint32_t *)D.t64[2];
+    {
+        ProfScope ps(PK_NONSAMPLE, double(z.n02) * 4 + double(z.n0) * (sizeof(CharT) + 8), st);
+        LOR_TILE_LAUNCH(D, z.n02, k_nonsample<CharT>, SAR, z.n02, z.n0, s, z.n, k0, D.t32[4], LB_ARGS(D));
+    }
+    uint32_t *kr, *vr;
+    const int rc = radix_sort_pairs<uint32_t>(D.rs, k0, D.t32[4], k1, D.t32[5], z.n0, 0, bits, false, &kr, &vr);
+    if (rc) return rc;
+    *B = vr;
+    return LOR_OK;
+}
+
+// Step 3: merge of the sample order (SAR, ranks in Rl) and the nonsample
+// order B into out (the dummy, when present, is the smallest sample).  The
+// records go to the two adjacent 64-bit buffers.
+template <typename CharT>
+int merge_level(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t *Rl, const int32_t *SAR,
+                const uint32_t *B, int32_t *out) {
+    cudaStream_t st = D.s;
+    const int64_t n = z.n;
+    GroupRec<CharT> *rec = (GroupRec<CharT> *)D.t64[1];
+    const size_t rec_bytes = align256(sizeof(GroupRec<CharT>) * size_t(z.n0));
+    {
+        ProfScope ps(PK_MERGE, double(z.n0) * (3.0 * sizeof(CharT) + 12 + sizeof(GroupRec<CharT>)), st);
+        k_group_records<CharT><<<grid_for(z.n0, 256), 256, 0, st>>>(s, n, z.n0, z.n2, Rl, rec);
+    }
+    LOR_LAUNCH_CHECK();
+    MergeIn<CharT> a;
+    a.rec = rec;
+    a.n0 = int32_t(z.n0);
+    const int64_t dummy = (z.n0 > z.n1) ? 1 : 0;
+    a.A = SAR + dummy;
+    a.na = z.n02 - dummy;
+    a.B = B;
+    a.nb = z.n0;
+    const int64_t ntiles = cdiv(n, kMergeTile);
+    // The records fill at most t64[1..2] (16 bytes per position at level 0,
+    // 32 per group of three below); the partition has a region of its own.
+    if (rec_bytes > size_t((char *)D.t64[2] - (char *)D.t64[1]) * 2) return LOR_ERR_WORKSPACE;
+    int64_t *split = (int64_t *)(D.ws + D.L.split);
+    {
+        ProfScope ps(PK_MERGE, double(n) * (4 + 4 + sizeof(GroupRec<CharT>)), st);
+        k_merge_partition<CharT><<<grid_for(ntiles + 1, 128), 128, 0, st>>>(a, ntiles, split);
+        LOR_LAUNCH_CHECK();
+        if (tune_config().merge_items == 4)
+            k_merge<CharT, 4><<<unsigned(ntiles), kMergeTile / 4, 0, st>>>(a, split, out, D.status);
+        else
+            k_merge<CharT, 2><<<unsigned(ntiles), kMergeTile / 2, 0, st>>>(a, split, out, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
+
 // Doubling replaces the next level when at most 1/kDoublingShare of the
 // samples lost their name to a duplicate (LOR_DC3_DOUBLING: "0" never,
 // "force" whenever names repeat; a test hook).
 constexpr int64_t kDoublingShare = 16;
+
+// ---- prefix doubling with every round enqueued up front (graph mode)
+//
+// The unresolved count stays on the device: round r (step h = 2^r) reads it,
+// and its kernels do nothing once it is 0.  bit_width(m) rounds always
+// finish (after the round with step h the order is by 2h symbols of R, and
+// 2h >= m suffices); the single-block tail runs after the second round and
+// again after the last, taking over whenever few samples are left.
+int sa_by_doubling_graph(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_t *NSl,
+                         bool r_unwritten) {
+    cudaStream_t st = D.s;
+    int32_t *headof = (int32_t *)D.t32[0];
+    uint32_t *ul = D.t32[1], *ul2 = D.t32[2], *runid = D.t32[3], *val = D.t32[4], *rstart = D.t32[5];
+    uint32_t *valt = D.t32[0];
+    uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
+    uint32_t *cnt = D.d_count, *cnt2 = D.d_count + 1;
+    k_dbl_headof<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof);
+    LOR_LAUNCH_CHECK();
+    if (r_unwritten) {
+        uint32_t *H = D.t32[1];
+        k_dbl_heads<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof, H);
+        LOR_LAUNCH_CHECK();
+        int rc = bucketed_scatter(D.rs, (const uint32_t *)SAR, H, m, m, D.t32[2], D.t32[3], D.t32[4], Rl, 0);
+        if (rc) return rc;
+    } else {
+        k_dbl_init<<<grid_for(m, 256), 256, 0, st>>>(Rl, m, headof);
+        LOR_LAUNCH_CHECK();
+    }
+    {
+        const int64_t ntiles = cdiv(m, kScanTile);
+        LOR_TILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, cnt, LB_ARGS(D), ntiles);
+    }
+    const int shift = bit_width_u64(uint64_t(m));
+    const int rounds = shift > 0 ? shift : 1;
+    const size_t small_smem = sizeof(DblSmallSmem);
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_dbl_small, cudaFuncAttributeMaxDynamicSharedMemorySize, int(small_smem)));
+    const unsigned gcap = scan_grid_cap();
+    const unsigned ggrid = unsigned(min64(cdiv(m, 256), gcap));
+    for (int r = 0; r < rounds; ++r) {
+        const int64_t h = int64_t(1) << r;
+        k_dbl_keys_dev<<<ggrid, 256, 0, st>>>(ul, cnt, SAR, Rl, m, h, shift, k0, val);
+        LOR_LAUNCH_CHECK();
+        uint64_t *kr;
+        uint32_t *vr;
+        int rc = radix_sort_pairs<uint64_t>(D.rs, k0, val, k1, valt, m, 0, 2 * shift, false, &kr, &vr, false, cnt);
+        if (rc) return rc;
+        unsigned long long *ctr, base;
+        rc = take_counter(D.rs, true, &ctr, &base);
+        if (rc) return rc;
+        D.rs.epoch++;
+        k_dbl_runs_dev<<<unsigned(min64(cdiv(m, kScanTile), gcap)), kScanThreads, 0, st>>>(
+            kr, vr, ul, cnt, SAR, runid, rstart, D.rs.lookback, ctr, D.rs.epoch, D.status);
+        LOR_LAUNCH_CHECK();
+        k_dbl_rank_dev<<<ggrid, 256, 0, st>>>(vr, runid, rstart, ul, cnt, Rl);
+        LOR_LAUNCH_CHECK();
+        rc = take_counter(D.rs, true, &ctr, &base);
+        if (rc) return rc;
+        D.rs.epoch++;
+        k_dbl_next_dev<<<unsigned(min64(cdiv(m, kScanTile), gcap)), kScanThreads, 0, st>>>(
+            runid, ul, cnt, ul2, cnt2, D.rs.lookback, ctr, D.rs.epoch, D.status);
+        LOR_LAUNCH_CHECK();
+        uint32_t *t = ul;
+        ul = ul2;
+        ul2 = t;
+        t = cnt;
+        cnt = cnt2;
+        cnt2 = t;
+        if (r == 1 || r == rounds - 1) {
+            k_dbl_small<<<1, kDblSmallThreads, small_smem, st>>>(ul, cnt, m, 2 * h, shift, SAR, Rl, D.status, 1);
+            LOR_LAUNCH_CHECK();
+        }
+    }
+    k_dbl_check_done<<<1, 32, 0, st>>>(cnt, D.status);
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
+// DC3 with no host round trip, for capture in a CUDA graph: level 0 sorts
+// its sample by the 48-bit prefix, its reduced string is finished by the
+// enqueued doubling rounds above (whatever the number of repeated names),
+// then Steps 2 and 3 as in dc3_level.
+int dc3_graph(Dc3Run &D, const uint8_t *s, int64_t n, int64_t maxc, int32_t *out) {
+    cudaStream_t st = D.s;
+    const LevelSizes z = level_sizes(n);
+    int32_t *Rl = (int32_t *)(D.ws + D.L.lev_R[0]);
+    int32_t *SAR = (int32_t *)(D.ws + D.L.lev_SAR[0]);
+    int32_t *NSl = (int32_t *)(D.ws + D.L.lev_NS[0]);
+    const int bits = bit_width_u64(uint64_t(maxc));
+    const int kchars = level0_kchars(bits, maxc);
+    uint64_t T = 1;
+    for (int t = 0; t < kchars && T; ++t)
+        T = T > ~uint64_t(0) / (uint64_t(maxc) + 1) ? 0 : T * (uint64_t(maxc) + 1);
+    if (!T) return LOR_ERR_INVALID_ARG;
+    const int key_bits = bit_width_u64(T - 1);
+    LOR_CUDA_TRY(cudaMemsetAsync(Rl + z.n02, 0, sizeof(int32_t) * kPad, st));
+    int rc = key_bits <= 32
+                 ? sample_sort_and_name<uint8_t, uint32_t>(D, 0, s, z, kchars, key_bits, maxc, Rl, SAR, NSl)
+                 : sample_sort_and_name<uint8_t, uint64_t>(D, 0, s, z, kchars, key_bits, maxc, Rl, SAR, NSl);
+    if (rc) return rc;
+    rc = sa_by_doubling_graph(D, Rl, z.n02, SAR, NSl, bucket_names(D, z));
+    if (rc) return rc;
+    const uint32_t *B;
+    rc = nonsample_by_sort<uint8_t>(D, s, z, bits, SAR, &B);
+    if (rc) return rc;
+    return merge_level<uint8_t>(D, s, z, Rl, SAR, B, out);
+}
 
 template <typename CharT>
 int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32_t *out, const int32_t *PS,
@@ -1459,47 +1687,11 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
         }
         B = T0;
     } else {
-        uint32_t *k0 = (uint32_t *)D.t64[1], *k1 = (uint32_t *)D.t64[2];
-        {
-            ProfScope ps(PK_NONSAMPLE, double(z.n02) * 4 + double(z.n0) * (sizeof(CharT) + 8), st);
-            LOR_TILE_LAUNCH(D, z.n02, k_nonsample<CharT>, SAR, z.n02, z.n0, s, n, k0, D.t32[4], LB_ARGS(D));
-        }
-        uint32_t *kr, *vr;
-        rc = radix_sort_pairs<uint32_t>(D.rs, k0, D.t32[4], k1, D.t32[5], z.n0, 0, bits, false, &kr, &vr);
+        rc = nonsample_by_sort<CharT>(D, s, z, bits, SAR, &B);
         if (rc) return rc;
-        B = vr;
     }
 
-    // Step 3: merge (the dummy, when present, is the smallest sample).  The
-    // records and the partition go to the two adjacent 64-bit buffers.
-    GroupRec<CharT> *rec = (GroupRec<CharT> *)D.t64[1];
-    const size_t rec_bytes = align256(sizeof(GroupRec<CharT>) * size_t(z.n0));
-    {
-        ProfScope ps(PK_MERGE, double(z.n0) * (3.0 * sizeof(CharT) + 12 + sizeof(GroupRec<CharT>)), st);
-        k_group_records<CharT><<<grid_for(z.n0, 256), 256, 0, st>>>(s, n, z.n0, z.n2, Rl, rec);
-    }
-    LOR_LAUNCH_CHECK();
-    MergeIn<CharT> a;
-    a.rec = rec;
-    a.n0 = int32_t(z.n0);
-    const int64_t dummy = (z.n0 > z.n1) ? 1 : 0;
-    a.A = SAR + dummy;
-    a.na = z.n02 - dummy;
-    a.B = B;
-    a.nb = z.n0;
-    const int64_t ntiles = cdiv(n, kMergeTile);
-    // The records fill at most t64[1..2] (16 bytes per position at level 0,
-    // 32 per group of three below); the partition has a region of its own.
-    if (rec_bytes > size_t((char *)D.t64[2] - (char *)D.t64[1]) * 2) return LOR_ERR_WORKSPACE;
-    int64_t *split = (int64_t *)(D.ws + D.L.split);
-    {
-        ProfScope ps(PK_MERGE, double(n) * (4 + 4 + sizeof(GroupRec<CharT>)), st);
-        k_merge_partition<CharT><<<grid_for(ntiles + 1, 128), 128, 0, st>>>(a, ntiles, split);
-        LOR_LAUNCH_CHECK();
-        k_merge<CharT><<<unsigned(ntiles), kMergeThreads, 0, st>>>(a, split, out, D.status);
-    }
-    LOR_LAUNCH_CHECK();
-    return LOR_OK;
+    return merge_level<CharT>(D, s, z, Rl, SAR, B, out);
 }
 
 }  // namespace
@@ -1515,8 +1707,15 @@ extern "C" size_t lor_build_sa_workspace_size(int64_t n, int32_t sigma) {
 
 extern "C" int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa, void *d_ws,
                             size_t ws_bytes, lor_stream_t stream) {
+    return lor::build_sa_impl(d_text, n, sigma, d_sa, d_ws, ws_bytes, (cudaStream_t)stream, nullptr, 0);
+}
+
+int lor::build_sa_impl(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa, void *d_ws,
+                       size_t ws_bytes, cudaStream_t stream, unsigned long long *graph_ctr_pool,
+                       int graph_pool_size) {
     if (!d_text || !d_sa || n < 1 || sigma < 2 || sigma > 256) return LOR_ERR_INVALID_ARG;
     if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    const bool graph = graph_ctr_pool != nullptr;
     Dc3Run D;
     D.L = dc3_layout(n);
     if (!d_ws || ws_bytes < D.L.total || (uintptr_t(d_ws) & 255)) return LOR_ERR_WORKSPACE;
@@ -1546,6 +1745,14 @@ extern "C" int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int
     LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.lookback, 0, D.L.lookback_bytes, D.s));
     g_trace.clear();
     g_trace_extra.clear();
+    if (graph) {
+        D.rs.graph = true;
+        D.rs.ctr_pool = graph_ctr_pool;
+        D.rs.ctr_pool_size = graph_pool_size;
+        LOR_CUDA_TRY(cudaMemsetAsync(graph_ctr_pool, 0, sizeof(unsigned long long) * size_t(graph_pool_size), D.s));
+        D.force_lsd = false;
+        return dc3_graph(D, d_text, n, int64_t(sigma - 1), d_sa);
+    }
     return dc3_level<uint8_t>(D, 0, d_text, n, int64_t(sigma - 1), d_sa, nullptr, nullptr);
 }
 

@@ -10,6 +10,8 @@
 // shared memory so that every digit run is written contiguously.
 #pragma once
 
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace lor {
@@ -18,7 +20,7 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 256;
 constexpr int kSortThreads = 256;  // == kRadix: one thread per digit in the look-back
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kMaxPasses = 8;  // 64-bit keys
+constexpr int kMaxPasses = 16;  // 64-bit keys at 4-bit digits
 
 // Keys per thread: sized so that four 256-thread blocks fit an SM (64
 // registers per thread, under 57 KB of shared memory per block; the few
@@ -34,15 +36,30 @@ enum ValMode {
     VM_IOTA = 1,      // idx (32-bit values)
     VM_IDX_PREV = 2,  // 64-bit values: low word idx, high word the previous key (kin[idx-1], or ~0)
 };
-constexpr int kMinSortTile = kSortThreads * 12;
+constexpr int kMinSortTile = kSortThreads * 8;  // the smallest tile of any pass
+
+// Lanes of the warp holding the same 9-bit value d as this lane (digit, or
+// 0x100 for an empty slot): one ballot per bit, kept or inverted by this
+// lane's bit.  The same set as __match_any_sync, from cheap vote instructions.
+__device__ __forceinline__ uint32_t warp_peers9(uint32_t d) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
 
 template <typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask = 0xFFu) {
     return uint32_t(k >> shift) & mask;
 }
-// Digit mask of the pass starting at `shift` when the key ends at end_bit.
-__host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int end_bit) {
-    const int w = end_bit - shift < kRadixBits ? end_bit - shift : kRadixBits;
+// Digit mask of the pass starting at `shift` when the key ends at end_bit
+// (digits of `bits` bits, at most 8).
+__host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int end_bit, int bits = kRadixBits) {
+    const int w = end_bit - shift < bits ? end_bit - shift : bits;
     return (1u << w) - 1u;
 }
 
@@ -51,8 +68,9 @@ __host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int end_bit) 
 // entropy passes) one lane adds 32 instead.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_radix_hist(const KeyT *__restrict__ keys, int64_t m,
-                                                    int begin_bit, int end_bit, int npasses,
-                                                    uint32_t *__restrict__ hist) {
+                                                    const uint32_t *m_dev, int begin_bit, int end_bit,
+                                                    int npasses, int dbits, uint32_t *__restrict__ hist) {
+    if (m_dev) m = int64_t(*m_dev);
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     for (int i = threadIdx.x; i < npasses * kRadix; i += blockDim.x) sh[i] = 0;
     __syncthreads();
@@ -69,8 +87,8 @@ __global__ void __launch_bounds__(256) k_radix_hist(const KeyT *__restrict__ key
             k[u] = valid[u] ? keys[i] : KeyT(0);
         }
         for (int p = 0; p < npasses; ++p) {
-            const int sft = begin_bit + p * kRadixBits;
-            const uint32_t dm = digit_mask(sft, end_bit);
+            const int sft = begin_bit + p * dbits;
+            const uint32_t dm = digit_mask(sft, end_bit, dbits);
 #pragma unroll
             for (int u = 0; u < kPer; ++u) {
                 const uint32_t d = digit_of(k[u], sft, dm);
@@ -99,35 +117,83 @@ static __global__ void __launch_bounds__(256) k_radix_offsets(const uint32_t *__
     offsets[p * kRadix + threadIdx.x] = block_excl_scan<kRadix>(v, scratch, &total);
 }
 
-template <typename KeyT, typename ValT>
+template <typename KeyT, typename ValT, int kItems = sort_items<KeyT, ValT>()>
 struct OnesweepSmem {
-    KeyT keys[sort_tile<KeyT, ValT>()];
-    ValT vals[sort_tile<KeyT, ValT>()];
+    KeyT keys[kSortThreads * kItems];
+    ValT vals[kSortThreads * kItems];
     uint32_t warp_hist[kSortWarps][kRadix];
     uint32_t local_start[kRadix];
     long long gbase[kRadix];
     uint32_t scratch[kSortWarps + 1];
     long long tile;
+    long long next;
 };
 
-// One LSD pass over digit (shift .. shift+7).  Tiles are claimed in launch
-// order from a running counter, so every predecessor a block waits on is
-// already resident; each wait is still bounded by kSpinLimitNs.
-template <typename KeyT, typename ValT, int kVMode>
+// Exclusive prefix of digit dg over the tiles before `tile`: walks back over
+// the predecessors' descriptors, kLookWindow of them per round of independent
+// loads (the walk is a chain of L2 round trips, so fewer rounds is less
+// waiting), summing aggregates up to the first inclusive prefix.  A
+// descriptor not yet published ends the round; the walk resumes there.  The
+// whole wait is bounded by kSpinLimitNs (then LOR_ERR_TIMEOUT).
+constexpr int kLookWindow = 4;
+
+__device__ __forceinline__ uint32_t lookback_digit(const uint64_t *lb, int64_t tile, int dg, uint32_t epoch,
+                                                   int *status) {
+    uint32_t excl = 0;
+    int64_t j = tile - 1;
+    const uint64_t t0 = global_ns();
+    while (j >= 0) {
+        uint64_t w[kLookWindow];
+#pragma unroll
+        for (int u = 0; u < kLookWindow; ++u)
+            w[u] = j - u >= 0 ? ld_volatile_u64(&lb[(j - u) * kRadix + dg]) : lb_pack(epoch, kFlagIncl, 0);
+        bool done = false;
+        int used = 0;
+#pragma unroll
+        for (int u = 0; u < kLookWindow; ++u) {
+            if (done || used < u) break;  // stop at the first descriptor not yet published
+            if (lb_epoch(w[u]) != epoch || lb_flag(w[u]) == 0) break;
+            excl += lb_value(w[u]);
+            used = u + 1;
+            if (lb_flag(w[u]) == kFlagIncl) done = true;
+        }
+        if (done) break;
+        j -= used;
+        if (used == 0 && global_ns() - t0 > kSpinLimitNs) {
+            atomicCAS(status, 0, LOR_ERR_TIMEOUT);
+            break;
+        }
+    }
+    return excl;
+}
+
+// One LSD pass over digit (shift .. shift+7).  A grid of a few blocks per SM
+// stays resident and every block claims tiles from the running counter until
+// it draws one past the end, so a tile only ever waits on tiles claimed
+// before it by running blocks; each wait is still bounded by kSpinLimitNs.
+// Every block makes exactly one claim past the last tile: a launch advances
+// the counter by ntiles + gridDim.x.  When m_dev is given the element count
+// is read from device memory (the count of an earlier kernel), so that the
+// launch needs no host round trip.
+template <typename KeyT, typename ValT, int kVMode, int kItems>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const KeyT *__restrict__ kin, const ValT *__restrict__ vin, KeyT *__restrict__ kout,
-    ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask,
+    ValT *__restrict__ vout, int64_t m, const uint32_t *m_dev, int shift, uint32_t dmask,
     const uint32_t *__restrict__ offsets,
     uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
     uint32_t epoch, int *status, int64_t ahead) {
-    constexpr int kItems = sort_items<KeyT, ValT>();
-    constexpr int kTile = sort_tile<KeyT, ValT>();
+    constexpr int kTile = kSortThreads * kItems;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    OnesweepSmem<KeyT, ValT> &S = *reinterpret_cast<OnesweepSmem<KeyT, ValT> *>(smem_raw);
+    OnesweepSmem<KeyT, ValT, kItems> &S = *reinterpret_cast<OnesweepSmem<KeyT, ValT, kItems> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
-        const int64_t b2 = (S.tile + ahead) * kTile;
+    if (m_dev) m = int64_t(*m_dev);
+    const int64_t ntiles = cdiv(m, kTile);
+    // A claim also asks the L2 for the data of the tile `ahead` claims later.
+    // (A tile is claimed only when its block is ready to work on it: a tile
+    // claimed early would hold up the look-back of every later tile.)
+    auto claim = [&]() {
+        const long long t = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+        const int64_t b2 = (t + ahead) * kTile;
         if (ahead > 0 && b2 < m) {
             const int64_t c2 = min64(int64_t(kTile), m - b2);
             const uint32_t kb = uint32_t(c2 * int64_t(sizeof(KeyT))) & ~15u;
@@ -137,97 +203,89 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
                 if (vb) prefetch_l2_bulk(vin + b2, vb);
             }
         }
-    }
-    for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t tile = S.tile;
-    const int64_t base = tile * kTile;
-    const int64_t wbase = base + int64_t(warp) * (kItems * 32);
+        return t;
+    };
+    for (;;) {
+        if (tid == 0) S.next = claim();
+        for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t tile = S.next;
+        if (tile >= ntiles) break;  // uniform over the block
+        const int64_t base = tile * kTile;
+        const int64_t wbase = base + int64_t(warp) * (kItems * 32);
 
-    KeyT k[kItems];
-    ValT v[kItems];
-    uint32_t r[kItems];
+        KeyT k[kItems];
+        ValT v[kItems];
+        uint32_t r[kItems];
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int64_t idx = wbase + i * 32 + lane;
-        const bool valid = idx < m;
-        k[i] = valid ? kin[idx] : KeyT(0);
-        if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[idx] : ValT(0);
-        if constexpr (kVMode == VM_IDX_PREV)
-            v[i] = uint64_t(uint32_t(idx)) |
-                   (uint64_t(valid && idx > 0 ? uint32_t(kin[idx - 1]) : 0xFFFFFFFFu) << 32);
-    }
-    // Stable rank inside the warp: items in order, lanes in order.  Slots
-    // past the end of the input use digit 256 and are never counted.
-    uint32_t *wh = S.warp_hist[warp];
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t idx = wbase + i * 32 + lane;
+            const bool valid = idx < m;
+            k[i] = valid ? kin[idx] : KeyT(0);
+            if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[idx] : ValT(0);
+            if constexpr (kVMode == VM_IDX_PREV)
+                v[i] = uint64_t(uint32_t(idx)) |
+                       (uint64_t(valid && idx > 0 ? uint32_t(kin[idx - 1]) : 0xFFFFFFFFu) << 32);
+        }
+        // Stable rank inside the warp: items in order, lanes in order.  Slots
+        // past the end of the input use digit 256 and are never counted.
+        uint32_t *wh = S.warp_hist[warp];
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const bool valid = wbase + i * 32 + lane < m;
-        const uint32_t d = valid ? digit_of(k[i], shift, dmask) : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t lt = __popc(peers & lanemask_lt());
-        const uint32_t cnt = valid ? wh[d] : 0u;
-        r[i] = cnt + lt;
-        __syncwarp();
-        if (valid && lt == 0) wh[d] = cnt + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    const int dg = tid;
-    uint32_t total = 0;
+        for (int i = 0; i < kItems; ++i) {
+            const bool valid = wbase + i * 32 + lane < m;
+            const uint32_t d = valid ? digit_of(k[i], shift, dmask) : 0x100u;
+            const uint32_t peers = warp_peers9(d);
+            const uint32_t lt = __popc(peers & lanemask_lt());
+            const uint32_t cnt = valid ? wh[d] : 0u;
+            r[i] = cnt + lt;
+            __syncwarp();
+            if (valid && lt == 0) wh[d] = cnt + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        const int dg = tid;
+        uint32_t total = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t c = S.warp_hist[w][dg];
-        S.warp_hist[w][dg] = total;
-        total += c;
-    }
-    uint32_t tile_total;
-    const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
-    S.local_start[dg] = lstart;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = S.warp_hist[w][dg];
+            S.warp_hist[w][dg] = total;
+            total += c;
+        }
+        uint32_t tile_total;
+        const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
+        S.local_start[dg] = lstart;
 
-    // Decoupled look-back, one digit per thread.
-    uint32_t excl = 0;
-    uint64_t *lb = lookback;
-    if (tile == 0) {
-        st_volatile_u64(&lb[dg], lb_pack(epoch, kFlagIncl, total));
-    } else {
-        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
-        int64_t j = tile - 1;
-        const uint64_t t0 = global_ns();
-        while (j >= 0) {
-            const uint64_t w = ld_volatile_u64(&lb[j * kRadix + dg]);
-            if (lb_epoch(w) != epoch || lb_flag(w) == 0) {
-                if (global_ns() - t0 > kSpinLimitNs) {
-                    atomicCAS(status, 0, LOR_ERR_TIMEOUT);
-                    break;
-                }
-                continue;
+        // Decoupled look-back, one digit per thread.
+        uint32_t excl = 0;
+        uint64_t *lb = lookback;
+        if (tile == 0) {
+            st_volatile_u64(&lb[dg], lb_pack(epoch, kFlagIncl, total));
+        } else {
+            st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
+            excl = lookback_digit(lb, tile, dg, epoch, status);
+            st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
+        }
+        S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t idx = wbase + i * 32 + lane;
+            if (idx < m) {
+                const uint32_t d = digit_of(k[i], shift, dmask);
+                const uint32_t pos = S.local_start[d] + S.warp_hist[warp][d] + r[i];
+                S.keys[pos] = k[i];
+                S.vals[pos] = kVMode == VM_IOTA ? ValT(uint32_t(idx)) : v[i];
             }
-            excl += lb_value(w);
-            if (lb_flag(w) == kFlagIncl) break;
-            --j;
         }
-        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
-    }
-    S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int64_t idx = wbase + i * 32 + lane;
-        if (idx < m) {
-            const uint32_t d = digit_of(k[i], shift, dmask);
-            const uint32_t pos = S.local_start[d] + S.warp_hist[warp][d] + r[i];
-            S.keys[pos] = k[i];
-            S.vals[pos] = kVMode == VM_IOTA ? ValT(uint32_t(idx)) : v[i];
+        __syncthreads();
+        const int cnt_tile = int(min64(int64_t(kTile), m - base));
+        for (int i = tid; i < cnt_tile; i += kSortThreads) {
+            const KeyT kk = S.keys[i];
+            const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
+            kout[o] = kk;
+            vout[o] = S.vals[i];
         }
-    }
-    __syncthreads();
-    const int cnt_tile = int(min64(int64_t(kTile), m - base));
-    for (int i = tid; i < cnt_tile; i += kSortThreads) {
-        const KeyT kk = S.keys[i];
-        const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
-        kout[o] = kk;
-        vout[o] = S.vals[i];
+        __syncthreads();  // staging, histograms and S.tile are reused by the next tile
     }
 }
 
@@ -290,21 +348,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
         st_volatile_u64(&lb[dg], lb_pack(epoch, kFlagIncl, total));
     } else {
         st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
-        int64_t j = tile - 1;
-        const uint64_t t0 = global_ns();
-        while (j >= 0) {
-            const uint64_t w = ld_volatile_u64(&lb[j * kRadix + dg]);
-            if (lb_epoch(w) != epoch || lb_flag(w) == 0) {
-                if (global_ns() - t0 > kSpinLimitNs) {
-                    atomicCAS(status, 0, LOR_ERR_TIMEOUT);
-                    break;
-                }
-                continue;
-            }
-            excl += lb_value(w);
-            if (lb_flag(w) == kFlagIncl) break;
-            --j;
-        }
+        excl = lookback_digit(lb, tile, dg, epoch, status);
         st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
     }
     S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
@@ -334,6 +378,13 @@ static __global__ void k_iota_u32(uint32_t *__restrict__ v, int64_t m) {
 }
 
 // Scratch that one sort needs besides the two key/value buffer pairs.
+//
+// Graph mode (`graph` set) is for work enqueued under CUDA stream capture:
+// no call reads anything back to the host, so sorts run every pass (no
+// skipping of passes whose digit is the same for all keys), and launches
+// whose number of tile claims depends on a count held on the device take a
+// counter of their own from `ctr_pool` (zeroed, like the look-back area, at
+// the start of the captured work) instead of the running counter.
 struct RadixScratch {
     uint32_t *hist = nullptr;          // kMaxPasses * kRadix
     uint32_t *offsets = nullptr;       // kMaxPasses * kRadix
@@ -344,7 +395,39 @@ struct RadixScratch {
     int64_t max_tiles = 0;
     int *status = nullptr;
     cudaStream_t stream = 0;
+    bool graph = false;
+    unsigned long long *ctr_pool = nullptr;
+    int ctr_pool_size = 0, ctr_next = 0;
 };
+
+// Resident blocks of a persistent sort pass: four per SM.
+inline int sort_grid_cap() {
+    static thread_local int dev = -1, cap = 0;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return 4 * 148;
+    if (cur != dev) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur) != cudaSuccess || sms <= 0) sms = 148;
+        cap = 4 * sms;
+        dev = cur;
+    }
+    return cap;
+}
+
+// The tile counter of one launch: the running counter and its host mirror,
+// or (graph mode, device-sized launches) a fresh counter from the pool.
+inline int take_counter(RadixScratch &rs, bool device_sized, unsigned long long **ctr,
+                        unsigned long long *base) {
+    if (rs.graph && device_sized) {
+        if (!rs.ctr_pool || rs.ctr_next >= rs.ctr_pool_size) return LOR_ERR_WORKSPACE;
+        *ctr = rs.ctr_pool + rs.ctr_next++;
+        *base = 0;
+    } else {
+        *ctr = rs.tile_ctr;
+        *base = rs.tile_base;
+    }
+    return LOR_OK;
+}
 
 inline size_t radix_lookback_bytes(int64_t max_m) {
     return size_t(cdiv(max_m > 0 ? max_m : 1, kMinSortTile)) * kRadix * sizeof(uint64_t);
@@ -356,65 +439,51 @@ inline size_t radix_lookback_bytes(int64_t max_m) {
 // are taken to be 0..m-1 and v0 is not read.
 // When hist_ready is set the caller has already counted every pass's digits
 // into rs.hist (zeroed first), e.g. in the kernel that made the keys.
-template <typename KeyT>
-int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v1, int64_t m,
-                     int begin_bit, int end_bit, bool iota_vals, KeyT **kres, uint32_t **vres,
-                     bool hist_ready = false) {
+// When m_dev is given the number of pairs is read from device memory and m
+// is only its upper bound (buffer and grid sizes).
+// The passes of one sort at kItems keys per thread (see radix_sort_pairs).
+template <typename KeyT, int kItems>
+int radix_passes(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v1, int64_t m, int begin_bit,
+                 int end_bit, int dbits, int npasses, const uint32_t *hh, bool vals_ready,
+                 const uint32_t *m_dev, KeyT **kres, uint32_t **vres) {
     cudaStream_t s = rs.stream;
-    *kres = k0;
-    *vres = v0;
-    if (m <= 0) return LOR_OK;
-    const int npasses = int(cdiv(end_bit - begin_bit, kRadixBits));
-    if (begin_bit < 0 || end_bit < begin_bit || end_bit > int(8 * sizeof(KeyT)) ||
-        npasses > kMaxPasses)
-        return LOR_ERR_INVALID_ARG;
-    if (cdiv(m, sort_tile<KeyT, uint32_t>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
-    uint32_t hh[kMaxPasses * kRadix];
-    if (npasses > 0) {
-        if (!hist_ready) {
-            LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * npasses * kRadix, s));
-            {
-                ProfScope ps(PK_RADIX_HIST, double(m) * sizeof(KeyT), s);
-                const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
-                k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, begin_bit, end_bit, npasses, rs.hist);
-            }
-            LOR_LAUNCH_CHECK();
-        }
-        k_radix_offsets<<<npasses, kRadix, 0, s>>>(rs.hist, rs.offsets);
-        LOR_LAUNCH_CHECK();
-        LOR_CUDA_TRY(cudaMemcpyAsync(hh, rs.hist, sizeof(uint32_t) * npasses * kRadix,
-                                     cudaMemcpyDeviceToHost, s));
-        LOR_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    const size_t smem = sizeof(OnesweepSmem<KeyT, uint32_t>);
-    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, uint32_t, VM_IOTA>,
+    constexpr int kTile = kSortThreads * kItems;
+    if (cdiv(m, kTile) > rs.max_tiles) return LOR_ERR_WORKSPACE;
+    const size_t smem = sizeof(OnesweepSmem<KeyT, uint32_t, kItems>);
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, uint32_t, VM_IOTA, kItems>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, uint32_t, VM_LOAD>,
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_onesweep<KeyT, uint32_t, VM_LOAD, kItems>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     KeyT *ki = k0, *ko = k1;
     uint32_t *vi = v0, *vo = v1;
-    bool vals_ready = !iota_vals;
-    const int64_t ntiles = cdiv(m, sort_tile<KeyT, uint32_t>());
+    const int64_t ntiles = cdiv(m, kTile);
+    const unsigned grid = unsigned(min64(ntiles, sort_grid_cap()));
     for (int p = 0; p < npasses; ++p) {
-        bool trivial = false;
-        for (int dgt = 0; dgt < kRadix; ++dgt)
-            if (int64_t(hh[p * kRadix + dgt]) == m) trivial = true;
-        if (trivial) continue;  // every key has the same digit: order unchanged
-        const int shift = begin_bit + p * kRadixBits;
+        if (hh) {
+            bool trivial = false;
+            for (int dgt = 0; dgt < kRadix; ++dgt)
+                if (int64_t(hh[p * kRadix + dgt]) == m) trivial = true;
+            if (trivial) continue;  // every key has the same digit: order unchanged
+        }
+        const int shift = begin_bit + p * dbits;
+        const uint32_t dmask = digit_mask(shift, end_bit, dbits);
         rs.epoch++;
+        unsigned long long *ctr, base;
+        int rc = take_counter(rs, m_dev != nullptr, &ctr, &base);
+        if (rc) return rc;
         {
             ProfScope ps(PK_RADIX_PASS, double(m) * 2.0 * (sizeof(KeyT) + 4), s);
             if (vals_ready)
-                k_onesweep<KeyT, uint32_t, VM_LOAD><<<unsigned(ntiles), kSortThreads, smem, s>>>(
-                    ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
-                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status, prefetch_ahead(ki, vi));
+                k_onesweep<KeyT, uint32_t, VM_LOAD, kItems><<<grid, kSortThreads, smem, s>>>(
+                    ki, vi, ko, vo, m, m_dev, shift, dmask, rs.offsets + p * kRadix, rs.lookback, ctr, base,
+                    rs.epoch, rs.status, prefetch_ahead(ki, vi, grid));
             else
-                k_onesweep<KeyT, uint32_t, VM_IOTA><<<unsigned(ntiles), kSortThreads, smem, s>>>(
-                    ki, vi, ko, vo, m, shift, digit_mask(shift, end_bit), rs.offsets + p * kRadix,
-                    rs.lookback, rs.tile_ctr, rs.tile_base, rs.epoch, rs.status, prefetch_ahead(ki, ki));
+                k_onesweep<KeyT, uint32_t, VM_IOTA, kItems><<<grid, kSortThreads, smem, s>>>(
+                    ki, vi, ko, vo, m, m_dev, shift, dmask, rs.offsets + p * kRadix, rs.lookback, ctr, base,
+                    rs.epoch, rs.status, prefetch_ahead(ki, ki, grid));
         }
         LOR_LAUNCH_CHECK();
-        rs.tile_base += (unsigned long long)ntiles;
+        if (ctr == rs.tile_ctr) rs.tile_base += (unsigned long long)(ntiles + grid);
         vals_ready = true;
         KeyT *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;
@@ -426,6 +495,67 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
     *kres = ki;
     *vres = vi;
     return LOR_OK;
+}
+
+// Sort m pairs by bits [begin_bit, end_bit) of the keys.  (k0, v0) hold the
+// input; (k1, v1) are same-sized buffers.  On return *kres / *vres point at
+// whichever pair holds the sorted result.  When iota_vals is set the values
+// are taken to be 0..m-1 and v0 is not read.
+// When hist_ready is set the caller has already counted every pass's digits
+// into rs.hist (zeroed first; digits of tune_config().digit_bits), e.g. in the
+// kernel that made the keys.
+// When m_dev is given the number of pairs is read from device memory and m
+// is only its upper bound (buffer and grid sizes).
+// Digit width and keys per thread come from tune_config().
+template <typename KeyT>
+int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v1, int64_t m,
+                     int begin_bit, int end_bit, bool iota_vals, KeyT **kres, uint32_t **vres,
+                     bool hist_ready = false, const uint32_t *m_dev = nullptr) {
+    cudaStream_t s = rs.stream;
+    *kres = k0;
+    *vres = v0;
+    if (m <= 0) return LOR_OK;
+    const TuneConfig cfg = tune_config();
+    const int dbits = cfg.digit_bits;
+    const int npasses = int(cdiv(end_bit - begin_bit, dbits));
+    if (begin_bit < 0 || end_bit < begin_bit || end_bit > int(8 * sizeof(KeyT)) ||
+        npasses > kMaxPasses)
+        return LOR_ERR_INVALID_ARG;
+    const bool sync_free = rs.graph || m_dev;
+    uint32_t hh[kMaxPasses * kRadix];
+    if (npasses > 0) {
+        if (!hist_ready) {
+            LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * npasses * kRadix, s));
+            {
+                ProfScope ps(PK_RADIX_HIST, double(m) * sizeof(KeyT), s);
+                const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
+                k_radix_hist<KeyT><<<grid, 256, 0, s>>>(k0, m, m_dev, begin_bit, end_bit, npasses, dbits,
+                                                        rs.hist);
+            }
+            LOR_LAUNCH_CHECK();
+        }
+        k_radix_offsets<<<npasses, kRadix, 0, s>>>(rs.hist, rs.offsets);
+        LOR_LAUNCH_CHECK();
+        if (!sync_free) {
+            LOR_CUDA_TRY(cudaMemcpyAsync(hh, rs.hist, sizeof(uint32_t) * npasses * kRadix,
+                                         cudaMemcpyDeviceToHost, s));
+            LOR_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    }
+    const uint32_t *h = sync_free ? nullptr : hh;
+    const int items = sizeof(KeyT) == 8 ? cfg.sort_items_64 : cfg.sort_items_32;
+    if (sizeof(KeyT) == 8) {
+        if (items == 8)
+            return radix_passes<KeyT, 8>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
+                                         m_dev, kres, vres);
+        return radix_passes<KeyT, 12>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
+                                      m_dev, kres, vres);
+    }
+    if (items == 12)
+        return radix_passes<KeyT, 12>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
+                                      m_dev, kres, vres);
+    return radix_passes<KeyT, 16>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
+                                  m_dev, kres, vres);
 }
 
 // ---- bucketed scatter: dst[key[i]] = val[i] + add for distinct keys in
@@ -461,7 +591,7 @@ int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int
     {
         ProfScope ps(PK_RADIX_HIST, double(m) * 4, s);
         const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
-        k_radix_hist<uint32_t><<<grid, 256, 0, s>>>(keys, m, lo, top, 1, rs.hist);
+        k_radix_hist<uint32_t><<<grid, 256, 0, s>>>(keys, m, nullptr, lo, top, 1, kRadixBits, rs.hist);
     }
     LOR_LAUNCH_CHECK();
     k_radix_offsets<<<1, kRadix, 0, s>>>(rs.hist, rs.offsets);

@@ -158,10 +158,127 @@ __global__ void k_rmq_query(const int32_t *__restrict__ table, int64_t stride,
     out[i] = min(lv[r1 + 1], lv[r2 - (int64_t(1) << j) + 1]);
 }
 
+// ---- block-sparse RMQ in linear space
+//
+// The LCP array is cut into blocks of kRmqBlock entries; a sparse table is
+// built over the block minima only (n / 32 entries per row instead of n), and
+// a query over ranks (r1, r2] takes the minimum of the partial blocks at both
+// ends, read from the LCP array itself, and of the whole blocks between them,
+// read from two windows of the block table.
+
+constexpr int kRmqBlock = 32;
+
+int64_t rmqb_blocks(int64_t n) { return cdiv(n, kRmqBlock); }
+
+// bm[b] = min(lcp[32b .. min(32b + 32, n) - 1]): one warp per block.
+__global__ void k_rmqb_blockmin(const int32_t *__restrict__ lcp, int64_t n, int64_t nb, int32_t *__restrict__ bm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t b = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; b < nb; b += warps) {
+        const int64_t i = b * kRmqBlock + lane;
+        const int v = i < n ? lcp[i] : INT_MAX;
+        const int m = __reduce_min_sync(0xffffffffu, v);
+        if (lane == 0) bm[b] = m;
+    }
+}
+
+// min(lcp[a .. b]) for a <= b inside one block.
+__device__ __forceinline__ int32_t rmqb_scan(const int32_t *__restrict__ lcp, int64_t a, int64_t b) {
+    int32_t m = lcp[a];
+    for (int64_t i = a + 1; i <= b; ++i) m = min(m, lcp[i]);
+    return m;
+}
+
+__global__ void k_rmqb_query(const int32_t *__restrict__ table, int64_t stride, const int32_t *__restrict__ lcp,
+                             const int32_t *__restrict__ isa, int64_t n, const int32_t *__restrict__ P,
+                             const int32_t *__restrict__ Q, int64_t nq, int32_t *__restrict__ out, int *status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const int32_t p = P[i], q = Q[i];
+    if (p < 0 || p >= n || q < 0 || q >= n) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        out[i] = -1;
+        return;
+    }
+    if (p == q) {
+        out[i] = int32_t(n - p);
+        return;
+    }
+    int32_t r1 = isa[p], r2 = isa[q];
+    if (r1 < 0 || r1 >= n || r2 < 0 || r2 >= n || r1 == r2) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        out[i] = -1;
+        return;
+    }
+    if (r1 > r2) {
+        const int32_t tmp = r1;
+        r1 = r2;
+        r2 = tmp;
+    }
+    const int64_t a = int64_t(r1) + 1, b = r2;  // minimum of lcp[a .. b]
+    const int64_t ba = a / kRmqBlock, bb = b / kRmqBlock;
+    int32_t m;
+    if (ba == bb) {
+        m = rmqb_scan(lcp, a, b);
+    } else {
+        m = min(rmqb_scan(lcp, a, ba * kRmqBlock + kRmqBlock - 1), rmqb_scan(lcp, bb * kRmqBlock, b));
+        const int64_t len = bb - ba - 1;  // whole blocks ba+1 .. bb-1
+        if (len > 0) {
+            const int j = 63 - __clzll(len);
+            const int32_t *lv = table + int64_t(j) * stride;
+            m = min(m, min(lv[ba + 1], lv[bb - (int64_t(1) << j)]));
+        }
+    }
+    out[i] = m;
+}
+
 }  // namespace
 }  // namespace lor
 
 using namespace lor;
+
+extern "C" int64_t lor_rmq_block_table_elems(int64_t n) {
+    if (n < 1 || n > LOR_MAX_N) return 0;
+    const int64_t nb = rmqb_blocks(n);
+    return int64_t(levels_for(nb)) * row_stride(nb);
+}
+
+extern "C" int lor_rmq_block_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
+                                   lor_stream_t stream) {
+    if (!d_lcp || !d_table || n < 1) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    if (table_elems < lor_rmq_block_table_elems(n)) return LOR_ERR_WORKSPACE;
+    if (uintptr_t(d_table) & 255) return LOR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nb = rmqb_blocks(n);
+    {
+        ProfScope ps(PK_RMQ_LEVEL, double(n) * 4 + double(nb) * 4, s);
+        const unsigned grid = unsigned(min64(cdiv(nb * 32, 256), 152 * 16));
+        k_rmqb_blockmin<<<grid, 256, 0, s>>>(d_lcp, n, nb, d_table);
+    }
+    LOR_LAUNCH_CHECK();
+    // row 0 now holds the block minima: the rows above are its sparse table
+    return rmq_build_levels(d_table, nb, levels_for(nb), d_table, s);
+}
+
+extern "C" int lor_rmq_block_query(const int32_t *d_table, const int32_t *d_lcp, const int32_t *d_isa, int64_t n,
+                                   const int32_t *d_p, const int32_t *d_q, int64_t nq, int32_t *d_out,
+                                   lor_stream_t stream) {
+    if (!d_table || !d_lcp || !d_isa || n < 1 || nq < 0) return LOR_ERR_INVALID_ARG;
+    if (nq == 0) return LOR_OK;
+    if (!d_p || !d_q || !d_out) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *status = tu_status_ptr();
+    if (!status) return LOR_ERR_CUDA;
+    {
+        ProfScope ps(PK_RMQ_QUERY, double(nq) * (4 + 4 + 4 + 4 + 4 + 4 + 4 + 4), s);
+        k_rmqb_query<<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(d_table, row_stride(rmqb_blocks(n)), d_lcp, d_isa, n,
+                                                             d_p, d_q, nq, d_out, status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
 
 extern "C" int64_t lor_rmq_row_stride(int64_t n) {
     if (n < 1 || n > LOR_MAX_N) return 0;

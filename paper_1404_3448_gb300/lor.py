@@ -65,10 +65,22 @@ def load():
         "lor_longest_overlap": ([vp, vp, i64, vp, i32, vp, vp, i64, vp, sz, vp], ctypes.c_int),
         "lor_batch_workspace_size": ([vp, i32], sz),
         "lor_batch_overlap": ([vp, vp, i32, vp, vp, vp, i64, vp, sz, vp], ctypes.c_int),
+        "lor_batch_graph_workspace_size": ([vp, i32], sz),
+        "lor_batch_graph_create": ([vp, vp, i32, vp, vp, vp, i64, vp, sz, vp], ctypes.c_int),
+        "lor_batch_graph_launch": ([vp, vp], ctypes.c_int),
+        "lor_batch_graph_kernels": ([vp], i64),
+        "lor_batch_graph_destroy": ([vp], ctypes.c_int),
+        "lor_tune_default": ([vp], None),
+        "lor_tune_get": ([vp], ctypes.c_int),
+        "lor_tune_set": ([vp], ctypes.c_int),
+        "lor_autotune_batch": ([vp, vp, i32, vp, vp, vp, i64, vp, sz, i32, vp, vp, vp], ctypes.c_int),
         "lor_rmq_table_elems": ([i64], i64),
         "lor_rmq_row_stride": ([i64], i64),
         "lor_rmq_build": ([vp, i64, vp, i64, vp], ctypes.c_int),
         "lor_rmq_query": ([vp, vp, i64, vp, vp, i64, vp, vp], ctypes.c_int),
+        "lor_rmq_block_table_elems": ([i64], i64),
+        "lor_rmq_block_build": ([vp, i64, vp, i64, vp], ctypes.c_int),
+        "lor_rmq_block_query": ([vp, vp, vp, i64, vp, vp, i64, vp, vp], ctypes.c_int),
         "lor_radix_sort_workspace_size": ([i64], sz),
         "lor_radix_sort_pairs": ([vp, vp, i64, i32, vp, sz, vp], ctypes.c_int),
         "lor_device_status": ([vp], ctypes.c_int),
@@ -141,6 +153,27 @@ def lor_batch_workspace_size(h_lens, npairs):
 def lor_batch_overlap(d_ascii, h_lens, npairs, d_out, d_pos_off, d_pos, pos_cap, d_ws, ws_bytes, stream):
     return load().lor_batch_overlap(d_ascii, h_lens, npairs, d_out, d_pos_off, d_pos, pos_cap, d_ws,
                                     ws_bytes, stream)
+
+
+def lor_batch_graph_workspace_size(h_lens, npairs):
+    return load().lor_batch_graph_workspace_size(h_lens, npairs)
+
+
+def lor_batch_graph_create(d_ascii, h_lens, npairs, d_out, d_pos_off, d_pos, pos_cap, d_ws, ws_bytes, out):
+    return load().lor_batch_graph_create(d_ascii, h_lens, npairs, d_out, d_pos_off, d_pos, pos_cap, d_ws,
+                                         ws_bytes, out)
+
+
+def lor_batch_graph_launch(g, stream):
+    return load().lor_batch_graph_launch(g, stream)
+
+
+def lor_batch_graph_kernels(g):
+    return load().lor_batch_graph_kernels(g)
+
+
+def lor_batch_graph_destroy(g):
+    return load().lor_batch_graph_destroy(g)
 
 
 def lor_rmq_table_elems(n):
@@ -336,6 +369,98 @@ class Batch:
         return res
 
 
+class Tune(ctypes.Structure):
+    """lor_tune: launch parameters (every value gives the same results)."""
+    _fields_ = [("digit_bits", ctypes.c_int32), ("level0_key_bits", ctypes.c_int32),
+                ("sort_items_64", ctypes.c_int32), ("sort_items_32", ctypes.c_int32),
+                ("merge_items", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+def tune_default() -> dict:
+    t = Tune()
+    load().lor_tune_default(ctypes.byref(t))
+    return t.as_dict()
+
+
+def tune_get() -> dict:
+    t = Tune()
+    _check(load().lor_tune_get(ctypes.byref(t)), "lor_tune_get")
+    return t.as_dict()
+
+
+def tune_set(**values) -> dict:
+    """Set some launch parameters (the others keep their current values)."""
+    t = Tune(**{**tune_get(), **values})
+    _check(load().lor_tune_set(ctypes.byref(t)), "lor_tune_set")
+    return t.as_dict()
+
+
+def autotune_batch(batch: "Batch", ascii_dev, reps: int = 2, stream=None):
+    """lor_autotune_batch on a Batch's pairs and buffers; returns (the
+    configuration now set, its ms per batch)."""
+    best = Tune()
+    ms = ctypes.c_double()
+    ptr = _ptr(ascii_dev, torch.uint8, "ascii") if ascii_dev.numel() else None
+    _check(load().lor_autotune_batch(ptr, batch.lens.ctypes.data, batch.npairs, batch.out.data_ptr(),
+                                     batch.pos_off.data_ptr(), batch.pos.data_ptr(), batch.pos_cap,
+                                     batch.ws.data_ptr(), batch.ws.numel(), int(reps), _stream(stream),
+                                     ctypes.byref(best), ctypes.byref(ms)), "lor_autotune_batch")
+    return best.as_dict(), float(ms.value)
+
+
+class BatchGraph(Batch):
+    """lor_batch_graph over a fixed list of pair lengths and a fixed device
+    input buffer: the grouped pipeline is captured once into a CUDA graph;
+    run() replays it on whatever bases the input buffer holds."""
+
+    def __init__(self, lens, ascii_dev, device="cuda", pos_cap=1 << 20):
+        self.lens = np.ascontiguousarray(np.asarray(lens, dtype=np.int64))
+        if self.lens.size % 2:
+            raise ValueError("lens must hold two lengths per pair")
+        self.npairs = int(self.lens.size // 2)
+        dev = torch.device(device)
+        self.ascii = ascii_dev
+        self.out = torch.empty((self.npairs, 8), dtype=torch.int32, device=dev)
+        self.pos_off = torch.empty(self.npairs + 1, dtype=torch.int64, device=dev)
+        self.pos_cap = int(pos_cap)
+        self.pos = torch.empty(max(self.pos_cap, 1), dtype=torch.int32, device=dev)
+        need = lor_batch_graph_workspace_size(self.lens.ctypes.data, self.npairs)
+        if need == 0:
+            raise ValueError("bad pair lengths")
+        self.ws = workspace(need, dev)
+        ptr = _ptr(ascii_dev, torch.uint8, "ascii") if ascii_dev.numel() else None
+        h = ctypes.c_void_p()
+        _check(lor_batch_graph_create(ptr, self.lens.ctypes.data, self.npairs, self.out.data_ptr(),
+                                      self.pos_off.data_ptr(), self.pos.data_ptr(), self.pos_cap,
+                                      self.ws.data_ptr(), self.ws.numel(), ctypes.byref(h)),
+               "lor_batch_graph_create")
+        self._g = h
+
+    @property
+    def kernels(self) -> int:
+        return int(lor_batch_graph_kernels(self._g))
+
+    def run(self, ascii_dev=None, stream=None):
+        if ascii_dev is not None and ascii_dev.data_ptr() != self.ascii.data_ptr():
+            raise ValueError("a batch graph reads the input buffer it was created with")
+        _check(lor_batch_graph_launch(self._g, _stream(stream)), "lor_batch_graph_launch")
+        return self.out, self.pos_off, self.pos
+
+    def close(self):
+        if getattr(self, "_g", None):
+            lor_batch_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("workers", ctypes.c_int32),
                 ("max_batch_pairs", ctypes.c_int32), ("max_batch_symbols", ctypes.c_int64)]
@@ -471,6 +596,28 @@ def rmq_build(lcp_arr: torch.Tensor, table=None, stream=None) -> torch.Tensor:
                        table.numel(), _stream(stream))
     _check(rc, "lor_rmq_build")
     return table
+
+
+def rmq_block_build(lcp_arr: torch.Tensor, table=None, stream=None) -> torch.Tensor:
+    """Block-sparse (linear-space) table over an LCP array (lor_rmq_block_build)."""
+    n = lcp_arr.numel()
+    elems = int(load().lor_rmq_block_table_elems(n))
+    if table is None:
+        table = torch.empty(elems, dtype=torch.int32, device=lcp_arr.device)
+    _check(load().lor_rmq_block_build(_ptr(lcp_arr, torch.int32, "lcp"), n, _ptr(table, torch.int32, "table"),
+                                      table.numel(), _stream(stream)), "lor_rmq_block_build")
+    return table
+
+
+def rmq_block_query(table, lcp_arr, isa, p, q, out=None, stream=None) -> torch.Tensor:
+    """LCP of suffix pairs through the block-sparse table (lor_rmq_block_query)."""
+    if out is None:
+        out = torch.empty_like(p)
+    _check(load().lor_rmq_block_query(_ptr(table, torch.int32, "table"), _ptr(lcp_arr, torch.int32, "lcp"),
+                                      _ptr(isa, torch.int32, "isa"), isa.numel(), _ptr(p, torch.int32, "p"),
+                                      _ptr(q, torch.int32, "q"), p.numel(), _ptr(out, torch.int32, "out"),
+                                      _stream(stream)), "lor_rmq_block_query")
+    return out
 
 
 def rmq_query(table, isa, p, q, out=None, stream=None) -> torch.Tensor:

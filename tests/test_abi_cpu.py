@@ -147,3 +147,37 @@ def test_server_create_without_device_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.lor_server_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LOR_ERR_CUDA
     assert not h.value
+
+
+def test_batch_graph_workspace_covers_the_batch_workspace(lib):
+    lens = np.array([1000, 2000, 0, 5, 300000, 1], dtype=np.int64)
+    base = L.lor_batch_workspace_size(lens.ctypes.data, 3)
+    g = L.lor_batch_graph_workspace_size(lens.ctypes.data, 3)
+    assert base > 0 and g > base and g % 256 == 0
+    assert L.lor_batch_graph_workspace_size(lens.ctypes.data, 0) == 0
+    h = ctypes.c_void_p()
+    # bad arguments are refused on the host, before any capture
+    assert L.lor_batch_graph_create(None, lens.ctypes.data, 0, None, None, None, 0, None, 0,
+                                    ctypes.byref(h)) == -1
+    assert L.lor_batch_graph_launch(None, None) == -1
+    assert L.lor_batch_graph_destroy(None) == 0
+
+
+def test_tune_configuration_round_trip_and_range_checks(lib):
+    import paper_1404_3448_gb300 as P
+    d = P.tune_default()
+    assert d == {"digit_bits": 8, "level0_key_bits": 48, "sort_items_64": 12, "sort_items_32": 16,
+                 "merge_items": 2}
+    try:
+        assert P.tune_set(digit_bits=6, merge_items=4)["digit_bits"] == 6
+        assert P.tune_get()["merge_items"] == 4
+        for bad in [dict(digit_bits=4), dict(digit_bits=9), dict(level0_key_bits=23),
+                    dict(level0_key_bits=61), dict(sort_items_64=16), dict(sort_items_32=8),
+                    dict(merge_items=3)]:
+            before = P.tune_get()
+            with pytest.raises(L.LorError):
+                P.tune_set(**bad)
+            assert P.tune_get() == before  # a refused value changes nothing
+    finally:
+        P.tune_set(**d)
+    assert P.tune_get() == d

@@ -105,3 +105,67 @@ def test_batch_repeated_pair_many_copies(L, oracle_mod):
     for p in range(300):
         assert_same(res[p], exp, p)
     assert_same(res[300], expect_pair(oracle_mod, seqs[1], seqs[0]), 300)
+
+
+# ------------------------------------------------------------------ CUDA graph replay
+
+def graph_results(L, pairs, ascii_dev=None, pos_cap=1 << 22):
+    flat = [s for pr in pairs for s in pr]
+    lens = [len(s) for s in flat]
+    if ascii_dev is None:
+        ascii_dev = torch.from_numpy(np.concatenate(flat) if sum(lens) else np.zeros(1, np.uint8)).cuda()
+    g = L.lor.BatchGraph(lens, ascii_dev, pos_cap=pos_cap)
+    return g, ascii_dev
+
+
+def test_batch_graph_replays_equal_eager_and_oracle(L, oracle_mod):
+    """The captured pipeline (no host round trip; doubling rounds enqueued up
+    front) gives every pair's record and positions, on two replays in a row,
+    and again after the input bytes change under the same lengths."""
+    pairs = []
+    for i in range(700):  # two groups (at most 512 pairs each)
+        alpha = [b"ACGT", b"AC", b"A"][i % 3]
+        a, b = gen.fuzz_sequences(9100 + i, nseq=2, max_len=[5, 60, 300][i % 3], alphabet=alpha)
+        if i % 19 == 0:
+            a = a[:0]
+        pairs.append([a, b])
+    pairs += gen.pair_batch(npairs=12, lo=1_000, hi=40_000, seed=140434491)
+    g, ascii_dev = graph_results(L, pairs)
+    assert g.kernels > 0
+    for rep in range(2):
+        g.run()
+        L.check_device(where=f"graph replay {rep}")
+        res = g.results()
+        for p, (a, b) in enumerate(pairs):
+            assert_same(res[p], expect_pair(oracle_mod, a, b), (rep, p))
+    # new bases, same lengths: the graph reads its input buffer at every replay
+    rng = np.random.default_rng(5)
+    alpha = np.frombuffer(b"ACGT", np.uint8)
+    pairs2 = [[alpha[rng.integers(0, 4, len(a))], alpha[rng.integers(0, 4, len(b))]] for a, b in pairs]
+    flat2 = np.concatenate([s for pr in pairs2 for s in pr])
+    ascii_dev.copy_(torch.from_numpy(flat2))
+    g.run()
+    L.check_device(where="graph replay, new input")
+    res = g.results()
+    eager = run_batch(L, pairs2)
+    for p, (a, b) in enumerate(pairs2):
+        assert_same(res[p], {**eager[p], "positions": eager[p]["positions"]}, p)
+        if p % 50 == 0:
+            assert_same(res[p], expect_pair(oracle_mod, a, b), p)
+    g.close()
+
+
+def test_batch_graph_long_repeats(L, oracle_mod):
+    """Copies of one pair make the group text one long repeat: many doubling
+    rounds run inside the graph before every sample is resolved."""
+    seqs, _ = gen.pair_uniform(n_each=1500, plant_len=120, seed=78)
+    pairs = [seqs] * 200 + [[np.frombuffer(b"A" * 3000, np.uint8), np.frombuffer(b"A" * 700, np.uint8)]]
+    g, _ = graph_results(L, pairs)
+    g.run()
+    L.check_device(where="graph replay, repeats")
+    res = g.results()
+    exp = expect_pair(oracle_mod, *seqs)
+    for p in range(200):
+        assert_same(res[p], exp, p)
+    assert_same(res[200], expect_pair(oracle_mod, *pairs[200]), 200)
+    g.close()

@@ -204,6 +204,33 @@ def test_sparse_table_is_window_minimum(oracle_mod):
                 assert st[j, i] == lcp[i:min(i + (1 << j), n)].min()
 
 
+def test_block_table_windows_are_ranges_of_the_lcp_array(oracle_mod):
+    """Entry (j, b) of the block table is the minimum of the LCP entries of
+    blocks b .. b + 2^j - 1 (clipped at n), by brute force on small arrays;
+    and the minimum of any rank range split into partial blocks and whole
+    blocks equals the range minimum (the query rule of the linear-space RMQ)."""
+    rng = np.random.default_rng(10)
+    for n in [1, 31, 32, 33, 64, 100, 1000]:
+        lcp = rng.integers(0, 50, n).astype(np.int32)
+        bt = oracle_mod.block_sparse_table(lcp)
+        nb = -(-n // 32)
+        assert bt.shape == (oracle_mod.sparse_table_levels(nb), nb)
+        for j in range(bt.shape[0]):
+            for b in range(nb):
+                assert bt[j, b] == lcp[b * 32:min((b + (1 << j)) * 32, n)].min()
+        for _ in range(200):
+            a, e = sorted(int(x) for x in rng.integers(0, n, 2))
+            ba, bb = a // 32, e // 32
+            if ba == bb:
+                m = lcp[a:e + 1].min()
+            else:
+                m = min(lcp[a:(ba + 1) * 32].min(), lcp[bb * 32:e + 1].min())
+                if bb - ba - 1 > 0:
+                    j = (bb - ba - 1).bit_length() - 1
+                    m = min(m, bt[j, ba + 1], bt[j, bb - (1 << j)])
+            assert m == lcp[a:e + 1].min()
+
+
 # ---------------------------------------------------------------- LCS DP pins
 
 def _brute_lcs(a: bytes, b: bytes):
