@@ -427,6 +427,15 @@ __global__ void k_group_records(const CharT *__restrict__ s, int64_t n, int64_t 
     rec[t] = g;
 }
 
+// Nonsample suffix 3t with its comparison key, in nonsample order (written
+// by k_nonsample_rec at level 0): t, t_3t | t_3t+1 << 8, rank(S_3t+1),
+// rank(S_3t+2).
+struct __align__(16) BRec16 {
+    int32_t t;
+    uint32_t c01;
+    int32_t r1, r2;
+};
+
 template <typename CharT>
 struct MergeIn {
     const GroupRec<CharT> *rec;
@@ -435,6 +444,7 @@ struct MergeIn {
     int64_t na;
     const uint32_t *B;  // nonsample order (group indices t; position 3t)
     int64_t nb;
+    const BRec16 *Bx;  // when set: the nonsample records in order (B unused)
 };
 
 // Sample suffix p: key (t_p, rank(S_p+1)) for p = 1 mod 3 (marked c1 = -1),
@@ -471,6 +481,15 @@ __device__ __forceinline__ BRec make_b(const GroupRec<CharT> &g, uint32_t t) {
     y.r2 = g.r2;
     return y;
 }
+__device__ __forceinline__ BRec make_bx(const BRec16 &g) {
+    BRec y;
+    y.pos = 3 * g.t;
+    y.c0 = int32_t(g.c01 & 0xFFu);
+    y.c1 = int32_t((g.c01 >> 8) & 0xFFu);
+    y.r1 = g.r1;
+    y.r2 = g.r2;
+    return y;
+}
 // Is the sample suffix x smaller than the nonsample suffix y?
 __device__ __forceinline__ bool a_less_b(const ARec &x, const BRec &y) {
     if (x.c0 != y.c0) return x.c0 < y.c0;
@@ -493,9 +512,14 @@ __device__ int64_t merge_split(const MergeIn<CharT> &a, int64_t d) {
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         const int32_t r = a.A[mid];
-        const uint32_t t = a.B[d - 1 - mid];
         const ARec x = make_a(a.rec[a_group(r, a.n0)], r, a.n0);
-        const BRec y = make_b(a.rec[t], t);
+        BRec y;
+        if (a.Bx) {
+            y = make_bx(a.Bx[d - 1 - mid]);
+        } else {
+            const uint32_t t = a.B[d - 1 - mid];
+            y = make_b(a.rec[t], t);
+        }
         if (a_less_b(x, y)) lo = mid + 1;
         else hi = mid;
     }
@@ -536,23 +560,47 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge(MergeIn<Char
     const int na = int(a1 - a0), nb = int(b1 - b0), nt = int(d1 - d0);
     // Load the tile: all indices first, then all record gathers, so that each
     // thread keeps kMergeItems independent loads in flight.
-    int32_t idx[kMergeItems];
+    if (a.Bx) {
+        // Nonsample records arrive in order: only the samples are gathered.
+        int32_t idx[kMergeItems];
 #pragma unroll
-    for (int k = 0; k < kMergeItems; ++k) {
-        const int sl = int(threadIdx.x) + k * kMergeThreads;
-        idx[k] = sl < na ? a.A[a0 + sl] : (sl < nt ? int32_t(a.B[b0 + sl - na]) : 0);
-    }
-    GroupRec<CharT> g[kMergeItems];
+        for (int k = 0; k < kMergeItems; ++k) {
+            const int sl = int(threadIdx.x) + k * kMergeThreads;
+            idx[k] = sl < na ? a.A[a0 + sl] : 0;
+        }
+        GroupRec<CharT> g[kMergeItems];
+        BRec16 bx[kMergeItems];
 #pragma unroll
-    for (int k = 0; k < kMergeItems; ++k) {
-        const int sl = int(threadIdx.x) + k * kMergeThreads;
-        if (sl < nt) g[k] = a.rec[sl < na ? a_group(idx[k], a.n0) : idx[k]];
-    }
+        for (int k = 0; k < kMergeItems; ++k) {
+            const int sl = int(threadIdx.x) + k * kMergeThreads;
+            if (sl < na) g[k] = a.rec[a_group(idx[k], a.n0)];
+            else if (sl < nt) bx[k] = a.Bx[b0 + sl - na];
+        }
 #pragma unroll
-    for (int k = 0; k < kMergeItems; ++k) {
-        const int sl = int(threadIdx.x) + k * kMergeThreads;
-        if (sl < na) As[sl] = make_a(g[k], idx[k], a.n0);
-        else if (sl < nt) Bs[sl - na] = make_b(g[k], uint32_t(idx[k]));
+        for (int k = 0; k < kMergeItems; ++k) {
+            const int sl = int(threadIdx.x) + k * kMergeThreads;
+            if (sl < na) As[sl] = make_a(g[k], idx[k], a.n0);
+            else if (sl < nt) Bs[sl - na] = make_bx(bx[k]);
+        }
+    } else {
+        int32_t idx[kMergeItems];
+#pragma unroll
+        for (int k = 0; k < kMergeItems; ++k) {
+            const int sl = int(threadIdx.x) + k * kMergeThreads;
+            idx[k] = sl < na ? a.A[a0 + sl] : (sl < nt ? int32_t(a.B[b0 + sl - na]) : 0);
+        }
+        GroupRec<CharT> g[kMergeItems];
+#pragma unroll
+        for (int k = 0; k < kMergeItems; ++k) {
+            const int sl = int(threadIdx.x) + k * kMergeThreads;
+            if (sl < nt) g[k] = a.rec[sl < na ? a_group(idx[k], a.n0) : idx[k]];
+        }
+#pragma unroll
+        for (int k = 0; k < kMergeItems; ++k) {
+            const int sl = int(threadIdx.x) + k * kMergeThreads;
+            if (sl < na) As[sl] = make_a(g[k], idx[k], a.n0);
+            else if (sl < nt) Bs[sl - na] = make_b(g[k], uint32_t(idx[k]));
+        }
     }
     __syncthreads();
     const int dl = min(int(threadIdx.x) * kMergeItems, nt);
@@ -572,6 +620,108 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge(MergeIn<Char
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nt; i += kMergeThreads) out[d0 + i] = Os[i];
+}
+
+// ---- Step 2 at level 0 with the records: the nonsample suffixes 3t in the
+// order of rank(S_3t+1) (that is, of the B1 samples in SAR) are split stably
+// by their first symbol t_3t, and each carries its record (gathered here once,
+// from the group records) so that the merge reads them in order.
+
+// hist[c] = number of nonsample positions 3t (t < n0) holding symbol c.
+__global__ void k_first_sym_hist(const uint8_t *__restrict__ s, int64_t n0, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t sh[kRadix];
+    sh[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n0; t += int64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&sh[s[3 * t]], 1u);
+    __syncthreads();
+    if (sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
+}
+
+constexpr int kNsItems = 8;
+constexpr int kNsTile = kSortThreads * kNsItems;
+
+struct NsSmem {
+    BRec16 rec[kNsTile];
+    uint32_t warp_hist[kSortWarps][kRadix];
+    uint32_t local_start[kRadix];
+    long long gbase[kRadix];
+    uint32_t scratch[kSortWarps + 1];
+    uint32_t count;
+    long long tile;
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_nonsample_rec(
+    const int32_t *__restrict__ SAR, int64_t n02, int64_t n0, const GroupRec<uint8_t> *__restrict__ rec,
+    const uint32_t *__restrict__ offsets, BRec16 *__restrict__ out, uint64_t *__restrict__ lookback,
+    unsigned long long *tile_ctr, unsigned long long tile_base, uint32_t epoch, int *status) {
+    __shared__ NsSmem S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
+    for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t tile = S.tile;
+    const int64_t wbase = tile * kNsTile + int64_t(warp) * (kNsItems * 32);
+    BRec16 v[kNsItems];
+    uint32_t dig[kNsItems], r[kNsItems];
+#pragma unroll
+    for (int i = 0; i < kNsItems; ++i) {
+        const int64_t idx = wbase + i * 32 + lane;
+        const int32_t x = idx < n02 ? SAR[idx] : -1;
+        dig[i] = 0x100u;
+        if (x >= 0 && x < n0) {
+            const GroupRec<uint8_t> g = rec[x];
+            v[i].t = x;
+            v[i].c01 = g.c4 & 0xFFFFu;
+            v[i].r1 = g.r1;
+            v[i].r2 = g.r2;
+            dig[i] = g.c4 & 0xFFu;
+        }
+    }
+    uint32_t *wh = S.warp_hist[warp];
+#pragma unroll
+    for (int i = 0; i < kNsItems; ++i) {
+        const uint32_t d = dig[i];
+        const uint32_t peers = warp_peers9(d);
+        const uint32_t lt = __popc(peers & lanemask_lt());
+        const uint32_t cnt = d < 0x100u ? wh[d] : 0u;
+        r[i] = cnt + lt;
+        __syncwarp();
+        if (d < 0x100u && lt == 0) wh[d] = cnt + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int dg = tid;
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = S.warp_hist[w][dg];
+        S.warp_hist[w][dg] = total;
+        total += c;
+    }
+    uint32_t tile_total;
+    const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
+    S.local_start[dg] = lstart;
+    if (tid == 0) S.count = tile_total;
+    uint32_t excl = 0;
+    if (tile == 0) {
+        st_volatile_u64(&lookback[dg], lb_pack(epoch, kFlagIncl, total));
+    } else {
+        st_volatile_u64(&lookback[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
+        excl = lookback_digit(lookback, tile, dg, epoch, status);
+        st_volatile_u64(&lookback[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
+    }
+    S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kNsItems; ++i)
+        if (dig[i] < 0x100u) S.rec[S.local_start[dig[i]] + S.warp_hist[warp][dig[i]] + r[i]] = v[i];
+    __syncthreads();
+    const int cnt_tile = int(S.count);
+    for (int i = tid; i < cnt_tile; i += kSortThreads) {
+        const BRec16 g = S.rec[i];
+        out[S.gbase[g.c01 & 0xFFu] + i] = g;
+    }
 }
 
 template <typename CharT>
@@ -830,17 +980,46 @@ __global__ void k_dbl_init(int32_t *__restrict__ R, int64_t m, const int32_t *__
     if (j < m) R[j] = headof[R[j]];
 }
 
-// Positions (in name order) of samples that share their name.
+// Positions (in name order) of samples that share their name.  Each thread
+// loads its run of names with 16-byte loads, plus one name on either side.
 __global__ void __launch_bounds__(kScanThreads) k_dbl_unresolved(
     const int32_t *__restrict__ NS, int64_t m, uint32_t *__restrict__ ul, uint32_t *count, uint64_t *lb,
     unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch, int *status, int64_t ntiles) {
-    tile_compact(
-        m,
-        [&](int64_t k) {
-            const int32_t v = NS[k];
-            return (k > 0 && NS[k - 1] == v) || (k + 1 < m && NS[k + 1] == v);
-        },
-        [&](int64_t k, uint32_t d) { ul[d] = uint32_t(k); }, lb, ctr, tile_base, epoch, status, count, ntiles);
+    __shared__ long long s_tile;
+    __shared__ uint32_t scratch[kScanThreads / 32 + 1];
+    __shared__ uint32_t s_prefix;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
+    int32_t v[kScanItems];
+    load_run<int32_t, kScanItems>(NS, base, m, -1, v);
+    const int32_t before = base > 0 && base - 1 < m ? NS[base - 1] : -1;
+    const int32_t after = base + kScanItems < m ? NS[base + kScanItems] : -2;
+    uint32_t flags = 0, cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int32_t prev = i > 0 ? v[i - 1] : before;
+        const int32_t next = i + 1 < kScanItems ? v[i + 1] : after;
+        const bool in = base + i < m && (prev == v[i] || (base + i + 1 < m && next == v[i]));
+        flags |= uint32_t(in) << i;
+        cnt += in ? 1u : 0u;
+    }
+    uint32_t agg;
+    const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
+    if (tid < 32) {
+        const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
+        if (tid == 0) {
+            s_prefix = p;
+            if (count && tile == ntiles - 1) *count = p + agg;
+        }
+    }
+    __syncthreads();
+    uint32_t o = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if ((flags >> i) & 1u) ul[o++] = uint32_t(base + i);
 }
 
 __global__ void k_dbl_keys(const uint32_t *__restrict__ ul, int64_t U, const int32_t *__restrict__ SAR,
@@ -1440,17 +1619,73 @@ int nonsample_by_sort(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits, 
 // order B into out (the dummy, when present, is the smallest sample).  The
 // records go to the two adjacent 64-bit buffers.
 template <typename CharT>
-int merge_level(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t *Rl, const int32_t *SAR,
-                const uint32_t *B, int32_t *out) {
+int merge_run(Dc3Run &D, const LevelSizes &z, const GroupRec<CharT> *rec, const int32_t *SAR, const uint32_t *B,
+              const BRec16 *Bx, int32_t *out);
+
+// The group records of Step 3 (rank(S_x) from Rl) in t64[1..2].
+template <typename CharT>
+int build_records(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t *Rl, GroupRec<CharT> **rec_out) {
     cudaStream_t st = D.s;
-    const int64_t n = z.n;
     GroupRec<CharT> *rec = (GroupRec<CharT> *)D.t64[1];
     const size_t rec_bytes = align256(sizeof(GroupRec<CharT>) * size_t(z.n0));
+    // The records fill at most t64[1..2] (16 bytes per position at level 0,
+    // 32 per group of three below).
+    if (rec_bytes > size_t((char *)D.t64[2] - (char *)D.t64[1]) * 2) return LOR_ERR_WORKSPACE;
     {
         ProfScope ps(PK_MERGE, double(z.n0) * (3.0 * sizeof(CharT) + 12 + sizeof(GroupRec<CharT>)), st);
-        k_group_records<CharT><<<grid_for(z.n0, 256), 256, 0, st>>>(s, n, z.n0, z.n2, Rl, rec);
+        k_group_records<CharT><<<grid_for(z.n0, 256), 256, 0, st>>>(s, z.n, z.n0, z.n2, Rl, rec);
     }
     LOR_LAUNCH_CHECK();
+    *rec_out = rec;
+    return LOR_OK;
+}
+
+// Steps 2 and 3 at level 0: records first, then the nonsample split carrying
+// them (into t32[0..3]), then the merge reading them in order.
+int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z, const int32_t *Rl,
+                               const int32_t *SAR, int32_t *out) {
+    cudaStream_t st = D.s;
+    GroupRec<uint8_t> *rec;
+    int rc = build_records<uint8_t>(D, s, z, Rl, &rec);
+    if (rc) return rc;
+    BRec16 *Bx = (BRec16 *)D.t32[0];
+    if (size_t((char *)D.t32[4] - (char *)D.t32[0]) < sizeof(BRec16) * size_t(z.n0)) return LOR_ERR_WORKSPACE;
+    LOR_CUDA_TRY(cudaMemsetAsync(D.rs.hist, 0, sizeof(uint32_t) * kRadix, st));
+    {
+        ProfScope ps(PK_NONSAMPLE, double(z.n0), st);
+        k_first_sym_hist<<<unsigned(min64(cdiv(z.n0, 256), 152 * 4)), 256, 0, st>>>(s, z.n0, D.rs.hist);
+        LOR_LAUNCH_CHECK();
+        k_radix_offsets<<<1, kRadix, 0, st>>>(D.rs.hist, D.rs.offsets);
+        LOR_LAUNCH_CHECK();
+    }
+    {
+        ProfScope ps(PK_NONSAMPLE, double(z.n02) * 4 + double(z.n0) * (16 + 16), st);
+        const int64_t ntiles = cdiv(z.n02, kNsTile);
+        if (ntiles > D.rs.max_tiles) return LOR_ERR_WORKSPACE;
+        D.rs.epoch++;
+        k_nonsample_rec<<<unsigned(ntiles), kSortThreads, 0, st>>>(SAR, z.n02, z.n0, rec, D.rs.offsets, Bx,
+                                                                   D.rs.lookback, D.rs.tile_ctr, D.rs.tile_base,
+                                                                   D.rs.epoch, D.status);
+        LOR_LAUNCH_CHECK();
+        D.rs.tile_base += (unsigned long long)ntiles;
+    }
+    return merge_run<uint8_t>(D, z, rec, SAR, nullptr, Bx, out);
+}
+
+template <typename CharT>
+int merge_level(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t *Rl, const int32_t *SAR,
+                const uint32_t *B, int32_t *out) {
+    GroupRec<CharT> *rec;
+    const int rc = build_records<CharT>(D, s, z, Rl, &rec);
+    if (rc) return rc;
+    return merge_run<CharT>(D, z, rec, SAR, B, nullptr, out);
+}
+
+template <typename CharT>
+int merge_run(Dc3Run &D, const LevelSizes &z, const GroupRec<CharT> *rec, const int32_t *SAR, const uint32_t *B,
+              const BRec16 *Bx, int32_t *out) {
+    cudaStream_t st = D.s;
+    const int64_t n = z.n;
     MergeIn<CharT> a;
     a.rec = rec;
     a.n0 = int32_t(z.n0);
@@ -1459,10 +1694,8 @@ int merge_level(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t *R
     a.na = z.n02 - dummy;
     a.B = B;
     a.nb = z.n0;
+    a.Bx = Bx;
     const int64_t ntiles = cdiv(n, kMergeTile);
-    // The records fill at most t64[1..2] (16 bytes per position at level 0,
-    // 32 per group of three below); the partition has a region of its own.
-    if (rec_bytes > size_t((char *)D.t64[2] - (char *)D.t64[1]) * 2) return LOR_ERR_WORKSPACE;
     int64_t *split = (int64_t *)(D.ws + D.L.split);
     {
         ProfScope ps(PK_MERGE, double(n) * (4 + 4 + sizeof(GroupRec<CharT>)), st);
@@ -1583,10 +1816,7 @@ int dc3_graph(Dc3Run &D, const uint8_t *s, int64_t n, int64_t maxc, int32_t *out
     if (rc) return rc;
     rc = sa_by_doubling_graph(D, Rl, z.n02, SAR, NSl, bucket_names(D, z));
     if (rc) return rc;
-    const uint32_t *B;
-    rc = nonsample_by_sort<uint8_t>(D, s, z, bits, SAR, &B);
-    if (rc) return rc;
-    return merge_level<uint8_t>(D, s, z, Rl, SAR, B, out);
+    return level0_nonsample_and_merge(D, s, z, Rl, SAR, out);
 }
 
 template <typename CharT>
@@ -1660,6 +1890,9 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     // Rl now holds rank(S_i) by reduced-string index (unique names are ranks).
 
     // Step 2: nonsample order, as group indices t (position 3t).
+    if constexpr (sizeof(CharT) == 1) {
+        if (!PS && !D.force_lsd) return level0_nonsample_and_merge(D, s, z, Rl, SAR, out);
+    }
     const uint32_t *B;
     if (PS && !D.force_lsd) {
         uint32_t *T0 = D.t32[0], *P0 = D.t32[1], *Dslot = D.t32[2], *Dt = D.t32[3];

@@ -191,8 +191,9 @@ __device__ __forceinline__ uint32_t window_exc(const uint32_t *__restrict__ E, i
 
 // Symbols from p on out of the 16-byte chunk holding p: 32 of them when p
 // sits in the chunk's first half, else the 64 - (p mod 64) up to its end.
-__device__ __forceinline__ uint64_t window_chunk(const uint64_t *__restrict__ P, int64_t p, int &avail) {
-    const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(P)[p >> 6];
+__device__ __forceinline__ uint64_t window_chunk(const uint64_t *__restrict__ P, int64_t p, int &avail,
+                                                 uint64_t keep) {
+    const ulonglong2 v = ld_u64x2_hint(reinterpret_cast<const ulonglong2 *>(P) + (p >> 6), keep);
     const int off = int(p & 63);
     if (off < 32) {
         avail = 32;
@@ -230,8 +231,15 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
     const int32_t *lst = nexc <= kExcShared ? s_exc : T.list;
     if (nexc <= kExcShared)
         for (int i = threadIdx.x; i < nexc; i += kPlcpThreads) s_exc[i] = T.list[i];
-    // ISA in text order (coalesced); the PHI reads below hit the same lines.
-    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) isa[base + i] = ip[base + i].x;
+    // The packed text is read at random positions (the PHI side) and should
+    // stay in L2; the {ISA, PHI} pairs, ISA and PLCP stream through once.
+    const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
+    // ISA in text order (coalesced), PHI staged beside the output slots.
+    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) {
+        const int2 v = ld_i32x2_hint(ip + base + i, once);
+        st_i32_hint(isa + base + i, v.x, once);
+        s_out[chunk_slot(i)] = v.y;
+    }
     __syncthreads();
     const uint64_t *__restrict__ P = T.P;
     int64_t h = 0;
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
     const int l0 = int(threadIdx.x) * kPlcpPer;
     for (int l = l0; l < l0 + kPlcpPer && l < cnt; ++l) {
         const int64_t i = base + l;
-        const int64_t j = ip[i].y;
+        const int64_t j = s_out[chunk_slot(l)];
         if (j < 0 || j >= n) {
             if (j != -1) bad = true;
             h = 0;
@@ -257,8 +265,8 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
                 bool mism = false;
                 while (k < lim) {
                     int aa, ab;
-                    const uint64_t wa = window_chunk(P, a + k, aa);
-                    const uint64_t wb = window_chunk(P, b + k, ab);
+                    const uint64_t wa = window_chunk(P, a + k, aa, keep);
+                    const uint64_t wb = window_chunk(P, b + k, ab, keep);
                     int len = aa < ab ? aa : ab;
                     if (lim - k < len) len = int(lim - k);
                     uint64_t d = wa ^ wb;
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
     }
     if (bad) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) plcp[base + i] = s_out[chunk_slot(i)];
+    for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) st_i32_hint(plcp + base + i, s_out[chunk_slot(i)], once);
 }
 
 // LCP[k] = PLCP[SA[k]] (a position without predecessor has PLCP 0).

@@ -135,7 +135,7 @@ struct OnesweepSmem {
 // waiting), summing aggregates up to the first inclusive prefix.  A
 // descriptor not yet published ends the round; the walk resumes there.  The
 // whole wait is bounded by kSpinLimitNs (then LOR_ERR_TIMEOUT).
-constexpr int kLookWindow = 4;
+constexpr int kLookWindow = 2;
 
 __device__ __forceinline__ uint32_t lookback_digit(const uint64_t *lb, int64_t tile, int dg, uint32_t epoch,
                                                    int *status) {
@@ -367,6 +367,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
     for (int i = tid; i < cnt_tile; i += kSortThreads) {
         const uint32_t kk = S.keys[i];
         const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
+        if (o < 0 || o >= m) {  // keys that were to be a permutation were not
+            atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+            continue;
+        }
         kout[o] = kk;
         vout[o] = S.vals[i];
     }
@@ -563,6 +567,9 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
 // on the top 8 bits of the keys groups the pairs by destination window
 // (bound / 256 entries), and a streaming pass then writes them: consecutive
 // blocks write into the same small window, so the stores combine in L2.
+// When m == bound the keys are a permutation of [0, m) (every inverse-array
+// scatter of the path): each window then holds exactly bound / 256 keys and
+// the pass needs no histogram of them.
 
 static __global__ void k_scatter_pairs(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                                        int64_t m, int32_t *__restrict__ dst, int32_t add, int64_t bound,
@@ -582,20 +589,34 @@ static __global__ void k_scatter_pairs(const uint32_t *__restrict__ key, const u
 // are generated).  The caller accounts the scatter kernel's launch.
 // One partition pass of m keys by bits [lo, top) (top - lo <= 8): histogram,
 // offsets and k_partition.  No host synchronisation.
+// Keys that are a permutation of [0, m) fill every bucket of 2^lo keys
+// exactly: its start is known without counting.
+static __global__ void k_perm_offsets(uint32_t *__restrict__ offsets, int lo, int64_t m) {
+    const int64_t o = int64_t(threadIdx.x) << lo;
+    offsets[threadIdx.x] = uint32_t(o < m ? o : m);
+}
+
+// (perm: the keys are a permutation of [0, m), as for every inverse-array
+// scatter here; then the bucket starts need no histogram.)
 template <typename ValT, int kVMode>
 int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int64_t m, int lo, int top,
-                   uint32_t *kout, ValT *vout) {
+                   uint32_t *kout, ValT *vout, bool perm = false) {
     cudaStream_t s = rs.stream;
     if (cdiv(m, sort_tile<uint32_t, ValT>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
-    LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * kRadix, s));
-    {
-        ProfScope ps(PK_RADIX_HIST, double(m) * 4, s);
-        const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
-        k_radix_hist<uint32_t><<<grid, 256, 0, s>>>(keys, m, nullptr, lo, top, 1, kRadixBits, rs.hist);
+    if (perm) {
+        k_perm_offsets<<<1, kRadix, 0, s>>>(rs.offsets, lo, m);
+        LOR_LAUNCH_CHECK();
+    } else {
+        LOR_CUDA_TRY(cudaMemsetAsync(rs.hist, 0, sizeof(uint32_t) * kRadix, s));
+        {
+            ProfScope ps(PK_RADIX_HIST, double(m) * 4, s);
+            const int grid = int(min64(cdiv(m, 256 * 4), 152 * 8));
+            k_radix_hist<uint32_t><<<grid, 256, 0, s>>>(keys, m, nullptr, lo, top, 1, kRadixBits, rs.hist);
+        }
+        LOR_LAUNCH_CHECK();
+        k_radix_offsets<<<1, kRadix, 0, s>>>(rs.hist, rs.offsets);
+        LOR_LAUNCH_CHECK();
     }
-    LOR_LAUNCH_CHECK();
-    k_radix_offsets<<<1, kRadix, 0, s>>>(rs.hist, rs.offsets);
-    LOR_LAUNCH_CHECK();
     const size_t smem = sizeof(OnesweepSmem<uint32_t, ValT>);
     LOR_CUDA_TRY(cudaFuncSetAttribute(k_partition<ValT, kVMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(smem)));
@@ -620,8 +641,8 @@ inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32
     if (m <= 0) return LOR_OK;
     const int top = bit_width_u64(uint64_t(bound > 1 ? bound - 1 : 1));
     const int lo = top > kRadixBits ? top - kRadixBits : 0;
-    const int rc = vals ? partition_pass<uint32_t, VM_LOAD>(rs, keys, vals, m, lo, top, kbuf, vbuf0)
-                        : partition_pass<uint32_t, VM_IOTA>(rs, keys, nullptr, m, lo, top, kbuf, vbuf0);
+    const int rc = vals ? partition_pass<uint32_t, VM_LOAD>(rs, keys, vals, m, lo, top, kbuf, vbuf0, m == bound)
+                        : partition_pass<uint32_t, VM_IOTA>(rs, keys, nullptr, m, lo, top, kbuf, vbuf0, m == bound);
     if (rc) return rc;
     {
         ProfScope ps(PK_RANK_SCATTER, double(m) * 12, rs.stream);
@@ -657,7 +678,7 @@ inline int bucketed_isa_phi(RadixScratch &rs, const int32_t *sa, int64_t m, int6
     const int top = bit_width_u64(uint64_t(bound > 1 ? bound - 1 : 1));
     const int lo = top > kRadixBits ? top - kRadixBits : 0;
     const int rc = partition_pass<uint64_t, VM_IDX_PREV>(rs, reinterpret_cast<const uint32_t *>(sa), nullptr, m,
-                                                          lo, top, kbuf, vbuf);
+                                                          lo, top, kbuf, vbuf, m == bound);
     if (rc) return rc;
     {
         ProfScope ps(PK_ISA_SCATTER, double(m) * 20, rs.stream);
