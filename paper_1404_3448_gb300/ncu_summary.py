@@ -29,14 +29,16 @@ KINDS = [
     ("k_name", "naming"), ("k_par_name", "naming"), ("k_dense_scan", "naming"), ("k_dense_write", "naming"),
     ("k_dbl_", "naming"),
     ("k_rank_scatter", "rank_scatter"), ("k_scatter_pairs", "rank_scatter"), ("k_dense_sorted", "rank_scatter"),
-    ("k_nonsample", "nonsample"), ("k_par_nonsamples", "nonsample"), ("k_par_ns_", "nonsample"),
+    ("k_nonsample", "nonsample"), ("k_first_sym_hist", "nonsample"), ("k_par_nonsamples", "nonsample"),
+    ("k_par_ns_", "nonsample"), ("k_perm_offsets", "radix_hist"),
     ("k_gather_pri", "nonsample"), ("k_par_dup_writeback", "nonsample"),
     ("k_group_records", "merge"), ("k_merge", "merge"),
     ("k_isa_phi", "isa_scatter"), ("k_scatter_isa_phi", "isa_scatter"),
     ("k_text_max", "kasai"), ("k_pack_text", "kasai"), ("k_sort_exc", "kasai"), ("k_plcp", "kasai"),
     ("k_lcp_", "kasai"),
     ("k_ov_argmax", "overlap_scan"), ("k_ov_", "overlap_collect"), ("k_copy_u32_i32", "overlap_collect"),
-    ("k_rmq_query", "rmq_query"), ("k_rmq_", "rmq_level"),
+    ("k_rmq_query", "rmq_query"), ("k_rmqb_query", "rmq_query"), ("k_rmq_", "rmq_level"),
+    ("k_rmqb_", "rmq_level"),
 ]
 
 
@@ -49,7 +51,7 @@ def kind_of(kernel: str) -> str:
 
 def short_name(name: str) -> str:
     name = re.sub(r"\(.*", "", name.replace("(anonymous namespace)::", ""))
-    name = name.replace("unnamed>::", "").replace("lor::", "").strip()
+    name = name.replace("<unnamed>::", "").replace("unnamed>::", "").replace("lor::", "").strip()
     return name[5:] if name.startswith("void ") else name
 
 
