@@ -244,6 +244,15 @@ int lor_rmq_block_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64
 int lor_rmq_block_query(const int32_t *d_table, const int32_t *d_lcp, const int32_t *d_isa, int64_t n,
                         const int32_t *d_p, const int32_t *d_q, int64_t nq, int32_t *d_out,
                         lor_stream_t stream);
+/* The index form of the RMQ (Section 3: RMQ returns the position of the
+ * minimum): for suffixes p[i] != q[i] with ranks r1 < r2, d_val[i] = the
+ * minimum of lcp(r1, r2] (the LCP of the two suffixes) and d_arg[i] = the
+ * leftmost rank k in (r1, r2] where it occurs; p[i] == q[i] gives
+ * d_val[i] = n - p[i], d_arg[i] = -1.  Same table, inputs and errors as
+ * lor_rmq_block_query (a bad position yields -1 in both outputs). */
+int lor_rmq_block_argmin(const int32_t *d_table, const int32_t *d_lcp, const int32_t *d_isa, int64_t n,
+                         const int32_t *d_p, const int32_t *d_q, int64_t nq, int32_t *d_val, int32_t *d_arg,
+                         lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Launch parameters and their autotuner (no counterpart in the paper).
@@ -259,8 +268,8 @@ int lor_rmq_block_query(const int32_t *d_table, const int32_t *d_lcp, const int3
  *                   and leave fewer repeated names for the later rounds
  *   sort_items_64   keys per thread of a sort pass over 64-bit keys: 8 or 12 (12)
  *   sort_items_32   keys per thread over 32-bit keys: 12 or 16 (16)
- *   merge_items     merged suffixes per thread of the Step-3 merge: 2 (512-thread
- *                   blocks) or 4 (256-thread blocks); default 2
+ *   merge_items     merged suffixes per thread of the Step-3 merge: 2, 4 or 8
+ *                   (512-, 256- or 128-thread blocks); default 4
  * lor_tune_set returns LOR_ERR_INVALID_ARG for a value out of range (and
  * changes nothing).
  *
@@ -327,8 +336,9 @@ int lor_rmq_query(const int32_t *d_table, const int32_t *d_isa, int64_t n, const
  * or a request is released; requests are admitted in arrival order), copies
  * the pairs to the device and runs the grouped pipeline of lor_batch_overlap
  * on them.  Batches of different workers run on the device at once.  After a
- * batch, its workspace is returned to the reservation; the batch's ISA and a
- * sparse table over its LCP array stay resident until every request of the
+ * batch, its workspace is returned to the reservation; the batch's ISA, its
+ * LCP array and a block table over it (the linear-space RMQ of
+ * lor_rmq_block_build, about 10.6 bytes per symbol in all) stay resident until every request of the
  * batch has been released.
  *
  * Results do not depend on how requests are batched: a request's record,

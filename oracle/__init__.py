@@ -341,6 +341,25 @@ def block_sparse_table(lcp, block: int = 32) -> np.ndarray:
     return sparse_table(block_minima(lcp, block))
 
 
+def rmq_argmin(lcp, isa, p, q):
+    """Section 3, RMQ returning the index: for suffixes p != q with ranks
+    r1 < r2, (min(lcp[r1+1 .. r2]), the leftmost rank k in (r1, r2] holding
+    it); p == q gives (n - p, -1).  By definition, one query at a time."""
+    lcp = np.asarray(lcp)
+    n = lcp.size
+    val = np.empty(len(p), dtype=np.int32)
+    arg = np.empty(len(p), dtype=np.int32)
+    for i, (a, b) in enumerate(zip(p, q)):
+        if a == b:
+            val[i], arg[i] = n - a, -1
+            continue
+        r1, r2 = sorted((int(isa[a]), int(isa[b])))
+        w = lcp[r1 + 1:r2 + 1]
+        j = int(np.argmin(w))  # first occurrence of the minimum
+        val[i], arg[i] = w[j], r1 + 1 + j
+    return val, arg
+
+
 def lcp_pairs(text, p, q) -> np.ndarray:
     """LCP of suffixes p[i] and q[i] by direct symbol comparison; the LCP of a
     suffix with itself is its length (Section 3, lcp of arbitrary suffixes)."""

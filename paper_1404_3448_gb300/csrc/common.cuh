@@ -62,7 +62,7 @@ struct TuneConfig {
     int level0_key_bits = 48;  // width of the level-0 sample keys (the symbols named at level 0)
     int sort_items_64 = 12;    // keys per thread of a sort pass over 64-bit keys: 8 or 12
     int sort_items_32 = 16;    // ... over 32-bit keys: 12 or 16
-    int merge_items = 2;       // merged suffixes per thread of the Step-3 merge: 2 (512 threads) or 4 (256)
+    int merge_items = 4;       // merged suffixes per thread of the Step-3 merge: 2, 4 or 8 (512, 256, 128 threads)
 };
 TuneConfig tune_config();
 // Records an event pair around one launch when profiling is on.

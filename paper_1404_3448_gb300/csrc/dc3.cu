@@ -445,6 +445,7 @@ struct MergeIn {
     const uint32_t *B;  // nonsample order (group indices t; position 3t)
     int64_t nb;
     const BRec16 *Bx;  // when set: the nonsample records in order (B unused)
+    const uint64_t *Ax;  // when set: the sample keys in sample order, aligned with A (no record gathers)
 };
 
 // Sample suffix p: key (t_p, rank(S_p+1)) for p = 1 mod 3 (marked c1 = -1),
@@ -471,6 +472,21 @@ __device__ __forceinline__ ARec make_a(const GroupRec<CharT> &g, int32_t r, int3
     }
     return x;
 }
+// A sample's comparison key packed in 8 bytes (level 0): rank in the low
+// word, then t_p and t_p+1 (0xFF when the key has one symbol: p = 1 mod 3).
+__device__ __forceinline__ uint64_t pack_a(const ARec &x) {
+    return uint64_t(uint32_t(x.r)) | (uint64_t(uint32_t(x.c0) & 0xFFu) << 32) |
+           (uint64_t(x.c1 < 0 ? 0xFFu : uint32_t(x.c1) & 0xFFu) << 40);
+}
+__device__ __forceinline__ ARec unpack_a(uint64_t w, int32_t r, int32_t n0) {
+    ARec x;
+    x.pos = r < n0 ? 3 * r + 1 : 3 * (r - n0) + 2;
+    x.r = int32_t(uint32_t(w));
+    x.c0 = int32_t((w >> 32) & 0xFFu);
+    x.c1 = r < n0 ? -1 : int32_t((w >> 40) & 0xFFu);
+    return x;
+}
+
 template <typename CharT>
 __device__ __forceinline__ BRec make_b(const GroupRec<CharT> &g, uint32_t t) {
     BRec y;
@@ -498,9 +514,10 @@ __device__ __forceinline__ bool a_less_b(const ARec &x, const BRec &y) {
     return x.r < y.r2;
 }
 
-// A merge tile is 1024 outputs: 512 threads x 2 (the default: the record
-// gathers are latency bound, and wide blocks with few items each keep the most
-// of them in flight per SM) or 256 threads x 4 (tune_config().merge_items).
+// A merge tile is 1024 outputs: 512 threads x 2, 256 x 4 or 128 x 8
+// (tune_config().merge_items).  Wide blocks with few items each keep the most
+// record gathers in flight; with the level-0 records carried in order there is
+// nothing to gather and more items per thread amortise the merge-path search.
 constexpr int kMergeTile = 1024;
 static_assert(kMergeTile >= 1024, "the workspace holds a partition entry per 1024 merged suffixes");
 
@@ -512,7 +529,7 @@ __device__ int64_t merge_split(const MergeIn<CharT> &a, int64_t d) {
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         const int32_t r = a.A[mid];
-        const ARec x = make_a(a.rec[a_group(r, a.n0)], r, a.n0);
+        const ARec x = a.Ax ? unpack_a(a.Ax[mid], r, a.n0) : make_a(a.rec[a_group(r, a.n0)], r, a.n0);
         BRec y;
         if (a.Bx) {
             y = make_bx(a.Bx[d - 1 - mid]);
@@ -560,7 +577,15 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge(MergeIn<Char
     const int na = int(a1 - a0), nb = int(b1 - b0), nt = int(d1 - d0);
     // Load the tile: all indices first, then all record gathers, so that each
     // thread keeps kMergeItems independent loads in flight.
-    if (a.Bx) {
+    if (a.Bx && a.Ax) {
+        // Both orders arrive with their keys: no gathers at all.
+#pragma unroll
+        for (int k = 0; k < kMergeItems; ++k) {
+            const int sl = int(threadIdx.x) + k * kMergeThreads;
+            if (sl < na) As[sl] = unpack_a(a.Ax[a0 + sl], a.A[a0 + sl], a.n0);
+            else if (sl < nt) Bs[sl - na] = make_bx(a.Bx[b0 + sl - na]);
+        }
+    } else if (a.Bx) {
         // Nonsample records arrive in order: only the samples are gathered.
         int32_t idx[kMergeItems];
 #pragma unroll
@@ -651,10 +676,14 @@ struct NsSmem {
     long long tile;
 };
 
+// Every sample's own merge key is taken from the same gathered record (a B1
+// sample 3x+1 and the nonsample 3x share group x) and written to Ax in
+// sample order, so that the merge reads both orders without gathers.
 __global__ void __launch_bounds__(kSortThreads) k_nonsample_rec(
     const int32_t *__restrict__ SAR, int64_t n02, int64_t n0, const GroupRec<uint8_t> *__restrict__ rec,
-    const uint32_t *__restrict__ offsets, BRec16 *__restrict__ out, uint64_t *__restrict__ lookback,
-    unsigned long long *tile_ctr, unsigned long long tile_base, uint32_t epoch, int *status) {
+    const uint32_t *__restrict__ offsets, BRec16 *__restrict__ out, uint64_t *__restrict__ Ax,
+    uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base, uint32_t epoch,
+    int *status) {
     __shared__ NsSmem S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
@@ -669,13 +698,16 @@ __global__ void __launch_bounds__(kSortThreads) k_nonsample_rec(
         const int64_t idx = wbase + i * 32 + lane;
         const int32_t x = idx < n02 ? SAR[idx] : -1;
         dig[i] = 0x100u;
-        if (x >= 0 && x < n0) {
-            const GroupRec<uint8_t> g = rec[x];
-            v[i].t = x;
-            v[i].c01 = g.c4 & 0xFFFFu;
-            v[i].r1 = g.r1;
-            v[i].r2 = g.r2;
-            dig[i] = g.c4 & 0xFFu;
+        if (x >= 0 && x < n02) {
+            const GroupRec<uint8_t> g = rec[a_group(x, int32_t(n0))];
+            Ax[idx] = pack_a(make_a(g, x, int32_t(n0)));
+            if (x < n0) {
+                v[i].t = x;
+                v[i].c01 = g.c4 & 0xFFFFu;
+                v[i].r1 = g.r1;
+                v[i].r2 = g.r2;
+                dig[i] = g.c4 & 0xFFu;
+            }
         }
     }
     uint32_t *wh = S.warp_hist[warp];
@@ -722,6 +754,87 @@ __global__ void __launch_bounds__(kSortThreads) k_nonsample_rec(
         const BRec16 g = S.rec[i];
         out[S.gbase[g.c01 & 0xFFu] + i] = g;
     }
+}
+
+// ---- the level-0 merge on packed keys
+//
+// With both orders carried in sequence (Ax, Bx) the merge reads no records at
+// random, and its cost is the in-tile merge-path search.  At level 0 every
+// comparison key fits one 64-bit integer: a B1 sample p (and a nonsample, for
+// that comparison) is (t_p << 32 | rank(S_p+1)), a B2 sample p (and a
+// nonsample) is (t_p << 40 | t_p+1 << 32 | rank(S_p+2)); symbols are bytes and
+// ranks fit 31 bits.  A sample's key carries its class in bit 63, a nonsample
+// keeps both keys, and "sample before nonsample" is one integer comparison.
+constexpr uint64_t kClass2 = uint64_t(1) << 63;
+
+__device__ __forceinline__ bool ka_less(uint64_t ka, uint64_t kb1, uint64_t kb2) {
+    return (ka & kClass2) ? (ka & ~kClass2) < kb2 : ka < kb1;
+}
+
+template <int kMergeItems>
+__global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge_packed(MergeIn<uint8_t> a,
+                                                                           const int64_t *__restrict__ split,
+                                                                           int32_t *__restrict__ out, int *status) {
+    constexpr int kMergeThreads = kMergeTile / kMergeItems;
+    __shared__ uint64_t KA[kMergeTile];
+    __shared__ uint64_t KB1[kMergeTile], KB2[kMergeTile];
+    __shared__ int32_t PA[kMergeTile], PB[kMergeTile];
+    const int64_t t = blockIdx.x;
+    const int64_t tot = a.na + a.nb;
+    const int64_t d0 = t * kMergeTile;
+    const int64_t d1 = d0 + kMergeTile < tot ? d0 + kMergeTile : tot;
+    int64_t a0 = split[t], a1 = split[t + 1];
+    const int64_t a0c = min64(max64(a0, max64(0, d0 - a.nb)), min64(d0, a.na));
+    int64_t a1c = min64(max64(a1, max64(0, d1 - a.nb)), min64(d1, a.na));
+    a1c = min64(max64(a1c, a0c), a0c + (d1 - d0));
+    if ((a0c != a0 || a1c != a1) && threadIdx.x == 0) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+    a0 = a0c;
+    a1 = a1c;
+    const int64_t b0 = d0 - a0, b1 = d1 - a1;
+    const int na = int(a1 - a0), nb = int(b1 - b0), nt = int(d1 - d0);
+    for (int sl = threadIdx.x; sl < nt; sl += kMergeThreads) {
+        if (sl < na) {
+            const int32_t r = a.A[a0 + sl];
+            const uint64_t w = a.Ax[a0 + sl];
+            const uint64_t rk = w & 0xFFFFFFFFull, c0 = (w >> 32) & 0xFFu, c1 = (w >> 40) & 0xFFu;
+            if (r < a.n0) {
+                KA[sl] = (c0 << 32) | rk;
+                PA[sl] = 3 * r + 1;
+            } else {
+                KA[sl] = kClass2 | (c0 << 40) | (c1 << 32) | rk;
+                PA[sl] = 3 * (r - a.n0) + 2;
+            }
+        } else {
+            const BRec16 g = a.Bx[b0 + sl - na];
+            const uint64_t c0 = g.c01 & 0xFFu, c1 = (g.c01 >> 8) & 0xFFu;
+            KB1[sl - na] = (c0 << 32) | uint64_t(uint32_t(g.r1));
+            KB2[sl - na] = (c0 << 40) | (c1 << 32) | uint64_t(uint32_t(g.r2));
+            PB[sl - na] = 3 * g.t;
+        }
+    }
+    __syncthreads();
+    const int dl = min(int(threadIdx.x) * kMergeItems, nt);
+    int lo = max(0, dl - nb), hi = min(dl, na);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int j = dl - 1 - mid;
+        if (ka_less(KA[mid], KB1[j], KB2[j])) lo = mid + 1;
+        else hi = mid;
+    }
+    int ia = lo, ib = dl - lo;
+    int32_t o[kMergeItems];
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k) {
+        if (dl + k >= nt) break;
+        const bool take_a = ib >= nb || (ia < na && ka_less(KA[ia], KB1[ib], KB2[ib]));
+        o[k] = take_a ? PA[ia++] : PB[ib++];
+    }
+    __syncthreads();  // the key arrays are dead: reuse PA as the output staging
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k)
+        if (dl + k < nt) PA[dl + k] = o[k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += kMergeThreads) out[d0 + i] = PA[i];
 }
 
 template <typename CharT>
@@ -1620,7 +1733,7 @@ int nonsample_by_sort(Dc3Run &D, const CharT *s, const LevelSizes &z, int bits, 
 // records go to the two adjacent 64-bit buffers.
 template <typename CharT>
 int merge_run(Dc3Run &D, const LevelSizes &z, const GroupRec<CharT> *rec, const int32_t *SAR, const uint32_t *B,
-              const BRec16 *Bx, int32_t *out);
+              const BRec16 *Bx, const uint64_t *Ax, int32_t *out);
 
 // The group records of Step 3 (rank(S_x) from Rl) in t64[1..2].
 template <typename CharT>
@@ -1650,6 +1763,7 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
     if (rc) return rc;
     BRec16 *Bx = (BRec16 *)D.t32[0];
     if (size_t((char *)D.t32[4] - (char *)D.t32[0]) < sizeof(BRec16) * size_t(z.n0)) return LOR_ERR_WORKSPACE;
+    uint64_t *Ax = D.t64[0];  // 8 bytes per sample, in sample order
     LOR_CUDA_TRY(cudaMemsetAsync(D.rs.hist, 0, sizeof(uint32_t) * kRadix, st));
     {
         ProfScope ps(PK_NONSAMPLE, double(z.n0), st);
@@ -1663,13 +1777,13 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
         const int64_t ntiles = cdiv(z.n02, kNsTile);
         if (ntiles > D.rs.max_tiles) return LOR_ERR_WORKSPACE;
         D.rs.epoch++;
-        k_nonsample_rec<<<unsigned(ntiles), kSortThreads, 0, st>>>(SAR, z.n02, z.n0, rec, D.rs.offsets, Bx,
+        k_nonsample_rec<<<unsigned(ntiles), kSortThreads, 0, st>>>(SAR, z.n02, z.n0, rec, D.rs.offsets, Bx, Ax,
                                                                    D.rs.lookback, D.rs.tile_ctr, D.rs.tile_base,
                                                                    D.rs.epoch, D.status);
         LOR_LAUNCH_CHECK();
         D.rs.tile_base += (unsigned long long)ntiles;
     }
-    return merge_run<uint8_t>(D, z, rec, SAR, nullptr, Bx, out);
+    return merge_run<uint8_t>(D, z, rec, SAR, nullptr, Bx, Ax, out);
 }
 
 template <typename CharT>
@@ -1678,12 +1792,12 @@ int merge_level(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t *R
     GroupRec<CharT> *rec;
     const int rc = build_records<CharT>(D, s, z, Rl, &rec);
     if (rc) return rc;
-    return merge_run<CharT>(D, z, rec, SAR, B, nullptr, out);
+    return merge_run<CharT>(D, z, rec, SAR, B, nullptr, nullptr, out);
 }
 
 template <typename CharT>
 int merge_run(Dc3Run &D, const LevelSizes &z, const GroupRec<CharT> *rec, const int32_t *SAR, const uint32_t *B,
-              const BRec16 *Bx, int32_t *out) {
+              const BRec16 *Bx, const uint64_t *Ax, int32_t *out) {
     cudaStream_t st = D.s;
     const int64_t n = z.n;
     MergeIn<CharT> a;
@@ -1695,13 +1809,29 @@ int merge_run(Dc3Run &D, const LevelSizes &z, const GroupRec<CharT> *rec, const 
     a.B = B;
     a.nb = z.n0;
     a.Bx = Bx;
+    a.Ax = Ax ? Ax + dummy : nullptr;
     const int64_t ntiles = cdiv(n, kMergeTile);
     int64_t *split = (int64_t *)(D.ws + D.L.split);
     {
         ProfScope ps(PK_MERGE, double(n) * (4 + 4 + sizeof(GroupRec<CharT>)), st);
         k_merge_partition<CharT><<<grid_for(ntiles + 1, 128), 128, 0, st>>>(a, ntiles, split);
         LOR_LAUNCH_CHECK();
-        if (tune_config().merge_items == 4)
+        const int mi = tune_config().merge_items;
+        if constexpr (sizeof(CharT) == 1) {
+            if (Ax && Bx) {
+                if (mi == 8)
+                    k_merge_packed<8><<<unsigned(ntiles), kMergeTile / 8, 0, st>>>(a, split, out, D.status);
+                else if (mi == 4)
+                    k_merge_packed<4><<<unsigned(ntiles), kMergeTile / 4, 0, st>>>(a, split, out, D.status);
+                else
+                    k_merge_packed<2><<<unsigned(ntiles), kMergeTile / 2, 0, st>>>(a, split, out, D.status);
+                LOR_LAUNCH_CHECK();
+                return LOR_OK;
+            }
+        }
+        if (mi == 8)
+            k_merge<CharT, 8><<<unsigned(ntiles), kMergeTile / 8, 0, st>>>(a, split, out, D.status);
+        else if (mi == 4)
             k_merge<CharT, 4><<<unsigned(ntiles), kMergeTile / 4, 0, st>>>(a, split, out, D.status);
         else
             k_merge<CharT, 2><<<unsigned(ntiles), kMergeTile / 2, 0, st>>>(a, split, out, D.status);

@@ -13,7 +13,7 @@
 // floor(log2(r2 - r1)).
 #include <climits>
 
-#include "common.cuh"
+#include "rmq_block.cuh"
 
 LOR_DEFINE_TU_STATUS(lor_status_rmq)
 
@@ -166,9 +166,6 @@ __global__ void k_rmq_query(const int32_t *__restrict__ table, int64_t stride,
 // ends, read from the LCP array itself, and of the whole blocks between them,
 // read from two windows of the block table.
 
-constexpr int kRmqBlock = 32;
-
-int64_t rmqb_blocks(int64_t n) { return cdiv(n, kRmqBlock); }
 
 // bm[b] = min(lcp[32b .. min(32b + 32, n) - 1]): one warp per block.
 __global__ void k_rmqb_blockmin(const int32_t *__restrict__ lcp, int64_t n, int64_t nb, int32_t *__restrict__ bm) {
@@ -182,12 +179,6 @@ __global__ void k_rmqb_blockmin(const int32_t *__restrict__ lcp, int64_t n, int6
     }
 }
 
-// min(lcp[a .. b]) for a <= b inside one block.
-__device__ __forceinline__ int32_t rmqb_scan(const int32_t *__restrict__ lcp, int64_t a, int64_t b) {
-    int32_t m = lcp[a];
-    for (int64_t i = a + 1; i <= b; ++i) m = min(m, lcp[i]);
-    return m;
-}
 
 __global__ void k_rmqb_query(const int32_t *__restrict__ table, int64_t stride, const int32_t *__restrict__ lcp,
                              const int32_t *__restrict__ isa, int64_t n, const int32_t *__restrict__ P,
@@ -215,21 +206,84 @@ __global__ void k_rmqb_query(const int32_t *__restrict__ table, int64_t stride, 
         r1 = r2;
         r2 = tmp;
     }
-    const int64_t a = int64_t(r1) + 1, b = r2;  // minimum of lcp[a .. b]
+    out[i] = rmqb_range_min(table, stride, lcp, int64_t(r1) + 1, r2);
+}
+
+// First index in [a, b] (one block) holding the value v, or -1.
+__device__ __forceinline__ int64_t rmqb_first(const int32_t *__restrict__ lcp, int64_t a, int64_t b, int32_t v) {
+    for (int64_t i = a; i <= b; ++i)
+        if (lcp[i] == v) return i;
+    return -1;
+}
+
+// The leftmost minimum of lcp(r1, r2] (Section 3: the RMQ returns the index
+// of the minimum; the leftmost one when it repeats) and its value.  After the
+// value m is known, the partial block at the left end is scanned first; then
+// the leftmost whole block whose minimum is m is found by binary lifting over
+// the table rows (skip every power-of-two window, largest first, whose
+// minimum exceeds m) and scanned; last the partial block at the right end.
+__global__ void k_rmqb_argmin(const int32_t *__restrict__ table, int64_t stride, const int32_t *__restrict__ lcp,
+                              const int32_t *__restrict__ isa, int64_t n, const int32_t *__restrict__ P,
+                              const int32_t *__restrict__ Q, int64_t nq, int32_t *__restrict__ val,
+                              int32_t *__restrict__ arg, int *status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const int32_t p = P[i], q = Q[i];
+    if (p < 0 || p >= n || q < 0 || q >= n) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        val[i] = -1;
+        arg[i] = -1;
+        return;
+    }
+    if (p == q) {
+        val[i] = int32_t(n - p);
+        arg[i] = -1;
+        return;
+    }
+    int32_t r1 = isa[p], r2 = isa[q];
+    if (r1 < 0 || r1 >= n || r2 < 0 || r2 >= n || r1 == r2) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        val[i] = -1;
+        arg[i] = -1;
+        return;
+    }
+    if (r1 > r2) {
+        const int32_t tmp = r1;
+        r1 = r2;
+        r2 = tmp;
+    }
+    const int64_t a = int64_t(r1) + 1, b = r2;
     const int64_t ba = a / kRmqBlock, bb = b / kRmqBlock;
     int32_t m;
+    int64_t k;
     if (ba == bb) {
         m = rmqb_scan(lcp, a, b);
+        k = rmqb_first(lcp, a, b, m);
     } else {
-        m = min(rmqb_scan(lcp, a, ba * kRmqBlock + kRmqBlock - 1), rmqb_scan(lcp, bb * kRmqBlock, b));
-        const int64_t len = bb - ba - 1;  // whole blocks ba+1 .. bb-1
-        if (len > 0) {
-            const int j = 63 - __clzll(len);
+        const int64_t aend = ba * kRmqBlock + kRmqBlock - 1, bbeg = bb * kRmqBlock;
+        const int32_t ma = rmqb_scan(lcp, a, aend), mb = rmqb_scan(lcp, bbeg, b);
+        m = min(ma, mb);
+        const int64_t lo = ba + 1, hi = bb - 1;  // whole blocks
+        int32_t mw = INT_MAX;
+        if (hi >= lo) {
+            const int j = 63 - __clzll(hi - lo + 1);
             const int32_t *lv = table + int64_t(j) * stride;
-            m = min(m, min(lv[ba + 1], lv[bb - (int64_t(1) << j)]));
+            mw = min(lv[lo], lv[hi - (int64_t(1) << j) + 1]);
+            m = min(m, mw);
+        }
+        if (ma == m) {
+            k = rmqb_first(lcp, a, aend, m);
+        } else if (mw == m) {
+            int64_t pos = lo;
+            for (int j = 63 - __clzll(hi - lo + 1); j >= 0; --j)
+                if (pos + (int64_t(1) << j) - 1 <= hi && table[int64_t(j) * stride + pos] > m) pos += int64_t(1) << j;
+            k = rmqb_first(lcp, pos * kRmqBlock, min64(pos * kRmqBlock + kRmqBlock - 1, n - 1), m);
+        } else {
+            k = rmqb_first(lcp, bbeg, b, m);
         }
     }
-    out[i] = m;
+    val[i] = m;
+    arg[i] = int32_t(k);
 }
 
 }  // namespace
@@ -237,19 +291,34 @@ __global__ void k_rmqb_query(const int32_t *__restrict__ table, int64_t stride, 
 
 using namespace lor;
 
+extern "C" int lor_rmq_block_argmin(const int32_t *d_table, const int32_t *d_lcp, const int32_t *d_isa, int64_t n,
+                                    const int32_t *d_p, const int32_t *d_q, int64_t nq, int32_t *d_val,
+                                    int32_t *d_arg, lor_stream_t stream) {
+    if (!d_table || !d_lcp || !d_isa || n < 1 || nq < 0) return LOR_ERR_INVALID_ARG;
+    if (nq == 0) return LOR_OK;
+    if (!d_p || !d_q || !d_val || !d_arg) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *status = tu_status_ptr();
+    if (!status) return LOR_ERR_CUDA;
+    {
+        ProfScope ps(PK_RMQ_QUERY, double(nq) * (4 * 10), s);
+        k_rmqb_argmin<<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(d_table, row_stride(rmqb_blocks(n)), d_lcp, d_isa, n,
+                                                              d_p, d_q, nq, d_val, d_arg, status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
 extern "C" int64_t lor_rmq_block_table_elems(int64_t n) {
     if (n < 1 || n > LOR_MAX_N) return 0;
     const int64_t nb = rmqb_blocks(n);
     return int64_t(levels_for(nb)) * row_stride(nb);
 }
 
-extern "C" int lor_rmq_block_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
-                                   lor_stream_t stream) {
-    if (!d_lcp || !d_table || n < 1) return LOR_ERR_INVALID_ARG;
-    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
-    if (table_elems < lor_rmq_block_table_elems(n)) return LOR_ERR_WORKSPACE;
-    if (uintptr_t(d_table) & 255) return LOR_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+int64_t lor::rmq_row_stride_of(int64_t m) { return row_stride(m); }
+
+int lor::rmq_block_levels(const int32_t *d_lcp, int64_t n, int levels, int32_t *d_table, cudaStream_t s) {
     const int64_t nb = rmqb_blocks(n);
     {
         ProfScope ps(PK_RMQ_LEVEL, double(n) * 4 + double(nb) * 4, s);
@@ -258,7 +327,16 @@ extern "C" int lor_rmq_block_build(const int32_t *d_lcp, int64_t n, int32_t *d_t
     }
     LOR_LAUNCH_CHECK();
     // row 0 now holds the block minima: the rows above are its sparse table
-    return rmq_build_levels(d_table, nb, levels_for(nb), d_table, s);
+    return rmq_build_levels(d_table, nb, levels, d_table, s);
+}
+
+extern "C" int lor_rmq_block_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
+                                   lor_stream_t stream) {
+    if (!d_lcp || !d_table || n < 1) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    if (table_elems < lor_rmq_block_table_elems(n)) return LOR_ERR_WORKSPACE;
+    if (uintptr_t(d_table) & 255) return LOR_ERR_INVALID_ARG;
+    return rmq_block_levels(d_lcp, n, levels_for(rmqb_blocks(n)), d_table, (cudaStream_t)stream);
 }
 
 extern "C" int lor_rmq_block_query(const int32_t *d_table, const int32_t *d_lcp, const int32_t *d_isa, int64_t n,

@@ -1,16 +1,17 @@
 // serve.cu -- request server over the grouped pipeline: pair requests arrive
 // one at a time, free workers take the oldest waiting requests as one batch
 // when the batch fits in the server's device reservation, and each request
-// keeps its batch's ISA and a sparse table over the batch's LCP array on the
-// device for LCP queries between arbitrary suffixes of its own text (Section
-// 3: the LCP of two suffixes is the minimum of the adjacent LCPs between
-// their ranks).
+// keeps its batch's ISA, LCP array and a linear-space (block) RMQ table over
+// that LCP array on the device for LCP queries between arbitrary suffixes of
+// its own text (Section 3: the LCP of two suffixes is the minimum of the
+// adjacent LCPs between their ranks).
 //
 // Memory: one cudaMalloc of the whole budget at creation, managed by a
 // first-fit allocator in 1 MiB granules.  A batch takes two blocks: its
 // workspace (grouped-pipeline workspace, ASCII input, records, offsets and
 // positions), returned as soon as the batch's results are on the host, and
-// its resident state (ISA + sparse table), returned when the last of its
+// its resident state (ISA + LCP + block table, about 10.6 bytes per symbol
+// where a full sparse table would need 4 + 4 * log2(n)), returned when the last of its
 // requests is released.  A worker that cannot place the oldest waiting batch
 // waits for memory to come back; requests are admitted in arrival order.
 //
@@ -18,10 +19,11 @@
 // suffix array is the suffix array of pair p's own text (see batch.cu), so
 // ranks inside the block, the block's LCP values and the overlap record are
 // those of the pair alone.  A query (p, q) of pair p reads ranks inside block
-// p only: both ISA entries lie in the block and every window of the range
-// (r1, r2] lies inside it, so the sparse-table rows need only
-// floor(log2(longest pair text)) + 1 levels and rows that span two blocks are
-// never read.
+// p only: both ISA entries lie in the block, the partial 32-entry blocks at
+// the ends of the range (r1, r2] are scanned inside it, and every window of
+// whole blocks between them lies inside it, so the table rows need only
+// bit_width(longest pair text / 32) levels and entries that span two pairs
+// are never read.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -34,6 +36,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "rmq_block.cuh"
 
 LOR_DEFINE_TU_STATUS(lor_status_serve)
 
@@ -96,14 +99,15 @@ class Arena {
 };
 
 // Byte plan of one batch: workspace block [grouped workspace | ASCII |
-// records | position offsets | positions] and resident block [ISA | table].
+// records | position offsets | positions] and resident block [ISA | LCP |
+// block table].
 struct BatchPlan {
     BatchLayout L;
     int np = 0;
     int64_t n = 0, in_bytes = 0, stride = 0;
     int levels = 0;
     size_t o_ascii = 0, o_out = 0, o_off = 0, o_pos = 0, work = 0;
-    size_t o_table = 0, resident = 0;
+    size_t o_lcp = 0, o_table = 0, resident = 0;
 };
 
 BatchPlan plan_batch(const int64_t *lens, int np) {
@@ -128,16 +132,18 @@ BatchPlan plan_batch(const int64_t *lens, int np) {
     P.o_off = take(sizeof(int64_t) * size_t(np + 1));
     P.o_pos = take(sizeof(int32_t) * size_t(P.n));  // positions never exceed n
     P.work = off;
-    P.levels = bit_width_u64(uint64_t(pmax));
-    P.stride = (P.n + 63) & ~int64_t(63);
-    P.o_table = align256(sizeof(int32_t) * size_t(P.n));
+    // whole blocks inside one pair's rank range: at most pmax / 32
+    P.levels = bit_width_u64(uint64_t(pmax / kRmqBlock > 0 ? pmax / kRmqBlock : 1));
+    P.stride = rmq_row_stride_of(rmqb_blocks(P.n));
+    P.o_lcp = align256(sizeof(int32_t) * size_t(P.n));
+    P.o_table = P.o_lcp + align256(sizeof(int32_t) * size_t(P.n));
     P.resident = P.o_table + sizeof(int32_t) * size_t(P.levels) * size_t(P.stride);
     return P;
 }
 
 struct Resident {
     size_t off = 0, bytes = 0;
-    int32_t *isa = nullptr, *table = nullptr;
+    int32_t *isa = nullptr, *lcp = nullptr, *table = nullptr;
     int64_t stride = 0;
     int live = 0;  // requests of the batch not yet released
 };
@@ -158,9 +164,11 @@ struct Request {
 };
 
 // out[i] = LCP of suffixes P[i], Q[i] of the pair text at [off, off + len) of
-// a batch text, from the batch ISA and sparse table (host-validated queries).
+// a batch text, from the batch ISA, LCP and block table (host-validated
+// queries).
 __global__ void k_serve_query(const int32_t *__restrict__ table, int64_t stride, const int32_t *__restrict__ isa,
-                              int64_t off, int64_t len, const int32_t *__restrict__ P,
+                              const int32_t *__restrict__ lcp, int64_t off, int64_t len,
+                              const int32_t *__restrict__ P,
                               const int32_t *__restrict__ Q, int nq, int32_t *__restrict__ out, int *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nq) return;
@@ -185,9 +193,7 @@ __global__ void k_serve_query(const int32_t *__restrict__ table, int64_t stride,
         out[i] = -1;
         return;
     }
-    const int j = 63 - __clzll(r2 - r1);
-    const int32_t *lv = table + int64_t(j) * stride;
-    out[i] = min(lv[r1 + 1], lv[r2 - (int64_t(1) << j) + 1]);
+    out[i] = rmqb_range_min(table, stride, lcp, r1 + 1, r2);
 }
 
 }  // namespace
@@ -276,7 +282,9 @@ int run_batch(lor_server *S, const std::vector<Request *> &batch, const BatchPla
     if (rc) return rc;
     LOR_CUDA_TRY(cudaMemcpyAsync(res->isa, wsb + P.L.isa, sizeof(int32_t) * size_t(P.n),
                                  cudaMemcpyDeviceToDevice, s));
-    rc = rmq_build_levels((const int32_t *)(wsb + P.L.lcp), P.n, P.levels, res->table, s);
+    LOR_CUDA_TRY(cudaMemcpyAsync(res->lcp, wsb + P.L.lcp, sizeof(int32_t) * size_t(P.n),
+                                 cudaMemcpyDeviceToDevice, s));
+    rc = rmq_block_levels(res->lcp, P.n, P.levels, res->table, s);
     if (rc) return rc;
     outs->resize(np);
     offs->resize(np + 1);
@@ -341,6 +349,7 @@ void worker_main(lor_server *S) {
         res->off = off_r;
         res->bytes = P.resident;
         res->isa = (int32_t *)(S->base + off_r);
+        res->lcp = (int32_t *)(S->base + off_r + P.o_lcp);
         res->table = (int32_t *)(S->base + off_r + P.o_table);
         res->stride = P.stride;
         res->live = P.np;
@@ -506,7 +515,7 @@ extern "C" int lor_server_query(lor_server *S, int64_t id, const int32_t *h_p, c
         memcpy(S->hq, h_p + b, sizeof(int32_t) * c);
         memcpy(S->hq + kQueryCap, h_q + b, sizeof(int32_t) * c);
         LOR_CUDA_TRY(cudaMemcpyAsync(S->dq, S->hq, sizeof(int32_t) * 2 * kQueryCap, cudaMemcpyHostToDevice, S->qs));
-        k_serve_query<<<unsigned(cdiv(c, 128)), 128, 0, S->qs>>>(res->table, res->stride, res->isa, off, len, S->dq,
+        k_serve_query<<<unsigned(cdiv(c, 128)), 128, 0, S->qs>>>(res->table, res->stride, res->isa, res->lcp, off, len, S->dq,
                                                                  S->dq + kQueryCap, c, S->dq + 2 * kQueryCap,
                                                                  status);
         LOR_LAUNCH_CHECK();

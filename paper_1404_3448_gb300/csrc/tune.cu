@@ -59,7 +59,7 @@ extern "C" int lor_autotune_batch(const uint8_t *d_ascii, const int64_t *h_lens,
         {&lor_tune::digit_bits, {6, 7, 8}},
         {&lor_tune::sort_items_64, {8, 12}},
         {&lor_tune::sort_items_32, {12, 16}},
-        {&lor_tune::merge_items, {2, 4}},
+        {&lor_tune::merge_items, {2, 4, 8}},
     };
     for (const Knob &k : knobs) {
         for (int32_t v : k.values) {

@@ -81,6 +81,7 @@ def load():
         "lor_rmq_block_table_elems": ([i64], i64),
         "lor_rmq_block_build": ([vp, i64, vp, i64, vp], ctypes.c_int),
         "lor_rmq_block_query": ([vp, vp, vp, i64, vp, vp, i64, vp, vp], ctypes.c_int),
+        "lor_rmq_block_argmin": ([vp, vp, vp, i64, vp, vp, i64, vp, vp, vp], ctypes.c_int),
         "lor_radix_sort_workspace_size": ([i64], sz),
         "lor_radix_sort_pairs": ([vp, vp, i64, i32, vp, sz, vp], ctypes.c_int),
         "lor_device_status": ([vp], ctypes.c_int),
@@ -618,6 +619,17 @@ def rmq_block_query(table, lcp_arr, isa, p, q, out=None, stream=None) -> torch.T
                                       _ptr(q, torch.int32, "q"), p.numel(), _ptr(out, torch.int32, "out"),
                                       _stream(stream)), "lor_rmq_block_query")
     return out
+
+
+def rmq_block_argmin(table, lcp_arr, isa, p, q, stream=None):
+    """(value, leftmost rank of the minimum) per suffix pair (lor_rmq_block_argmin)."""
+    val = torch.empty_like(p)
+    arg = torch.empty_like(p)
+    _check(load().lor_rmq_block_argmin(_ptr(table, torch.int32, "table"), _ptr(lcp_arr, torch.int32, "lcp"),
+                                       _ptr(isa, torch.int32, "isa"), isa.numel(), _ptr(p, torch.int32, "p"),
+                                       _ptr(q, torch.int32, "q"), p.numel(), _ptr(val, torch.int32, "val"),
+                                       _ptr(arg, torch.int32, "arg"), _stream(stream)), "lor_rmq_block_argmin")
+    return val, arg
 
 
 def rmq_query(table, isa, p, q, out=None, stream=None) -> torch.Tensor:

@@ -110,9 +110,12 @@ def test_server_batch_bytes_host_only(lib):
     work1, res1 = L.server_batch_bytes([1000, 2000])
     assert work1 > 0 and res1 > 0
     # one pair: workspace covers the grouped pipeline (text 3002 symbols) plus
-    # input, records and positions; resident = ISA + 12 table rows (3002 < 2^12)
+    # input, records and positions; resident = ISA + LCP + the block table over
+    # ceil(3002 / 32) = 94 block minima, with bit_width(3002 // 32) = 7 rows of
+    # 128 entries (linear space, far below a full sparse table's 12 rows of n)
     n = 3002
-    assert res1 >= 4 * n + 4 * 12 * n
+    assert res1 >= 4 * n + 4 * n + 4 * 7 * 128
+    assert res1 < 4 * n + 4 * 12 * n
     assert work1 >= L.lor_batch_workspace_size(np.array([1000, 2000], np.int64).ctypes.data, 1)
     work2, res2 = L.server_batch_bytes([1000, 2000, 5, 7])
     assert work2 >= work1 and res2 >= res1
@@ -167,13 +170,13 @@ def test_tune_configuration_round_trip_and_range_checks(lib):
     import paper_1404_3448_gb300 as P
     d = P.tune_default()
     assert d == {"digit_bits": 8, "level0_key_bits": 48, "sort_items_64": 12, "sort_items_32": 16,
-                 "merge_items": 2}
+                 "merge_items": 4}
     try:
-        assert P.tune_set(digit_bits=6, merge_items=4)["digit_bits"] == 6
-        assert P.tune_get()["merge_items"] == 4
+        assert P.tune_set(digit_bits=6, merge_items=8)["digit_bits"] == 6
+        assert P.tune_get()["merge_items"] == 8
         for bad in [dict(digit_bits=4), dict(digit_bits=9), dict(level0_key_bits=23),
                     dict(level0_key_bits=61), dict(sort_items_64=16), dict(sort_items_32=8),
-                    dict(merge_items=3)]:
+                    dict(merge_items=3), dict(merge_items=16)]:
             before = P.tune_get()
             with pytest.raises(L.LorError):
                 P.tune_set(**bad)

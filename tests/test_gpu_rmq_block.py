@@ -43,12 +43,21 @@ def run_case(L, O, seqs, nq, seed, all_pairs=False):
         p, q = pp.ravel().copy(), qq.ravel().copy()
     else:
         p, q = gen.random_queries(n, count=nq, seed=seed)
-    ans = L.rmq_block_query(table, lcp, isa, torch.from_numpy(p).cuda(), torch.from_numpy(q).cuda())
+    pd, qd = torch.from_numpy(p).cuda(), torch.from_numpy(q).cuda()
+    ans = L.rmq_block_query(table, lcp, isa, pd, qd)
+    val, arg = L.rmq_block_argmin(table, lcp, isa, pd, qd)
     L.check_device(where="block rmq")
-    lcp_o = O.lcp_array(text, O.suffix_array(text))
+    sa_o = O.suffix_array(text)
+    lcp_o = O.lcp_array(text, sa_o)
     np.testing.assert_array_equal(lcp.cpu().numpy(), lcp_o)
     np.testing.assert_array_equal(block_view(C, table, n).cpu().numpy(), O.block_sparse_table(lcp_o))
-    np.testing.assert_array_equal(ans.cpu().numpy(), O.lcp_pairs(text, p, q))
+    exp = O.lcp_pairs(text, p, q)
+    np.testing.assert_array_equal(ans.cpu().numpy(), exp)
+    np.testing.assert_array_equal(val.cpu().numpy(), exp)
+    k = min(p.size, 20_000)  # the argmin oracle runs one query at a time
+    ev, ea = O.rmq_argmin(lcp_o, O.inverse_suffix_array(sa_o), p[:k], q[:k])
+    np.testing.assert_array_equal(val.cpu().numpy()[:k], ev)
+    np.testing.assert_array_equal(arg.cpu().numpy()[:k], ea)
 
 
 @pytest.mark.parametrize("total", [1, 2, 30, 31, 32, 33, 63, 64, 65, 95, 1000, 4097])

@@ -231,6 +231,32 @@ def test_block_table_windows_are_ranges_of_the_lcp_array(oracle_mod):
             assert m == lcp[a:e + 1].min()
 
 
+def test_rmq_argmin_is_the_leftmost_minimum_and_the_suffix_lcp(oracle_mod):
+    """The index form of the RMQ: the value is the LCP of the two suffixes by
+    direct comparison (Section 3's identity), and the index is the first rank
+    of the range that holds it."""
+    rng = np.random.default_rng(11)
+    for alpha in [b"AC", b"A", b"ACGT"]:
+        a = np.frombuffer(alpha, np.uint8)
+        seqs = [a[rng.integers(0, a.size, 40)], a[rng.integers(0, a.size, 25)]]
+        text, _, _ = oracle_mod.encode_concat(seqs)
+        n = text.size
+        sa = oracle_mod.suffix_array(text)
+        lcp = oracle_mod.lcp_array(text, sa)
+        isa = oracle_mod.inverse_suffix_array(sa)
+        pp, qq = np.meshgrid(np.arange(n, dtype=np.int32), np.arange(n, dtype=np.int32))
+        p, q = pp.ravel(), qq.ravel()
+        val, arg = oracle_mod.rmq_argmin(lcp, isa, p, q)
+        np.testing.assert_array_equal(val, oracle_mod.lcp_pairs(text, p, q))
+        for i in range(p.size):
+            if p[i] == q[i]:
+                assert arg[i] == -1
+                continue
+            r1, r2 = sorted((isa[p[i]], isa[q[i]]))
+            assert r1 < arg[i] <= r2 and lcp[arg[i]] == val[i]
+            assert (lcp[r1 + 1:arg[i]] > val[i]).all()
+
+
 # ---------------------------------------------------------------- LCS DP pins
 
 def _brute_lcs(a: bytes, b: bytes):
