@@ -387,6 +387,50 @@ def batch_vs_plain(npairs, steps, warmup, dev, seed=140434484):
     }
 
 
+# --------------------------------------------------------------------------- multi-query
+
+def multi_query_run(nq, steps, warmup, dev, ref_len=1 << 24, seed=140434487):
+    """One noncoding-like reference of ref_len bases against nq queries
+    (log-uniform lengths in [100, 10,000]; half reads of the reference with
+    substitutions) through lor_multi_query_overlap: one suffix array over the
+    reference and all queries."""
+    import torch
+    import lor_inputs as gen
+    import paper_1404_3448_gb300 as lor
+    ref, qs = gen.multi_query(ref_len=ref_len, nq=nq, seed=seed)
+    lens = [len(q) for q in qs]
+    qbases = int(sum(lens))
+    ref_dev = torch.from_numpy(ref).to(dev)
+    q_dev = torch.from_numpy(np.concatenate(qs)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((nq, 4), dtype=torch.int32, device=dev)
+    need = lor.lor.load().lor_multi_query_workspace_size(ref.size, np.asarray(lens, np.int64).ctypes.data, nq)
+    ws = lor.workspace(need, dev)
+    for _ in range(warmup):
+        lor.multi_query_overlap(ref_dev, q_dev, lens, out=out, ws=ws)
+    torch.cuda.synchronize(dev)
+    lor.check_device(where="multi query warmup")
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for i in range(steps):
+        lor.multi_query_overlap(ref_dev, q_dev, lens, out=out, ws=ws)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = evs[0].elapsed_time(evs[-1]) / steps
+    found = out[:, 0].cpu().numpy()
+    del ws
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"one {ref_len}-base noncoding-like reference against {nq} queries (log-uniform lengths "
+                    f"in [100, 10000], half reads of the reference with 1-5 % substitutions, half background "
+                    f"with one planted 20-200-base piece); {qbases} query bases",
+        "queries": nq, "query_bases": qbases, "ms_per_step": ms,
+        "value": (qbases + ref_len) / (ms / 1000.0), "unit": UNIT,
+        "queries_per_s": nq / (ms / 1000.0),
+        "median_match_length": float(np.median(found)),
+    }
+
+
 # --------------------------------------------------------------------------- served
 
 def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed=140434485):
@@ -664,6 +708,9 @@ def run_lor(args):
             del pipe
             torch.cuda.empty_cache()
             line["batch_vs_plain"] = batch_vs_plain(args.batch_pairs, 3, 1, dev)
+        if args.multi_queries > 0:
+            torch.cuda.empty_cache()
+            line["multi_query"] = multi_query_run(args.multi_queries, 3, 1, dev)
         if args.serve_seconds > 0:
             torch.cuda.empty_cache()
             line["serving"] = serving(args.serve_seconds, args.serve_rate, args.serve_pool, args.serve_workers,
@@ -685,6 +732,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=4096,
                     help="pairs of the batched-vs-plain sub-measurement (0 skips it)")
+    ap.add_argument("--multi-queries", type=int, default=65_536,
+                    help="queries of the one-reference-many-queries sub-measurement (0 skips it)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson arrivals of the served sub-measurement (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="pair requests per second")

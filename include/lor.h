@@ -255,6 +255,38 @@ int lor_rmq_block_argmin(const int32_t *d_table, const int32_t *d_lcp, const int
                          lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * One reference against many query sequences (the paper's experiments take
+ * 512 .. 2,097,152 query sequences against a reference; Section 3 defines
+ * the overlap through common prefixes of suffixes).
+ *
+ * For each query Q_i: the longest substring it shares with the reference R
+ * (length), the smallest offset in Q_i where a substring of that length
+ * shared with R starts (query_pos), and the smallest offset in R where
+ * Q_i[query_pos, query_pos + length) occurs (ref_pos).  length 0 (no common
+ * base, or an empty sequence) gives query_pos = ref_pos = -1.
+ * d_ref: ASCII ACGT/acgt, ref_len bytes (device).  d_queries: the queries'
+ * ASCII bases back to back (device), lengths h_q_lens[0 .. nq) (host).
+ * d_out: device lor_mq_hit[nq].  d_ws: lor_multi_query_workspace_size bytes,
+ * 256-byte aligned.  One suffix array is built over R 1 Q_1 2 Q_2 2 ...
+ * (code 1 ends the reference, code 2 every query), so the work is that of
+ * one text of ref_len + sum(lengths) + nq + 1 symbols, not one per query.
+ * nq <= LOR_MQ_MAX_QUERIES and the text at most LOR_MAX_N symbols, else
+ * LOR_ERR_TOO_LARGE.  A symbol outside ACGT/acgt sets LOR_ERR_BAD_SYMBOL in
+ * the status word.
+ * ------------------------------------------------------------------------- */
+#define LOR_MQ_MAX_QUERIES 4194304
+typedef struct {
+    int32_t length;
+    int32_t query_pos;
+    int32_t ref_pos;
+    int32_t reserved;
+} lor_mq_hit;
+size_t lor_multi_query_workspace_size(int64_t ref_len, const int64_t *h_q_lens, int32_t nq);
+int lor_multi_query_overlap(const uint8_t *d_ref, int64_t ref_len, const uint8_t *d_queries,
+                            const int64_t *h_q_lens, int32_t nq, lor_mq_hit *d_out, void *d_ws,
+                            size_t ws_bytes, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Launch parameters and their autotuner (no counterpart in the paper).
  *
  * Every value gives the same results; only the speed differs.  The

@@ -14,6 +14,8 @@ for them with the shapes the workloads name:
   10-20 % point mutation, ~3 % microsatellites (period 1-6, 10-60 copies),
   and one shared 10 kb region with 1 % mutations around an exact 2 kb core;
 * ``pair_batch``       -- many pairs of uneven, log-uniform length;
+* ``multi_query``      -- one reference and many query sequences (reads of
+  the reference with substitutions, and background with a planted piece);
 * ``random_queries``   -- uniform (p, q) suffix pairs for LCP queries;
 * ``poisson_arrivals`` -- request arrival times of a Poisson process, and
   ``request_stream``   -- which pool pair each arrival asks for and its
@@ -157,6 +159,32 @@ def pair_batch(npairs=4096, lo=1_000, hi=1_000_000, seed=SEED_BASE + 4):
         s2, _ = noncoding_sequence(rng, l2, consensi, shared, core=plen)
         pairs.append([s1, s2])
     return pairs
+
+
+def multi_query(ref_len=1 << 24, nq=65_536, lo=100, hi=10_000, seed=SEED_BASE + 7):
+    """One noncoding-like reference and ``nq`` query sequences of log-uniform
+    length in [lo, hi]: every second query is a copy of a random reference
+    window with 1-5 % substitutions (a read of the reference), the others are
+    noncoding-like background with one planted exact reference piece of
+    20-200 bases (clamped to the query).  Returns (ref, [queries])."""
+    rng = _rng(seed)
+    consensi = [random_bases(rng, 300) for _ in range(5)]
+    ref, _ = noncoding_sequence(rng, ref_len, consensi, random_bases(rng, 0), 0)
+    qs = []
+    for i in range(nq):
+        L = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        L = min(L, ref_len) if ref_len else L
+        if i % 2 == 0 and ref_len >= L > 0:
+            off = int(rng.integers(0, ref_len - L + 1))
+            qs.append(mutate(rng, ref[off:off + L], float(rng.uniform(0.01, 0.05))))
+        else:
+            q, _ = noncoding_sequence(rng, L, consensi, random_bases(rng, 0), 0)
+            plen = min(int(rng.integers(20, 201)), L, ref_len)
+            if plen > 0:
+                off = int(rng.integers(0, ref_len - plen + 1))
+                _plant(rng, q, ref[off:off + plen].copy())
+            qs.append(q)
+    return ref, qs
 
 
 def poisson_arrivals(rate, seconds, seed=SEED_BASE + 5):

@@ -79,6 +79,8 @@ def _load():
             lib.oracle_lcp_pairs.restype = ctypes.c_int
             lib.oracle_lcs_dp.argtypes = [u8p, i64, u8p, i64, u8p, u8p]
             lib.oracle_lcs_dp.restype = ctypes.c_int64
+            lib.oracle_multi_query_one.argtypes = [u8p, i64, i32p, u8p, i64, ctypes.c_void_p]
+            lib.oracle_multi_query_one.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -358,6 +360,25 @@ def rmq_argmin(lcp, isa, p, q):
         j = int(np.argmin(w))  # first occurrence of the minimum
         val[i], arg[i] = w[j], r1 + 1 + j
     return val, arg
+
+
+def multi_query(ref, queries):
+    """One reference against many queries (uppercase ASCII): per query (L, q, r) with L the
+    length of the longest substring it shares with the reference, q the
+    smallest query offset where a length-L shared substring starts and r the
+    smallest reference offset of that substring ((0, -1, -1) when L = 0).
+    Works on the ASCII bases; the reference's suffixes are sorted once
+    (plain merge sort) and every query suffix is matched by binary search
+    with direct comparison."""
+    r = _u8(ref)
+    sa_r = suffix_array(r) if r.size else np.zeros(0, np.int32)
+    out = np.empty((len(queries), 3), dtype=np.int64)
+    res = np.empty(3, dtype=np.int64)
+    for i, qs in enumerate(queries):
+        q = _u8(qs)
+        _load().oracle_multi_query_one(_ptr(r), r.size, _ptr(sa_r), _ptr(q), q.size, _ptr(res))
+        out[i] = res
+    return out
 
 
 def lcp_pairs(text, p, q) -> np.ndarray:

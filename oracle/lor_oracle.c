@@ -22,6 +22,10 @@
  *     (a brute force independent of suffix arrays) -- used to pin the
  *     overlap that the method derives from SA + LCP (Section 3, "longest
  *     overlap prefix of two sequences").
+ *   - one query against a reference: for every query suffix, its longest
+ *     prefix occurring in the reference, by binary search over the
+ *     reference's sorted suffixes with direct comparisons (the longest match
+ *     is with one of the two suffixes around the insertion point).
  *
  * Sorting uses a plain top-down merge sort with a direct suffix comparison.
  * The pthread variant only splits the same merge sort across threads.
@@ -284,4 +288,63 @@ int64_t oracle_lcs_dp(const uint8_t *a, int64_t na, const uint8_t *b, int64_t nb
     free(prev);
     free(cur);
     return best;
+}
+
+/* Common prefix length of a[0..na) and b[0..nb). */
+static int64_t common_prefix(const uint8_t *a, int64_t na, const uint8_t *b, int64_t nb)
+{
+    int64_t l = 0;
+    while (l < na && l < nb && a[l] == b[l]) l++;
+    return l;
+}
+
+/* Longest substring of q shared with r (r's suffix array sa_r given, by
+ * direct comparison of suffixes): out[0] = its length L, out[1] = the
+ * smallest offset in q where a length-L match starts, out[2] = the smallest
+ * offset in r holding q[out[1] .. out[1] + L); -1 for both when L = 0. */
+int oracle_multi_query_one(const uint8_t *r, int64_t rn, const int32_t *sa_r, const uint8_t *q, int64_t qn,
+                           int64_t *out)
+{
+    int64_t best = 0, bq = -1;
+    for (int64_t i = 0; i < qn && rn > 0; i++) {
+        /* first reference suffix not smaller than q[i..] */
+        int64_t lo = 0, hi = rn;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            const int64_t x = sa_r[mid];
+            const int64_t l = common_prefix(r + x, rn - x, q + i, qn - i);
+            int less; /* r[x..] < q[i..] */
+            if (l == rn - x) less = (l < qn - i); /* proper prefix sorts first */
+            else if (l == qn - i) less = 0;
+            else less = r[x + l] < q[i + l];
+            if (less) lo = mid + 1;
+            else hi = mid;
+        }
+        int64_t m = 0;
+        if (lo < rn) {
+            const int64_t x = sa_r[lo];
+            const int64_t l = common_prefix(r + x, rn - x, q + i, qn - i);
+            if (l > m) m = l;
+        }
+        if (lo > 0) {
+            const int64_t x = sa_r[lo - 1];
+            const int64_t l = common_prefix(r + x, rn - x, q + i, qn - i);
+            if (l > m) m = l;
+        }
+        if (m > best) {
+            best = m;
+            bq = i;
+        }
+    }
+    out[0] = best;
+    out[1] = best > 0 ? bq : -1;
+    out[2] = -1;
+    if (best > 0) {
+        for (int64_t x = 0; x + best <= rn; x++)
+            if (memcmp(r + x, q + bq, (size_t)best) == 0) {
+                out[2] = x;
+                break;
+            }
+    }
+    return 0;
 }

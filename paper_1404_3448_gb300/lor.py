@@ -70,6 +70,8 @@ def load():
         "lor_batch_graph_launch": ([vp, vp], ctypes.c_int),
         "lor_batch_graph_kernels": ([vp], i64),
         "lor_batch_graph_destroy": ([vp], ctypes.c_int),
+        "lor_multi_query_workspace_size": ([i64, vp, i32], sz),
+        "lor_multi_query_overlap": ([vp, i64, vp, vp, i32, vp, vp, sz, vp], ctypes.c_int),
         "lor_tune_default": ([vp], None),
         "lor_tune_get": ([vp], ctypes.c_int),
         "lor_tune_set": ([vp], ctypes.c_int),
@@ -368,6 +370,27 @@ class Batch:
             d["positions"] = pos[a:min(b, self.pos_cap)].astype(np.int64)
             res.append(d)
         return res
+
+
+def multi_query_overlap(ref_dev: torch.Tensor, queries_dev: torch.Tensor, q_lens, out=None, ws=None,
+                        stream=None) -> torch.Tensor:
+    """lor_multi_query_overlap: per query (length, query_pos, ref_pos, 0) as
+    an int32 (nq, 4) device tensor."""
+    lens = np.ascontiguousarray(np.asarray(q_lens, dtype=np.int64))
+    nq = int(lens.size)
+    dev = ref_dev.device if ref_dev.numel() else queries_dev.device
+    if out is None:
+        out = torch.empty((nq, 4), dtype=torch.int32, device=dev)
+    need = load().lor_multi_query_workspace_size(ref_dev.numel(), lens.ctypes.data, nq)
+    if need == 0:
+        raise ValueError("bad reference or query lengths")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    rp = _ptr(ref_dev, torch.uint8, "ref") if ref_dev.numel() else None
+    qp = _ptr(queries_dev, torch.uint8, "queries") if queries_dev.numel() else None
+    _check(load().lor_multi_query_overlap(rp, ref_dev.numel(), qp, lens.ctypes.data, nq, out.data_ptr(),
+                                          ws.data_ptr(), ws.numel(), _stream(stream)), "lor_multi_query_overlap")
+    return out
 
 
 class Tune(ctypes.Structure):

@@ -257,6 +257,30 @@ def test_rmq_argmin_is_the_leftmost_minimum_and_the_suffix_lcp(oracle_mod):
             assert (lcp[r1 + 1:arg[i]] > val[i]).all()
 
 
+def test_multi_query_oracle_against_the_dp(oracle_mod):
+    """One reference against many queries: the length is the DP's longest
+    common substring, the query offset the smallest DP start in the query,
+    the reference offset the first occurrence of that substring (bytes.find),
+    on random, repetitive and degenerate cases."""
+    rng = np.random.default_rng(12)
+    A = np.frombuffer(b"ACGT", np.uint8)
+    refs = [A[rng.integers(0, 4, 400)], np.frombuffer(b"ACACACACACACAC" * 8, np.uint8),
+            np.frombuffer(b"A", np.uint8), np.zeros(0, np.uint8)]
+    for ref in refs:
+        qs = [A[rng.integers(0, 4, int(rng.integers(0, 50)))] for _ in range(25)]
+        qs += [np.frombuffer(b"CA" * 7, np.uint8), np.zeros(0, np.uint8), np.frombuffer(b"T", np.uint8)]
+        if ref.size > 60:
+            qs.append(ref[17:60].copy())
+        res = oracle_mod.multi_query(ref, qs)
+        for q, (L, qq, rr) in zip(qs, res):
+            Ld, _, sb = oracle_mod.lcs_dp(ref, q) if len(q) and len(ref) else (0, [], [])
+            if Ld == 0:
+                assert (L, qq, rr) == (0, -1, -1)
+                continue
+            eq = int(min(sb))
+            assert (L, qq, rr) == (Ld, eq, bytes(ref).find(bytes(q[eq:eq + Ld])))
+
+
 # ---------------------------------------------------------------- LCS DP pins
 
 def _brute_lcs(a: bytes, b: bytes):
