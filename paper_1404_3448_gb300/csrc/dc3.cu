@@ -1079,14 +1079,6 @@ __global__ void k_dbl_headof(const int32_t *__restrict__ NS, int64_t m, int32_t 
     if (k < m && (k == 0 || NS[k] != NS[k - 1])) headof[NS[k]] = int32_t(k + 1);
 }
 
-// H[k] = headof[NS[k]]: the rank of every sample in name order (NS is sorted,
-// so the table reads are monotone).
-__global__ void k_dbl_heads(const int32_t *__restrict__ NS, int64_t m, const int32_t *__restrict__ headof,
-                            uint32_t *__restrict__ H) {
-    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (k < m) H[k] = uint32_t(headof[NS[k]]);
-}
-
 // R[j] = rank of R-suffix j by its first symbol.
 __global__ void k_dbl_init(int32_t *__restrict__ R, int64_t m, const int32_t *__restrict__ headof) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -1357,6 +1349,30 @@ __global__ void __launch_bounds__(kScanThreads) k_dbl_next_dev(
             return (i > 0 && runid[i - 1] == r) || (i + 1 < U && runid[i + 1] == r);
         },
         [&](int64_t i, uint32_t d) { ul2[d] = ul[i]; }, lb, ctr, epoch, status, count);
+}
+
+// Ranks of the samples that share their name, once every sample holds
+// 1 + its position in name order (exact for the samples whose name is
+// unique): in the unresolved list (name order, the members of every group of
+// two or more) the first of each run of equal names is its group's head, and
+// every member takes the head's rank.
+__global__ void k_dbl_group_heads(const uint32_t *__restrict__ ul, const uint32_t *U_dev,
+                                  const int32_t *__restrict__ NS, int32_t *__restrict__ headof) {
+    const int64_t U = int64_t(*U_dev);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < U; i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t k = ul[i];
+        const int32_t v = NS[k];
+        if (i == 0 || NS[ul[i - 1]] != v) headof[v] = int32_t(k + 1);
+    }
+}
+__global__ void k_dbl_group_ranks(const uint32_t *__restrict__ ul, const uint32_t *U_dev,
+                                  const int32_t *__restrict__ NS, const int32_t *__restrict__ SAR,
+                                  const int32_t *__restrict__ headof, int32_t *__restrict__ R) {
+    const int64_t U = int64_t(*U_dev);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < U; i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t k = ul[i];
+        R[SAR[k]] = headof[NS[k]];
+    }
 }
 
 // After the last enqueued round nothing may be left unresolved.
@@ -1643,22 +1659,19 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
     uint32_t *ul = D.t32[1], *ul2 = D.t32[2], *runid = D.t32[3], *val = D.t32[4], *rstart = D.t32[5];
     uint32_t *valt = D.t32[0];  // headof is dead once the ranks are initialised
     uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
-    {
-        ProfScope ps(PK_NAMING, double(m) * 8, st);
-        k_dbl_headof<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof);
-        LOR_LAUNCH_CHECK();
-    }
     if (r_unwritten) {
-        // Large levels left R unwritten: scatter the ranks instead of the names.
-        uint32_t *H = D.t32[1];
-        {
-            ProfScope ps(PK_NAMING, double(m) * 12, st);
-            k_dbl_heads<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof, H);
-            LOR_LAUNCH_CHECK();
-        }
-        int rc = bucketed_scatter(D.rs, (const uint32_t *)SAR, H, m, m, D.t32[2], D.t32[3], D.t32[4], Rl, 0);
+        // Large levels left R unwritten: every sample first takes 1 + its
+        // position in name order (an inverse-permutation scatter with the
+        // values generated), then the members of the groups of equal names take
+        // their group head's rank.
+        int rc = bucketed_scatter(D.rs, (const uint32_t *)SAR, nullptr, m, m, D.t32[2], D.t32[3], D.t32[4], Rl, 1);
         if (rc) return rc;
     } else {
+        {
+            ProfScope ps(PK_NAMING, double(m) * 8, st);
+            k_dbl_headof<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof);
+            LOR_LAUNCH_CHECK();
+        }
         ProfScope ps(PK_NAMING, double(m) * 12, st);
         k_dbl_init<<<grid_for(m, 256), 256, 0, st>>>(Rl, m, headof);
         LOR_LAUNCH_CHECK();
@@ -1671,6 +1684,14 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
     uint32_t hU = 0;
     int rc = read_u32(D, D.d_count, &hU);
     if (rc) return rc;
+    if (r_unwritten && hU > 0) {
+        ProfScope ps(PK_NAMING, double(hU) * 24, st);
+        const unsigned g = unsigned(min64(cdiv(hU, 256), 152 * 8));
+        k_dbl_group_heads<<<g, 256, 0, st>>>(ul, D.d_count, NSl, headof);
+        LOR_LAUNCH_CHECK();
+        k_dbl_group_ranks<<<g, 256, 0, st>>>(ul, D.d_count, NSl, SAR, headof, Rl);
+        LOR_LAUNCH_CHECK();
+    }
     *U0 = hU;
     const int shift = bit_width_u64(uint64_t(m));
     for (int64_t h = 1; hU > 0; h *= 2) {
@@ -1861,21 +1882,25 @@ int sa_by_doubling_graph(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const 
     uint32_t *valt = D.t32[0];
     uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
     uint32_t *cnt = D.d_count, *cnt2 = D.d_count + 1;
-    k_dbl_headof<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof);
-    LOR_LAUNCH_CHECK();
     if (r_unwritten) {
-        uint32_t *H = D.t32[1];
-        k_dbl_heads<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof, H);
-        LOR_LAUNCH_CHECK();
-        int rc = bucketed_scatter(D.rs, (const uint32_t *)SAR, H, m, m, D.t32[2], D.t32[3], D.t32[4], Rl, 0);
+        int rc = bucketed_scatter(D.rs, (const uint32_t *)SAR, nullptr, m, m, D.t32[2], D.t32[3], D.t32[4], Rl, 1);
         if (rc) return rc;
     } else {
+        k_dbl_headof<<<grid_for(m, 256), 256, 0, st>>>(NSl, m, headof);
+        LOR_LAUNCH_CHECK();
         k_dbl_init<<<grid_for(m, 256), 256, 0, st>>>(Rl, m, headof);
         LOR_LAUNCH_CHECK();
     }
     {
         const int64_t ntiles = cdiv(m, kScanTile);
         LOR_TILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, cnt, LB_ARGS(D), ntiles);
+    }
+    if (r_unwritten) {
+        const unsigned g = unsigned(min64(cdiv(m, 256), scan_grid_cap()));
+        k_dbl_group_heads<<<g, 256, 0, st>>>(ul, cnt, NSl, headof);
+        LOR_LAUNCH_CHECK();
+        k_dbl_group_ranks<<<g, 256, 0, st>>>(ul, cnt, NSl, SAR, headof, Rl);
+        LOR_LAUNCH_CHECK();
     }
     const int shift = bit_width_u64(uint64_t(m));
     const int rounds = shift > 0 ? shift : 1;

@@ -22,7 +22,7 @@ def L():
 
 
 def run(L, ref, qs):
-    ref_dev = torch.from_numpy(np.ascontiguousarray(ref, dtype=np.uint8)).cuda()
+    ref_dev = torch.from_numpy(np.array(ref, dtype=np.uint8)).cuda()
     flat = np.concatenate(qs) if sum(len(q) for q in qs) else np.zeros(0, np.uint8)
     q_dev = torch.from_numpy(np.ascontiguousarray(flat, dtype=np.uint8)).cuda()
     out = L.multi_query_overlap(ref_dev, q_dev, [len(q) for q in qs])
