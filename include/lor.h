@@ -255,6 +255,25 @@ int lor_rmq_block_argmin(const int32_t *d_table, const int32_t *d_lcp, const int
                          lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * The K longest maximal overlaps (extends a10 from the maximum to the K
+ * largest values of the same quantity).
+ * A candidate is a rank k in [1, n) whose adjacent suffixes a = SA[k-1],
+ * b = SA[k] start in different sequences, with LCP[k] > 0, and that is
+ * left-maximal: a == 0, b == 0, or text[a-1] != text[b-1] (so each shared
+ * region is reported once, not once per shifted copy).  d_out[0 .. *d_count)
+ * receives the min(K, candidates) largest by (LCP desc, rank asc) as overlap
+ * records (length, rank, seq_a/pos_a on the lower sequence id, seq_b/pos_b;
+ * n_pos = 0).  Inputs as for lor_longest_overlap plus the text; d_count is
+ * one device int32.  1 <= K <= LOR_TOPK_MAX.  d_ws:
+ * lor_topk_overlaps_workspace_size(n) bytes, 256-byte aligned.
+ * ------------------------------------------------------------------------- */
+#define LOR_TOPK_MAX 65536
+size_t lor_topk_overlaps_workspace_size(int64_t n);
+int lor_topk_overlaps(const uint8_t *d_text, const int32_t *d_sa, const int32_t *d_lcp, int64_t n,
+                      const int32_t *d_seq_starts, int32_t nseq, int32_t K, lor_overlap *d_out,
+                      int32_t *d_count, void *d_ws, size_t ws_bytes, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * One reference against many query sequences (the paper's experiments take
  * 512 .. 2,097,152 query sequences against a reference; Section 3 defines
  * the overlap through common prefixes of suffixes).

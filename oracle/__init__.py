@@ -362,6 +362,37 @@ def rmq_argmin(lcp, isa, p, q):
     return val, arg
 
 
+def topk_overlaps(text, sa, lcp, seq_starts, K):
+    """The K largest left-maximal cross-sequence adjacent pairs by (LCP desc,
+    rank asc), by definition over every rank: candidates are ranks k >= 1
+    with SA[k-1], SA[k] in different sequences, LCP[k] > 0, and a or b = 0 or
+    text[a-1] != text[b-1].  Returns records like longest_overlap's (without
+    positions), largest first."""
+    t = _u8(text)
+    sa = np.asarray(sa)
+    lcp = np.asarray(lcp)
+    seq = seq_of(sa, seq_starts)
+    cand = []
+    for k in range(1, t.size):
+        a, b = int(sa[k - 1]), int(sa[k])
+        if lcp[k] <= 0 or seq[k - 1] == seq[k]:
+            continue
+        if a != 0 and b != 0 and t[a - 1] == t[b - 1]:
+            continue
+        cand.append((-int(lcp[k]), k))
+    cand.sort()
+    out = []
+    starts = np.asarray(seq_starts)
+    for negl, k in cand[:K]:
+        a, b = int(sa[k - 1]), int(sa[k])
+        qa, qb = int(seq[k - 1]), int(seq[k])
+        if qa > qb:
+            a, b, qa, qb = b, a, qb, qa
+        out.append(dict(length=-negl, rank=k, seq_a=qa, pos_a=a - int(starts[qa]), seq_b=qb,
+                        pos_b=b - int(starts[qb])))
+    return out
+
+
 def multi_query(ref, queries):
     """One reference against many queries (uppercase ASCII): per query (L, q, r) with L the
     length of the longest substring it shares with the reference, q the

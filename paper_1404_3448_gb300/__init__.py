@@ -9,5 +9,5 @@ from .lor import (  # noqa: F401
     Batch, BatchGraph, LorError, Pipeline, Server, build_sa, check_device, device_status, encode_concat, last_dc3_trace,
     lcp, load, longest_overlap, overlap_dict, profile_enable, profile_read, profile_reset,
     radix_sort_pairs, rmq_build, rmq_query, rmq_block_build, rmq_block_query, rmq_block_argmin, server_batch_bytes, workspace, tune_default, tune_get, tune_set,
-    autotune_batch, multi_query_overlap,
+    autotune_batch, multi_query_overlap, topk_overlaps,
 )

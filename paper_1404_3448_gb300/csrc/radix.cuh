@@ -419,16 +419,38 @@ inline int sort_grid_cap() {
 }
 
 // The tile counter of one launch: the running counter and its host mirror,
-// or (graph mode, device-sized launches) a fresh counter from the pool.
+// or for a device-sized launch (whose number of claims the host does not
+// know) a fresh counter: one from the pool in graph mode, else the running
+// counter zeroed before the launch (and again by end_counter after it).
 inline int take_counter(RadixScratch &rs, bool device_sized, unsigned long long **ctr,
                         unsigned long long *base) {
     if (rs.graph && device_sized) {
         if (!rs.ctr_pool || rs.ctr_next >= rs.ctr_pool_size) return LOR_ERR_WORKSPACE;
         *ctr = rs.ctr_pool + rs.ctr_next++;
         *base = 0;
+    } else if (device_sized) {
+        LOR_CUDA_TRY(cudaMemsetAsync(rs.tile_ctr, 0, sizeof(unsigned long long), rs.stream));
+        rs.tile_base = 0;
+        *ctr = rs.tile_ctr;
+        *base = 0;
     } else {
         *ctr = rs.tile_ctr;
         *base = rs.tile_base;
+    }
+    return LOR_OK;
+}
+
+// After a launch that took its counter from take_counter: advances the host
+// mirror by the launch's claims, or re-zeroes a running counter that a
+// device-sized launch advanced by an unknown amount.
+inline int end_counter(RadixScratch &rs, bool device_sized, const unsigned long long *ctr,
+                       unsigned long long claims) {
+    if (ctr != rs.tile_ctr) return LOR_OK;
+    if (device_sized) {
+        LOR_CUDA_TRY(cudaMemsetAsync(rs.tile_ctr, 0, sizeof(unsigned long long), rs.stream));
+        rs.tile_base = 0;
+    } else {
+        rs.tile_base += claims;
     }
     return LOR_OK;
 }
@@ -487,7 +509,8 @@ int radix_passes(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v
                     rs.epoch, rs.status, prefetch_ahead(ki, ki, grid));
         }
         LOR_LAUNCH_CHECK();
-        if (ctr == rs.tile_ctr) rs.tile_base += (unsigned long long)(ntiles + grid);
+        rc = end_counter(rs, m_dev != nullptr, ctr, (unsigned long long)(ntiles + grid));
+        if (rc) return rc;
         vals_ready = true;
         KeyT *tk = ki; ki = ko; ko = tk;
         uint32_t *tv = vi; vi = vo; vo = tv;

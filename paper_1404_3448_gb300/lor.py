@@ -70,6 +70,8 @@ def load():
         "lor_batch_graph_launch": ([vp, vp], ctypes.c_int),
         "lor_batch_graph_kernels": ([vp], i64),
         "lor_batch_graph_destroy": ([vp], ctypes.c_int),
+        "lor_topk_overlaps_workspace_size": ([i64], sz),
+        "lor_topk_overlaps": ([vp, vp, vp, i64, vp, i32, i32, vp, vp, vp, sz, vp], ctypes.c_int),
         "lor_multi_query_workspace_size": ([i64, vp, i32], sz),
         "lor_multi_query_overlap": ([vp, i64, vp, vp, i32, vp, vp, sz, vp], ctypes.c_int),
         "lor_tune_default": ([vp], None),
@@ -370,6 +372,23 @@ class Batch:
             d["positions"] = pos[a:min(b, self.pos_cap)].astype(np.int64)
             res.append(d)
         return res
+
+
+def topk_overlaps(text, sa, lcp_arr, seq_starts, nseq, K, ws=None, stream=None):
+    """lor_topk_overlaps: the K longest left-maximal cross-sequence overlaps as
+    a list of dicts (host), largest first."""
+    n = text.numel()
+    out = torch.empty((K, 8), dtype=torch.int32, device=text.device)
+    cnt = torch.zeros(1, dtype=torch.int32, device=text.device)
+    need = load().lor_topk_overlaps_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, text.device)
+    _check(load().lor_topk_overlaps(_ptr(text, torch.uint8, "text"), _ptr(sa, torch.int32, "sa"),
+                                    _ptr(lcp_arr, torch.int32, "lcp"), n, _ptr(seq_starts, torch.int32, "starts"),
+                                    int(nseq), int(K), out.data_ptr(), cnt.data_ptr(), ws.data_ptr(), ws.numel(),
+                                    _stream(stream)), "lor_topk_overlaps")
+    c = int(cnt.item())
+    return [dict(zip(OVERLAP_FIELDS, row)) for row in out[:c].cpu().numpy().tolist()]
 
 
 def multi_query_overlap(ref_dev: torch.Tensor, queries_dev: torch.Tensor, q_lens, out=None, ws=None,

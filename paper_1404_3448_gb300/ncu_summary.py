@@ -22,7 +22,8 @@ import re
 # kernel name prefix -> timing kind (the scope each launch is timed under)
 KINDS = [
     ("k_encode", "encode"), ("k_mq_encode", "encode"), ("k_mq_rindex", "overlap_scan"),
-    ("k_mq_best", "overlap_scan"), ("k_mq_result", "overlap_collect"),
+    ("k_mq_best", "overlap_scan"), ("k_mq_result", "overlap_collect"), ("k_topk_hist", "overlap_scan"),
+    ("k_topk_", "overlap_collect"),
     ("k_sample_keys", "sample_keys"), ("k_dense_mark", "sample_keys"), ("k_par_samples", "sample_keys"),
     ("k_par_dups", "sample_keys"), ("k_first_char", "sample_keys"), ("k_dbl_keys", "sample_keys"),
     ("k_radix_hist", "radix_hist"), ("k_radix_offsets", "radix_hist"),

@@ -281,6 +281,42 @@ def test_multi_query_oracle_against_the_dp(oracle_mod):
             assert (L, qq, rr) == (Ld, eq, bytes(ref).find(bytes(q[eq:eq + Ld])))
 
 
+def test_topk_overlaps_first_is_the_longest_overlap_and_entries_are_maximal(oracle_mod):
+    """The largest left-maximal cross pair is the longest overlap (a pair at
+    the maximum is always left-maximal: one more equal symbol on the left
+    would give a longer cross overlap), so the first top-k entry equals
+    longest_overlap's record and its length the DP's; every entry is a cross
+    pair, left-maximal, with the length of the direct common prefix, in
+    (length desc, rank asc) order."""
+    rng = np.random.default_rng(13)
+    A = np.frombuffer(b"ACGT", np.uint8)
+    for trial in range(40):
+        alpha = [A, A[:2], A[:1]][trial % 3]
+        seqs = [alpha[rng.integers(0, alpha.size, int(rng.integers(1, 60)))] for _ in range(2 + trial % 3)]
+        text, starts, _ = oracle_mod.encode_concat(seqs)
+        sa = oracle_mod.suffix_array(text)
+        lcp = oracle_mod.lcp_array(text, sa)
+        ov = oracle_mod.longest_overlap(text, sa, lcp, starts)
+        top = oracle_mod.topk_overlaps(text, sa, lcp, starts, 50)
+        if ov["length"] == 0:
+            assert top == []
+            continue
+        assert {k: top[0][k] for k in ("length", "rank", "seq_a", "pos_a", "seq_b", "pos_b")} == \
+            {k: ov[k] for k in ("length", "rank", "seq_a", "pos_a", "seq_b", "pos_b")}
+        assert top[0]["length"] == oracle_mod.overlap_by_dp(seqs)[0]
+        prev = None
+        for e in top:
+            a = int(starts[e["seq_a"]]) + e["pos_a"]
+            b = int(starts[e["seq_b"]]) + e["pos_b"]
+            assert e["seq_a"] < e["seq_b"]
+            assert a == 0 or b == 0 or text[a - 1] != text[b - 1]
+            assert e["length"] == oracle_mod.lcp_pairs(text, np.array([a], np.int32), np.array([b], np.int32))[0]
+            assert sorted((sa[e["rank"] - 1], sa[e["rank"]])) == sorted((a, b))
+            key = (-e["length"], e["rank"])
+            assert prev is None or key > prev
+            prev = key
+
+
 # ---------------------------------------------------------------- LCS DP pins
 
 def _brute_lcs(a: bytes, b: bytes):
