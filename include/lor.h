@@ -22,7 +22,9 @@
  *     (bad symbols, out-of-range indices in inputs, a bounded wait that ran
  *     out) are recorded in a per-device status word that lor_device_status()
  *     reads and clears.  No call traps, aborts or throws.
- *   - Indices are int32: texts hold at most LOR_MAX_N symbols.
+ *   - Indices are int32: texts hold at most LOR_MAX_N symbols.  The *64
+ *     entry points (section "64-bit indices" below) take and return int64
+ *     indices for texts of up to LOR_MAX_N64 symbols.
  */
 #ifndef LOR_H
 #define LOR_H
@@ -40,7 +42,7 @@ typedef struct CUstream_st *lor_stream_t; /* same type as cudaStream_t */
 #define LOR_OK 0
 #define LOR_ERR_INVALID_ARG (-1) /* null pointer, negative or zero size, bad nseq */
 #define LOR_ERR_BAD_SYMBOL (-2)  /* input symbol outside ACGT/acgt, or text code out of [1, sigma) */
-#define LOR_ERR_TOO_LARGE (-3)   /* n > LOR_MAX_N */
+#define LOR_ERR_TOO_LARGE (-3)   /* n > LOR_MAX_N (LOR_MAX_N64 for the *64 calls), or an LCP past INT32_MAX */
 #define LOR_ERR_WORKSPACE (-4)   /* workspace null or smaller than the *_workspace_size query */
 #define LOR_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define LOR_ERR_TIMEOUT (-6)     /* a bounded inter-block wait ran out on the device */
@@ -50,6 +52,12 @@ typedef struct CUstream_st *lor_stream_t; /* same type as cudaStream_t */
 /* Largest supported text length (int32 indices with head-room for DC3's
  * dummy sample and padding). */
 #define LOR_MAX_N 2147483000LL
+
+/* Largest text length of the *64 entry points: positions are held as 32-bit
+ * unsigned integers inside the library (every radix count, look-back value
+ * and position fits), and a text this long already needs about 100 GB of
+ * workspace. */
+#define LOR_MAX_N64 4294901760LL
 
 /* Largest number of sequences in one concatenated text (codes fit a byte). */
 #define LOR_MAX_SEQ 250
@@ -232,7 +240,9 @@ int lor_batch_graph_destroy(lor_batch_graph *g);
  * blockmin[b] = min(lcp[32b .. min(32b + 32, n) - 1]).  d_table must be
  * 256-byte aligned and hold lor_rmq_block_table_elems(n) int32 entries
  * (n / 32 * (log2 n - 4) words, under a tenth of the sparse table at any n
- * above 2^16).
+ * above 2^16).  lor_rmq_block_table_elems and lor_rmq_block_build accept n up
+ * to LOR_MAX_N64 (the table of a 64-bit text; query it with
+ * lor_rmq_block_query64).
  * lor_rmq_block_query answers exactly what lor_rmq_query answers (same
  * arguments, same errors) and also reads d_lcp: the partial blocks at both
  * ends of a rank range are scanned in the LCP array, the whole blocks between
@@ -467,6 +477,64 @@ int lor_server_destroy(lor_server *srv);
 size_t lor_radix_sort_workspace_size(int64_t m);
 int lor_radix_sort_pairs(uint64_t *d_keys, uint32_t *d_vals, int64_t m, int32_t key_bits,
                          void *d_ws, size_t ws_bytes, lor_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * 64-bit indices: the path a1-a12 for texts longer than LOR_MAX_N, up to
+ * LOR_MAX_N64 symbols (chromosome-scale concatenations).  Indices that can
+ * pass 2^31 (text positions, suffix-array ranks, sequence starts, offsets and
+ * counts) are int64; LCP values stay int32 (an LCP above INT32_MAX sets
+ * LOR_ERR_TOO_LARGE in the status word).  Any n >= 1 is accepted, so the
+ * calls can be checked on small texts.  Errors as for the int32 calls, with
+ * LOR_MAX_N64 in place of LOR_MAX_N.
+ * ------------------------------------------------------------------------- */
+
+/* a1: as lor_encode_concat; d_seq_starts is device int64[nseq + 1]. */
+int lor_encode_concat64(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq, uint8_t *d_text,
+                        int64_t *d_seq_starts, lor_stream_t stream);
+
+/* a2-a8: the suffix array (the order of Section 3, Tables 1-3) as int64[n].
+ * Built by prefix doubling over all suffixes (the reduced-string finisher of
+ * lor_build_sa, started on the text): one LSD radix sort of every suffix's
+ * first floor(64 / b) codes (b = bits of sigma - 1), then rounds that sort
+ * only the still-tied suffixes by the rank of the suffix h symbols on,
+ * h doubling each round.  Same text convention and errors as lor_build_sa.
+ * d_ws: lor_build_sa64_workspace_size(n, sigma) bytes (about 44 n),
+ * 256-byte aligned.  Synchronises `stream` once per round and per radix sort. */
+size_t lor_build_sa64_workspace_size(int64_t n, int32_t sigma);
+int lor_build_sa64(const uint8_t *d_text, int64_t n, int32_t sigma, int64_t *d_sa, void *d_ws, size_t ws_bytes,
+                   lor_stream_t stream);
+
+/* a9: ISA (int64[n]) and LCP (int32[n]) from an int64 suffix array, as
+ * lor_lcp.  d_ws: lor_lcp64_workspace_size(n) bytes (about 29 n). */
+size_t lor_lcp64_workspace_size(int64_t n);
+int lor_lcp64(const uint8_t *d_text, const int64_t *d_sa, int64_t n, int64_t *d_isa, int32_t *d_lcp, void *d_ws,
+              size_t ws_bytes, lor_stream_t stream);
+
+/* a10: the longest overlap record with int64 rank, offsets and count, and the
+ * sorted positions as int64; otherwise as lor_longest_overlap (same tie rule,
+ * same position set).  d_seq_starts: device int64[nseq + 1].
+ * d_ws: lor_longest_overlap64_workspace_size(n) bytes. */
+typedef struct {
+    int32_t length;   /* L; 0 if none */
+    int32_t seq_a;    /* lower sequence id of the pair at rank k; -1 if L == 0 */
+    int32_t seq_b;    /* higher sequence id; -1 if L == 0 */
+    int32_t reserved;
+    int64_t rank;     /* k; -1 if L == 0 */
+    int64_t pos_a;    /* offset inside seq_a; -1 if L == 0 */
+    int64_t pos_b;    /* offset inside seq_b; -1 if L == 0 */
+    int64_t n_pos;    /* number of positions (may exceed pos_cap) */
+} lor_overlap64;
+size_t lor_longest_overlap64_workspace_size(int64_t n);
+int lor_longest_overlap64(const int64_t *d_sa, const int32_t *d_lcp, int64_t n, const int64_t *d_seq_starts,
+                          int32_t nseq, lor_overlap64 *d_out, int64_t *d_pos, int64_t pos_cap, void *d_ws,
+                          size_t ws_bytes, lor_stream_t stream);
+
+/* a12 on the block table of a 64-bit text (lor_rmq_block_build with the
+ * int32 LCP array): int64 ISA, query positions and answers (p == q answers
+ * the suffix length n - p); otherwise as lor_rmq_block_query. */
+int lor_rmq_block_query64(const int32_t *d_table, const int32_t *d_lcp, const int64_t *d_isa, int64_t n,
+                          const int64_t *d_p, const int64_t *d_q, int64_t nq, int64_t *d_out,
+                          lor_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Status, diagnostics and instrumentation (no counterpart in the paper).

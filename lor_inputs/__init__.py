@@ -16,6 +16,8 @@ for them with the shapes the workloads name:
 * ``pair_batch``       -- many pairs of uneven, log-uniform length;
 * ``multi_query``      -- one reference and many query sequences (reads of
   the reference with substitutions, and background with a planted piece);
+* ``pair_int64``       -- two uniform sequences whose concatenation passes
+  2^31 symbols (the 64-bit index path), and ``random_queries64``;
 * ``random_queries``   -- uniform (p, q) suffix pairs for LCP queries;
 * ``poisson_arrivals`` -- request arrival times of a Poisson process, and
   ``request_stream``   -- which pool pair each arrival asks for and its
@@ -134,6 +136,30 @@ def pair_large(n_each=SIZE_LARGE, seed=SEED_BASE + 3, plant_len=500):
     """Two iid uniform sequences of 134,217,728 bases with one 500-base plant
     (the same generator as the 2 x 100,000 instance)."""
     return pair_uniform(n_each=n_each, plant_len=plant_len, seed=seed)
+
+
+# Past the int32 index range: n = 2 * (2^30 + 2^15) + 2 = 2^31 + 2^16 + 2.
+SIZE_INT64 = (1 << 30) + (1 << 15)
+
+
+def pair_int64(n_each=SIZE_INT64, seed=SEED_BASE + 8, plant_len=500):
+    """Two iid uniform sequences whose concatenation passes 2^31 symbols, with
+    one 500-base plant at a uniform offset in the first and 600 bases before
+    the end of the second, so that its text position there lies past 2^31."""
+    rng = _rng(seed)
+    s1 = random_bases(rng, n_each)
+    s2 = random_bases(rng, n_each)
+    piece = random_bases(rng, plant_len)
+    o1 = _plant(rng, s1, piece)
+    o2 = n_each - plant_len - 100
+    s2[o2:o2 + plant_len] = piece
+    return [s1, s2], dict(plant_len=plant_len, plant_offsets=(o1, o2), seed=seed)
+
+
+def random_queries64(n, count=1_000_000, seed=SEED_BASE + 8):
+    """``count`` (p, q) pairs uniform in [0, n)^2 (int64)."""
+    rng = _rng(seed + 1000)
+    return (rng.integers(0, n, size=count, dtype=np.int64), rng.integers(0, n, size=count, dtype=np.int64))
 
 
 def random_queries(n, count=1_000_000, seed=SEED_BASE + 3):

@@ -77,6 +77,13 @@ def _load():
             lib.oracle_check_suffix_array.restype = ctypes.c_int64
             lib.oracle_lcp_pairs.argtypes = [u8p, i64, i32p, i32p, i64, i32p]
             lib.oracle_lcp_pairs.restype = ctypes.c_int
+            vp = ctypes.c_void_p
+            lib.oracle_check_suffix_array64.argtypes = [u8p, i64, vp, ctypes.c_int]
+            lib.oracle_check_suffix_array64.restype = ctypes.c_int64
+            lib.oracle_lcp_array64.argtypes = [u8p, i64, vp, i32p, ctypes.c_int]
+            lib.oracle_lcp_array64.restype = ctypes.c_int
+            lib.oracle_lcp_pairs64.argtypes = [u8p, i64, vp, vp, i64, vp]
+            lib.oracle_lcp_pairs64.restype = ctypes.c_int
             lib.oracle_lcs_dp.argtypes = [u8p, i64, u8p, i64, u8p, u8p]
             lib.oracle_lcs_dp.restype = ctypes.c_int64
             lib.oracle_multi_query_one.argtypes = [u8p, i64, i32p, u8p, i64, ctypes.c_void_p]
@@ -422,6 +429,94 @@ def lcp_pairs(text, p, q) -> np.ndarray:
     if _load().oracle_lcp_pairs(_ptr(t), t.size, _ptr(p), _ptr(q), p.size, _ptr(out)) != 0:
         raise ValueError("query position out of range")
     return out
+
+
+# --------------------------------------------------------------------------
+# the same definitions with int64 indices (texts past 2^31 symbols)
+# --------------------------------------------------------------------------
+
+def check_suffix_array64(text, sa, nthreads: int = 1) -> int:
+    """check_suffix_array for an int64 suffix array."""
+    t = _u8(text)
+    s = np.ascontiguousarray(sa, dtype=np.int64)
+    if s.size != t.size:
+        return t.size
+    return int(_load().oracle_check_suffix_array64(_ptr(t), t.size, s.ctypes.data, int(nthreads)))
+
+
+def lcp_array64(text, sa, nthreads: int = 1) -> np.ndarray:
+    """lcp_array for an int64 suffix array (int32 values; ValueError when one
+    does not fit)."""
+    t = _u8(text)
+    s = np.ascontiguousarray(sa, dtype=np.int64)
+    lcp = np.empty(t.size, dtype=np.int32)
+    if _load().oracle_lcp_array64(_ptr(t), t.size, s.ctypes.data, _ptr(lcp), int(nthreads)) != 0:
+        raise ValueError("oracle_lcp_array64 failed")
+    return lcp
+
+
+def lcp_pairs64(text, p, q) -> np.ndarray:
+    """lcp_pairs with int64 positions and answers."""
+    t = _u8(text)
+    p = np.ascontiguousarray(p, dtype=np.int64)
+    q = np.ascontiguousarray(q, dtype=np.int64)
+    out = np.empty(p.size, dtype=np.int64)
+    if _load().oracle_lcp_pairs64(_ptr(t), t.size, p.ctypes.data, q.ctypes.data, p.size, out.ctypes.data) != 0:
+        raise ValueError("query position out of range")
+    return out
+
+
+def overlap_max_scan(sa, lcp, seq_starts, chunk: int = 1 << 24):
+    """(L, k) of longest_overlap -- the largest LCP between rank-adjacent
+    suffixes of different sequences and the smallest rank attaining it
+    (Section 3) -- scanned over ranks in chunks, so that arrays of billions of
+    entries need no whole-array temporaries.  (0, -1) when no such pair shares
+    a symbol."""
+    sa = np.asarray(sa)
+    lcp = np.asarray(lcp)
+    n = sa.size
+    best, best_k = 0, -1
+    for lo in range(1, n, chunk):
+        hi = min(n, lo + chunk)
+        sq = seq_of(sa[lo - 1:hi], seq_starts)
+        cross = sq[1:] != sq[:-1]
+        cand = np.where(cross, lcp[lo:hi].astype(np.int64), -1)
+        m = int(cand.max())
+        if m > best:
+            best, best_k = m, lo + int(np.argmax(cand == m))
+    return best, best_k
+
+
+def longest_overlap_large(text, sa, lcp, seq_starts):
+    """longest_overlap for texts of billions of symbols.  L and k come from
+    overlap_max_scan; the positions are those of longest_overlap applied to
+    the ranks that can hold them: every maximal run of ranks with adjacent
+    LCP >= L (LCP set to 0 at each run's first rank, so that runs stay
+    apart), which is where longest_overlap finds its qualifying runs."""
+    lcp = np.asarray(lcp)
+    sa = np.asarray(sa)
+    L, k = overlap_max_scan(sa, lcp, seq_starts)
+    res = dict(length=0, rank=-1, seq_a=-1, pos_a=-1, seq_b=-1, pos_b=-1,
+               positions=np.zeros(0, dtype=np.int64))
+    if L <= 0:
+        return res
+    hits = np.flatnonzero(lcp >= L)
+    hits = hits[hits >= 1]
+    ranks = np.unique(np.concatenate([hits - 1, hits]))
+    sub_lcp = lcp[ranks].astype(np.int64)
+    first = np.ones(ranks.size, dtype=bool)
+    first[1:] = ranks[1:] != ranks[:-1] + 1
+    first |= sub_lcp < L
+    sub_lcp[first] = 0
+    sub = longest_overlap(text, sa[ranks], sub_lcp, seq_starts)
+    starts = np.asarray(seq_starts, dtype=np.int64)
+    a, b = int(sa[k - 1]), int(sa[k])
+    qa, qb = (int(x) for x in seq_of(np.array([a, b]), starts))
+    if qa > qb:
+        a, b, qa, qb = b, a, qb, qa
+    res.update(length=L, rank=k, seq_a=qa, pos_a=a - int(starts[qa]), seq_b=qb, pos_b=b - int(starts[qb]),
+               positions=sub["positions"])
+    return res
 
 
 # --------------------------------------------------------------------------

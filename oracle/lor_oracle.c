@@ -155,32 +155,59 @@ int oracle_suffix_array(const uint8_t *t, int64_t n, int32_t *sa, int nthreads)
 /* ---- LCP array (Section 3, LCP table: lcp[0] = 0) ------------------------ */
 
 typedef struct {
-    const uint8_t *t; int64_t n; const int32_t *sa; int32_t *lcp; int64_t lo, hi;
+    const uint8_t *t; int64_t n; const int32_t *sa; const int64_t *sa64; int32_t *lcp; int64_t lo, hi;
+    int too_long;
 } lcp_job;
+
+/* SA entry k of a job (int32 or int64 array). */
+static int64_t job_sa(const int32_t *sa, const int64_t *sa64, int64_t k)
+{
+    return sa64 ? sa64[k] : (int64_t)sa[k];
+}
 
 static void *lcp_worker(void *arg)
 {
     lcp_job *j = (lcp_job *)arg;
-    for (int64_t k = j->lo; k < j->hi; k++)
-        j->lcp[k] = (k == 0) ? 0
-                             : (int32_t)lcp_direct(j->t, j->n, j->sa[k - 1], j->sa[k]);
+    for (int64_t k = j->lo; k < j->hi; k++) {
+        int64_t h = (k == 0) ? 0
+                             : lcp_direct(j->t, j->n, job_sa(j->sa, j->sa64, k - 1), job_sa(j->sa, j->sa64, k));
+        if (h > INT32_MAX) { j->too_long = 1; h = INT32_MAX; }
+        j->lcp[k] = (int32_t)h;
+    }
     return NULL;
 }
 
-int oracle_lcp_array(const uint8_t *t, int64_t n, const int32_t *sa, int32_t *lcp,
-                     int nthreads)
+static int lcp_array_any(const uint8_t *t, int64_t n, const int32_t *sa, const int64_t *sa64, int32_t *lcp,
+                         int nthreads)
 {
-    if (n < 0 || (n > 0 && (!t || !sa || !lcp))) return -1;
+    if (n < 0 || (n > 0 && (!t || !(sa || sa64) || !lcp))) return -1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 64) nthreads = 64;
     pthread_t th[64];
     lcp_job jb[64];
     for (int c = 0; c < nthreads; c++) {
-        jb[c] = (lcp_job){t, n, sa, lcp, n * c / nthreads, n * (c + 1) / nthreads};
+        jb[c] = (lcp_job){t, n, sa, sa64, lcp, n * c / nthreads, n * (c + 1) / nthreads, 0};
         pthread_create(&th[c], NULL, lcp_worker, &jb[c]);
     }
-    for (int c = 0; c < nthreads; c++) pthread_join(th[c], NULL);
-    return 0;
+    int too_long = 0;
+    for (int c = 0; c < nthreads; c++) {
+        pthread_join(th[c], NULL);
+        too_long |= jb[c].too_long;
+    }
+    return too_long ? -2 : 0;
+}
+
+int oracle_lcp_array(const uint8_t *t, int64_t n, const int32_t *sa, int32_t *lcp,
+                     int nthreads)
+{
+    return lcp_array_any(t, n, sa, NULL, lcp, nthreads);
+}
+
+/* The same with an int64 suffix array (texts past 2^31 symbols); -2 when an
+ * LCP value does not fit int32. */
+int oracle_lcp_array64(const uint8_t *t, int64_t n, const int64_t *sa, int32_t *lcp, int nthreads)
+{
+    return lcp_array_any(t, n, NULL, sa, lcp, nthreads);
 }
 
 /* ---- check a given suffix array by direct comparison -------------------- */
@@ -191,7 +218,7 @@ int oracle_lcp_array(const uint8_t *t, int64_t n, const int32_t *sa, int32_t *lc
  * fails (k = n signals "not a permutation").
  */
 typedef struct {
-    const uint8_t *t; int64_t n; const int32_t *sa; int64_t lo, hi; int64_t bad;
+    const uint8_t *t; int64_t n; const int32_t *sa; const int64_t *sa64; int64_t lo, hi; int64_t bad;
 } chk_job;
 
 static void *chk_worker(void *arg)
@@ -199,19 +226,22 @@ static void *chk_worker(void *arg)
     chk_job *j = (chk_job *)arg;
     j->bad = -1;
     for (int64_t k = j->lo < 1 ? 1 : j->lo; k < j->hi; k++) {
-        if (suffix_cmp(j->t, j->n, j->sa[k - 1], j->sa[k]) >= 0) { j->bad = k; return NULL; }
+        if (suffix_cmp(j->t, j->n, job_sa(j->sa, j->sa64, k - 1), job_sa(j->sa, j->sa64, k)) >= 0) {
+            j->bad = k;
+            return NULL;
+        }
     }
     return NULL;
 }
 
-int64_t oracle_check_suffix_array(const uint8_t *t, int64_t n, const int32_t *sa,
-                                  int nthreads)
+static int64_t check_suffix_array_any(const uint8_t *t, int64_t n, const int32_t *sa, const int64_t *sa64,
+                                      int nthreads)
 {
     if (n <= 0) return -1;
     uint8_t *seen = (uint8_t *)calloc((size_t)n, 1);
     if (!seen) return n;
     for (int64_t k = 0; k < n; k++) {
-        int32_t p = sa[k];
+        int64_t p = job_sa(sa, sa64, k);
         if (p < 0 || p >= n || seen[p]) { free(seen); return n; }
         seen[p] = 1;
     }
@@ -221,7 +251,7 @@ int64_t oracle_check_suffix_array(const uint8_t *t, int64_t n, const int32_t *sa
     pthread_t th[64];
     chk_job jb[64];
     for (int c = 0; c < nthreads; c++) {
-        jb[c] = (chk_job){t, n, sa, n * c / nthreads, n * (c + 1) / nthreads, -1};
+        jb[c] = (chk_job){t, n, sa, sa64, n * c / nthreads, n * (c + 1) / nthreads, -1};
         pthread_create(&th[c], NULL, chk_worker, &jb[c]);
     }
     int64_t bad = -1;
@@ -232,6 +262,17 @@ int64_t oracle_check_suffix_array(const uint8_t *t, int64_t n, const int32_t *sa
     return bad;
 }
 
+int64_t oracle_check_suffix_array(const uint8_t *t, int64_t n, const int32_t *sa,
+                                  int nthreads)
+{
+    return check_suffix_array_any(t, n, sa, NULL, nthreads);
+}
+
+int64_t oracle_check_suffix_array64(const uint8_t *t, int64_t n, const int64_t *sa, int nthreads)
+{
+    return check_suffix_array_any(t, n, NULL, sa, nthreads);
+}
+
 /* ---- LCP of arbitrary suffix pairs (Section 3, lcp identity; direct) ---- */
 
 int oracle_lcp_pairs(const uint8_t *t, int64_t n, const int32_t *p, const int32_t *q,
@@ -240,6 +281,15 @@ int oracle_lcp_pairs(const uint8_t *t, int64_t n, const int32_t *p, const int32_
     for (int64_t i = 0; i < nq; i++) {
         if (p[i] < 0 || p[i] >= n || q[i] < 0 || q[i] >= n) return -1;
         out[i] = (int32_t)lcp_direct(t, n, p[i], q[i]);
+    }
+    return 0;
+}
+
+int oracle_lcp_pairs64(const uint8_t *t, int64_t n, const int64_t *p, const int64_t *q, int64_t nq, int64_t *out)
+{
+    for (int64_t i = 0; i < nq; i++) {
+        if (p[i] < 0 || p[i] >= n || q[i] < 0 || q[i] >= n) return -1;
+        out[i] = lcp_direct(t, n, p[i], q[i]);
     }
     return 0;
 }

@@ -10,4 +10,5 @@ from .lor import (  # noqa: F401
     lcp, load, longest_overlap, overlap_dict, profile_enable, profile_read, profile_reset,
     radix_sort_pairs, rmq_build, rmq_query, rmq_block_build, rmq_block_query, rmq_block_argmin, server_batch_bytes, workspace, tune_default, tune_get, tune_set,
     autotune_batch, multi_query_overlap, topk_overlaps,
+    encode_concat64, build_sa64, lcp64, longest_overlap64, overlap64_dict, rmq_block_query64,
 )

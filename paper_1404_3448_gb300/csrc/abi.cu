@@ -161,7 +161,7 @@ extern "C" int lor_device_status(lor_stream_t stream) {
     int (*fns[])(cudaStream_t, int) = {lor_status_encode, lor_status_dc3, lor_status_lcp,
                                        lor_status_overlap, lor_status_rmq, lor_status_abi,
                                        lor_status_batch, lor_status_serve, lor_status_multi,
-                                       lor_status_topk};
+                                       lor_status_topk, lor_status_sa64};
     for (auto f : fns) {
         const int v = f(s, 1);
         if (v != LOR_OK && first == LOR_OK) first = v;

@@ -352,6 +352,7 @@ int lor_status_batch(cudaStream_t s, int clear);
 int lor_status_serve(cudaStream_t s, int clear);
 int lor_status_multi(cudaStream_t s, int clear);
 int lor_status_topk(cudaStream_t s, int clear);
+int lor_status_sa64(cudaStream_t s, int clear);
 
 namespace lor {
 // Sparse-table rows 0..levels-1 over lcp[0..n) (rmq.cu); rows are

@@ -19,9 +19,10 @@ struct EncParams {
 constexpr int kEncThreads = 256;
 constexpr int kEncItems = 16;  // bytes per thread
 
+template <typename StT>
 __global__ void __launch_bounds__(kEncThreads) k_encode(const uint8_t *__restrict__ ascii, EncParams P,
                                                         uint8_t *__restrict__ text, int64_t n,
-                                                        int32_t *__restrict__ starts, int *status) {
+                                                        StT *__restrict__ starts, int *status) {
     __shared__ int64_t so[LOR_MAX_SEQ + 1];
     __shared__ uint8_t lut[256];
     const int nseq = P.nseq;
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint8_t *__restric
     }
     __syncthreads();
     const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (starts && gid <= nseq) starts[gid] = int32_t(so[gid]);
+    if (starts && gid <= nseq) starts[gid] = StT(so[gid]);
     const int64_t o0 = gid * kEncItems;
     if (o0 >= n) return;
     // sequence holding o0
@@ -73,8 +74,12 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint8_t *__restric
 
 using namespace lor;
 
-extern "C" int lor_encode_concat(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq,
-                                 uint8_t *d_text, int32_t *d_seq_starts, lor_stream_t stream) {
+namespace lor {
+namespace {
+
+template <typename StT>
+int encode_impl(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq, uint8_t *d_text, StT *d_seq_starts,
+                lor_stream_t stream, int64_t max_n) {
     if (nseq < 1 || nseq > LOR_MAX_SEQ || !h_lens || !d_text) return LOR_ERR_INVALID_ARG;
     EncParams P;
     P.nseq = nseq;
@@ -83,7 +88,7 @@ extern "C" int lor_encode_concat(const uint8_t *d_ascii, const int64_t *h_lens, 
         if (h_lens[i] < 0) return LOR_ERR_INVALID_ARG;
         P.out_start[i] = total;
         total += h_lens[i] + 1;
-        if (total > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+        if (total > max_n) return LOR_ERR_TOO_LARGE;
     }
     P.out_start[nseq] = total;
     if (total > nseq && !d_ascii) return LOR_ERR_INVALID_ARG;
@@ -93,9 +98,22 @@ extern "C" int lor_encode_concat(const uint8_t *d_ascii, const int64_t *h_lens, 
     const int64_t threads = cdiv(total, kEncItems) > nseq + 1 ? cdiv(total, kEncItems) : nseq + 1;
     {
         ProfScope ps(PK_ENCODE, double(total) * 2, s);
-        k_encode<<<unsigned(cdiv(threads, kEncThreads)), kEncThreads, 0, s>>>(d_ascii, P, d_text, total,
+        k_encode<StT><<<unsigned(cdiv(threads, kEncThreads)), kEncThreads, 0, s>>>(d_ascii, P, d_text, total,
                                                                                d_seq_starts, status);
     }
     LOR_LAUNCH_CHECK();
     return LOR_OK;
+}
+
+}  // namespace
+}  // namespace lor
+
+extern "C" int lor_encode_concat(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq, uint8_t *d_text,
+                                 int32_t *d_seq_starts, lor_stream_t stream) {
+    return encode_impl(d_ascii, h_lens, nseq, d_text, d_seq_starts, stream, LOR_MAX_N);
+}
+
+extern "C" int lor_encode_concat64(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq, uint8_t *d_text,
+                                   int64_t *d_seq_starts, lor_stream_t stream) {
+    return encode_impl(d_ascii, h_lens, nseq, d_text, d_seq_starts, stream, LOR_MAX_N64);
 }

@@ -214,6 +214,29 @@ __device__ __forceinline__ int64_t next_exc(const int32_t *__restrict__ lst, int
     return lo < cnt ? int64_t(lst[lo]) : n;
 }
 
+// lcp(T[i..], T[j..]) given that the first h symbols match: 32 symbols at a
+// time on the 2-bit copy, with the exception bitmap marking the symbols that
+// must be compared as bytes.
+__device__ __forceinline__ int64_t extend_bitmap(const uint8_t *__restrict__ t, const PackedText &T, int64_t n,
+                                                 int64_t i, int64_t j, int64_t h) {
+    while (i + h + 32 <= n && j + h + 32 <= n) {
+        const uint64_t d = window2(T.P, i + h) ^ window2(T.P, j + h);
+        const uint32_t e = window_exc(T.E, i + h) | window_exc(T.E, j + h);
+        const int dpos = d ? (__ffsll((long long)d) - 1) >> 1 : 32;
+        const int epos = e ? __ffs(int(e)) - 1 : 32;
+        if (dpos < epos) return h + dpos;
+        if (epos < 32) {
+            h += epos;
+            if (t[i + h] != t[j + h]) return h;
+            ++h;
+        } else {
+            h += 32;
+        }
+    }
+    while (i + h < n && j + h < n && t[i + h] == t[j + h]) ++h;
+    return h;
+}
+
 // Shared-memory index of position l of a tile: one pad word per 16, so that
 // the 16-position chunks of a warp's threads fall in different banks.
 __device__ __forceinline__ int chunk_slot(int l) { return l + (l >> 4); }
@@ -283,25 +306,7 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
                 ++h;
             }
         } else {
-            bool done = false;
-            while (!done && i + h + 32 <= n && j + h + 32 <= n) {
-                const uint64_t d = window2(P, i + h) ^ window2(P, j + h);
-                const uint32_t e = window_exc(T.E, i + h) | window_exc(T.E, j + h);
-                const int dpos = d ? (__ffsll((long long)d) - 1) >> 1 : 32;
-                const int epos = e ? __ffs(int(e)) - 1 : 32;
-                if (dpos < epos) {
-                    h += dpos;
-                    done = true;
-                } else if (epos < 32) {
-                    h += epos;
-                    if (t[i + h] != t[j + h]) done = true;
-                    else ++h;
-                } else {
-                    h += 32;
-                }
-            }
-            if (!done)
-                while (i + h < n && j + h < n && t[i + h] == t[j + h]) ++h;
+            h = extend_bitmap(t, T, n, i, j, h);
         }
         s_out[chunk_slot(l)] = int32_t(h);
         if (h > 0) --h;

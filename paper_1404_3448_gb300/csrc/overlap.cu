@@ -49,7 +49,8 @@ OvLayout ov_layout(int64_t n) {
 }
 
 // Sequence holding text position p: largest s with starts[s] <= p.
-__device__ __forceinline__ int seq_of(const int32_t *starts, int nseq, int32_t p) {
+template <typename StT, typename PT>
+__device__ __forceinline__ int seq_of(const StT *starts, int nseq, PT p) {
     int lo = 0, hi = nseq - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -60,8 +61,9 @@ __device__ __forceinline__ int seq_of(const int32_t *starts, int nseq, int32_t p
 }
 
 // Candidate rank k of the argmax: keeps the larger packed key.
-__device__ __forceinline__ void ov_consider(unsigned long long &my, const int32_t *sst, int nseq, int32_t a,
-                                           int32_t b, int32_t l, int64_t k) {
+template <typename StT, typename SaT>
+__device__ __forceinline__ void ov_consider(unsigned long long &my, const StT *sst, int nseq, SaT a, SaT b, int32_t l,
+                                           int64_t k) {
     if (uint32_t(l) < uint32_t(my >> 32)) return;  // cannot win: skip the sequence lookups
     if (seq_of(sst, nseq, a) != seq_of(sst, nseq, b)) {
         const unsigned long long key =
@@ -70,12 +72,14 @@ __device__ __forceinline__ void ov_consider(unsigned long long &my, const int32_
     }
 }
 
-// vec: SA and LCP are 16-byte aligned, so four ranks are read per load.
-__global__ void __launch_bounds__(256) k_ov_argmax(const int32_t *__restrict__ sa,
+// vec: SA and LCP are 16-byte aligned, so four ranks are read per load
+// (int32 suffix arrays only).
+template <typename SaT, typename StT>
+__global__ void __launch_bounds__(256) k_ov_argmax(const SaT *__restrict__ sa,
                                                    const int32_t *__restrict__ lcp, int64_t n,
-                                                   const int32_t *__restrict__ starts, int nseq, int vec,
+                                                   const StT *__restrict__ starts, int nseq, int vec,
                                                    unsigned long long *best) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ StT sst[LOR_MAX_SEQ + 1];
     __shared__ unsigned long long wbest[8];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
@@ -83,18 +87,20 @@ __global__ void __launch_bounds__(256) k_ov_argmax(const int32_t *__restrict__ s
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     int64_t k0 = 1;
-    if (vec) {
-        const int64_t nv = n / 4;
-        for (int64_t v = tid; v < nv; v += stride) {
-            const int4 s4 = reinterpret_cast<const int4 *>(sa)[v];
-            const int4 l4 = reinterpret_cast<const int4 *>(lcp)[v];
-            const int64_t k = 4 * v;
-            if (k > 0) ov_consider(my, sst, nseq, sa[k - 1], s4.x, l4.x, k);
-            ov_consider(my, sst, nseq, s4.x, s4.y, l4.y, k + 1);
-            ov_consider(my, sst, nseq, s4.y, s4.z, l4.z, k + 2);
-            ov_consider(my, sst, nseq, s4.z, s4.w, l4.w, k + 3);
+    if constexpr (sizeof(SaT) == 4) {
+        if (vec) {
+            const int64_t nv = n / 4;
+            for (int64_t v = tid; v < nv; v += stride) {
+                const int4 s4 = reinterpret_cast<const int4 *>(sa)[v];
+                const int4 l4 = reinterpret_cast<const int4 *>(lcp)[v];
+                const int64_t k = 4 * v;
+                if (k > 0) ov_consider(my, sst, nseq, sa[k - 1], s4.x, l4.x, k);
+                ov_consider(my, sst, nseq, s4.x, s4.y, l4.y, k + 1);
+                ov_consider(my, sst, nseq, s4.y, s4.z, l4.z, k + 2);
+                ov_consider(my, sst, nseq, s4.z, s4.w, l4.w, k + 3);
+            }
+            k0 = nv * 4 > 1 ? nv * 4 : 1;
         }
-        k0 = nv * 4 > 1 ? nv * 4 : 1;
     }
     for (int64_t k = k0 + tid; k < n; k += stride) ov_consider(my, sst, nseq, sa[k - 1], sa[k], lcp[k], k);
 #pragma unroll
@@ -164,12 +170,13 @@ __device__ __forceinline__ bool hit_starts_run(const uint32_t *hits, int64_t i) 
 
 // Run ids of the hits; a run qualifies when one of its hits pairs suffixes
 // of two sequences.
+template <typename SaT, typename StT>
 __global__ void __launch_bounds__(kScanThreads) k_ov_hit_runs(
-    const int32_t *__restrict__ sa, const uint32_t *__restrict__ hits, int64_t c,
-    const int32_t *__restrict__ starts, int nseq, uint32_t *__restrict__ run, uint8_t *__restrict__ qual,
+    const SaT *__restrict__ sa, const uint32_t *__restrict__ hits, int64_t c,
+    const StT *__restrict__ starts, int nseq, uint32_t *__restrict__ run, uint8_t *__restrict__ qual,
     uint32_t *n_runs, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
     int *status) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+    __shared__ StT sst[LOR_MAX_SEQ + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
     tile_names(
@@ -183,9 +190,10 @@ __global__ void __launch_bounds__(kScanThreads) k_ov_hit_runs(
 }
 
 // Members of qualifying runs in rank order: a run's first hit k adds SA[k-1]
-// and SA[k], every other hit adds SA[k].
+// and SA[k], every other hit adds SA[k] (positions < 2^32 as uint32).
+template <typename SaT>
 __global__ void __launch_bounds__(kScanThreads) k_ov_hit_members(
-    const int32_t *__restrict__ sa, const uint32_t *__restrict__ hits, int64_t c,
+    const SaT *__restrict__ sa, const uint32_t *__restrict__ hits, int64_t c,
     const uint32_t *__restrict__ run, const uint8_t *__restrict__ qual, uint32_t *__restrict__ out,
     uint32_t *count, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
     int *status, int64_t ntiles) {
@@ -231,42 +239,48 @@ __global__ void __launch_bounds__(kScanThreads) k_ov_hit_members(
     }
 }
 
-__global__ void k_ov_result(const int32_t *__restrict__ sa, const int32_t *__restrict__ starts, int nseq,
-                            const unsigned long long *best, const uint32_t *count, lor_overlap *out) {
-    __shared__ int32_t sst[LOR_MAX_SEQ + 1];
+// OutT: lor_overlap (int32 fields) or lor_overlap64 (int64 rank, offsets
+// and count).
+template <typename SaT, typename StT, typename OutT>
+__global__ void k_ov_result(const SaT *__restrict__ sa, const StT *__restrict__ starts, int nseq,
+                            const unsigned long long *best, const uint32_t *count, OutT *out) {
+    __shared__ StT sst[LOR_MAX_SEQ + 1];
     for (int i = threadIdx.x; i <= nseq; i += blockDim.x) sst[i] = starts[i];
     __syncthreads();
     if (threadIdx.x != 0) return;
-    lor_overlap r;
+    OutT r;
     const unsigned long long b = *best;
     const int32_t L = int32_t(b >> 32);
     r.reserved = 0;
     if (L <= 0) {
         r.length = 0;
-        r.rank = r.seq_a = r.pos_a = r.seq_b = r.pos_b = -1;
+        r.rank = -1;
+        r.seq_a = r.seq_b = -1;
+        r.pos_a = r.pos_b = -1;
         r.n_pos = 0;
     } else {
         const int64_t k = int64_t(0xFFFFFFFFull - (b & 0xFFFFFFFFull));
-        int32_t a = sa[k - 1], c = sa[k];
+        SaT a = sa[k - 1], c = sa[k];
         int sa_ = seq_of(sst, nseq, a), sc_ = seq_of(sst, nseq, c);
         if (sa_ > sc_) {
-            const int32_t t = a; a = c; c = t;
+            const SaT t = a; a = c; c = t;
             const int u = sa_; sa_ = sc_; sc_ = u;
         }
         r.length = L;
-        r.rank = int32_t(k);
+        r.rank = decltype(r.rank)(k);
         r.seq_a = sa_;
-        r.pos_a = a - sst[sa_];
+        r.pos_a = decltype(r.pos_a)(a - sst[sa_]);
         r.seq_b = sc_;
-        r.pos_b = c - sst[sc_];
-        r.n_pos = int32_t(*count);
+        r.pos_b = decltype(r.pos_b)(c - sst[sc_]);
+        r.n_pos = decltype(r.n_pos)(*count);
     }
     *out = r;
 }
 
-__global__ void k_copy_u32_i32(const uint32_t *__restrict__ src, int32_t *__restrict__ dst, int64_t m) {
+template <typename PosT>
+__global__ void k_copy_u32(const uint32_t *__restrict__ src, PosT *__restrict__ dst, int64_t m) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < m) dst[i] = int32_t(src[i]);
+    if (i < m) dst[i] = PosT(src[i]);
 }
 
 }  // namespace
@@ -279,14 +293,17 @@ extern "C" size_t lor_longest_overlap_workspace_size(int64_t n) {
     return ov_layout(n).total;
 }
 
-extern "C" int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, int64_t n,
-                                   const int32_t *d_seq_starts, int32_t nseq, lor_overlap *d_out,
-                                   int32_t *d_pos, int64_t pos_cap, void *d_ws, size_t ws_bytes,
-                                   lor_stream_t stream) {
+namespace lor {
+namespace {
+
+template <typename SaT, typename StT, typename OutT, typename PosT>
+int longest_overlap_impl(const SaT *d_sa, const int32_t *d_lcp, int64_t n, const StT *d_seq_starts, int32_t nseq,
+                         OutT *d_out, PosT *d_pos, int64_t pos_cap, void *d_ws, size_t ws_bytes,
+                         lor_stream_t stream, int64_t max_n) {
     if (!d_sa || !d_lcp || !d_seq_starts || !d_out || n < 1 || pos_cap < 0) return LOR_ERR_INVALID_ARG;
     if (nseq < 1 || nseq > LOR_MAX_SEQ) return LOR_ERR_INVALID_ARG;
     if (pos_cap > 0 && !d_pos) return LOR_ERR_INVALID_ARG;
-    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    if (n > max_n) return LOR_ERR_TOO_LARGE;
     const OvLayout L = ov_layout(n);
     if (!d_ws || ws_bytes < L.total || (uintptr_t(d_ws) & 255)) return LOR_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -315,8 +332,8 @@ extern "C" int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, in
     {
         ProfScope ps(PK_OVERLAP_SCAN, double(n) * 8, s);
         const unsigned grid = unsigned(min64(cdiv(n, 1024), 152 * 16));
-        const int vec = ((uintptr_t(d_sa) | uintptr_t(d_lcp)) & 15) == 0;
-        k_ov_argmax<<<grid, 256, 0, s>>>(d_sa, d_lcp, n, d_seq_starts, nseq, vec, best);
+        const int vec = sizeof(SaT) == 4 && ((uintptr_t(d_sa) | uintptr_t(d_lcp)) & 15) == 0;
+        k_ov_argmax<SaT, StT><<<grid, 256, 0, s>>>(d_sa, d_lcp, n, d_seq_starts, nseq, vec, best);
     }
     LOR_LAUNCH_CHECK();
     {
@@ -344,13 +361,13 @@ extern "C" int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, in
         {
             ProfScope ps(PK_OVERLAP_COLLECT, double(c) * 21, s);
             rs.epoch++;
-            k_ov_hit_runs<<<unsigned(ct), kScanThreads, 0, s>>>(d_sa, hits, c, d_seq_starts, nseq, run, qual,
+            k_ov_hit_runs<SaT, StT><<<unsigned(ct), kScanThreads, 0, s>>>(d_sa, hits, c, d_seq_starts, nseq, run, qual,
                                                                n_runs, rs.lookback, rs.tile_ctr, rs.tile_base,
                                                                rs.epoch, status);
             LOR_LAUNCH_CHECK();
             rs.tile_base += (unsigned long long)ct;
             rs.epoch++;
-            k_ov_hit_members<<<unsigned(ct), kScanThreads, 0, s>>>(d_sa, hits, c, run, qual, ka, count,
+            k_ov_hit_members<SaT><<<unsigned(ct), kScanThreads, 0, s>>>(d_sa, hits, c, run, qual, ka, count,
                                                                   rs.lookback, rs.tile_ctr, rs.tile_base,
                                                                   rs.epoch, status, ct);
             LOR_LAUNCH_CHECK();
@@ -368,12 +385,36 @@ extern "C" int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, in
         const int rc = radix_sort_pairs<uint32_t>(rs, ka, va, kb, vb, m, 0, bits, true, &kr, &vr);
         if (rc) return rc;
     }
-    k_ov_result<<<1, 256, 0, s>>>(d_sa, d_seq_starts, nseq, best, count, d_out);
+    k_ov_result<SaT, StT, OutT><<<1, 256, 0, s>>>(d_sa, d_seq_starts, nseq, best, count, d_out);
     LOR_LAUNCH_CHECK();
     const int64_t ncopy = m < pos_cap ? m : pos_cap;
     if (ncopy > 0) {
-        k_copy_u32_i32<<<unsigned(cdiv(ncopy, 256)), 256, 0, s>>>(kr, d_pos, ncopy);
+        k_copy_u32<PosT><<<unsigned(cdiv(ncopy, 256)), 256, 0, s>>>(kr, d_pos, ncopy);
         LOR_LAUNCH_CHECK();
     }
     return LOR_OK;
+}
+
+}  // namespace
+}  // namespace lor
+
+extern "C" int lor_longest_overlap(const int32_t *d_sa, const int32_t *d_lcp, int64_t n,
+                                   const int32_t *d_seq_starts, int32_t nseq, lor_overlap *d_out,
+                                   int32_t *d_pos, int64_t pos_cap, void *d_ws, size_t ws_bytes,
+                                   lor_stream_t stream) {
+    return longest_overlap_impl(d_sa, d_lcp, n, d_seq_starts, nseq, d_out, d_pos, pos_cap, d_ws, ws_bytes, stream,
+                                LOR_MAX_N);
+}
+
+extern "C" size_t lor_longest_overlap64_workspace_size(int64_t n) {
+    if (n < 1 || n > LOR_MAX_N64) return 0;
+    return ov_layout(n).total;
+}
+
+extern "C" int lor_longest_overlap64(const int64_t *d_sa, const int32_t *d_lcp, int64_t n,
+                                     const int64_t *d_seq_starts, int32_t nseq, lor_overlap64 *d_out,
+                                     int64_t *d_pos, int64_t pos_cap, void *d_ws, size_t ws_bytes,
+                                     lor_stream_t stream) {
+    return longest_overlap_impl(d_sa, d_lcp, n, d_seq_starts, nseq, d_out, d_pos, pos_cap, d_ws, ws_bytes, stream,
+                                LOR_MAX_N64);
 }

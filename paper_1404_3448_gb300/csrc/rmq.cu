@@ -180,33 +180,36 @@ __global__ void k_rmqb_blockmin(const int32_t *__restrict__ lcp, int64_t n, int6
 }
 
 
+// IdxT: int32 or int64 ISA and query positions; OutT: int32 or int64 answers
+// (p == q answers the suffix length n - p, which needs 64 bits past 2^31).
+template <typename IdxT, typename OutT>
 __global__ void k_rmqb_query(const int32_t *__restrict__ table, int64_t stride, const int32_t *__restrict__ lcp,
-                             const int32_t *__restrict__ isa, int64_t n, const int32_t *__restrict__ P,
-                             const int32_t *__restrict__ Q, int64_t nq, int32_t *__restrict__ out, int *status) {
+                             const IdxT *__restrict__ isa, int64_t n, const IdxT *__restrict__ P,
+                             const IdxT *__restrict__ Q, int64_t nq, OutT *__restrict__ out, int *status) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= nq) return;
-    const int32_t p = P[i], q = Q[i];
+    const int64_t p = P[i], q = Q[i];
     if (p < 0 || p >= n || q < 0 || q >= n) {
         atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
         out[i] = -1;
         return;
     }
     if (p == q) {
-        out[i] = int32_t(n - p);
+        out[i] = OutT(n - p);
         return;
     }
-    int32_t r1 = isa[p], r2 = isa[q];
+    int64_t r1 = isa[p], r2 = isa[q];
     if (r1 < 0 || r1 >= n || r2 < 0 || r2 >= n || r1 == r2) {
         atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
         out[i] = -1;
         return;
     }
     if (r1 > r2) {
-        const int32_t tmp = r1;
+        const int64_t tmp = r1;
         r1 = r2;
         r2 = tmp;
     }
-    out[i] = rmqb_range_min(table, stride, lcp, int64_t(r1) + 1, r2);
+    out[i] = OutT(rmqb_range_min(table, stride, lcp, r1 + 1, r2));
 }
 
 // First index in [a, b] (one block) holding the value v, or -1.
@@ -311,7 +314,7 @@ extern "C" int lor_rmq_block_argmin(const int32_t *d_table, const int32_t *d_lcp
 }
 
 extern "C" int64_t lor_rmq_block_table_elems(int64_t n) {
-    if (n < 1 || n > LOR_MAX_N) return 0;
+    if (n < 1 || n > LOR_MAX_N64) return 0;
     const int64_t nb = rmqb_blocks(n);
     return int64_t(levels_for(nb)) * row_stride(nb);
 }
@@ -333,7 +336,7 @@ int lor::rmq_block_levels(const int32_t *d_lcp, int64_t n, int levels, int32_t *
 extern "C" int lor_rmq_block_build(const int32_t *d_lcp, int64_t n, int32_t *d_table, int64_t table_elems,
                                    lor_stream_t stream) {
     if (!d_lcp || !d_table || n < 1) return LOR_ERR_INVALID_ARG;
-    if (n > LOR_MAX_N) return LOR_ERR_TOO_LARGE;
+    if (n > LOR_MAX_N64) return LOR_ERR_TOO_LARGE;
     if (table_elems < lor_rmq_block_table_elems(n)) return LOR_ERR_WORKSPACE;
     if (uintptr_t(d_table) & 255) return LOR_ERR_INVALID_ARG;
     return rmq_block_levels(d_lcp, n, levels_for(rmqb_blocks(n)), d_table, (cudaStream_t)stream);
@@ -351,7 +354,7 @@ extern "C" int lor_rmq_block_query(const int32_t *d_table, const int32_t *d_lcp,
     if (!status) return LOR_ERR_CUDA;
     {
         ProfScope ps(PK_RMQ_QUERY, double(nq) * (4 + 4 + 4 + 4 + 4 + 4 + 4 + 4), s);
-        k_rmqb_query<<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(d_table, row_stride(rmqb_blocks(n)), d_lcp, d_isa, n,
+        k_rmqb_query<int32_t, int32_t><<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(d_table, row_stride(rmqb_blocks(n)), d_lcp, d_isa, n,
                                                              d_p, d_q, nq, d_out, status);
     }
     LOR_LAUNCH_CHECK();
@@ -416,6 +419,25 @@ extern "C" int lor_rmq_query(const int32_t *d_table, const int32_t *d_isa, int64
         ProfScope ps(PK_RMQ_QUERY, double(nq) * (4 + 4 + 4 + 4 + 4 + 4 + 4), s);
         k_rmq_query<<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(d_table, row_stride(n), d_isa, n, d_p, d_q,
                                                             nq, d_out, status);
+    }
+    LOR_LAUNCH_CHECK();
+    return LOR_OK;
+}
+
+extern "C" int lor_rmq_block_query64(const int32_t *d_table, const int32_t *d_lcp, const int64_t *d_isa, int64_t n,
+                                     const int64_t *d_p, const int64_t *d_q, int64_t nq, int64_t *d_out,
+                                     lor_stream_t stream) {
+    if (!d_table || !d_lcp || !d_isa || n < 1 || nq < 0) return LOR_ERR_INVALID_ARG;
+    if (nq == 0) return LOR_OK;
+    if (!d_p || !d_q || !d_out) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_MAX_N64) return LOR_ERR_TOO_LARGE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *status = tu_status_ptr();
+    if (!status) return LOR_ERR_CUDA;
+    {
+        ProfScope ps(PK_RMQ_QUERY, double(nq) * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8), s);
+        k_rmqb_query<int64_t, int64_t><<<unsigned(cdiv(nq, 256)), 256, 0, s>>>(
+            d_table, row_stride(rmqb_blocks(n)), d_lcp, d_isa, n, d_p, d_q, nq, d_out, status);
     }
     LOR_LAUNCH_CHECK();
     return LOR_OK;

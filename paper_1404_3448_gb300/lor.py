@@ -30,6 +30,8 @@ LOR_ERR_CANCELLED = -8
 LOR_MAX_SEQ = 250
 
 OVERLAP_FIELDS = ("length", "rank", "seq_a", "pos_a", "seq_b", "pos_b", "n_pos", "reserved")
+LOR_MAX_N = 2147483000
+LOR_MAX_N64 = 4294901760
 
 _lib = None
 
@@ -88,6 +90,14 @@ def load():
         "lor_rmq_block_argmin": ([vp, vp, vp, i64, vp, vp, i64, vp, vp, vp], ctypes.c_int),
         "lor_radix_sort_workspace_size": ([i64], sz),
         "lor_radix_sort_pairs": ([vp, vp, i64, i32, vp, sz, vp], ctypes.c_int),
+        "lor_encode_concat64": ([vp, vp, i32, vp, vp, vp], ctypes.c_int),
+        "lor_build_sa64_workspace_size": ([i64, i32], sz),
+        "lor_build_sa64": ([vp, i64, i32, vp, vp, sz, vp], ctypes.c_int),
+        "lor_lcp64_workspace_size": ([i64], sz),
+        "lor_lcp64": ([vp, vp, i64, vp, vp, vp, sz, vp], ctypes.c_int),
+        "lor_longest_overlap64_workspace_size": ([i64], sz),
+        "lor_longest_overlap64": ([vp, vp, i64, vp, i32, vp, vp, i64, vp, sz, vp], ctypes.c_int),
+        "lor_rmq_block_query64": ([vp, vp, vp, i64, vp, vp, i64, vp, vp], ctypes.c_int),
         "lor_device_status": ([vp], ctypes.c_int),
         "lor_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lor_launch_count": ([], ctypes.c_uint64),
@@ -683,6 +693,100 @@ def rmq_query(table, isa, p, q, out=None, stream=None) -> torch.Tensor:
                        _ptr(p, torch.int32, "p"), _ptr(q, torch.int32, "q"), nq,
                        _ptr(out, torch.int32, "out"), _stream(stream))
     _check(rc, "lor_rmq_query")
+    return out
+
+
+# ------------------------------------------------- 64-bit indices (*64 calls)
+
+def encode_concat64(ascii_dev: torch.Tensor, lens, stream=None):
+    """As encode_concat, with int64 sequence starts (lor_encode_concat64)."""
+    lens = np.ascontiguousarray(np.asarray(lens, dtype=np.int64))
+    nseq = int(lens.size)
+    n = int(lens.sum()) + nseq
+    dev = ascii_dev.device
+    text = torch.empty(n, dtype=torch.uint8, device=dev)
+    starts = torch.empty(nseq + 1, dtype=torch.int64, device=dev)
+    rc = load().lor_encode_concat64(_ptr(ascii_dev, torch.uint8, "ascii") if ascii_dev.numel() else None,
+                                    lens.ctypes.data, nseq, _ptr(text), _ptr(starts), _stream(stream))
+    _check(rc, "lor_encode_concat64")
+    return text, starts, nseq + 5
+
+
+def build_sa64(text: torch.Tensor, sigma: int, sa=None, ws=None, stream=None) -> torch.Tensor:
+    """int64 suffix array (lor_build_sa64)."""
+    n = text.numel()
+    if sa is None:
+        sa = torch.empty(n, dtype=torch.int64, device=text.device)
+    need = load().lor_build_sa64_workspace_size(n, sigma)
+    if need == 0:
+        raise LorError(LOR_ERR_TOO_LARGE if n > LOR_MAX_N64 else LOR_ERR_INVALID_ARG, "lor_build_sa64")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, text.device)
+    rc = load().lor_build_sa64(_ptr(text, torch.uint8, "text"), n, sigma, _ptr(sa, torch.int64, "sa"),
+                               ws.data_ptr(), ws.numel(), _stream(stream))
+    _check(rc, "lor_build_sa64")
+    return sa
+
+
+def lcp64(text: torch.Tensor, sa: torch.Tensor, isa=None, lcp_out=None, ws=None, stream=None):
+    """(int64 ISA, int32 LCP) from an int64 suffix array (lor_lcp64)."""
+    n = text.numel()
+    if isa is None:
+        isa = torch.empty(n, dtype=torch.int64, device=text.device)
+    if lcp_out is None:
+        lcp_out = torch.empty(n, dtype=torch.int32, device=text.device)
+    need = load().lor_lcp64_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, text.device)
+    rc = load().lor_lcp64(_ptr(text, torch.uint8, "text"), _ptr(sa, torch.int64, "sa"), n,
+                          _ptr(isa, torch.int64, "isa"), _ptr(lcp_out, torch.int32, "lcp"), ws.data_ptr(),
+                          ws.numel(), _stream(stream))
+    _check(rc, "lor_lcp64")
+    return isa, lcp_out
+
+
+OVERLAP64_FIELDS = ("length", "seq_a", "seq_b", "reserved", "rank", "pos_a", "pos_b", "n_pos")
+
+
+def longest_overlap64(sa, lcp_arr, seq_starts, nseq, pos_cap=1 << 16, out=None, pos=None, ws=None, stream=None):
+    """(out: 48-byte lor_overlap64 as a uint8 device tensor, pos: int64 device
+    tensor of pos_cap entries) (lor_longest_overlap64)."""
+    n = sa.numel()
+    if out is None:
+        out = torch.empty(48, dtype=torch.uint8, device=sa.device)
+    if pos is None:
+        pos = torch.empty(max(int(pos_cap), 1), dtype=torch.int64, device=sa.device)
+    need = load().lor_longest_overlap64_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, sa.device)
+    rc = load().lor_longest_overlap64(_ptr(sa, torch.int64, "sa"), _ptr(lcp_arr, torch.int32, "lcp"), n,
+                                      _ptr(seq_starts, torch.int64, "seq_starts"), int(nseq), _ptr(out),
+                                      _ptr(pos, torch.int64, "pos"), int(pos_cap), ws.data_ptr(), ws.numel(),
+                                      _stream(stream))
+    _check(rc, "lor_longest_overlap64")
+    return out, pos
+
+
+def overlap64_dict(out: torch.Tensor, pos: torch.Tensor) -> dict:
+    """Host view of a lor_overlap64 result, keyed like overlap_dict."""
+    raw = out.cpu().numpy().tobytes()
+    head = np.frombuffer(raw[:16], dtype=np.int32).tolist()
+    tail = np.frombuffer(raw[16:48], dtype=np.int64).tolist()
+    d = dict(zip(OVERLAP64_FIELDS, head + tail))
+    k = min(d["n_pos"], pos.numel())
+    d["positions"] = pos[:k].cpu().numpy().astype(np.int64)
+    return d
+
+
+def rmq_block_query64(table, lcp_arr, isa, p, q, out=None, stream=None) -> torch.Tensor:
+    """LCP of suffix pairs of a 64-bit text through its block table
+    (lor_rmq_block_query64): int64 ISA, positions and answers."""
+    if out is None:
+        out = torch.empty(p.numel(), dtype=torch.int64, device=p.device)
+    _check(load().lor_rmq_block_query64(_ptr(table, torch.int32, "table"), _ptr(lcp_arr, torch.int32, "lcp"),
+                                        _ptr(isa, torch.int64, "isa"), isa.numel(), _ptr(p, torch.int64, "p"),
+                                        _ptr(q, torch.int64, "q"), p.numel(), _ptr(out, torch.int64, "out"),
+                                        _stream(stream)), "lor_rmq_block_query64")
     return out
 
 

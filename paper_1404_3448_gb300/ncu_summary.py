@@ -38,7 +38,9 @@ KINDS = [
     ("k_isa_phi", "isa_scatter"), ("k_scatter_isa_phi", "isa_scatter"),
     ("k_text_max", "kasai"), ("k_pack_text", "kasai"), ("k_sort_exc", "kasai"), ("k_plcp", "kasai"),
     ("k_lcp_", "kasai"),
-    ("k_ov_argmax", "overlap_scan"), ("k_ov_", "overlap_collect"), ("k_copy_u32_i32", "overlap_collect"),
+    ("k_ov_argmax", "overlap_scan"), ("k_ov_", "overlap_collect"), ("k_copy_u32", "overlap_collect"),
+    ("k_sa64_keys0", "sample_keys"), ("k_sa64_round_keys", "sample_keys"), ("k_sa64_names", "naming"),
+    ("k_sa64_settle", "rank_scatter"), ("k_narrow_sa64", "isa_scatter"),
     ("k_rmq_query", "rmq_query"), ("k_rmqb_query", "rmq_query"), ("k_rmq_", "rmq_level"),
     ("k_rmqb_", "rmq_level"),
 ]

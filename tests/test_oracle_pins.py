@@ -428,3 +428,62 @@ def test_encode_concat_codes_and_errors(oracle_mod):
     assert starts.tolist() == [0, 3, 6] and sigma == 7
     with pytest.raises(ValueError):
         oracle_mod.encode_concat([b"ACN", b"GT"])
+
+
+# ---------------------------------------------------------------- int64 index variants
+
+def test_int64_checks_against_python_string_order(oracle_mod):
+    # brute force: Python's string order and os.path.commonprefix
+    for s in ["GATTACA", "AAAAAA", "ACACAC", "TGCATGCA", "CAGTTGAC"]:
+        text, _ = oracle_mod.encode_raw(s.encode())
+        ref = sorted(range(len(s)), key=lambda i: s[i:])
+        sa = np.array(ref, np.int64)
+        assert oracle_mod.check_suffix_array64(text, sa) == -1
+        ref_lcp = [0] + [len(os.path.commonprefix([s[ref[k - 1]:], s[ref[k]:]])) for k in range(1, len(s))]
+        assert oracle_mod.lcp_array64(text, sa).tolist() == ref_lcp
+        p = np.array([i for i in range(len(s)) for _ in range(len(s))], np.int64)
+        q = np.array([j for _ in range(len(s)) for j in range(len(s))], np.int64)
+        ref_q = [len(os.path.commonprefix([s[i:], s[j:]])) for i, j in zip(p.tolist(), q.tolist())]
+        assert oracle_mod.lcp_pairs64(text, p, q).tolist() == ref_q
+
+
+def test_int64_check_rejects_wrong_arrays(oracle_mod):
+    seqs, _ = gen.pair_uniform(n_each=700, plant_len=40, seed=4)
+    text, _, _ = oracle_mod.encode_concat(seqs)
+    sa = oracle_mod.suffix_array(text).astype(np.int64)
+    assert oracle_mod.check_suffix_array64(text, sa, nthreads=3) == -1
+    bad = sa.copy()
+    bad[20], bad[21] = bad[21], bad[20]
+    assert oracle_mod.check_suffix_array64(text, bad) == 21
+    dup = sa.copy()
+    dup[5] = dup[6]
+    assert oracle_mod.check_suffix_array64(text, dup) == len(text)
+    wide = sa.copy()
+    wide[0] = 2**32 + int(sa[0])  # would alias sa[0] if truncated to 32 bits
+    assert oracle_mod.check_suffix_array64(text, wide) == len(text)
+
+
+def test_longest_overlap_large_against_dp(oracle_mod):
+    # the scan-and-runs form gives the record and positions the DP fixes
+    for seed in range(80):
+        nseq = 2 if seed % 3 else 3
+        alpha = [b"ACGT", b"AC", b"A", b"GT"][seed % 4]
+        seqs = gen.fuzz_sequences(5000 + seed, nseq=nseq, max_len=40, alphabet=alpha)
+        text, starts, _ = oracle_mod.encode_concat(seqs)
+        sa = oracle_mod.suffix_array(text)
+        lcp = oracle_mod.lcp_array(text, sa)
+        got = oracle_mod.longest_overlap_large(text, sa.astype(np.int64), lcp, starts)
+        exp = _check_overlap_vs_dp(oracle_mod, seqs)
+        for k in ("length", "rank", "seq_a", "pos_a", "seq_b", "pos_b"):
+            assert got[k] == exp[k], (seed, k)
+        assert got["positions"].tolist() == exp["positions"].tolist(), seed
+
+
+def test_overlap_max_scan_chunks_do_not_change_the_answer(oracle_mod):
+    seqs, _ = gen.pair_noncoding(n_each=30_000, seed=9, shared_len=2000, core=400)
+    text, starts, _ = oracle_mod.encode_concat(seqs)
+    sa = oracle_mod.suffix_array(text, nthreads=4)
+    lcp = oracle_mod.lcp_array(text, sa, nthreads=4)
+    ov = oracle_mod.longest_overlap(text, sa, lcp, starts)
+    for chunk in (1, 7, 4096, 1 << 24):
+        assert oracle_mod.overlap_max_scan(sa, lcp, starts, chunk=chunk) == (ov["length"], ov["rank"])
