@@ -431,6 +431,73 @@ def multi_query_run(nq, steps, warmup, dev, ref_len=1 << 24, seed=140434487):
     }
 
 
+# --------------------------------------------------------------------------- 64-bit indices
+
+def int64_run(n_each, steps, warmup, dev):
+    """The 64-bit index path (lor_encode_concat64 once, then per step
+    lor_build_sa64, lor_lcp64 and lor_longest_overlap64) on two uniform
+    sequences whose concatenation passes 2^31 symbols.  One workspace serves
+    the suffix array and the LCP call (they run one after the other)."""
+    import torch
+    import lor_inputs as gen
+    import paper_1404_3448_gb300 as lor
+    C = lor.lor.load()
+    seqs, info = gen.pair_int64(n_each=n_each)
+    lens = [len(x) for x in seqs]
+    ascii_dev = torch.from_numpy(np.concatenate(seqs)).to(dev)
+    del seqs
+    text, starts, sigma = lor.encode_concat64(ascii_dev, lens)
+    del ascii_dev
+    n = text.numel()
+    need = max(C.lor_build_sa64_workspace_size(n, sigma), C.lor_lcp64_workspace_size(n),
+               C.lor_longest_overlap64_workspace_size(n))
+    ws = lor.workspace(need, dev)
+    sa = torch.empty(n, dtype=torch.int64, device=dev)
+    isa = torch.empty(n, dtype=torch.int64, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    out = torch.empty(48, dtype=torch.uint8, device=dev)
+    pos = torch.empty(1 << 16, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        lor.build_sa64(text, sigma, sa=sa, ws=ws)
+        if evs:
+            evs[1].record(stream)
+        lor.lcp64(text, sa, isa=isa, lcp_out=lcp, ws=ws)
+        if evs:
+            evs[2].record(stream)
+        lor.longest_overlap64(sa, lcp, starts, 2, pos_cap=pos.numel(), out=out, pos=pos, ws=ws)
+        if evs:
+            evs[3].record(stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    lor.check_device(where="int64 warmup")
+    parts = np.zeros(3)
+    for _ in range(steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        step(evs)
+        torch.cuda.synchronize(dev)
+        parts += [evs[i].elapsed_time(evs[i + 1]) for i in range(3)]
+    lor.check_device(where="int64 steps")
+    parts /= steps
+    ms = float(parts.sum())
+    rec = lor.overlap64_dict(out, pos)
+    del ws, sa, isa, lcp, text
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"2x{n_each} iid-uniform DNA (n={n}, past 2^31) with one 500-base plant, the copy in the "
+                    f"second sequence past text position 2^31; int64 SA/ISA, int32 LCP",
+        "n": n, "input_bases": int(sum(lens)), "steps": steps, "ms_per_step": ms,
+        "value": sum(lens) / (ms / 1000.0), "unit": UNIT,
+        "stage_ms": {"build_sa64": float(parts[0]), "lcp64": float(parts[1]), "overlap64": float(parts[2])},
+        "overlap": {"length": int(rec["length"]), "n_pos": int(rec["n_pos"])},
+    }
+
+
 # --------------------------------------------------------------------------- served
 
 def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed=140434485):
@@ -711,6 +778,9 @@ def run_lor(args):
         if args.multi_queries > 0:
             torch.cuda.empty_cache()
             line["multi_query"] = multi_query_run(args.multi_queries, 3, 1, dev)
+        if args.int64_bases > 0:
+            torch.cuda.empty_cache()
+            line["int64"] = int64_run(args.int64_bases // 2, 2, 1, dev)
         if args.serve_seconds > 0:
             torch.cuda.empty_cache()
             line["serving"] = serving(args.serve_seconds, args.serve_rate, args.serve_pool, args.serve_workers,
@@ -734,6 +804,8 @@ def main():
                     help="pairs of the batched-vs-plain sub-measurement (0 skips it)")
     ap.add_argument("--multi-queries", type=int, default=65_536,
                     help="queries of the one-reference-many-queries sub-measurement (0 skips it)")
+    ap.add_argument("--int64-bases", type=int, default=2 * ((1 << 30) + (1 << 15)),
+                    help="input bases of the 64-bit index sub-measurement (past 2^31 symbols; 0 skips it)")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson arrivals of the served sub-measurement (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="pair requests per second")
