@@ -146,11 +146,14 @@ __global__ void __launch_bounds__(256) k_sample_keys(const CharT *__restrict__ s
 constexpr int kKeyTile = 2048;
 constexpr int kKeyMaxChars = 64;
 
+// The key is formed by Horner's rule over 32-bit chunks of `chunk` symbols
+// (radix^chunk <= 2^32), the chunks joined with one 64-bit multiply-add each.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_sample_keys0(const uint8_t *__restrict__ s, int64_t n, int64_t n0,
-                                                      int64_t n2, int kchars, uint32_t radix, int64_t maxc,
-                                                      KeyT *__restrict__ keys, int npasses, int end_bit,
-                                                      int dbits, uint32_t *__restrict__ hist, int *status) {
+                                                      int64_t n2, int kchars, int chunk, uint32_t radix,
+                                                      int64_t maxc, KeyT *__restrict__ keys, int npasses,
+                                                      int end_bit, int dbits, uint32_t *__restrict__ hist,
+                                                      int *status) {
     __shared__ uint8_t txt[3 * kKeyTile + kKeyMaxChars];
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     const int tid = threadIdx.x;
@@ -181,11 +184,25 @@ __global__ void __launch_bounds__(256) k_sample_keys0(const uint8_t *__restrict_
     }
     __syncthreads();
     KeyT *out = keys + (cls == 0 ? 0 : n0) + j0;
+    const int tail = kchars % chunk;
+    uint64_t pw_chunk = 1, pw_tail = 1;
+    for (int t = 0; t < chunk; ++t) pw_chunk *= radix;
+    for (int t = 0; t < tail; ++t) pw_tail *= radix;
     for (int k = tid; k < nj; k += 256) {
         const uint8_t *w = txt + 3 * k;
-        KeyT key = 0;
-        for (int t = 0; t < kchars; ++t) key = key * KeyT(radix) + KeyT(w[t]);
-        out[k] = key;
+        uint64_t key = 0;
+        int t = 0;
+        for (; t + chunk <= kchars; t += chunk) {
+            uint32_t part = 0;
+            for (int u = 0; u < chunk; ++u) part = part * radix + w[t + u];
+            key = key * pw_chunk + part;
+        }
+        if (tail) {
+            uint32_t part = 0;
+            for (int u = 0; u < tail; ++u) part = part * radix + w[t + u];
+            key = key * pw_tail + part;
+        }
+        out[k] = KeyT(key);
         if (hist)
             for (int p = 0; p < npasses; ++p) {
                 const int sft = p * dbits;
@@ -1485,7 +1502,9 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
         LOR_CUDA_TRY(cudaMemsetAsync(D.rs.hist, 0, sizeof(uint32_t) * kMaxPasses * kRadix, st));
         ProfScope ps(PK_SAMPLE_KEYS, double(z.n02) * sizeof(KeyT) + double(z.n), st);
         const dim3 grid(unsigned(cdiv(max64(z.n0, z.n2), kKeyTile)), 2);
-        k_sample_keys0<KeyT><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n2, kchars, uint32_t(radix), maxc, k0,
+        int chunk = 1;
+        for (uint64_t T = radix; T * radix <= (uint64_t(1) << 32); T *= radix) ++chunk;
+        k_sample_keys0<KeyT><<<grid, 256, 0, st>>>(s, z.n, z.n0, z.n2, kchars, chunk, uint32_t(radix), maxc, k0,
                                                    npasses, key_bits, dbits, D.rs.hist, D.status);
         hist_ready = true;
     } else {

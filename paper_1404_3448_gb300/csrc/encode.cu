@@ -49,22 +49,32 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint8_t *__restric
     }
     int sq = lo;
     bool bad = false;
+    // The 16 codes are assembled in registers and stored with one 16-byte
+    // write when the run is whole and aligned (byte stores from lanes 16
+    // bytes apart would each touch a separate sector).
+    uint32_t w[kEncItems / 4] = {0, 0, 0, 0};
+#pragma unroll
     for (int k = 0; k < kEncItems; ++k) {
         const int64_t o = o0 + k;
         if (o >= n) break;
         while (o >= so[sq + 1]) ++sq;
         const int64_t term = so[sq + 1] - 1;
-        uint8_t v;
+        uint32_t v;
         if (o == term) {
-            v = uint8_t(nseq - sq);
+            v = uint32_t(nseq - sq);
         } else {
             v = lut[ascii[o - sq]];
             if (v == 0) {
                 bad = true;
-                v = uint8_t(nseq + 1);
+                v = uint32_t(nseq + 1);
             }
         }
-        text[o] = v;
+        w[k >> 2] |= v << (8 * (k & 3));
+    }
+    if (o0 + kEncItems <= n && ((uintptr_t(text + o0) & 15) == 0)) {
+        *reinterpret_cast<uint4 *>(text + o0) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+        for (int k = 0; k < kEncItems && o0 + k < n; ++k) text[o0 + k] = uint8_t(w[k >> 2] >> (8 * (k & 3)));
     }
     if (bad) atomicCAS(status, 0, LOR_ERR_BAD_SYMBOL);
 }
