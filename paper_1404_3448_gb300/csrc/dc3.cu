@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_sample_keys(const CharT *__restrict__ s
 // bytes the tile needs are read once, coalesced, and validated (codes must
 // lie in [1, maxc]); every radix pass's digit histogram is counted on the
 // way, so the sort needs no separate histogram read of the keys.
-constexpr int kKeyTile = 2048;
+constexpr int kKeyTile = 4096;
 constexpr int kKeyMaxChars = 64;
 
 // The key is formed by Horner's rule over 32-bit chunks of `chunk` symbols

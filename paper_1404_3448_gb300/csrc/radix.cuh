@@ -122,6 +122,7 @@ struct OnesweepSmem {
     KeyT keys[kSortThreads * kItems];
     ValT vals[kSortThreads * kItems];
     uint32_t warp_hist[kSortWarps][kRadix];
+    uint32_t early[kRadix];
     uint32_t local_start[kRadix];
     long long gbase[kRadix];
     uint32_t scratch[kSortWarps + 1];
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     for (;;) {
         if (tid == 0) S.next = claim();
         for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
+        S.early[tid] = 0;
         __syncthreads();
         const int64_t tile = S.next;
         if (tile >= ntiles) break;  // uniform over the block
@@ -226,6 +228,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
             if constexpr (kVMode == VM_IDX_PREV)
                 v[i] = uint64_t(uint32_t(idx)) |
                        (uint64_t(valid && idx > 0 ? uint32_t(kin[idx - 1]) : 0xFFFFFFFFu) << 32);
+        }
+        // Early counts: the tile's digit totals from shared-memory atomics,
+        // published before the (slower) stable ranking, so that later tiles'
+        // look-back finds this tile's aggregate sooner.
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+            if (wbase + i * 32 + lane < m) atomicAdd(&S.early[digit_of(k[i], shift, dmask)], 1u);
+        __syncthreads();
+        {
+            const uint32_t e = S.early[tid];
+            st_volatile_u64(&lookback[tile * kRadix + tid], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, e));
         }
         // Stable rank inside the warp: items in order, lanes in order.  Slots
         // past the end of the input use digit 256 and are never counted.
@@ -255,13 +268,11 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
         S.local_start[dg] = lstart;
 
-        // Decoupled look-back, one digit per thread.
+        // Decoupled look-back, one digit per thread (the aggregate, equal to
+        // the early count, is already published).
         uint32_t excl = 0;
         uint64_t *lb = lookback;
-        if (tile == 0) {
-            st_volatile_u64(&lb[dg], lb_pack(epoch, kFlagIncl, total));
-        } else {
-            st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
+        if (tile != 0) {
             excl = lookback_digit(lb, tile, dg, epoch, status);
             st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
         }
@@ -339,15 +350,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
     __syncthreads();
     const int dg = tid;
     const uint32_t total = cnt[dg];
+    uint64_t *lb = lookback;
+    // The aggregate goes out before the block scan: later tiles wait on it.
+    st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, total));
     uint32_t tile_total;
     const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
     S.local_start[dg] = lstart;
     uint32_t excl = 0;
-    uint64_t *lb = lookback;
-    if (tile == 0) {
-        st_volatile_u64(&lb[dg], lb_pack(epoch, kFlagIncl, total));
-    } else {
-        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
+    if (tile != 0) {
         excl = lookback_digit(lb, tile, dg, epoch, status);
         st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
     }

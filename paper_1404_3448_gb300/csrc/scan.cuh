@@ -8,7 +8,7 @@
 namespace lor {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Loads the N consecutive items p[base .. base+N) of one thread (entries at
