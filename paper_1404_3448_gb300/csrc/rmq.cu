@@ -7,8 +7,9 @@
 // Rows are padded to a multiple of 64 entries so that every row starts on a
 // 256-byte boundary.  Levels 0..8 are produced by one kernel that stages a
 // tile plus a 256-entry halo of the LCP array in shared memory and writes the
-// nine rows; every higher level is one streaming pass with 16-byte accesses
-// (the second operand, 2^(j-1) >= 256 entries ahead, is 16-byte aligned too).
+// nine rows; the higher levels are made three at a time by comb passes with
+// 16-byte accesses (k_rmq_comb; the operands, multiples of 2^(j-1) >= 256
+// entries apart, are 16-byte aligned too).
 // A query over ranks (r1, r2] reads two overlapping windows of level
 // floor(log2(r2 - r1)).
 #include <climits>
@@ -68,61 +69,56 @@ __global__ void __launch_bounds__(kLowThreads) k_rmq_low(const int32_t *__restri
     }
 }
 
-// One level above the fused ones: four entries per thread, 16-byte accesses.
-__global__ void __launch_bounds__(256) k_rmq_level(const int32_t *__restrict__ src,
-                                                   int32_t *__restrict__ dst, int64_t n, int64_t h) {
-    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
-    if (i >= n) return;
-    const int4 a = *reinterpret_cast<const int4 *>(src + i);
-    int4 r = a;
-    if (i + h + 3 < n) {
-        const int4 b = *reinterpret_cast<const int4 *>(src + i + h);
-        r.x = min(a.x, b.x);
-        r.y = min(a.y, b.y);
-        r.z = min(a.z, b.z);
-        r.w = min(a.w, b.w);
-    } else {
-        if (i + h + 0 < n) r.x = min(a.x, src[i + h + 0]);
-        if (i + h + 1 < n) r.y = min(a.y, src[i + h + 1]);
-        if (i + h + 2 < n) r.z = min(a.z, src[i + h + 2]);
-    }
-    *reinterpret_cast<int4 *>(dst + i) = r;
+// K levels per pass over a comb: a thread loads the 16-byte groups at
+// x0 + q*h (q = 0 .. Q + 2^K - 2) of level j-1 (windows of h = 2^(j-1)) once,
+// and writes levels j .. j+K-1 at x0 + q*h (q < Q) from them: level j+k at a
+// position is the minimum of the 2^(k+1) level-(j-1) windows h apart that
+// start there, computed in place by doubling.  A row is read about
+// (Q + 2^K - 1) / Q times per pass whatever h is, where a pass that reads
+// its operands in address order re-reads far operands from DRAM once h
+// outgrows the L2.  Entries past n read as INT_MAX (windows are clipped).
+__device__ __forceinline__ int4 rmq_load4(const int32_t *__restrict__ src, int64_t x, int64_t n) {
+    if (x + 3 < n) return *reinterpret_cast<const int4 *>(src + x);
+    int4 r;
+    r.x = x + 0 < n ? src[x + 0] : INT_MAX;
+    r.y = x + 1 < n ? src[x + 1] : INT_MAX;
+    r.z = x + 2 < n ? src[x + 2] : INT_MAX;
+    r.w = x + 3 < n ? src[x + 3] : INT_MAX;
+    return r;
 }
 
-// Two levels per pass: dst1 = level j (windows of 2h, h = 2^(j-1)) and
-// dst2 = level j+1 (windows of 4h) from level j-1, reading src once from
-// DRAM (the operands h, 2h and 3h ahead were read by earlier blocks and are
-// mostly served by L2).
-__global__ void __launch_bounds__(256) k_rmq_level2(const int32_t *__restrict__ src,
-                                                    int32_t *__restrict__ dst1, int32_t *__restrict__ dst2,
-                                                    int64_t n, int64_t h) {
-    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
-    if (i >= n) return;
-    int4 a = *reinterpret_cast<const int4 *>(src + i);
-    int v[4] = {a.x, a.y, a.z, a.w};
-    int w[4];
-    // level j: min(src[i], src[i+h]); level j+1: min of src at i, i+h, i+2h, i+3h
+__device__ __forceinline__ int4 min4(int4 a, int4 b) {
+    return make_int4(min(a.x, b.x), min(a.y, b.y), min(a.z, b.z), min(a.w, b.w));
+}
+
+template <int K, int Q>
+__global__ void __launch_bounds__(256) k_rmq_comb(const int32_t *__restrict__ src, int32_t *__restrict__ dst,
+                                                  int64_t stride, int64_t n, int64_t h) {
+    constexpr int W = 1 << K;
+    constexpr int L = Q + W - 1;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t hq = h / 4;  // 16-byte groups per h entries (h is a multiple of 4)
+    const int64_t g = t / hq;
+    const int64_t x0 = g * Q * h + (t - g * hq) * 4;
+    if (x0 >= n) return;
+    int4 s[L];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) w[u] = v[u];
+    for (int q = 0; q < L; ++q) {
+        const int64_t x = x0 + int64_t(q) * h;
+        s[q] = x < n ? rmq_load4(src, x, n) : make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+    }
 #pragma unroll
-    for (int q = 1; q <= 3; ++q) {
-        const int64_t o = i + q * h;
-        int x[4];
-        if (o + 3 < n) {
-            const int4 b = *reinterpret_cast<const int4 *>(src + o);
-            x[0] = b.x; x[1] = b.y; x[2] = b.z; x[3] = b.w;
-        } else {
+    for (int k = 0; k < K; ++k) {
+        const int d = 1 << k;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = o + u < n ? src[o + u] : INT_MAX;
-        }
+        for (int q = 0; q + d < L; ++q) s[q] = min4(s[q], s[q + d]);
+        int32_t *row = dst + int64_t(k) * stride;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (q == 1) v[u] = min(v[u], x[u]);
-            w[u] = min(w[u], x[u]);
+        for (int q = 0; q < Q; ++q) {
+            const int64_t x = x0 + int64_t(q) * h;
+            if (x < n) *reinterpret_cast<int4 *>(row + x) = s[q];  // rows are padded to 64 entries
         }
     }
-    *reinterpret_cast<int4 *>(dst1 + i) = make_int4(v[0], v[1], v[2], v[3]);
-    *reinterpret_cast<int4 *>(dst2 + i) = make_int4(w[0], w[1], w[2], w[3]);
 }
 
 __global__ void k_rmq_query(const int32_t *__restrict__ table, int64_t stride,
@@ -380,19 +376,24 @@ int lor::rmq_build_levels(const int32_t *d_lcp, int64_t n, int J, int32_t *d_tab
         k_rmq_low<<<unsigned(cdiv(n, kLowTile)), kLowThreads, 0, s>>>(d_lcp, n, d_table, stride, top);
     }
     LOR_LAUNCH_CHECK();
-    const unsigned grid = unsigned(cdiv(cdiv(n, 4), 256));
-    int j = kLowLevels + 1;
-    for (; j + 1 < J; j += 2) {
-        ProfScope ps(PK_RMQ_LEVEL, double(n) * 12, s);
-        k_rmq_level2<<<grid, 256, 0, s>>>(d_table + int64_t(j - 1) * stride, d_table + int64_t(j) * stride,
-                                          d_table + int64_t(j + 1) * stride, n, int64_t(1) << (j - 1));
+    // Levels above the shared-memory ones: three per comb pass (the last
+    // pass takes what is left).
+    constexpr int kCombQ = 8;
+    for (int j = kLowLevels + 1; j < J;) {
+        const int K = J - j < 3 ? J - j : 3;
+        const int64_t h = int64_t(1) << (j - 1);
+        const int64_t threads = cdiv(n, kCombQ * h) * (h / 4);
+        const unsigned grid = unsigned(cdiv(threads, 256));
+        const int32_t *src = d_table + int64_t(j - 1) * stride;
+        int32_t *dst = d_table + int64_t(j) * stride;
+        {
+            ProfScope ps(PK_RMQ_LEVEL, double(n) * (4 + 4.0 * K), s);
+            if (K == 3) k_rmq_comb<3, kCombQ><<<grid, 256, 0, s>>>(src, dst, stride, n, h);
+            else if (K == 2) k_rmq_comb<2, kCombQ><<<grid, 256, 0, s>>>(src, dst, stride, n, h);
+            else k_rmq_comb<1, kCombQ><<<grid, 256, 0, s>>>(src, dst, stride, n, h);
+        }
         LOR_LAUNCH_CHECK();
-    }
-    for (; j < J; ++j) {
-        ProfScope ps(PK_RMQ_LEVEL, double(n) * 8, s);
-        k_rmq_level<<<grid, 256, 0, s>>>(d_table + int64_t(j - 1) * stride, d_table + int64_t(j) * stride,
-                                         n, int64_t(1) << (j - 1));
-        LOR_LAUNCH_CHECK();
+        j += K;
     }
     return LOR_OK;
 }
