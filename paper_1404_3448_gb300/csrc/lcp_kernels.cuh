@@ -214,6 +214,31 @@ __device__ __forceinline__ int64_t next_exc(const int32_t *__restrict__ lst, int
     return lo < cnt ? int64_t(lst[lo]) : n;
 }
 
+// 32-bit forms of window_chunk and next_exc for texts below 2^31 symbols
+// (the int32 path): position arithmetic in 32 bits halves the ALU work of
+// the comparison loop, which bounds the PLCP pass.
+__device__ __forceinline__ uint64_t window_chunk32(const uint64_t *__restrict__ P, uint32_t p, int &avail,
+                                                   uint64_t keep) {
+    const ulonglong2 v = ld_u64x2_hint(reinterpret_cast<const ulonglong2 *>(P) + (p >> 6), keep);
+    const uint32_t off = p & 63u;
+    if (off < 32) {
+        avail = 32;
+        return off ? (v.x >> (2 * off)) | (v.y << (64 - 2 * off)) : v.x;
+    }
+    avail = int(64 - off);
+    return v.y >> (2 * (off - 32));
+}
+
+__device__ __forceinline__ int32_t next_exc32(const int32_t *__restrict__ lst, int cnt, int32_t p, int32_t n) {
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (lst[mid] < p) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < cnt ? lst[lo] : n;
+}
+
 // lcp(T[i..], T[j..]) given that the first h symbols match: 32 symbols at a
 // time on the 2-bit copy, with the exception bitmap marking the symbols that
 // must be compared as bytes.
@@ -268,6 +293,7 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
     int64_t h = 0;
     bool bad = false;
     const int l0 = int(threadIdx.x) * kPlcpPer;
+    int32_t ea = -1;  // first exception at or after the text-order side (valid while a <= ea)
     for (int l = l0; l < l0 + kPlcpPer && l < cnt; ++l) {
         const int64_t i = base + l;
         const int64_t j = s_out[chunk_slot(l)];
@@ -280,18 +306,22 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
         if (listed) {
             // Compare packed symbols up to the next exception (or the end) on
             // either side; there compare the bytes and go on if they match.
+            // (32-bit positions: n < 2^31 on this path.)  The next exception
+            // on the text-order side only moves forward, so it is kept.
+            const int32_t n32 = int32_t(n), i32 = int32_t(i), j32 = int32_t(j);
+            int32_t h32 = int32_t(h);
             for (;;) {
-                const int64_t a = i + h, b = j + h;
-                const int64_t lim = min64(min64(next_exc(lst, nexc, a, n) - a, next_exc(lst, nexc, b, n) - b),
-                                          min64(n - a, n - b));
-                int64_t k = 0;
+                const int32_t a = i32 + h32, b = j32 + h32;
+                if (a > ea) ea = next_exc32(lst, nexc, a, n32);
+                const int32_t lim = min(min(ea - a, next_exc32(lst, nexc, b, n32) - b), min(n32 - a, n32 - b));
+                int32_t k = 0;
                 bool mism = false;
                 while (k < lim) {
                     int aa, ab;
-                    const uint64_t wa = window_chunk(P, a + k, aa, keep);
-                    const uint64_t wb = window_chunk(P, b + k, ab, keep);
+                    const uint64_t wa = window_chunk32(P, uint32_t(a + k), aa, keep);
+                    const uint64_t wb = window_chunk32(P, uint32_t(b + k), ab, keep);
                     int len = aa < ab ? aa : ab;
-                    if (lim - k < len) len = int(lim - k);
+                    if (lim - k < len) len = lim - k;
                     uint64_t d = wa ^ wb;
                     if (len < 32) d &= (uint64_t(1) << (2 * len)) - 1;
                     if (d) {
@@ -301,10 +331,11 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
                     }
                     k += len;
                 }
-                h += k;
-                if (mism || i + h >= n || j + h >= n || t[i + h] != t[j + h]) break;
-                ++h;
+                h32 += k;
+                if (mism || i32 + h32 >= n32 || j32 + h32 >= n32 || t[i32 + h32] != t[j32 + h32]) break;
+                ++h32;
             }
+            h = h32;
         } else {
             h = extend_bitmap(t, T, n, i, j, h);
         }
