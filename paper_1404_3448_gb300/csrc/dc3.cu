@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(256) k_sample_keys0(const uint8_t *__restrict_
 }
 
 // Step 1 naming: name(j) = 1 + number of key changes in sorted[0..j].
-// Writes R[val] = name, SA_R[j] = val, and the name count.
+// Writes R[val] = name, SA_R[j] = val, and the name count.  Persistent: a
+// resident grid claims tiles until it draws one past the end (launched by
+// LOR_PTILE_LAUNCH).
 template <typename KeyT>
 __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ keys,
                                                        const uint32_t *__restrict__ vals, int64_t m,
@@ -231,9 +233,12 @@ __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ 
     __shared__ uint32_t scratch[kScanThreads / 32 + 1];
     __shared__ uint32_t s_prefix;
     const int tid = threadIdx.x;
+    const int64_t ntiles = cdiv(m > 0 ? m : 1, kScanTile);
+    for (;;) {
     if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
     __syncthreads();
     const int64_t tile = s_tile;
+    if (tile >= ntiles) break;  // uniform over the block
     const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
     KeyT prev = (base > 0 && base - 1 < m) ? keys[base - 1] : KeyT(0);
     KeyT kk[kScanItems];
@@ -272,6 +277,8 @@ __global__ void __launch_bounds__(kScanThreads) k_name(const KeyT *__restrict__ 
     }
     store_run<int32_t, kScanItems>(SAR, base, m, reinterpret_cast<const int32_t(&)[kScanItems]>(vv));
     store_run<int32_t, kScanItems>(NS, base, m, nm);
+    __syncthreads();  // s_tile and s_prefix are reused by the next tile
+    }
 }
 
 // Naming after a two-stage sort: equality of triples is checked on the
@@ -1104,6 +1111,7 @@ __global__ void k_dbl_init(int32_t *__restrict__ R, int64_t m, const int32_t *__
 
 // Positions (in name order) of samples that share their name.  Each thread
 // loads its run of names with 16-byte loads, plus one name on either side.
+// Persistent, like k_name.
 __global__ void __launch_bounds__(kScanThreads) k_dbl_unresolved(
     const int32_t *__restrict__ NS, int64_t m, uint32_t *__restrict__ ul, uint32_t *count, uint64_t *lb,
     unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch, int *status, int64_t ntiles) {
@@ -1111,9 +1119,12 @@ __global__ void __launch_bounds__(kScanThreads) k_dbl_unresolved(
     __shared__ uint32_t scratch[kScanThreads / 32 + 1];
     __shared__ uint32_t s_prefix;
     const int tid = threadIdx.x;
+    const int64_t nt = ntiles > 0 ? ntiles : 1;  // an empty input still takes one (empty) tile
+    for (;;) {
     if (tid == 0) s_tile = (long long)(atomicAdd(ctr, 1ull) - tile_base);
     __syncthreads();
     const int64_t tile = s_tile;
+    if (tile >= nt) break;  // uniform over the block
     const int64_t base = tile * kScanTile + int64_t(tid) * kScanItems;
     int32_t v[kScanItems];
     load_run<int32_t, kScanItems>(NS, base, m, -1, v);
@@ -1142,6 +1153,8 @@ __global__ void __launch_bounds__(kScanThreads) k_dbl_unresolved(
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i)
         if ((flags >> i) & 1u) ul[o++] = uint32_t(base + i);
+    __syncthreads();  // s_tile and s_prefix are reused by the next tile
+    }
 }
 
 __global__ void k_dbl_keys(const uint32_t *__restrict__ ul, int64_t U, const int32_t *__restrict__ SAR,
@@ -1460,6 +1473,18 @@ int read_u32(Dc3Run &D, const uint32_t *d, uint32_t *h) {
         (D).rs.tile_base += (unsigned long long)_nt;                                      \
     } while (0)
 
+// The same for a persistent tile kernel: a resident grid claims tiles until
+// each block draws one past the end, so the launch makes ntiles + grid claims.
+#define LOR_PTILE_LAUNCH(D, m, kernel, ...)                                                \
+    do {                                                                                  \
+        const int64_t _nt = cdiv((m) > 0 ? (m) : 1, kScanTile);                           \
+        const unsigned _g = unsigned(min64(_nt, int64_t(scan_grid_cap())));               \
+        (D).rs.epoch++;                                                                   \
+        kernel<<<_g, kScanThreads, 0, (D).s>>>(__VA_ARGS__);                              \
+        LOR_LAUNCH_CHECK();                                                               \
+        (D).rs.tile_base += (unsigned long long)_nt + _g;                                 \
+    } while (0)
+
 #define LB_ARGS(D) (D).rs.lookback, (D).rs.tile_ctr, (D).rs.tile_base, (D).rs.epoch, (D).status
 
 // Inputs of at least this many entries scatter through bucketing.
@@ -1520,7 +1545,7 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
     if (rc) return rc;
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 16), st);
-        LOR_TILE_LAUNCH(D, z.n02, k_name<KeyT>, kr, vr, z.n02, bucket_names(D, z) ? nullptr : Rl, SAR, NSl,
+        LOR_PTILE_LAUNCH(D, z.n02, k_name<KeyT>, kr, vr, z.n02, bucket_names(D, z) ? nullptr : Rl, SAR, NSl,
                         D.d_names, LB_ARGS(D));
     }
     return LOR_OK;  // large levels: R is written by dc3_level once it knows how to continue
@@ -1698,7 +1723,7 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
     {
         ProfScope ps(PK_NAMING, double(m) * 8, st);
         const int64_t ntiles = cdiv(m, kScanTile);
-        LOR_TILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, D.d_count, LB_ARGS(D), ntiles);
+        LOR_PTILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, D.d_count, LB_ARGS(D), ntiles);
     }
     uint32_t hU = 0;
     int rc = read_u32(D, D.d_count, &hU);
@@ -1912,7 +1937,7 @@ int sa_by_doubling_graph(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const 
     }
     {
         const int64_t ntiles = cdiv(m, kScanTile);
-        LOR_TILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, cnt, LB_ARGS(D), ntiles);
+        LOR_PTILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, cnt, LB_ARGS(D), ntiles);
     }
     if (r_unwritten) {
         const unsigned g = unsigned(min64(cdiv(m, 256), scan_grid_cap()));
