@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
 // One non-stable partition pass (for the bucketed scatters, where the order
 // inside a bucket does not matter): an element's place inside its tile's
 // digit run comes from a shared-memory atomic instead of the stable warp
-// ranking; the look-back and the staged write are those of k_onesweep.
+// ranking; the look-back and the staged write are those of k_onesweep, and
+// so is the persistent grid (blocks claim tiles until one past the end).
 template <typename ValT, int kVMode>
 __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
     const uint32_t *__restrict__ kin, const ValT *__restrict__ vin, uint32_t *__restrict__ kout,
@@ -316,6 +317,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
     OnesweepSmem<uint32_t, ValT> &S = *reinterpret_cast<OnesweepSmem<uint32_t, ValT> *>(smem_raw);
     uint32_t *cnt = S.warp_hist[0];
     const int tid = threadIdx.x;
+    const int64_t ntiles = cdiv(m, kTile);
+    for (;;) {
     if (tid == 0) {
         S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
         const int64_t b2 = (S.tile + ahead) * kTile;
@@ -332,6 +335,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
     cnt[tid] = 0;
     __syncthreads();
     const int64_t tile = S.tile;
+    if (tile >= ntiles) break;  // uniform over the block
     const int64_t base = tile * kTile;
     uint32_t k[kItems], r[kItems];
     ValT v[kItems];
@@ -383,6 +387,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
         }
         kout[o] = kk;
         vout[o] = S.vals[i];
+    }
+    __syncthreads();  // counts, staging and S.tile are reused by the next tile
     }
 }
 
@@ -654,16 +660,17 @@ int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int
     LOR_CUDA_TRY(cudaFuncSetAttribute(k_partition<ValT, kVMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       int(smem)));
     const int64_t ntiles = cdiv(m, sort_tile<uint32_t, ValT>());
+    const unsigned grid = unsigned(min64(ntiles, sort_grid_cap()));
     rs.epoch++;
     {
         ProfScope ps(PK_RADIX_PASS, double(m) * (4 + (kVMode == VM_LOAD ? sizeof(ValT) : 0) + 4 + sizeof(ValT)),
                      s);
-        k_partition<ValT, kVMode><<<unsigned(ntiles), kSortThreads, smem, s>>>(
+        k_partition<ValT, kVMode><<<grid, kSortThreads, smem, s>>>(
             keys, vals, kout, vout, m, lo, digit_mask(lo, top), rs.offsets, rs.lookback, rs.tile_ctr,
             rs.tile_base, rs.epoch, rs.status, prefetch_ahead(keys, kVMode == VM_LOAD ? (const void *)vals : keys));
     }
     LOR_LAUNCH_CHECK();
-    rs.tile_base += (unsigned long long)ntiles;
+    rs.tile_base += (unsigned long long)ntiles + grid;  // every block claims once past the end
     return LOR_OK;
 }
 
