@@ -610,17 +610,36 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
 // scatter of the path): each window then holds exactly bound / 256 keys and
 // the pass needs no histogram of them.
 
+// Four pairs per thread (16-byte loads when the four are whole and aligned).
 static __global__ void k_scatter_pairs(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                                        int64_t m, int32_t *__restrict__ dst, int32_t add, int64_t bound,
                                        int *status) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const uint32_t r = key[i];
-    if (int64_t(r) >= bound) {
-        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
-        return;
+    const int64_t i0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
+    if (i0 >= m) return;
+    uint32_t kk[4], vv[4];
+    if (i0 + 4 <= m && ((uintptr_t(key + i0) | uintptr_t(val + i0)) & 15) == 0) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(key + i0);
+        const uint4 b = *reinterpret_cast<const uint4 *>(val + i0);
+        kk[0] = a.x; kk[1] = a.y; kk[2] = a.z; kk[3] = a.w;
+        vv[0] = b.x; vv[1] = b.y; vv[2] = b.z; vv[3] = b.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            kk[u] = i0 + u < m ? key[i0 + u] : 0xFFFFFFFFu;
+            vv[u] = i0 + u < m ? val[i0 + u] : 0u;
+        }
     }
-    dst[r] = int32_t(val[i]) + add;
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (i0 + u >= m) break;
+        if (int64_t(kk[u]) >= bound) {
+            bad = true;
+            continue;
+        }
+        dst[kk[u]] = int32_t(vv[u]) + add;
+    }
+    if (bad) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
 }
 
 // keys/vals: inputs (vals == nullptr means 0..m-1).  kbuf, vbuf0, vbuf1:
@@ -686,7 +705,7 @@ inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32
     if (rc) return rc;
     {
         ProfScope ps(PK_RANK_SCATTER, double(m) * 12, rs.stream);
-        k_scatter_pairs<<<unsigned(cdiv(m, 256)), 256, 0, rs.stream>>>(kbuf, vbuf0, m, dst, add, bound,
+        k_scatter_pairs<<<unsigned(cdiv(cdiv(m, 4), 256)), 256, 0, rs.stream>>>(kbuf, vbuf0, m, dst, add, bound,
                                                                       rs.status);
     }
     LOR_LAUNCH_CHECK();
