@@ -52,6 +52,18 @@ __device__ __forceinline__ uint32_t warp_peers9(uint32_t d) {
     return peers;
 }
 
+// The same for an 8-bit value (every slot valid).
+__device__ __forceinline__ uint32_t warp_peers8(uint32_t d) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 template <typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask = 0xFFu) {
     return uint32_t(k >> shift) & mask;
@@ -241,19 +253,34 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
             st_volatile_u64(&lookback[tile * kRadix + tid], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, e));
         }
         // Stable rank inside the warp: items in order, lanes in order.  Slots
-        // past the end of the input use digit 256 and are never counted.
+        // past the end of the input use digit 256 and are never counted (a
+        // whole tile has none, and its ranking needs one ballot fewer).
         uint32_t *wh = S.warp_hist[warp];
+        if (base + kTile <= m) {
 #pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const bool valid = wbase + i * 32 + lane < m;
-            const uint32_t d = valid ? digit_of(k[i], shift, dmask) : 0x100u;
-            const uint32_t peers = warp_peers9(d);
-            const uint32_t lt = __popc(peers & lanemask_lt());
-            const uint32_t cnt = valid ? wh[d] : 0u;
-            r[i] = cnt + lt;
-            __syncwarp();
-            if (valid && lt == 0) wh[d] = cnt + __popc(peers);
-            __syncwarp();
+            for (int i = 0; i < kItems; ++i) {
+                const uint32_t d = digit_of(k[i], shift, dmask);
+                const uint32_t peers = warp_peers8(d);
+                const uint32_t lt = __popc(peers & lanemask_lt());
+                const uint32_t cnt = wh[d];
+                r[i] = cnt + lt;
+                __syncwarp();
+                if (lt == 0) wh[d] = cnt + __popc(peers);
+                __syncwarp();
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                const bool valid = wbase + i * 32 + lane < m;
+                const uint32_t d = valid ? digit_of(k[i], shift, dmask) : 0x100u;
+                const uint32_t peers = warp_peers9(d);
+                const uint32_t lt = __popc(peers & lanemask_lt());
+                const uint32_t cnt = valid ? wh[d] : 0u;
+                r[i] = cnt + lt;
+                __syncwarp();
+                if (valid && lt == 0) wh[d] = cnt + __popc(peers);
+                __syncwarp();
+            }
         }
         __syncthreads();
         const int dg = tid;
