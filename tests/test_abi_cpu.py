@@ -184,3 +184,45 @@ def test_tune_configuration_round_trip_and_range_checks(lib):
     finally:
         P.tune_set(**d)
     assert P.tune_get() == d
+
+
+def test_int64_path_host_checks(lib):
+    """The *64 calls: sizes past the int32 range are accepted up to LOR_MAX_N64,
+    bad arguments are rejected before any device access."""
+    n32, n64 = L.LOR_MAX_N, L.LOR_MAX_N64
+    assert n64 > 2**31 and n64 < 2**32
+    # workspace queries: host only, monotone, zero outside [1, LOR_MAX_N64]
+    assert lib.lor_build_sa64_workspace_size(0, 7) == 0
+    assert lib.lor_build_sa64_workspace_size(n64 + 1, 7) == 0
+    assert lib.lor_build_sa64_workspace_size(1000, 1) == 0
+    big = lib.lor_build_sa64_workspace_size(n32 + 1, 7)
+    assert big > 0 and big % 256 == 0 and big < 48 * (n32 + 1)
+    assert lib.lor_lcp64_workspace_size(n64) > 0 and lib.lor_lcp64_workspace_size(n64 + 1) == 0
+    assert lib.lor_longest_overlap64_workspace_size(n32 + 1) > 0
+    assert L.lor_build_sa_workspace_size(n32 + 1, 7) == 0  # the int32 call stops at LOR_MAX_N
+    assert lib.lor_rmq_block_table_elems(n32 + 1) > 0  # the block table serves both paths
+    prev = 0
+    for n in [1, 2, 3, 10, 1000, 10**6]:
+        w = lib.lor_build_sa64_workspace_size(n, 7)
+        assert w >= prev
+        prev = w
+    # argument checks
+    assert lib.lor_build_sa64(None, 10, 7, None, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert lib.lor_build_sa64(256, 10, 1, 256, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert lib.lor_build_sa64(256, n64 + 1, 7, 256, None, 0, None) == L.LOR_ERR_TOO_LARGE
+    assert lib.lor_build_sa64(256, 10, 7, 256, None, 0, None) == L.LOR_ERR_WORKSPACE
+    assert lib.lor_build_sa64(256, 10, 7, 256, 256 + 8, 1 << 30, None) == L.LOR_ERR_WORKSPACE
+    assert lib.lor_lcp64(None, None, 5, None, None, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert lib.lor_lcp64(256, 256, n64 + 1, 256, 256, None, 0, None) == L.LOR_ERR_TOO_LARGE
+    assert lib.lor_lcp64(256, 256, 5, 256, 256, None, 0, None) == L.LOR_ERR_WORKSPACE
+    assert lib.lor_longest_overlap64(256, 256, 5, 256, 0, 256, None, 0, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert lib.lor_longest_overlap64(256, 256, 5, 256, 2, 256, None, 4, None, 0, None) == L.LOR_ERR_INVALID_ARG
+    assert lib.lor_longest_overlap64(256, 256, n64 + 1, 256, 2, 256, None, 0, None, 0, None) == L.LOR_ERR_TOO_LARGE
+    assert lib.lor_longest_overlap64(256, 256, 5, 256, 2, 256, None, 0, None, 0, None) == L.LOR_ERR_WORKSPACE
+    assert lib.lor_rmq_block_query64(None, None, None, 5, None, None, 1, None, None) == L.LOR_ERR_INVALID_ARG
+    assert lib.lor_rmq_block_query64(256, 256, 256, 5, None, None, 0, None, None) == L.LOR_OK
+    assert lib.lor_rmq_block_query64(256, 256, 256, n64 + 1, 256, 256, 1, 256, None) == L.LOR_ERR_TOO_LARGE
+    lens = (ctypes.c_int64 * 2)(3, 4)
+    assert lib.lor_encode_concat64(256, lens, 0, 256, None, None) == L.LOR_ERR_INVALID_ARG
+    huge = (ctypes.c_int64 * 2)(n64, 4)
+    assert lib.lor_encode_concat64(256, huge, 2, 256, None, None) == L.LOR_ERR_TOO_LARGE
