@@ -4,10 +4,11 @@
 // radix sort (Section 4, Algorithm 1: one 1-bit split per pass, block-local
 // chunks merged afterwards).  Here one pass moves 8 bits: an up-front
 // histogram kernel counts every pass's digits in one read of the keys, and
-// each pass is a single "onesweep" kernel -- a block ranks its tile of keys
-// with warp match/popc, learns the global offset of each digit from its
-// predecessors by decoupled look-back (bounded waits), and scatters through
-// shared memory so that every digit run is written contiguously.
+// each pass is a single "onesweep" kernel -- a block counts its tile's digits
+// and publishes them for the tiles after it, ranks the keys stably with warp
+// ballots, learns the global offset of each digit from its predecessors by
+// decoupled look-back (bounded waits), and scatters through shared memory so
+// that every digit run is written contiguously.
 #pragma once
 
 #include <cstdlib>
