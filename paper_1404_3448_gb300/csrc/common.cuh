@@ -109,45 +109,6 @@ inline int64_t prefetch_ahead(const void *a, const void *b, int64_t resident = 0
     return int64_t(4) * sms;
 }
 
-// ---- mbarrier + bulk (TMA) copies into shared memory
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return uint32_t(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-// Makes initialised barriers visible to the async proxy.
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// Orders this thread's earlier shared-memory accesses before later bulk
-// copies into shared memory (generic -> async proxy).
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-// from global to this CTA's shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 // ---- L2 cache policies: data that random reads will come back to is kept
 // (evict_last), data streamed once goes first (evict_first).
 
@@ -184,15 +145,6 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Every inter-block wait gives up after this long and reports LOR_ERR_TIMEOUT.
 constexpr uint64_t kSpinLimitNs = 2000000000ull;  // 2 s
-
-// Waits for phase `parity` of a barrier, at most kSpinLimitNs; false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kSpinLimitNs) return false;
-    return true;
-}
 
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
     uint64_t v;
