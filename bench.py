@@ -795,7 +795,7 @@ def run_lor(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lor", choices=["lor", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
