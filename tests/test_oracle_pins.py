@@ -317,6 +317,73 @@ def test_topk_overlaps_first_is_the_longest_overlap_and_entries_are_maximal(orac
             prev = key
 
 
+def _brute_topk(text, starts, nseq):
+    """Every cross-sequence left-maximal adjacent pair, by brute force: the
+    suffixes sorted as Python byte strings, the common prefix of each adjacent
+    pair counted symbol by symbol, the sequence of a position found by walking
+    the start offsets, the left symbols compared directly."""
+    t = bytes(np.asarray(text, np.uint8))
+    n = len(t)
+    order = sorted(range(n), key=lambda i: t[i:])
+    st = [int(x) for x in starts]
+
+    def seq(p):
+        q = 0
+        while q + 1 < len(st) and st[q + 1] <= p:
+            q += 1
+        return q
+
+    out = []
+    for k in range(1, n):
+        a, b = order[k - 1], order[k]
+        h = 0
+        while a + h < n and b + h < n and t[a + h] == t[b + h]:
+            h += 1
+        if h == 0 or seq(a) == seq(b):
+            continue
+        if a > 0 and b > 0 and t[a - 1] == t[b - 1]:
+            continue
+        qa, qb, pa, pb = seq(a), seq(b), a, b
+        if qa > qb:
+            qa, qb, pa, pb = qb, qa, pb, pa
+        out.append(dict(length=h, rank=k, seq_a=qa, pos_a=pa - st[qa], seq_b=qb, pos_b=pb - st[qb]))
+    out.sort(key=lambda e: (-e["length"], e["rank"]))
+    return out
+
+
+def test_topk_overlaps_is_complete_against_brute_force(oracle_mod):
+    """With K at least the number of candidates, topk_overlaps returns exactly
+    the set of cross-sequence left-maximal adjacent pairs (Section 3: the LCP
+    of adjacent suffixes from two different sequences, the longest overlap
+    being the largest), enumerated here by brute force, in (length desc, rank
+    asc) order; a smaller K returns a prefix of that list.  A skip rule that
+    drops a lesser candidate, or keeps a pair that is not left-maximal, fails
+    here."""
+    rng = np.random.default_rng(29)
+    A = np.frombuffer(b"ACGT", np.uint8)
+    cases = 0
+    for trial in range(60):
+        alpha = [A, A[:2], A[:1], A[:3]][trial % 4]
+        nseq = 2 + trial % 3
+        seqs = [alpha[rng.integers(0, alpha.size, int(rng.integers(1, 40)))] for _ in range(nseq)]
+        text, starts, _ = oracle_mod.encode_concat(seqs)
+        sa = oracle_mod.suffix_array(text)
+        lcp = oracle_mod.lcp_array(text, sa)
+        want = _brute_topk(text, starts, nseq)
+        got = oracle_mod.topk_overlaps(text, sa, lcp, starts, len(text) + 1)
+        assert got == want
+        for K in (0, 1, 2, max(1, len(want) // 2), len(want)):
+            assert oracle_mod.topk_overlaps(text, sa, lcp, starts, K) == want[:K]
+        cases += len(want) > 2
+    assert cases > 20  # most cases have more than the single longest pair
+    # a case with several pairs of one length, where only the rank orders them
+    seqs = [np.frombuffer(b"ACGTACGA", np.uint8), np.frombuffer(b"CGTTACGC", np.uint8)]
+    text, starts, _ = oracle_mod.encode_concat(seqs)
+    sa = oracle_mod.suffix_array(text)
+    lcp = oracle_mod.lcp_array(text, sa)
+    assert oracle_mod.topk_overlaps(text, sa, lcp, starts, 100) == _brute_topk(text, starts, 2)
+
+
 # ---------------------------------------------------------------- LCS DP pins
 
 def _brute_lcs(a: bytes, b: bytes):
