@@ -121,13 +121,18 @@ int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
 /* ---------------------------------------------------------------------------
  * Suffix array without a workspace argument, for callers that cannot
  * allocate device memory (the paper has no counterpart; this is a library
- * convenience).  Same result, arguments and errors as lor_build_sa, for
- * n <= LOR_NOALLOC_MAX_N; larger n returns LOR_ERR_TOO_LARGE before touching
- * the device.  The scratch is one 32 MiB array compiled into the library:
- * every GPU that loads liblor holds it until the process exits.  The first
- * call on a device looks up the array's device address (call it once before
- * any stream capture).  All calls share the array, so calls that can overlap
- * on the GPU race and must be serialised by the caller.  Allocates nothing.
+ * convenience).  Same result and arguments as lor_build_sa.  Errors: the
+ * argument checks of lor_build_sa come first (LOR_ERR_INVALID_ARG), then
+ * n > LOR_NOALLOC_MAX_N returns LOR_ERR_TOO_LARGE before touching the
+ * device; device-side errors as for lor_build_sa.  The scratch is one 32 MiB
+ * array compiled into the library: every GPU that loads liblor holds it until
+ * the process exits.  The first call on a device looks up the array's device
+ * address and keeps it; make that first call before any stream capture
+ * begins, and do not call this entry point again after cudaDeviceReset in
+ * the same process.  Like lor_build_sa it reads counts back and synchronises
+ * `stream` during the call.  All calls share the array, so calls that can
+ * overlap on the GPU race and must be serialised by the caller.  Allocates
+ * nothing.
  * ------------------------------------------------------------------------- */
 #define LOR_NOALLOC_MAX_N 262144LL
 int lor_build_sa_noalloc(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
@@ -567,6 +572,38 @@ int lor_profile_reset(void);
 int lor_profile_kinds(void);
 const char *lor_profile_kind_name(int kind);
 int lor_profile_read(int kind, int64_t *h_launches, double *h_ms, double *h_bytes);
+
+/* ---------------------------------------------------------------------------
+ * Route controls of the suffix array (DC3, Section 3 Steps 1-3).  They change
+ * how lor_build_sa orders its samples, never its result, and exist so that
+ * tests can force every route and a measurement can time the plain
+ * recursion.  Process-wide; read once at the start of each lor_build_sa call
+ * (also inside the batched, served and no-workspace calls).
+ *   level0_symbols: symbols named at level 0; 0 = the longest prefix whose key
+ *                   fits the tuned level-0 key width, else at least 3.
+ *   strategy      : 0 = pick per level (dense table, parent order or sort),
+ *                   1 = radix sort at every level.
+ *   doubling      : 0 = never (recurse while names repeat, as the paper
+ *                   does), 1 = finish by prefix doubling once names are almost
+ *                   unique (default), 2 = whenever names repeat.
+ * lor_dc3_route_set(0, 0, 1) restores the defaults.  Returns
+ * LOR_ERR_INVALID_ARG (and changes nothing) for a value out of range.
+ * ------------------------------------------------------------------------- */
+int lor_dc3_route_set(int32_t level0_symbols, int32_t strategy, int32_t doubling);
+int lor_dc3_route_get(int32_t *level0_symbols, int32_t *strategy, int32_t *doubling);
+
+/* ---------------------------------------------------------------------------
+ * Test-only control of the bounded waits (no counterpart in the paper).
+ * Every inter-block wait of every kernel gives up after limit_ns nanoseconds
+ * (0 = the default of 2 s, also the maximum) and records LOR_ERR_TIMEOUT.
+ * starve_first_tile = 1 makes the first tile of every LSD radix pass withhold
+ * its look-back descriptor, so that the tile after it must wait until the
+ * limit runs out: a way to exercise the timeout path without a fault.  The
+ * results of a call made in that state are unspecified (every access stays
+ * in bounds).  lor_test_set_wait(0, 0) restores normal operation.  Applies
+ * to work launched after the call; synchronous.
+ * ------------------------------------------------------------------------- */
+int lor_test_set_wait(uint64_t limit_ns, int32_t starve_first_tile);
 
 #ifdef __cplusplus
 }

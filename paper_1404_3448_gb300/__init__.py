@@ -11,4 +11,6 @@ from .lor import (  # noqa: F401
     radix_sort_pairs, rmq_build, rmq_query, rmq_block_build, rmq_block_query, rmq_block_argmin, server_batch_bytes, workspace, tune_default, tune_get, tune_set,
     autotune_batch, multi_query_overlap, topk_overlaps,
     encode_concat64, build_sa64, lcp64, longest_overlap64, overlap64_dict, rmq_block_query64,
+    dc3_route, dc3_route_get, dc3_route_set, test_set_wait, status_string,
+    LOR_OK, LOR_ERR_BAD_SYMBOL, LOR_ERR_TIMEOUT, LOR_ERR_INVALID_ARG,
 )

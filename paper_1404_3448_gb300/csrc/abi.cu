@@ -29,6 +29,20 @@ unsigned long long capture_end() {
 }
 void note_graph_launches(unsigned long long kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
 
+static thread_local int *t_status_slot = nullptr;
+int *status_slot() { return t_status_slot; }
+void set_status_slot(int *d_slot) { t_status_slot = d_slot; }
+int read_status_slot(int *d_slot, cudaStream_t s) {
+    int h = 0;
+    LOR_CUDA_TRY(cudaMemcpyAsync(&h, d_slot, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h != 0) {
+        LOR_CUDA_TRY(cudaMemsetAsync(d_slot, 0, sizeof(int), s));
+        LOR_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return h;
+}
+
 // ---------------------------------------------------------------- timing
 
 namespace {
@@ -167,6 +181,21 @@ extern "C" int lor_device_status(lor_stream_t stream) {
         if (v != LOR_OK && first == LOR_OK) first = v;
     }
     return first;
+}
+
+extern "C" int lor_test_set_wait(uint64_t limit_ns, int32_t starve_first_tile) {
+    if (starve_first_tile != 0 && starve_first_tile != 1) return LOR_ERR_INVALID_ARG;
+    const uint64_t lim = limit_ns ? limit_ns : kSpinLimitNs;
+    if (lim > kSpinLimitNs) return LOR_ERR_INVALID_ARG;
+    int (*fns[])(uint64_t, int) = {lor_status_encode_set_wait, lor_status_dc3_set_wait, lor_status_lcp_set_wait,
+                                   lor_status_overlap_set_wait, lor_status_rmq_set_wait, lor_status_abi_set_wait,
+                                   lor_status_batch_set_wait, lor_status_serve_set_wait, lor_status_multi_set_wait,
+                                   lor_status_topk_set_wait, lor_status_sa64_set_wait};
+    for (auto f : fns) {
+        const int rc = f(lim, starve_first_tile);
+        if (rc != LOR_OK) return rc;
+    }
+    return LOR_OK;
 }
 
 extern "C" const char *lor_status_string(int status) {

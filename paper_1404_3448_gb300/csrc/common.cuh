@@ -146,6 +146,14 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Every inter-block wait gives up after this long and reports LOR_ERR_TIMEOUT.
 constexpr uint64_t kSpinLimitNs = 2000000000ull;  // 2 s
 
+// The wait limit in force, one copy per translation unit (kSpinLimitNs unless
+// lor_test_set_wait changed it), and the test switch that keeps the first
+// tile of a radix pass from publishing its look-back descriptor, so that the
+// tiles after it must give up waiting on it.
+static __device__ uint64_t g_wait_limit_ns = kSpinLimitNs;
+static __device__ int g_starve_first_tile = 0;
+__device__ __forceinline__ uint64_t wait_limit_ns() { return *(volatile uint64_t *)&g_wait_limit_ns; }
+
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
     uint64_t v;
     asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -224,7 +232,7 @@ __device__ __forceinline__ uint32_t warp_lookback(uint64_t *lb, int64_t tile, ui
     if (lane == 0) st_volatile_u64(&lb[tile], lb_pack(epoch, kFlagAgg, agg));
     uint32_t excl = 0;
     int64_t j = tile - 1;
-    const uint64_t t0 = global_ns();
+    const uint64_t t0 = global_ns(), limit = wait_limit_ns();
     bool timed_out = false;
     while (true) {
         int64_t idx = j - lane;
@@ -234,7 +242,7 @@ __device__ __forceinline__ uint32_t warp_lookback(uint64_t *lb, int64_t tile, ui
             if (__all_sync(0xffffffffu, ready)) break;
             if (!ready) w = ld_volatile_u64(&lb[idx]);
             // warp-uniform decision: every lane leaves the loop together
-            if (__any_sync(0xffffffffu, global_ns() - t0 > kSpinLimitNs)) { timed_out = true; break; }
+            if (__any_sync(0xffffffffu, global_ns() - t0 > limit)) { timed_out = true; break; }
         }
         if (timed_out) {
             if (lane == 0) atomicCAS(status, 0, LOR_ERR_TIMEOUT);
@@ -260,10 +268,30 @@ __device__ __forceinline__ uint32_t warp_lookback(uint64_t *lb, int64_t tile, ui
 
 }  // namespace lor
 
+namespace lor {
+// A status slot that replaces the translation units' status words for the
+// launches of the calling host thread (nullptr: the words are used).  Server
+// workers point it at a slot of their own, so that their batches neither see
+// nor clear each other's errors.
+int *status_slot();
+void set_status_slot(int *d_slot);
+// Reads the slot after the stream's work, clears it when set, returns it.
+int read_status_slot(int *d_slot, cudaStream_t s);
+}  // namespace lor
+
 // One device status word per translation unit; kernels record the first
-// error with atomicCAS and the host reads it through the TU's accessor.
+// error with atomicCAS and the host reads it through the TU's accessor.  The
+// TU's wait limit and starve switch are set through name##_set_wait.
 #define LOR_DEFINE_TU_STATUS(name)                                                    \
     static __device__ int g_tu_status;                                                \
+    int name##_set_wait(uint64_t limit_ns, int starve) {                              \
+        if (cudaMemcpyToSymbol(lor::g_wait_limit_ns, &limit_ns, sizeof(limit_ns)) !=       \
+                cudaSuccess ||                                                        \
+            cudaMemcpyToSymbol(lor::g_starve_first_tile, &starve, sizeof(starve)) !=       \
+                cudaSuccess)                                                          \
+            return LOR_ERR_CUDA;                                                      \
+        return LOR_OK;                                                                \
+    }                                                                                 \
     int name(cudaStream_t s, int clear) {                                             \
         int h = 0;                                                                    \
         if (cudaMemcpyFromSymbolAsync(&h, g_tu_status, sizeof(int), 0,               \
@@ -280,6 +308,7 @@ __device__ __forceinline__ uint32_t warp_lookback(uint64_t *lb, int64_t tile, ui
         return h;                                                                     \
     }                                                                                 \
     static int *tu_status_ptr() {                                                     \
+        if (int *o = lor::status_slot()) return o;                                    \
         static thread_local int *p = nullptr;                                         \
         static thread_local int dev = -1;                                             \
         int cur = -1;                                                                 \
@@ -305,6 +334,17 @@ int lor_status_serve(cudaStream_t s, int clear);
 int lor_status_multi(cudaStream_t s, int clear);
 int lor_status_topk(cudaStream_t s, int clear);
 int lor_status_sa64(cudaStream_t s, int clear);
+int lor_status_encode_set_wait(uint64_t limit_ns, int starve);
+int lor_status_dc3_set_wait(uint64_t limit_ns, int starve);
+int lor_status_lcp_set_wait(uint64_t limit_ns, int starve);
+int lor_status_overlap_set_wait(uint64_t limit_ns, int starve);
+int lor_status_rmq_set_wait(uint64_t limit_ns, int starve);
+int lor_status_abi_set_wait(uint64_t limit_ns, int starve);
+int lor_status_batch_set_wait(uint64_t limit_ns, int starve);
+int lor_status_serve_set_wait(uint64_t limit_ns, int starve);
+int lor_status_multi_set_wait(uint64_t limit_ns, int starve);
+int lor_status_topk_set_wait(uint64_t limit_ns, int starve);
+int lor_status_sa64_set_wait(uint64_t limit_ns, int starve);
 
 namespace lor {
 // Sparse-table rows 0..levels-1 over lcp[0..n) (rmq.cu); rows are

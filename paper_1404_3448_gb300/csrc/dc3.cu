@@ -15,6 +15,7 @@
 //           (t_i, t_i+1, rank(S_i+2)) with (t_j, t_j+1, rank(S_j+2)).  (The
 //           paper prints rank(S_i+1) for B2; i+2 is the sample position.)
 // The host drives the recursion and reads one count per level.
+#include <atomic>
 #include <cstdlib>
 #include <vector>
 
@@ -1416,13 +1417,19 @@ struct TraceRow {
 };
 thread_local std::vector<TraceRow> g_trace;
 
+// Route controls (lor_dc3_route_set): they pick how the sample is ordered,
+// never what the suffix array is.
+std::atomic<int> g_route_k0{0};        // symbols named at level 0 (0: from the key width)
+std::atomic<int> g_route_strategy{0};  // 1: radix sort at every level
+std::atomic<int> g_route_doubling{1};  // 0 never, 1 when names are almost unique, 2 whenever names repeat
+
 // Symbols named at level 0: the longest prefix whose key, in base maxc + 1,
 // fits the configured key width (48 bits by default: six 8-bit radix passes,
 // 17 symbols for a DNA pair),
 // so that on text without long repeats the names come out almost unique and
 // the reduced string is finished by prefix doubling.  Naming by any prefix of
 // at least 3 symbols keeps the order of the reduced string's suffixes equal
-// to the order of the sample suffixes.  LOR_DC3_K0 overrides it (a test hook).
+// to the order of the sample suffixes.  lor_dc3_route_set can force it.
 int level0_kchars(int bits, int64_t maxc) {
     const int budget = tune_config().level0_key_bits;
     int k = 0;
@@ -1431,10 +1438,8 @@ int level0_kchars(int bits, int64_t maxc) {
         if (T > (unsigned __int128)1 << budget) break;
     }
     if (k < 3) k = 3;
-    if (const char *e = std::getenv("LOR_DC3_K0")) {
-        const int v = std::atoi(e);
-        if (v >= 3) k = v;
-    }
+    const int forced = g_route_k0.load(std::memory_order_relaxed);
+    if (forced >= 3) k = forced;
     const int kmax = 64 / (bits > 0 ? bits : 1);
     return k > kmax ? kmax : k;
 }
@@ -1907,8 +1912,8 @@ int merge_run(Dc3Run &D, const LevelSizes &z, const GroupRec<CharT> *rec, const 
 
 
 // Doubling replaces the next level when at most 1/kDoublingShare of the
-// samples lost their name to a duplicate (LOR_DC3_DOUBLING: "0" never,
-// "force" whenever names repeat; a test hook).
+// samples lost their name to a duplicate (lor_dc3_route_set's doubling
+// route: 0 never, 2 whenever names repeat).
 constexpr int64_t kDoublingShare = 16;
 
 // ---- prefix doubling with every round enqueued up front (graph mode)
@@ -2167,12 +2172,8 @@ int lor::build_sa_impl(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t 
     for (int i = 0; i < 6; ++i) D.t32[i] = (uint32_t *)(D.ws + D.L.t32[i]);
     D.tbl = (uint32_t *)(D.ws + D.L.tbl);
     D.d_count = (uint32_t *)(D.ws + D.L.ctrl + 128);
-    {
-        const char *e = std::getenv("LOR_DC3_STRATEGY");
-        D.force_lsd = e && e[0] == 's';  // "sort": radix-sort every level (test hook)
-        const char *d = std::getenv("LOR_DC3_DOUBLING");
-        D.doubling = !d ? 1 : (d[0] == '0' ? 0 : (d[0] == 'f' ? 2 : 1));
-    }
+    D.force_lsd = g_route_strategy.load(std::memory_order_relaxed) == 1;  // radix-sort every level
+    D.doubling = g_route_doubling.load(std::memory_order_relaxed);
     LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.ctrl, 0, 256, D.s));
     LOR_CUDA_TRY(cudaMemsetAsync(D.ws + D.L.lookback, 0, D.L.lookback_bytes, D.s));
     g_trace.clear();
@@ -2186,6 +2187,23 @@ int lor::build_sa_impl(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t 
         return dc3_graph(D, d_text, n, int64_t(sigma - 1), d_sa);
     }
     return dc3_level<uint8_t>(D, 0, d_text, n, int64_t(sigma - 1), d_sa, nullptr, nullptr);
+}
+
+extern "C" int lor_dc3_route_set(int32_t level0_symbols, int32_t strategy, int32_t doubling) {
+    if (level0_symbols < 0 || level0_symbols > kKeyMaxChars || (level0_symbols > 0 && level0_symbols < 3) ||
+        strategy < 0 || strategy > 1 || doubling < 0 || doubling > 2)
+        return LOR_ERR_INVALID_ARG;
+    g_route_k0.store(level0_symbols);
+    g_route_strategy.store(strategy);
+    g_route_doubling.store(doubling);
+    return LOR_OK;
+}
+
+extern "C" int lor_dc3_route_get(int32_t *level0_symbols, int32_t *strategy, int32_t *doubling) {
+    if (level0_symbols) *level0_symbols = g_route_k0.load();
+    if (strategy) *strategy = g_route_strategy.load();
+    if (doubling) *doubling = g_route_doubling.load();
+    return LOR_OK;
 }
 
 extern "C" int lor_last_dc3_trace(int64_t *h_n, int64_t *h_names, int32_t *h_key_bits,

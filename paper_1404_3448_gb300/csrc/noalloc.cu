@@ -15,6 +15,11 @@
 // serialised by the caller.  lor_build_sa clears the parts that must start at
 // zero (counters and look-back flags) at the start of every call, so the
 // contents left by the previous call do no harm.
+//
+// The array's device address is looked up once per device and kept for the
+// life of the process; after cudaDeviceReset the library's device memory is
+// gone (the array may come back elsewhere), so this entry point must not be
+// used again in that process.
 #include <mutex>
 
 #include "common.cuh"
@@ -48,8 +53,9 @@ int scratch_address(void **out) {
 
 extern "C" int lor_build_sa_noalloc(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
                                     lor_stream_t stream) {
-    if (n > LOR_NOALLOC_MAX_N) return LOR_ERR_TOO_LARGE;
+    // argument checks in lor_build_sa's order, then this entry point's size limit
     if (!d_text || !d_sa || n < 1 || sigma < 2 || sigma > 256) return LOR_ERR_INVALID_ARG;
+    if (n > LOR_NOALLOC_MAX_N) return LOR_ERR_TOO_LARGE;
     const size_t need = lor_build_sa_workspace_size(n, sigma);
     if (need == 0 || need > kNoAllocScratchBytes) return LOR_ERR_WORKSPACE;
     void *ws = nullptr;

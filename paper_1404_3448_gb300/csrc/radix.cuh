@@ -148,14 +148,14 @@ struct OnesweepSmem {
 // loads (the walk is a chain of L2 round trips, so fewer rounds is less
 // waiting), summing aggregates up to the first inclusive prefix.  A
 // descriptor not yet published ends the round; the walk resumes there.  The
-// whole wait is bounded by kSpinLimitNs (then LOR_ERR_TIMEOUT).
+// whole wait is bounded by the wait limit (then LOR_ERR_TIMEOUT).
 constexpr int kLookWindow = 2;
 
 __device__ __forceinline__ uint32_t lookback_digit(const uint64_t *lb, int64_t tile, int dg, uint32_t epoch,
                                                    int *status) {
     uint32_t excl = 0;
     int64_t j = tile - 1;
-    const uint64_t t0 = global_ns();
+    const uint64_t t0 = global_ns(), limit = wait_limit_ns();
     while (j >= 0) {
         uint64_t w[kLookWindow];
 #pragma unroll
@@ -173,7 +173,7 @@ __device__ __forceinline__ uint32_t lookback_digit(const uint64_t *lb, int64_t t
         }
         if (done) break;
         j -= used;
-        if (used == 0 && global_ns() - t0 > kSpinLimitNs) {
+        if (used == 0 && global_ns() - t0 > limit) {
             atomicCAS(status, 0, LOR_ERR_TIMEOUT);
             break;
         }
@@ -184,7 +184,7 @@ __device__ __forceinline__ uint32_t lookback_digit(const uint64_t *lb, int64_t t
 // One LSD pass over digit (shift .. shift+7).  A grid of a few blocks per SM
 // stays resident and every block claims tiles from the running counter until
 // it draws one past the end, so a tile only ever waits on tiles claimed
-// before it by running blocks; each wait is still bounded by kSpinLimitNs.
+// before it by running blocks; each wait is still bounded by the wait limit.
 // Every block makes exactly one claim past the last tile: a launch advances
 // the counter by ntiles + gridDim.x.  When m_dev is given the element count
 // is read from device memory (the count of an earlier kernel), so that the
@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (m_dev) m = int64_t(*m_dev);
     const int64_t ntiles = cdiv(m, kTile);
+    const bool starve = g_starve_first_tile != 0;  // test switch, off in normal use
     // A claim also asks the L2 for the data of the tile `ahead` claims later.
     // (A tile is claimed only when its block is ready to work on it: a tile
     // claimed early would hold up the look-back of every later tile.)
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         for (int i = 0; i < kItems; ++i)
             if (wbase + i * 32 + lane < m) atomicAdd(&S.early[digit_of(k[i], shift, dmask)], 1u);
         __syncthreads();
-        {
+        if (!(starve && tile == 0)) {
             const uint32_t e = S.early[tid];
             st_volatile_u64(&lookback[tile * kRadix + tid], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, e));
         }

@@ -102,6 +102,9 @@ def load():
         "lor_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lor_launch_count": ([], ctypes.c_uint64),
         "lor_last_dc3_trace": ([vp, vp, vp, vp, vp, i32], ctypes.c_int),
+        "lor_dc3_route_set": ([i32, i32, i32], ctypes.c_int),
+        "lor_dc3_route_get": ([vp, vp, vp], ctypes.c_int),
+        "lor_test_set_wait": ([ctypes.c_uint64, i32], ctypes.c_int),
         "lor_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "lor_profile_reset": ([], ctypes.c_int),
         "lor_profile_kinds": ([], ctypes.c_int),
@@ -449,6 +452,46 @@ def tune_set(**values) -> dict:
     t = Tune(**{**tune_get(), **values})
     _check(load().lor_tune_set(ctypes.byref(t)), "lor_tune_set")
     return t.as_dict()
+
+
+_STRATEGIES = {"auto": 0, "sort": 1}
+_DOUBLING = {"never": 0, "auto": 1, "force": 2}
+
+
+def dc3_route_get() -> dict:
+    k0, st, db = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().lor_dc3_route_get(ctypes.byref(k0), ctypes.byref(st), ctypes.byref(db)), "lor_dc3_route_get")
+    inv_s = {v: k for k, v in _STRATEGIES.items()}
+    inv_d = {v: k for k, v in _DOUBLING.items()}
+    return {"level0_symbols": int(k0.value), "strategy": inv_s[st.value], "doubling": inv_d[db.value]}
+
+
+def dc3_route_set(level0_symbols: int = 0, strategy: str = "auto", doubling: str = "auto") -> dict:
+    """lor_dc3_route_set: how the suffix array orders its samples (never what
+    it returns).  strategy "auto" | "sort"; doubling "never" | "auto" | "force"."""
+    _check(load().lor_dc3_route_set(int(level0_symbols), _STRATEGIES[strategy], _DOUBLING[doubling]),
+           "lor_dc3_route_set")
+    return dc3_route_get()
+
+
+class dc3_route:
+    """Context manager: a DC3 route for the body, the defaults afterwards."""
+
+    def __init__(self, **route):
+        self.route = route
+
+    def __enter__(self):
+        return dc3_route_set(**self.route)
+
+    def __exit__(self, *exc):
+        dc3_route_set()
+        return False
+
+
+def test_set_wait(limit_ns: int = 0, starve_first_tile: bool = False) -> None:
+    """lor_test_set_wait: the bounded waits' limit (0 = default 2 s) and the
+    switch that withholds the first radix tile's look-back descriptor."""
+    _check(load().lor_test_set_wait(int(limit_ns), 1 if starve_first_tile else 0), "lor_test_set_wait")
 
 
 def autotune_batch(batch: "Batch", ascii_dev, reps: int = 2, stream=None):

@@ -136,20 +136,28 @@ def test_encode_bad_symbol_reports_status(L):
 STRATEGIES = ["auto", "sort", "dbl"]
 
 
-def set_strategy(monkeypatch, strategy):
-    if strategy == "sort":
-        monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
-        monkeypatch.setenv("LOR_DC3_DOUBLING", "0")
-    elif strategy == "dbl":
-        monkeypatch.setenv("LOR_DC3_DOUBLING", "force")
-    elif strategy == "nodbl":
-        monkeypatch.setenv("LOR_DC3_DOUBLING", "0")
+@pytest.fixture
+def route(L):
+    """Sets a DC3 route (lor_dc3_route_set) for one test, then the default."""
+    def set_strategy(strategy="auto", k0=0):
+        if strategy == "sort":
+            L.dc3_route_set(k0, "sort", "never")
+        elif strategy == "dbl":
+            L.dc3_route_set(k0, "auto", "force")
+        elif strategy == "sortdbl":
+            L.dc3_route_set(k0, "sort", "force")
+        elif strategy == "nodbl":
+            L.dc3_route_set(k0, "auto", "never")
+        else:
+            L.dc3_route_set(k0)
+    yield set_strategy
+    L.dc3_route_set()
 
 
 
 @pytest.mark.parametrize("strategy", STRATEGIES)
-def test_fuzz_small_full_path(L, O, strategy, monkeypatch):
-    set_strategy(monkeypatch, strategy)
+def test_fuzz_small_full_path(L, O, strategy, route):
+    route(strategy)
     for seed in range(60):
         nseq = [2, 2, 3, 5][seed % 4]
         alpha = [b"ACGT", b"AC", b"A", b"ACGT"][seed % 4 if seed % 7 else 2]
@@ -184,8 +192,8 @@ SIZES = [1, 2, 3, 4, 5, 6, 7, 31, 32, 33, 1023, 1024, 1025, 2047, 2048, 2049, 40
 
 @pytest.mark.parametrize("strategy", STRATEGIES)
 @pytest.mark.parametrize("alpha", [b"ACGT", b"AC", b"A"])
-def test_sizes_span_tiles(L, O, alpha, strategy, monkeypatch):
-    set_strategy(monkeypatch, strategy)
+def test_sizes_span_tiles(L, O, alpha, strategy, route):
+    route(strategy)
     rng = np.random.default_rng(len(alpha))
     a = np.frombuffer(alpha, np.uint8)
     for total in SIZES:
@@ -200,9 +208,8 @@ def test_sizes_span_tiles(L, O, alpha, strategy, monkeypatch):
 
 @pytest.mark.parametrize("strategy", STRATEGIES + ["nodbl"])
 @pytest.mark.parametrize("k0", ["3", "4", "7", "10", "21"])
-def test_level0_prefix_lengths(L, O, k0, strategy, monkeypatch):
-    monkeypatch.setenv("LOR_DC3_K0", k0)
-    set_strategy(monkeypatch, strategy)
+def test_level0_prefix_lengths(L, O, k0, strategy, route):
+    route(strategy, int(k0))
     seqs, _ = gen.pair_noncoding(n_each=150_000, seed=31, shared_len=4000, core=900)
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -222,10 +229,9 @@ def test_deep_recursion_single_symbol(L, O):
 
 
 @pytest.mark.parametrize("seqlen", [35001, 4096])
-def test_doubling_on_one_symbol_runs(L, O, seqlen, monkeypatch):
+def test_doubling_on_one_symbol_runs(L, O, seqlen, route):
     # forced doubling from level 0: every group splits by one suffix per pass
-    set_strategy(monkeypatch, "dbl")
-    monkeypatch.setenv("LOR_DC3_STRATEGY", "sort")
+    route("sortdbl")
     seqs = [np.full(seqlen, ord("A"), np.uint8), np.full(seqlen // 2, ord("A"), np.uint8)]
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -234,11 +240,10 @@ def test_doubling_on_one_symbol_runs(L, O, seqlen, monkeypatch):
     assert [t["strategy"] for t in trace] == ["sort", "doubling"], trace
 
 
-def test_wide_triples_two_stage_sort(L, O, monkeypatch):
+def test_wide_triples_two_stage_sort(L, O, route):
     # radix sorts at every level: level-2 names need > 21 bits, so level-3
     # triples exceed 64 bits
-    monkeypatch.setenv("LOR_DC3_K0", "3")
-    set_strategy(monkeypatch, "sort")
+    route("sort", 3)
     seqs, _ = gen.pair_uniform(n_each=4_500_000, plant_len=700, seed=41)
     e = oracle_path(O, seqs, nthreads=NCPU)
     g = gpu_path(L, seqs, rmq=False)
@@ -289,10 +294,9 @@ def noncoding_16M(O):
 
 
 @pytest.mark.parametrize("strategy", ["auto", "nodbl", "k3nodbl"])
-def test_noncoding_workload_2x16M(L, O, noncoding_16M, strategy, monkeypatch):
-    if strategy == "k3nodbl":  # level 0 named by triples: a dense level, then sorted and parent levels
-        monkeypatch.setenv("LOR_DC3_K0", "3")
-    set_strategy(monkeypatch, "nodbl" if strategy == "k3nodbl" else strategy)
+def test_noncoding_workload_2x16M(L, O, noncoding_16M, strategy, route):
+    # k3nodbl: level 0 named by triples: a dense level, then sorted and parent levels
+    route("nodbl" if strategy == "k3nodbl" else strategy, 3 if strategy == "k3nodbl" else 0)
     seqs, info, e, p, q, answers = noncoding_16M
     g = gpu_path(L, seqs, (p, q), rmq=True)
     assert_full_parity(O, g, e, table=False)
