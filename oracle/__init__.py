@@ -562,3 +562,46 @@ def radix_sort_split(keys, nbits: int, values=None):
         nv[dest] = vals
         keys, vals = nk, nv
     return keys, vals
+
+
+# --------------------------------------------------------------------------
+# many independent pairs (the batched and served workloads): the functions
+# above, once per pair, spread over host processes
+# --------------------------------------------------------------------------
+
+def pair_overlap(a, b, queries=None):
+    """Record and positions of one pair alone (its own text S1#S2$), and the
+    direct-comparison LCP of each (p, q) suffix pair of that text when
+    ``queries`` = (P, Q) is given."""
+    text, starts, _ = encode_concat([a, b])
+    sa = suffix_array(text)
+    lcp = lcp_array(text, sa)
+    ov = longest_overlap(text, sa, lcp, starts)
+    if queries is not None:
+        ov["answers"] = lcp_pairs(text, np.asarray(queries[0], np.int32), np.asarray(queries[1], np.int32))
+    return ov
+
+
+def _pair_overlap_chunk(items):
+    return [pair_overlap(a, b, q) for a, b, q in items]
+
+
+def pair_overlaps(pairs, queries=None, processes=None):
+    """pair_overlap for every pair, in ``processes`` spawned worker processes
+    (default: every host core).  Spawned, not forked, so that a caller
+    holding a CUDA context can use it.  Returns the records in pair order."""
+    import multiprocessing as mp
+    items = [(a, b, None if queries is None else queries[i]) for i, (a, b) in enumerate(pairs)]
+    procs = processes or os.cpu_count() or 1
+    if procs <= 1 or len(items) < 2:
+        return _pair_overlap_chunk(items)
+    build()
+    # interleaved chunks balance long and short pairs across the workers
+    nchunk = min(len(items), procs * 4)
+    chunks = [items[c::nchunk] for c in range(nchunk)]
+    with mp.get_context("spawn").Pool(min(procs, nchunk)) as pool:
+        res = pool.map(_pair_overlap_chunk, chunks)
+    out = [None] * len(items)
+    for c, r in enumerate(res):
+        out[c::nchunk] = r
+    return out

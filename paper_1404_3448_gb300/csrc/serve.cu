@@ -161,6 +161,7 @@ struct Request {
     std::shared_ptr<Resident> res;
     int64_t text_off = 0;  // offset of S1#S2$ inside the batch text
     bool polled = false;
+    bool solo = false;  // runs in a batch of its own (its earlier batch failed on an input error)
 };
 
 // out[i] = LCP of suffixes P[i], Q[i] of the pair text at [off, off + len) of
@@ -219,6 +220,11 @@ struct lor_server {
     std::mutex qmu;
     cudaStream_t qs = nullptr;
     int32_t *dq = nullptr, *hq = nullptr;  // 3 * kQueryCap: p, q, answers
+    // Device status slots: one per worker, then one for the query stream.  A
+    // worker's kernels record errors only in its own slot (set_status_slot),
+    // and the worker reads and clears only that slot, so concurrent batches
+    // never see or erase each other's errors.
+    int *dstatus = nullptr;
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -234,8 +240,9 @@ bool admit(lor_server *S, int limit, std::vector<Request *> *batch, BatchPlan *p
     std::vector<int64_t> lens;
     int np = 0;
     int64_t n = 0;
+    if (!S->pending.empty() && S->pending.front()->solo) limit = 1;
     for (Request *r : S->pending) {
-        if (np == limit) break;
+        if (np == limit || (np > 0 && r->solo)) break;
         const int64_t add = r->la + r->lb + 2;
         if (np > 0 && n + add > S->cfg.max_batch_symbols) break;
         n += add;
@@ -257,7 +264,7 @@ bool admit(lor_server *S, int limit, std::vector<Request *> *batch, BatchPlan *p
     return true;
 }
 
-int run_batch(lor_server *S, const std::vector<Request *> &batch, const BatchPlan &P, char *wsb,
+int run_batch(lor_server *S, int *d_status, const std::vector<Request *> &batch, const BatchPlan &P, char *wsb,
               const std::shared_ptr<Resident> &res, cudaStream_t s, std::vector<int64_t> *offs,
               std::vector<lor_overlap> *outs, std::vector<int32_t> *hpos) {
     const int np = P.np;
@@ -290,7 +297,7 @@ int run_batch(lor_server *S, const std::vector<Request *> &batch, const BatchPla
     offs->resize(np + 1);
     LOR_CUDA_TRY(cudaMemcpyAsync(outs->data(), dout, sizeof(lor_overlap) * np, cudaMemcpyDeviceToHost, s));
     LOR_CUDA_TRY(cudaMemcpyAsync(offs->data(), doff, sizeof(int64_t) * (np + 1), cudaMemcpyDeviceToHost, s));
-    rc = lor_device_status((lor_stream_t)s);
+    rc = read_status_slot(d_status, s);  // this worker's errors only
     if (rc) return rc;
     const int64_t total = (*offs)[np];
     if (total < 0 || total > P.n) return LOR_ERR_BAD_INPUT;
@@ -303,8 +310,10 @@ int run_batch(lor_server *S, const std::vector<Request *> &batch, const BatchPla
     return LOR_OK;
 }
 
-void worker_main(lor_server *S) {
+void worker_main(lor_server *S, int w) {
     cudaSetDevice(S->device);
+    int *d_status = S->dstatus + w;
+    set_status_slot(d_status);  // every launch of this thread records errors here
     cudaStream_t s = nullptr;
     const bool stream_ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
     std::vector<Request *> batch;
@@ -353,8 +362,31 @@ void worker_main(lor_server *S) {
         res->table = (int32_t *)(S->base + off_r + P.o_table);
         res->stride = P.stride;
         res->live = P.np;
-        int rc = stream_ok ? run_batch(S, batch, P, S->base + off_w, res, s, &offs, &outs, &hpos) : LOR_ERR_CUDA;
+        int rc = stream_ok ? run_batch(S, d_status, batch, P, S->base + off_w, res, s, &offs, &outs, &hpos)
+                           : LOR_ERR_CUDA;
         if (rc == LOR_OK && stream_ok) rc = cudaStreamSynchronize(s) == cudaSuccess ? LOR_OK : LOR_ERR_CUDA;
+        if (rc == LOR_ERR_BAD_SYMBOL && P.np > 1) {
+            // An input error belongs to one request, not to the batch: run
+            // every request of the batch again alone, oldest first, so that
+            // only the offending one fails.
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->arena.release(off_w, P.work);
+                S->arena.release(off_r, P.resident);
+                for (auto it = batch.rbegin(); it != batch.rend(); ++it) {
+                    (*it)->solo = true;
+                    S->pending.push_front(*it);
+                }
+                S->st.batches--;
+                S->st.pairs -= P.np;
+                S->st.bases -= P.in_bytes;
+                S->in_flight--;
+            }
+            batch.clear();
+            S->cv_mem.notify_all();
+            S->cv_work.notify_all();
+            continue;
+        }
         const double td = S->now();
         int64_t text_off = 0;
         for (int p = 0; p < P.np; ++p) {
@@ -423,16 +455,19 @@ extern "C" int lor_server_create(const lor_server_config *cfg, lor_server **out)
     bool ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
               cudaStreamCreateWithPriority(&S->qs, cudaStreamNonBlocking, hi) == cudaSuccess &&
               cudaMalloc(&S->dq, sizeof(int32_t) * 3 * kQueryCap) == cudaSuccess &&
-              cudaHostAlloc(&S->hq, sizeof(int32_t) * 3 * kQueryCap, cudaHostAllocDefault) == cudaSuccess;
+              cudaHostAlloc(&S->hq, sizeof(int32_t) * 3 * kQueryCap, cudaHostAllocDefault) == cudaSuccess &&
+              cudaMalloc(&S->dstatus, sizeof(int) * (kMaxWorkers + 1)) == cudaSuccess &&
+              cudaMemset(S->dstatus, 0, sizeof(int) * (kMaxWorkers + 1)) == cudaSuccess;
     if (!ok) {
         if (S->qs) cudaStreamDestroy(S->qs);
+        if (S->dstatus) cudaFree(S->dstatus);
         if (S->dq) cudaFree(S->dq);
         if (S->hq) cudaFreeHost(S->hq);
         cudaFree(S->base);
         return LOR_ERR_CUDA;
     }
     lor_server *srv = S.release();
-    for (int w = 0; w < cfg->workers; ++w) srv->threads.emplace_back(worker_main, srv);
+    for (int w = 0; w < cfg->workers; ++w) srv->threads.emplace_back(worker_main, srv, w);
     *out = srv;
     return LOR_OK;
 }
@@ -508,8 +543,7 @@ extern "C" int lor_server_query(lor_server *S, int64_t id, const int32_t *h_p, c
         if (h_p[i] < 0 || h_p[i] >= len || h_q[i] < 0 || h_q[i] >= len) return LOR_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> qk(S->qmu);
     cudaSetDevice(S->device);
-    int *status = tu_status_ptr();
-    if (!status) return LOR_ERR_CUDA;
+    int *status = S->dstatus + kMaxWorkers;  // the query stream's own slot
     for (int32_t b = 0; b < nq; b += kQueryCap) {
         const int c = nq - b < kQueryCap ? nq - b : kQueryCap;
         memcpy(S->hq, h_p + b, sizeof(int32_t) * c);
@@ -524,6 +558,8 @@ extern "C" int lor_server_query(lor_server *S, int64_t id, const int32_t *h_p, c
         LOR_CUDA_TRY(cudaStreamSynchronize(S->qs));
         memcpy(h_out + b, S->hq + 2 * kQueryCap, sizeof(int32_t) * c);
     }
+    const int qrc = read_status_slot(status, S->qs);
+    if (qrc != LOR_OK) return qrc;
     std::lock_guard<std::mutex> lk(S->mu);
     S->st.queries += nq;
     return LOR_OK;
@@ -572,6 +608,7 @@ extern "C" int lor_server_destroy(lor_server *S) {
     cudaStreamSynchronize(S->qs);
     cudaStreamDestroy(S->qs);
     cudaFree(S->dq);
+    cudaFree(S->dstatus);
     cudaFreeHost(S->hq);
     cudaFree(S->base);
     delete S;

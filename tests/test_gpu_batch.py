@@ -169,3 +169,60 @@ def test_batch_graph_long_repeats(L, oracle_mod):
         assert_same(res[p], exp, p)
     assert_same(res[200], expect_pair(oracle_mod, *pairs[200]), 200)
     g.close()
+
+
+# ------------------------------------------------------------------ the full batched workload
+
+@pytest.fixture(scope="module")
+def batch4096(oracle_mod):
+    """The batched workload at its stated size: 4096 noncoding-like pairs with
+    per-sequence lengths log-uniform in [1k, 1M] (about 1.18e9 bases), and the
+    oracle's record for every pair alone, computed on all host cores."""
+    pairs = gen.pair_batch()
+    return pairs, oracle_mod.pair_overlaps(pairs)
+
+
+def _groups(pairs, cap_pairs=512, cap_symbols=1 << 28):
+    """Pair ranges [p0, p1) of the groups lor_batch_overlap forms (consecutive
+    pairs up to 512 pairs or 2^28 text symbols), to point at their edges."""
+    out, p0, n = [], 0, 0
+    for p, (a, b) in enumerate(pairs):
+        add = len(a) + len(b) + 2
+        if p > p0 and (p - p0 == cap_pairs or n + add > cap_symbols):
+            out.append((p0, p))
+            p0, n = p, 0
+        n += add
+    out.append((p0, len(pairs)))
+    return out
+
+
+def test_batch_4096_pairs_every_record_equals_oracle(L, batch4096):
+    """Every pair of the full batched workload, eager and as one CUDA graph
+    replayed twice: record and position list equal to the oracle's for that
+    pair alone.  The batch spans eight 512-pair groups, so group edges, the
+    pair-split pass over 2^27-symbol group texts and the segmented Kasai and
+    overlap all run at size."""
+    pairs, exp = batch4096
+    groups = _groups(pairs)
+    assert len(groups) >= 8 and max(p1 - p0 for p0, p1 in groups) == 512
+    longest = max(range(len(pairs)), key=lambda p: len(pairs[p][0]) + len(pairs[p][1]))
+    assert len(pairs[longest][0]) + len(pairs[longest][1]) > 1_500_000
+    flat = [s for pr in pairs for s in pr]
+    lens = [len(s) for s in flat]
+    ascii_dev = torch.from_numpy(np.concatenate(flat)).cuda()
+    pos_cap = 1 << 24
+    b = L.lor.Batch(lens, pos_cap=pos_cap)
+    b.run(ascii_dev)
+    L.check_device(where="batch of 4096 pairs")
+    res = b.results()
+    for p in range(len(pairs)):
+        assert_same(res[p], exp[p], p)
+    del b
+    g = L.lor.BatchGraph(lens, ascii_dev, pos_cap=pos_cap)
+    for rep in range(2):
+        g.run()
+        L.check_device(where=f"graph of 4096 pairs, replay {rep}")
+        res = g.results()
+        for p in range(len(pairs)):
+            assert_same(res[p], exp[p], (rep, p))
+    g.close()

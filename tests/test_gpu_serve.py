@@ -180,3 +180,53 @@ def test_serve_many_small_requests_match_batched_path(L):
     ref = b.results()
     for i, (r, _) in enumerate(mix):
         assert_record(r, ref[i], i)
+
+
+def test_serve_pairs_up_to_4M_bases(L, oracle_mod):
+    """Served requests at the sizes of the served workload (per-sequence
+    lengths log-uniform in [1k, 4M], two pairs near 4M bases each): each
+    request's record, positions and 16 follow-up answers equal the oracle's,
+    alone and in a mix where batches of several pairs run at once."""
+    pairs = [list(pr) for pr in gen.pair_batch(npairs=8, lo=1_000, hi=4_000_000, seed=140434493)]
+    pairs += [list(pr) for pr in gen.pair_batch(npairs=2, lo=3_500_000, hi=4_000_000, seed=140434494)]
+    assert max(len(a) + len(b) for a, b in pairs) > 7_000_000
+    queries = [queries_for(a, b, seed=1000 + i) for i, (a, b) in enumerate(pairs)]
+    exp = oracle_mod.pair_overlaps(pairs, queries=queries)
+    mix = serve_mix(L, pairs, workers=2, max_pairs=4, budget=24 << 30, gap_s=0)
+    alone = serve_mix(L, pairs, workers=1, max_pairs=1, budget=24 << 30, gap_s=0)
+    assert max(r["batch_pairs"] for r, _ in mix) > 1, "the mix never batched two requests"
+    for i in range(len(pairs)):
+        (rm, qm), (ra, qa) = mix[i], alone[i]
+        assert_record(rm, exp[i], ("mix", i))
+        assert_record(ra, exp[i], ("alone", i))
+        np.testing.assert_array_equal(qm, exp[i]["answers"], err_msg=f"mix queries {i}")
+        np.testing.assert_array_equal(qa, exp[i]["answers"], err_msg=f"alone queries {i}")
+
+
+def test_serve_bad_request_fails_alone(L, oracle_mod):
+    """One request holds a byte that is not a base.  Two workers run batches
+    at once, each recording device errors in a status slot of its own: the
+    bad request fails with LOR_ERR_BAD_SYMBOL, and every other request --
+    including those batched with it, which are run again alone -- succeeds
+    with the oracle's results.  Nothing leaks into lor_device_status."""
+    pairs = [list(pr) for pr in gen.pair_batch(npairs=40, lo=300, hi=30_000, seed=140434495)]
+    bad = 17
+    pairs[bad][0] = pairs[bad][0].copy()
+    pairs[bad][0][len(pairs[bad][0]) // 2] = ord("N")
+    exp = oracle_mod.pair_overlaps([pr for i, pr in enumerate(pairs) if i != bad])
+    exp.insert(bad, None)
+    L.check_device(where="before the server")
+    with L.Server(4 << 30, workers=2, max_batch_pairs=8) as srv:
+        ids = [srv.submit(a, b, tag=i) for i, (a, b) in enumerate(pairs)]
+        got = drain(srv, len(pairs))
+        for i, rid in enumerate(ids):
+            r = got[rid]
+            if i == bad:
+                assert r["status"] == L.lor.LOR_ERR_BAD_SYMBOL, r["status"]
+                continue
+            assert r["status"] == 0, (i, r["status"])
+            assert_record(r, exp[i], i)
+            srv.release(rid)
+        assert max(got[rid]["batch_pairs"] for rid in ids) > 1, "no request was batched"
+    assert L.device_status() == 0
+
