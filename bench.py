@@ -192,35 +192,99 @@ def ncu_traffic(kind, workload):
 
 # --------------------------------------------------------------------------- CPU (oracle)
 
-def cpu_sample_run(n_each, seed, nq):
-    """One pass of the oracle over a bounded sample of the same generator."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_path(seqs, threads, nq=0, seed=0, with_rmq=True):
+    """One pass of the oracle over an instance: encode, merge-sort suffix
+    array and direct-comparison LCP (on `threads` threads), overlap scan with
+    positions, and (with_rmq) the sparse table and nq direct-comparison LCP
+    queries.  Returns seconds."""
     import lor_inputs as gen
     import oracle
-    seqs, _ = gen.pair_uniform(n_each=n_each, plant_len=500, seed=seed)
     t0 = time.perf_counter()
     text, starts, _ = oracle.encode_concat(seqs)
-    sa = oracle.suffix_array(text, nthreads=1)
-    lcp = oracle.lcp_array(text, sa, nthreads=1)
+    sa = oracle.suffix_array(text, nthreads=threads)
+    lcp = oracle.lcp_array(text, sa, nthreads=threads)
     oracle.longest_overlap(text, sa, lcp, starts)
-    oracle.sparse_table(lcp)
-    p, q = gen.random_queries(len(text), count=nq, seed=seed)
-    oracle.lcp_pairs(text, p, q)
-    return time.perf_counter() - t0, 2 * n_each
+    if with_rmq:
+        oracle.sparse_table(lcp)
+        p, q = gen.random_queries(len(text), count=nq, seed=seed)
+        oracle.lcp_pairs(text, p, q)
+    return time.perf_counter() - t0
 
 
-def cpu_baseline(budget_s=15.0):
+def cpu_sample_run(n_each, seed, nq, threads):
+    """The oracle over a bounded sample of the large workload's generator."""
+    import lor_inputs as gen
+    seqs, _ = gen.pair_uniform(n_each=n_each, plant_len=500, seed=seed)
+    return cpu_path(seqs, threads, nq=nq, seed=seed), 2 * n_each
+
+
+def cpu_baseline(budget_s=20.0):
+    """The oracle on every host core over a bounded sample of the benchmark
+    workload (the same generator, a1-a12 as in the timed step, queries scaled
+    with the sample), grown until one pass takes about budget_s."""
     import oracle
     oracle.build()
-    n_each = 1 << 20
-    dt, bases = cpu_sample_run(n_each, 140434483, 10_000)
-    # scale the sample so it takes roughly the budget, then time it once more
-    scale = max(1, min(8, int(budget_s / max(dt, 1e-3))))
-    if scale > 1:
-        dt, bases = cpu_sample_run(n_each * scale, 140434483, 10_000 * scale)
-    return {"value": bases / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle (merge-sort SA, naive LCP, overlap scan, sparse table, direct-"
-                      f"comparison queries) on 2x{n_each * scale} iid-uniform bases, 1 thread, "
-                      f"{dt:.1f} s"}
+    cores = host_cores()
+    n_each, nq = 1 << 21, 8_000
+    dt, bases = cpu_sample_run(n_each, 140434483, nq, cores)
+    while dt < budget_s / 2.5 and n_each < (1 << 25):
+        n_each, nq = 2 * n_each, 2 * nq
+        dt, bases = cpu_sample_run(n_each, 140434483, nq, cores)
+    return {"value": bases / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle (merge-sort SA and LCP on {cores} threads; overlap scan, sparse table and "
+                      f"{nq} direct-comparison queries on one) on 2x{n_each} iid-uniform bases of the "
+                      f"benchmark's generator, {dt:.1f} s"}
+
+
+def cpu_full_large(rate_hint, cap_s):
+    """The oracle on the full 2 x 134,217,728 instance, a1-a10 (encode, suffix
+    array, LCP, overlap with positions) on every host core; skipped with its
+    predicted time when that exceeds cap_s."""
+    import lor_inputs as gen
+    cores = host_cores()
+    kw = WORKLOADS["large"][0]
+    bases = 2 * kw["n_each"]
+    # the n log n sort dominates: scale the sample's rate by the log ratio
+    predicted = bases / rate_hint * 1.25
+    rec = {"workload": WORKLOADS["large"][2].split(";")[0], "cores": cores, "unit": UNIT,
+           "cap_s": cap_s, "predicted_s": predicted, "steps": "a1-a10"}
+    if predicted > cap_s:
+        rec.update(value=None, note=f"> cap: predicted {predicted:.0f} s on {cores} cores")
+        return rec
+    seqs, _ = gen.pair_uniform(**kw)
+    dt = cpu_path(seqs, cores, with_rmq=False)
+    rec.update(value=bases / dt, seconds=dt)
+    return rec
+
+
+def cpu_single_thread_rows():
+    """The oracle on one thread, a1-a10, over the small workloads: the two
+    100,000-base sequences, the two 16,777,216-base noncoding-like sequences
+    and the first 64 pairs of the batched workload."""
+    import lor_inputs as gen
+    import oracle
+    out = {}
+    seqs, _ = gen.pair_uniform(**WORKLOADS["tiny"][0])
+    dt = cpu_path(seqs, 1, with_rmq=False)
+    out["2x100000 uniform"] = {"value": 2 * 100_000 / dt, "unit": UNIT, "seconds": dt}
+    seqs, _ = gen.pair_noncoding()
+    dt = cpu_path(seqs, 1, with_rmq=False)
+    out["2x16777216 noncoding-like"] = {"value": sum(len(x) for x in seqs) / dt, "unit": UNIT, "seconds": dt}
+    pairs = gen.pair_batch(npairs=64, seed=140434484)
+    t0 = time.perf_counter()
+    for a, b in pairs:
+        oracle.pair_overlap(a, b)
+    dt = time.perf_counter() - t0
+    out["64 pairs of the batched workload"] = {"value": sum(len(a) + len(b) for a, b in pairs) / dt,
+                                                "unit": UNIT, "seconds": dt}
+    return out
 
 
 def run_reference(args):
@@ -229,23 +293,24 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
+    cores = host_cores()
     n_each = args.ref_bases // 2
     for i in range(args.warmup):
-        cpu_sample_run(n_each, 1000 + i, 20000)
+        cpu_sample_run(n_each, 1000 + i, 20000, cores)
     total_t, total_b = 0.0, 0
     for i in range(args.steps):
-        dt, b = cpu_sample_run(n_each, 2000 + i, 20000)
+        dt, b = cpu_sample_run(n_each, 2000 + i, 20000, cores)
         total_t += dt
         total_b += b
     value = total_b / total_t
-    sample = (f"oracle on 2x{n_each} iid-uniform bases per step (encode, merge-sort SA, naive "
-              f"LCP, overlap scan, sparse table, 20000 direct-comparison queries), 1 thread")
+    sample = (f"oracle on 2x{n_each} iid-uniform bases per step (encode, merge-sort SA and LCP on {cores} "
+              f"threads, overlap scan, sparse table, 20000 direct-comparison queries)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * total_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload][2], "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -500,49 +565,121 @@ def int64_run(n_each, steps, warmup, dev):
 
 # --------------------------------------------------------------------------- served
 
-def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed=140434485):
+class PinnedRing:
+    """Pinned host staging for request bytes, handed out in arrival order and
+    taken back once a request's result has been polled (the server reads the
+    host bytes until then)."""
+
+    def __init__(self, nbytes):
+        import torch
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, pin_memory=True)
+        self.view = self.buf.numpy()
+        self.size = int(nbytes)
+        self.head = 0
+        self.live = []  # [start, end, done] in allocation order
+        self.stalls = 0
+
+    def alloc(self, nbytes, is_done):
+        """Offset of nbytes of free ring space; waits (counted as a stall)
+        while the oldest live requests in the way are not done."""
+        start = self.head if self.head + nbytes <= self.size else 0
+        end = start + nbytes
+        stalled = False
+        while True:
+            while self.live and is_done(self.live[0][2]):
+                self.live.pop(0)
+            if not any(a < end and start < b for a, b, _ in self.live):
+                break
+            if not stalled:
+                self.stalls += 1
+                stalled = True
+            time.sleep(0.0002)
+        self.head = end
+        return start
+
+    def hold(self, start, nbytes, key):
+        self.live.append((start, start + nbytes, key))
+
+
+def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, subset=1500,
+            src_bases=1 << 27, seed=140434485):
     """Requests arrive as a Poisson process (``rate`` per second for
-    ``seconds``), each asking for one pair of a pool of noncoding-like pairs
-    (per-sequence lengths log-uniform in [1k, 4M]) held in pinned host memory.
-    A submitter thread submits on the arrival clock to a lor_server with a
-    ``budget_gb`` device reservation; the main thread polls results, asks the
-    request's ``queries`` follow-up LCP queries on its resident state and
-    releases it.  Reports sustained input bases/s and latency percentiles."""
+    ``seconds``).  Every request is a fresh pair: per-sequence lengths
+    log-uniform in [1k, 4M]; S1 a window of one noncoding-like source
+    sequence, S2 a window of another with one exact piece of S1 (length
+    uniform in [50, 5000], clamped to the shorter sequence) planted at a
+    random offset, copied into pinned staging memory on the arrival clock.
+    A submitter thread submits to a lor_server with a ``budget_gb`` device
+    reservation; the main thread polls results, asks each request's
+    ``queries`` follow-up LCP queries on its resident state and releases it.
+    Reports sustained input bases/s, latency percentiles and queue growth.
+    Then the first ``subset`` requests run again, once submitted all at once
+    (the server saturated) and once one pair per call through the plain
+    path (encode, SA, LCP, overlap; bytes copied from pinned memory), and the
+    records of the three runs are compared."""
     import threading
     import torch
     import lor_inputs as gen
     import paper_1404_3448_gb300 as lor
+    from paper_1404_3448_gb300 import lor as C
 
-    pool = gen.pair_batch(npairs=pool_pairs, lo=1_000, hi=4_000_000, seed=seed)
-    lens = [(len(a), len(b)) for a, b in pool]
-    total = sum(a + b for a, b in lens)
-    host = torch.empty(total, dtype=torch.uint8, pin_memory=True)
-    hv = host.numpy()
-    ptrs, off = [], 0
-    for a, b in pool:
-        hv[off:off + len(a)] = a
-        hv[off + len(a):off + len(a) + len(b)] = b
-        ptrs.append((host.data_ptr() + off, host.data_ptr() + off + len(a)))
-        off += len(a) + len(b)
+    rng = gen._rng(seed)
+    consensi = [gen.random_bases(rng, 300) for _ in range(5)]
+    src = []
+    for _ in range(2):
+        x, _ = gen.noncoding_sequence(rng, src_bases, consensi, None)
+        t = torch.from_numpy(x).pin_memory()
+        src.append(t)
+    src_np = [t.numpy() for t in src]
     arrivals = gen.poisson_arrivals(rate, seconds, seed=seed + 1)
-    choice, P, Q = gen.request_stream(len(arrivals), lens, queries=queries, seed=seed + 2)
     nreq = len(arrivals)
+    r2 = gen._rng(seed + 2)
+    lo, hi = np.log(1_000), np.log(4_000_000)
+    l1 = np.rint(np.exp(r2.uniform(lo, hi, nreq))).astype(np.int64)
+    l2 = np.rint(np.exp(r2.uniform(lo, hi, nreq))).astype(np.int64)
+    o1 = (r2.random(nreq) * (src_bases - l1 + 1)).astype(np.int64)
+    o2 = (r2.random(nreq) * (src_bases - l2 + 1)).astype(np.int64)
+    plen = np.minimum(r2.integers(50, 5001, nreq), np.minimum(l1, l2))
+    ps = (r2.random(nreq) * (l1 - plen + 1)).astype(np.int64)
+    pd = (r2.random(nreq) * (l2 - plen + 1)).astype(np.int64)
+    P = np.empty((nreq, queries), np.int32)
+    Q = np.empty((nreq, queries), np.int32)
+    ntext = l1 + l2 + 2
+    P[:] = (r2.random((nreq, queries)) * ntext[:, None]).astype(np.int64)
+    Q[:] = (r2.random((nreq, queries)) * ntext[:, None]).astype(np.int64)
+    bases = int((l1 + l2).sum())
+    ring = PinnedRing(ring_gb * (1 << 30))
+    done_flags = np.zeros(nreq, dtype=bool)
+
+    def stage(k):
+        """S2 of request k in the ring (S1 is read in place); returns pointers."""
+        off = ring.alloc(int(l2[k]), lambda j: done_flags[j])
+        s2 = ring.view[off:off + int(l2[k])]
+        s2[:] = src_np[1][o2[k]:o2[k] + l2[k]]
+        s2[pd[k]:pd[k] + plen[k]] = src_np[0][o1[k] + ps[k]:o1[k] + ps[k] + plen[k]]
+        ring.hold(off, int(l2[k]), k)
+        return src[0].data_ptr() + int(o1[k]), ring.buf.data_ptr() + off
 
     srv = lor.Server(int(budget_gb * (1 << 30)), workers=workers, max_batch_pairs=512)
     try:
-        # warm-up: every pool pair once, so first-launch setup is not timed
-        for k in range(pool_pairs):
-            srv.submit_ptr(ptrs[k][0], lens[k][0], ptrs[k][1], lens[k][1], tag=k)
+        # warm-up: the first 64 requests, so first-launch setup is not timed
+        for k in range(min(64, nreq)):
+            pa, pb = stage(k)
+            srv.submit_ptr(pa, int(l1[k]), pb, int(l2[k]), tag=k)
         got = 0
-        while got < pool_pairs:
+        while got < min(64, nreq):
             for r in srv.poll(timeout_ms=100):
                 if r["status"] != 0:
                     raise RuntimeError(f"warm-up request failed: {lor.lor.status_string(r['status'])}")
                 srv.release(r["id"])
+                done_flags[int(r["tag"])] = True
                 got += 1
-        first = {}
+        done_flags[:] = False
+        ring.live.clear()
         lat, qlat, sub_t, done_t = [], [], [], []
+        records = {}
         errors = []
+        pending_samples = []
         t0 = srv.now() + 0.05
 
         def submitter():
@@ -553,16 +690,21 @@ def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed
                         if wait <= 0:
                             break
                         time.sleep(min(wait, 0.001))
-                    c = int(choice[k])
-                    srv.submit_ptr(ptrs[c][0], lens[c][0], ptrs[c][1], lens[c][1], tag=k)
+                    pa, pb = stage(k)
+                    srv.submit_ptr(pa, int(l1[k]), pb, int(l2[k]), tag=k)
             except Exception as e:  # surfaced by the main thread
                 errors.append(e)
 
         th = threading.Thread(target=submitter, daemon=True)
         th.start()
         done = 0
-        consistent = True
+        sane = True
+        next_sample = t0
         while done < nreq and not errors:
+            if srv.now() >= next_sample:
+                st = srv.stats()
+                pending_samples.append((srv.now() - t0, st["pending"], st["in_flight"]))
+                next_sample += 0.5
             for r in srv.poll(timeout_ms=20):
                 k = int(r["tag"])
                 if r["status"] != 0:
@@ -570,13 +712,12 @@ def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed
                 q0 = time.perf_counter()
                 ans = srv.query(r["id"], P[k], Q[k])
                 qlat.append((time.perf_counter() - q0) * 1000.0)
-                c = int(choice[k])
-                rec = (r["length"], r["rank"], r["pos_a"], r["pos_b"], r["n_pos"])
-                if first.setdefault(c, rec) != rec:
-                    consistent = False
-                if ans.min() < 0:
-                    consistent = False
+                if ans.min() < 0 or r["length"] < int(plen[k]):  # the planted piece is exact
+                    sane = False
+                if k < subset:
+                    records[k] = (r["length"], r["rank"], r["pos_a"], r["pos_b"], r["n_pos"])
                 srv.release(r["id"])
+                done_flags[k] = True
                 lat.append((r["t_done"] - r["t_submit"]) * 1000.0)
                 sub_t.append(r["t_submit"])
                 done_t.append(r["t_done"])
@@ -585,27 +726,146 @@ def serving(seconds, rate, pool_pairs, workers, budget_gb, dev, queries=16, seed
         if errors:
             raise errors[0]
         st = srv.stats()
+
+        # the first `subset` requests again, all submitted at once
+        m = min(subset, nreq)
+        done_flags[:] = False
+        ring.live.clear()
+        sat_records = {}
+        s0 = srv.now()
+        for k in range(m):
+            pa, pb = stage(k)
+            srv.submit_ptr(pa, int(l1[k]), pb, int(l2[k]), tag=k)
+        got = 0
+        while got < m:
+            for r in srv.poll(timeout_ms=50):
+                k = int(r["tag"])
+                if r["status"] != 0:
+                    raise RuntimeError(f"request {k} failed: {lor.lor.status_string(r['status'])}")
+                sat_records[k] = (r["length"], r["rank"], r["pos_a"], r["pos_b"], r["n_pos"])
+                srv.release(r["id"])
+                done_flags[k] = True
+                got += 1
+        sat_s = srv.now() - s0
+        sat_st = srv.stats()
     finally:
         srv.close()
-    bases = int(sum(lens[int(c)][0] + lens[int(c)][1] for c in choice))
+    sub_bases = int((l1[:m] + l2[:m]).sum())
+
+    # the same first requests one pair per call through the plain path
+    nmax = int((l1[:m] + l2[:m]).max()) + 2
+    host_pair = torch.empty(nmax, dtype=torch.uint8, pin_memory=True)
+    hp = host_pair.numpy()
+    dev_pair = torch.empty(nmax, dtype=torch.uint8, device=dev)
+    text = torch.empty(nmax, dtype=torch.uint8, device=dev)
+    starts = torch.empty(3, dtype=torch.int32, device=dev)
+    sa = torch.empty(nmax, dtype=torch.int32, device=dev)
+    isa = torch.empty(nmax, dtype=torch.int32, device=dev)
+    lcp = torch.empty(nmax, dtype=torch.int32, device=dev)
+    out = torch.empty(8, dtype=torch.int32, device=dev)
+    pos = torch.empty(1 << 20, dtype=torch.int32, device=dev)
+    host_out = torch.empty(8, dtype=torch.int32, pin_memory=True)
+    ws = lor.workspace(max(C.lor_build_sa_workspace_size(nmax, 7), C.lor_lcp_workspace_size(nmax),
+                           C.lor_longest_overlap_workspace_size(nmax)), dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = int(stream.cuda_stream)
+    plain_same = True
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter()
+    for k in range(m):
+        a, b = int(l1[k]), int(l2[k])
+        hp[:a] = src_np[0][o1[k]:o1[k] + a]
+        hp[a:a + b] = src_np[1][o2[k]:o2[k] + b]
+        hp[a + pd[k]:a + pd[k] + plen[k]] = src_np[0][o1[k] + ps[k]:o1[k] + ps[k] + plen[k]]
+        dev_pair[:a + b].copy_(host_pair[:a + b], non_blocking=True)
+        l2a = np.array([a, b], dtype=np.int64)
+        n = a + b + 2
+        C._check(C.lor_encode_concat(dev_pair.data_ptr(), l2a.ctypes.data, 2, text.data_ptr(),
+                                     starts.data_ptr(), sp), "encode")
+        C._check(C.lor_build_sa(text.data_ptr(), n, 7, sa.data_ptr(), ws.data_ptr(), ws.numel(), sp), "sa")
+        C._check(C.lor_lcp(text.data_ptr(), sa.data_ptr(), n, isa.data_ptr(), lcp.data_ptr(), ws.data_ptr(),
+                           ws.numel(), sp), "lcp")
+        C._check(C.lor_longest_overlap(sa.data_ptr(), lcp.data_ptr(), n, starts.data_ptr(), 2, out.data_ptr(),
+                                       pos.data_ptr(), pos.numel(), ws.data_ptr(), ws.numel(), sp), "overlap")
+        host_out.copy_(out, non_blocking=True)
+        stream.synchronize()
+        o = host_out.tolist()
+        if (o[0], o[1], o[3], o[5], o[6]) != records.get(k) or records.get(k) != sat_records.get(k):
+            plain_same = False
+    plain_s = time.perf_counter() - t_plain
+    lor.check_device(where="plain requests")
+    del ws, sa, isa, lcp, text, dev_pair
+    torch.cuda.empty_cache()
+
     span = max(done_t) - min(sub_t)
+    served = bases / span
+    sat_value = sub_bases / sat_s
+    plain_value = sub_bases / plain_s
+    peak_pending = max((p for _, p, _ in pending_samples), default=0)
     return {
-        "workload": f"Poisson arrivals at {rate:g} pair requests/s for {seconds:g} s; pairs drawn uniformly "
-                    f"from a pool of {pool_pairs} noncoding-like pairs (per-sequence lengths log-uniform in "
-                    f"[1k, 4M]) in pinned host memory; {queries} follow-up LCP queries per pair on resident "
-                    f"state; {budget_gb:g} GB device budget; {workers} workers",
-        "requests": nreq, "input_bases": bases,
+        "workload": f"Poisson arrivals at {rate:g} pair requests/s for {seconds:g} s; every request a fresh "
+                    f"noncoding-like pair (per-sequence lengths log-uniform in [1k, 4M]; windows of two "
+                    f"{src_bases}-base source sequences, one exact 50-5000-base piece of S1 planted in S2), "
+                    f"staged in pinned host memory on the arrival clock; {queries} follow-up LCP queries per "
+                    f"pair on resident state; {budget_gb:g} GB device budget; {workers} workers",
+        "seconds": seconds, "requests": nreq, "input_bases": bases,
         "offered_bases_per_s": bases / float(arrivals[-1]) if nreq else 0.0,
-        "value": bases / span, "unit": UNIT,
+        "value": served, "unit": UNIT,
         "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "max": max(lat)},
         "query_call_ms": {"p50": percentile(qlat, 50), "p99": percentile(qlat, 99)},
         "batches": st["batches"], "mean_batch_pairs": st["pairs"] / max(st["batches"], 1),
         "admission_waits": st["admission_waits"], "peak_reserved_gb": st["peak_bytes"] / 2**30,
-        "results_consistent": consistent,
+        "queue": {"peak_pending": peak_pending, "pending_at_end_of_arrivals":
+                  next((p for t, p, _ in pending_samples if t >= seconds), None),
+                  "staging_stalls": ring.stalls},
+        "results_sane": sane,
+        "same_requests": {
+            "requests": m, "input_bases": sub_bases,
+            "served_saturated": {"value": sat_value, "unit": UNIT, "seconds": sat_s,
+                                 "mean_batch_pairs": (sat_st["pairs"] - st["pairs"]) /
+                                 max(sat_st["batches"] - st["batches"], 1)},
+            "plain_one_pair_per_call": {"value": plain_value, "unit": UNIT, "seconds": plain_s},
+            "served_over_plain": served / plain_value,
+            "saturated_over_plain": sat_value / plain_value,
+            "records_equal": plain_same},
     }
 
 
 # --------------------------------------------------------------------------- GPU
+
+# Kernel kinds of the sparse table and the LCP queries (a11, a12); every
+# other kind belongs to a1-a10.
+A11_A12_KINDS = ("rmq_level", "rmq_query")
+
+
+def dc3_recursion_run(lor, pipe, ascii_dev, p_dev, q_dev, ans_dev, stream, dev, steps, n_bases, sa_default,
+                      rec_default):
+    """The same step with the suffix array built by the paper's route: DC3
+    recursion on the reduced string while names repeat (Section 3, Step 1),
+    no prefix doubling.  Reports its time and that its suffix array and
+    overlap record equal the default route's."""
+    import torch
+    with lor.dc3_route(doubling="never"):
+        out, _ = pipe.run(ascii_dev, p_dev, q_dev, ans_dev)
+        torch.cuda.synchronize(dev)
+        lor.check_device(where="recursion warmup")
+        trace = lor.last_dc3_trace()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for i in range(steps):
+            out, _ = pipe.run(ascii_dev, p_dev, q_dev, ans_dev)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        lor.check_device(where="recursion steps")
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    ms = evs[0].elapsed_time(evs[-1]) / steps
+    return {"route": "DC3 recursion while names repeat (no prefix doubling)",
+            "steps": steps, "ms_per_step": ms, "value": n_bases / (ms / 1000.0), "unit": UNIT,
+            "step_latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99)},
+            "levels": [{"n": t["n"], "names": t["names"], "strategy": t["strategy"]} for t in trace],
+            "sa_equal_default": bool(torch.equal(pipe.sa, sa_default)),
+            "record_equal_default": bool(torch.equal(out.cpu()[:6], rec_default[:6]))}
+
 
 def run_lor(args):
     import torch
@@ -630,7 +890,7 @@ def run_lor(args):
     ascii_dev = host_ascii.to(dev)
     p_dev, q_dev = host_p.to(dev), host_q.to(dev)
     ans_dev = torch.empty_like(p_dev)
-    pipe = lor.Pipeline(lens, device=dev, pos_cap=1 << 16)
+    pipe = lor.Pipeline(lens, device=dev, pos_cap=1 << 16, with_rmq=not args.no_rmq)
     host_out = torch.empty(8, dtype=torch.int32).pin_memory()
     host_pos = torch.empty(1 << 16, dtype=torch.int32).pin_memory()
     host_ans = torch.empty_like(host_p).pin_memory()
@@ -723,6 +983,15 @@ def run_lor(args):
     except Exception as exc:  # reported, not hidden
         rmq_linear = {"error": str(exc)}
 
+    # ---- the paper's own route: DC3 recursion while names repeat, no doubling
+    dc3_recursion = None
+    if args.recursion_steps > 0:
+        sa_default = pipe.sa.clone()
+        rec_default = host_out.clone()
+        dc3_recursion = dc3_recursion_run(lor, pipe, ascii_dev, p_dev, q_dev, ans_dev, stream, dev,
+                                          args.recursion_steps, n_bases, sa_default, rec_default)
+        del sa_default
+
     ms_all, e2e_all, p50, p99 = max_over_ranks(
         [ms, e2e_ms, percentile(step_ms, 50), percentile(step_ms, 99)], device=dev)
 
@@ -745,6 +1014,19 @@ def run_lor(args):
                     "avg_launch_ms": d["ms"] / d["launches"],
                     "traffic": ncu_traffic(dom, args.workload)}
         path_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
+        # a1-a10 alone (the metric's SA + LCP + longest overlap): every kind but
+        # the sparse table and the queries
+        a10 = [v for k, v in prof.items() if k not in A11_A12_KINDS]
+        a10_bytes = sum(v["bytes"] for v in a10) / args.steps
+        a10_ms = sum(v["ms"] for v in a10) / args.steps
+        rmq_ms = sum(v["ms"] for k, v in prof.items() if k in A11_A12_KINDS) / args.steps
+        roof_a10 = {"bound": "hbm", "achieved": a10_bytes / (a10_ms / 1000.0) / 1e9, "peak": peak,
+                    "unit": "GB/s", "peak_source": peak_src,
+                    "frac": a10_bytes / (a10_ms / 1000.0) / 1e9 / peak,
+                    "model_bytes_per_step": a10_bytes, "kernel_ms_per_step": a10_ms,
+                    "step_ms_without_a11_a12": ms - rmq_ms,
+                    "frac_of_step_time": a10_bytes / ((ms - rmq_ms) / 1000.0) / 1e9 / peak,
+                    "kinds": sorted(k for k in prof if k not in A11_A12_KINDS)}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all,
@@ -756,6 +1038,7 @@ def run_lor(args):
                        "step": "a1-a12: encode, DC3 SA, ISA+LCP, overlap+positions, sparse "
                                "table, LCP queries"},
             "roofline": roof,
+            "roofline_a1_a10": roof_a10,
             "path_model_bytes_per_step": path_bytes,
             "path_model_gbs": path_bytes / (ms / 1000.0) / 1e9,
             "stage_ms": stage_ms,
@@ -766,11 +1049,15 @@ def run_lor(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "rmq_linear": rmq_linear,
+            "dc3_recursion": dc3_recursion,
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            cb = cpu_baseline()
+            line["cpu_baseline"] = cb
+            line["cpu_baseline_full"] = cpu_full_large(cb["value"], args.cpu_full_cap)
+            line["cpu_single_thread"] = cpu_single_thread_rows()
         if args.batch_pairs > 0:
             del pipe
             torch.cuda.empty_cache()
@@ -783,8 +1070,8 @@ def run_lor(args):
             line["int64"] = int64_run(args.int64_bases // 2, 2, 1, dev)
         if args.serve_seconds > 0:
             torch.cuda.empty_cache()
-            line["serving"] = serving(args.serve_seconds, args.serve_rate, args.serve_pool, args.serve_workers,
-                                      args.serve_budget_gb, dev)
+            line["serving"] = serving(args.serve_seconds, args.serve_rate, args.serve_workers,
+                                      args.serve_budget_gb, dev, subset=args.serve_subset)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -800,19 +1087,26 @@ def main():
     ap.add_argument("--impl", default="lor", choices=["lor", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rmq", action="store_true",
+                    help="leave out the sparse table and the queries (a11, a12): smaller profiling captures")
     ap.add_argument("--batch-pairs", type=int, default=4096,
                     help="pairs of the batched-vs-plain sub-measurement (0 skips it)")
     ap.add_argument("--multi-queries", type=int, default=65_536,
                     help="queries of the one-reference-many-queries sub-measurement (0 skips it)")
     ap.add_argument("--int64-bases", type=int, default=2 * ((1 << 30) + (1 << 15)),
                     help="input bases of the 64-bit index sub-measurement (past 2^31 symbols; 0 skips it)")
-    ap.add_argument("--serve-seconds", type=float, default=3.0,
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="seconds of Poisson arrivals of the served sub-measurement (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="pair requests per second")
-    ap.add_argument("--serve-pool", type=int, default=256, help="distinct pairs the requests draw from")
+    ap.add_argument("--serve-subset", type=int, default=1500,
+                    help="first requests rerun saturated and one pair per call through the plain path")
     ap.add_argument("--serve-workers", type=int, default=2)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
-    ap.add_argument("--ref-bases", type=int, default=1 << 22,
+    ap.add_argument("--recursion-steps", type=int, default=5,
+                    help="timed steps of the DC3-recursion route (0 skips it)")
+    ap.add_argument("--cpu-full-cap", type=float, default=300.0,
+                    help="seconds the full-size oracle run may be predicted to take, else it is skipped")
+    ap.add_argument("--ref-bases", type=int, default=1 << 23,
                     help="bases per step of the reference (oracle) arm")
     args = ap.parse_args()
     if args.impl == "reference":

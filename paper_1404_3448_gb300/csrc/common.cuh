@@ -95,6 +95,14 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Asks the L2 for the whole 16-byte groups inside [a, e): a hint that touches
+// nothing outside the range.
+template <typename T>
+__device__ __forceinline__ void prefetch_inside(const T *a, const T *e) {
+    const uintptr_t lo = (uintptr_t(a) + 15) & ~uintptr_t(15), hi = uintptr_t(e) & ~uintptr_t(15);
+    if (hi > lo && hi - lo < (uintptr_t(1) << 31)) prefetch_l2_bulk((const void *)lo, uint32_t(hi - lo));
+}
+
 // Tiles a radix pass asks the L2 to fetch ahead of the one it works on: the
 // number of tiles resident at once (four 256-thread blocks per SM, or the
 // grid of a persistent pass), so that the data of the tile a block takes next
@@ -107,6 +115,45 @@ inline int64_t prefetch_ahead(const void *a, const void *b, int64_t resident = 0
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
     return int64_t(4) * sms;
+}
+
+// ---- mbarrier + bulk (TMA) copies into shared memory
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return uint32_t(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Makes initialised barriers visible to the async proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later bulk
+// copies into shared memory (generic -> async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
 // ---- L2 cache policies: data that random reads will come back to is kept
@@ -153,6 +200,15 @@ constexpr uint64_t kSpinLimitNs = 2000000000ull;  // 2 s
 static __device__ uint64_t g_wait_limit_ns = kSpinLimitNs;
 static __device__ int g_starve_first_tile = 0;
 __device__ __forceinline__ uint64_t wait_limit_ns() { return *(volatile uint64_t *)&g_wait_limit_ns; }
+
+// Waits for phase `parity` of a barrier for at most `limit` ns; false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit) return false;
+    return true;
+}
 
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
     uint64_t v;

@@ -50,7 +50,14 @@ std::vector<int64_t> level_chain(int64_t n) {
 
 constexpr size_t kPad = 4;  // zero symbols kept after every reduced string
 
+// Tiles of the level-0 nonsample split (entries of SAR per tile, 16 per
+// thread) and the number of tile ranges its scan works in.
+constexpr int kSpItems = 8;
+constexpr int kSpTile = 256 * kSpItems;
+constexpr int kSpRanges = 512;
+
 struct Dc3Layout {
+    size_t ns_table = 0;  // the split's per-tile starts (level 0)
     size_t ctrl = 0, hist = 0, offsets = 0, lookback = 0, lookback_bytes = 0;
     size_t tbl = 0;
     int64_t tbl_entries = 0;
@@ -92,6 +99,7 @@ Dc3Layout dc3_layout(int64_t n) {
     for (int i = 0; i < 3; ++i) L.t64[i] = take(sizeof(uint64_t) * size_t(L.max_m));
     L.split = take(sizeof(int64_t) * size_t(cdiv(n, 1024) + 2));
     for (int i = 0; i < 6; ++i) L.t32[i] = take(sizeof(uint32_t) * size_t(L.max_m));
+    L.ns_table = take(sizeof(uint32_t) * 256 * size_t(cdiv(L.max_m, kSpTile) + kSpRanges));
     for (size_t l = 0; l < L.lev_n.size(); ++l) {
         const int64_t m = level_sizes(L.lev_n[l]).n02;
         L.lev_R.push_back(take(sizeof(int32_t) * (size_t(m) + kPad)));
@@ -453,7 +461,7 @@ __global__ void k_group_records(const CharT *__restrict__ s, int64_t n, int64_t 
 }
 
 // Nonsample suffix 3t with its comparison key, in nonsample order (written
-// by k_nonsample_rec at level 0): t, t_3t | t_3t+1 << 8, rank(S_3t+1),
+// by k_nonsample_split at level 0): t, t_3t | t_3t+1 << 8, rank(S_3t+1),
 // rank(S_3t+2).
 struct __align__(16) BRec16 {
     int32_t t;
@@ -497,12 +505,10 @@ __device__ __forceinline__ ARec make_a(const GroupRec<CharT> &g, int32_t r, int3
     }
     return x;
 }
-// A sample's comparison key packed in 8 bytes (level 0): rank in the low
-// word, then t_p and t_p+1 (0xFF when the key has one symbol: p = 1 mod 3).
-__device__ __forceinline__ uint64_t pack_a(const ARec &x) {
-    return uint64_t(uint32_t(x.r)) | (uint64_t(uint32_t(x.c0) & 0xFFu) << 32) |
-           (uint64_t(x.c1 < 0 ? 0xFFu : uint32_t(x.c1) & 0xFFu) << 40);
-}
+// A sample's comparison key packed in 8 bytes (level 0, written by the
+// bucketed scatter of SampleKeySrc): rank in the low word, then t_p and, for
+// p = 2 mod 3, t_p+1 (for p = 1 mod 3 that byte holds t_p-1, which the
+// comparison does not read; the class comes from the reduced-string index).
 __device__ __forceinline__ ARec unpack_a(uint64_t w, int32_t r, int32_t n0) {
     ARec x;
     x.pos = r < n0 ? 3 * r + 1 : 3 * (r - n0) + 2;
@@ -701,83 +707,217 @@ struct NsSmem {
     long long tile;
 };
 
-// Every sample's own merge key is taken from the same gathered record (a B1
-// sample 3x+1 and the nonsample 3x share group x) and written to Ax in
-// sample order, so that the merge reads both orders without gathers.
-__global__ void __launch_bounds__(kSortThreads) k_nonsample_rec(
-    const int32_t *__restrict__ SAR, int64_t n02, int64_t n0, const GroupRec<uint8_t> *__restrict__ rec,
-    const uint32_t *__restrict__ offsets, BRec16 *__restrict__ out, uint64_t *__restrict__ Ax,
-    uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base, uint32_t epoch,
-    int *status) {
-    __shared__ NsSmem S;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
-    for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&S.warp_hist[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t tile = S.tile;
-    const int64_t wbase = tile * kNsTile + int64_t(warp) * (kNsItems * 32);
-    BRec16 v[kNsItems];
-    uint32_t dig[kNsItems], r[kNsItems];
-#pragma unroll
-    for (int i = 0; i < kNsItems; ++i) {
-        const int64_t idx = wbase + i * 32 + lane;
-        const int32_t x = idx < n02 ? SAR[idx] : -1;
-        dig[i] = 0x100u;
-        if (x >= 0 && x < n02) {
-            const GroupRec<uint8_t> g = rec[a_group(x, int32_t(n0))];
-            Ax[idx] = pack_a(make_a(g, x, int32_t(n0)));
-            if (x < n0) {
-                v[i].t = x;
-                v[i].c01 = g.c4 & 0xFFFFu;
-                v[i].r1 = g.r1;
-                v[i].r2 = g.r2;
-                dig[i] = g.c4 & 0xFFu;
-            }
+// Every sample's merge key (Step 3), made in reduced-string order x from the
+// text and the ranks (all read in sequence) and keyed by the sample's index
+// in sample order, j = rank(S_x) - 1, for a bucketed scatter into Ax[j]:
+//   B1 sample p = 3x+1: rank(S_p+1) in the low word, t_p in byte 4 and t_p-1
+//       (the first symbol of the nonsample 3x) in byte 5;
+//   B2 sample p = 3x'+2 (x = n0 + x'): rank(S_p+2), t_p, t_p+1.
+// (x = n0 - 1 is the dummy sample at p = n when n mod 3 == 1: symbols 0.)
+struct SampleKeySrc {
+    const uint8_t *s;
+    const int32_t *Rl;
+    int64_t n, n0, n2;
+    __device__ __forceinline__ void load(int64_t x, bool valid, uint32_t &k, uint64_t &v) const {
+        if (!valid) {
+            k = 0;
+            v = 0;
+            return;
+        }
+        k = uint32_t(Rl[x] - 1);
+        if (x < n0) {
+            const int64_t p = 3 * x + 1;
+            const uint64_t c0 = p < n ? s[p] : 0, cm = s[p - 1];
+            const uint32_t r = x < n2 ? uint32_t(Rl[n0 + x]) : 0u;
+            v = uint64_t(r) | (c0 << 32) | (cm << 40);
+        } else {
+            const int64_t xp = x - n0, p = 3 * xp + 2;
+            const uint64_t c0 = p < n ? s[p] : 0, c1 = p + 1 < n ? s[p + 1] : 0;
+            const uint32_t r = xp + 1 < n0 ? uint32_t(Rl[xp + 1]) : 0u;
+            v = uint64_t(r) | (c0 << 32) | (c1 << 40);
         }
     }
-    uint32_t *wh = S.warp_hist[warp];
-#pragma unroll
-    for (int i = 0; i < kNsItems; ++i) {
-        const uint32_t d = dig[i];
-        const uint32_t peers = warp_peers9(d);
-        const uint32_t lt = __popc(peers & lanemask_lt());
-        const uint32_t cnt = d < 0x100u ? wh[d] : 0u;
-        r[i] = cnt + lt;
-        __syncwarp();
-        if (d < 0x100u && lt == 0) wh[d] = cnt + __popc(peers);
-        __syncwarp();
+    // asks the L2 for the ranks and text that samples [b, b + c) read
+    __device__ __forceinline__ void prefetch(int64_t b, int64_t c) const {
+        const int64_t e = b + c;
+        if (b < n0) {
+            const int64_t e1 = e < n0 ? e : n0;
+            prefetch_inside(Rl + b, Rl + e1);
+            if (b < n2) prefetch_inside(Rl + n0 + b, Rl + n0 + (e1 < n2 ? e1 : n2));
+            prefetch_inside(s + 3 * b, s + (3 * e1 < n ? 3 * e1 : n));
+        }
+        if (e > n0) {
+            const int64_t b2 = (b > n0 ? b : n0) - n0, e2 = e - n0;
+            prefetch_inside(Rl + b, Rl + e);
+            prefetch_inside(Rl + b2 + 1, Rl + (e2 + 1 < n0 ? e2 + 1 : n0));
+            prefetch_inside(s + 3 * b2 + 2, s + (3 * e2 + 2 < n ? 3 * e2 + 2 : n));
+        }
     }
-    __syncthreads();
-    const int dg = tid;
-    uint32_t total = 0;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t c = S.warp_hist[w][dg];
-        S.warp_hist[w][dg] = total;
-        total += c;
+};
+
+// Ax[j] = v for the (j, v) pairs of the bucketed scatter above (j distinct).
+__global__ void k_scatter_u64(const uint32_t *__restrict__ key, const uint64_t *__restrict__ val, int64_t m,
+                              uint64_t *__restrict__ dst, int64_t bound, int *status) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t j = key[i];
+    if (int64_t(j) >= bound) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        return;
     }
-    uint32_t tile_total;
-    const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
-    S.local_start[dg] = lstart;
-    if (tid == 0) S.count = tile_total;
-    uint32_t excl = 0;
-    if (tile == 0) {
-        st_volatile_u64(&lookback[dg], lb_pack(epoch, kFlagIncl, total));
-    } else {
-        st_volatile_u64(&lookback[tile * kRadix + dg], lb_pack(epoch, kFlagAgg, total));
-        excl = lookback_digit(lookback, tile, dg, epoch, status);
-        st_volatile_u64(&lookback[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
-    }
-    S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
-    __syncthreads();
+    dst[j] = val[i];
+}
+
+// Step 2 at level 0: the nonsample suffixes 3x in the order of
+// rank(S_3x+1) -- the B1 samples x in sample order SAR -- split stably by
+// their first symbol t_3x, each with its merge record (t, t_3x | t_3x+1 << 8,
+// rank(S_3x+1) = j + 1, rank(S_3x+2)), all read in sequence from SAR and Ax.
+// Three steps with no inter-block wait: per tile of SAR, the number of B1
+// samples per first symbol; the tiles' starts per symbol (an exclusive scan
+// over the tiles, from the symbols' starts); per tile, each record written at
+// its tile's start plus its stable rank inside the tile.
+
+__global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__restrict__ SAR,
+                                                          const uint64_t *__restrict__ Ax, int64_t n02, int64_t n0,
+                                                          uint32_t *__restrict__ cnt) {
+    __shared__ uint32_t h[kRadix];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t ntiles = cdiv(n02, kSpTile);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        h[tid] = 0;
+        __syncthreads();
+        uint32_t d[kSpItems];
 #pragma unroll
-    for (int i = 0; i < kNsItems; ++i)
-        if (dig[i] < 0x100u) S.rec[S.local_start[dig[i]] + S.warp_hist[warp][dig[i]] + r[i]] = v[i];
-    __syncthreads();
-    const int cnt_tile = int(S.count);
-    for (int i = tid; i < cnt_tile; i += kSortThreads) {
-        const BRec16 g = S.rec[i];
-        out[S.gbase[g.c01 & 0xFFu] + i] = g;
+        for (int i = 0; i < kSpItems; ++i) {
+            // both loads issued at once (a sector of Ax almost always holds a
+            // B1 sample, so reading it whole costs nothing extra)
+            const int64_t idx = tile * kSpTile + i * kSortThreads + tid;
+            const int32_t x = idx < n02 ? SAR[idx] : -1;
+            const uint64_t w = idx < n02 ? Ax[idx] : 0;
+            d[i] = (x >= 0 && x < n0) ? uint32_t(w >> 40) & 0xFFu : 0x100u;
+        }
+        // one shared-memory add per distinct symbol of a warp (few symbols:
+        // per-lane adds would all queue on the same words)
+#pragma unroll
+        for (int i = 0; i < kSpItems; ++i) {
+            const uint32_t peers = warp_peers9(d[i]);
+            if (d[i] < 0x100u && __popc(peers & lanemask_lt()) == 0) atomicAdd(&h[d[i]], uint32_t(__popc(peers)));
+        }
+        (void)lane;
+        __syncthreads();
+        cnt[tile * kRadix + tid] = h[tid];
+        __syncthreads();
+    }
+}
+
+// Per digit (thread), the sum of the counts of each range of tiles.
+__global__ void __launch_bounds__(kRadix) k_ns_scan_ranges(const uint32_t *__restrict__ cnt, int64_t ntiles,
+                                                          int64_t per, uint32_t *__restrict__ part) {
+    const int d = threadIdx.x;
+    const int64_t t0 = blockIdx.x * per, t1 = min64(t0 + per, ntiles);
+    uint32_t sum = 0;
+    for (int64_t t = t0; t < t1; ++t) sum += cnt[t * kRadix + d];
+    part[blockIdx.x * kRadix + d] = sum;
+}
+
+// Per digit, the ranges' starts: the digit's start plus the counts before.
+__global__ void __launch_bounds__(kRadix) k_ns_scan_starts(uint32_t *__restrict__ part, int nranges,
+                                                          const uint32_t *__restrict__ offsets) {
+    const int d = threadIdx.x;
+    uint32_t run = offsets[d];
+    for (int r = 0; r < nranges; ++r) {
+        const uint32_t v = part[r * kRadix + d];
+        part[r * kRadix + d] = run;
+        run += v;
+    }
+}
+
+// Per digit, every tile's start (in place of its count).
+__global__ void __launch_bounds__(kRadix) k_ns_scan_tiles(uint32_t *__restrict__ cnt, int64_t ntiles, int64_t per,
+                                                         const uint32_t *__restrict__ part) {
+    const int d = threadIdx.x;
+    const int64_t t0 = blockIdx.x * per, t1 = min64(t0 + per, ntiles);
+    uint32_t run = part[blockIdx.x * kRadix + d];
+    for (int64_t t = t0; t < t1; ++t) {
+        const uint32_t v = cnt[t * kRadix + d];
+        cnt[t * kRadix + d] = run;
+        run += v;
+    }
+}
+
+// Every record at its tile's start for its first symbol plus its stable rank
+// in the tile (each warp owns a run of 512 consecutive entries: items in
+// order, lanes in order).
+__global__ void __launch_bounds__(kSortThreads, 4) k_ns_write(const int32_t *__restrict__ SAR,
+                                                             const uint64_t *__restrict__ Ax, int64_t n02, int64_t n0,
+                                                             const uint32_t *__restrict__ start,
+                                                             BRec16 *__restrict__ out, int *status) {
+    __shared__ uint32_t wh[kSortWarps][kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t ntiles = cdiv(n02, kSpTile);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&wh[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t wbase = tile * kSpTile + int64_t(warp) * (kSpItems * 32);
+        int32_t xs[kSpItems];
+        uint64_t ws[kSpItems];
+        uint32_t dig[kSpItems], r[kSpItems];
+#pragma unroll
+        for (int i = 0; i < kSpItems; ++i) {
+            const int64_t idx = wbase + i * 32 + lane;
+            xs[i] = idx < n02 ? SAR[idx] : -1;
+            ws[i] = idx < n02 ? Ax[idx] : 0;  // issued with the SAR load, not after it
+            dig[i] = 0x100u;
+            if (xs[i] >= 0 && xs[i] < n0) {
+                dig[i] = uint32_t(ws[i] >> 40) & 0xFFu;
+            } else if (idx < n02 && (xs[i] < 0 || xs[i] >= n02)) {
+                atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+            }
+        }
+        uint32_t *h = wh[warp];
+#pragma unroll
+        for (int i = 0; i < kSpItems; ++i) r[i] = warp_peers9(dig[i]);
+        const uint32_t lt_mask = lanemask_lt();
+#pragma unroll
+        for (int i = 0; i < kSpItems; ++i) {
+            const uint32_t d = dig[i];
+            const uint32_t peers = r[i];
+            const uint32_t lt = __popc(peers & lt_mask);
+            const uint32_t c = d < 0x100u ? h[d] : 0u;
+            r[i] = c + lt;
+            __syncwarp();
+            if (d < 0x100u && lt == 0) h[d] = c + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            // per digit: the counts of the warps before, plus the tile's start
+            const int d = tid;
+            uint32_t run = start[tile * kRadix + d];
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = wh[w][d];
+                wh[w][d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kSpItems; ++i) {
+            if (dig[i] >= 0x100u) continue;
+            const uint32_t o = wh[warp][dig[i]] + r[i];
+            if (int64_t(o) >= n0) {  // counts that did not match SAR
+                atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+                continue;
+            }
+            BRec16 v;
+            v.t = xs[i];
+            v.c01 = dig[i] | ((uint32_t(ws[i] >> 32) & 0xFFu) << 8);
+            v.r1 = int32_t(wbase + i * 32 + lane + 1);
+            v.r2 = int32_t(uint32_t(ws[i]));
+            out[o] = v;
+        }
+        __syncthreads();  // the warp counts are reused by the next tile
     }
 }
 
@@ -1545,8 +1685,11 @@ int sample_sort_and_name(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z
     LOR_LAUNCH_CHECK();
     KeyT *kr;
     uint32_t *vr;
+    // Level 0: samples with equal keys get one name, and neither the doubling
+    // that resolves them nor the recursion reads their order, so the first
+    // pass need not be stable.
     int rc = radix_sort_pairs<KeyT>(D.rs, k0, D.t32[0], k1, D.t32[1], z.n02, 0, key_bits, true, &kr, &vr,
-                                    hist_ready);
+                                    hist_ready, nullptr, sizeof(CharT) == 1);
     if (rc) return rc;
     {
         ProfScope ps(PK_NAMING, double(z.n02) * (sizeof(KeyT) + 16), st);
@@ -1823,17 +1966,42 @@ int build_records(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t 
     return LOR_OK;
 }
 
-// Steps 2 and 3 at level 0: records first, then the nonsample split carrying
-// them (into t32[0..3]), then the merge reading them in order.
+// Steps 2 and 3 at level 0.  Every sample's merge key goes to Ax in sample
+// order by a bucketed scatter keyed by its rank (the keys are made from the
+// text and the ranks read in sequence, and the scatter writes into
+// L2-sized windows), so no step reads a record at random; the nonsample split
+// then reads SAR and Ax in sequence (into t32[0..3]), and the merge reads
+// both orders in sequence.
 int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z, const int32_t *Rl,
                                const int32_t *SAR, int32_t *out) {
     cudaStream_t st = D.s;
-    GroupRec<uint8_t> *rec;
-    int rc = build_records<uint8_t>(D, s, z, Rl, &rec);
-    if (rc) return rc;
     BRec16 *Bx = (BRec16 *)D.t32[0];
     if (size_t((char *)D.t32[4] - (char *)D.t32[0]) < sizeof(BRec16) * size_t(z.n0)) return LOR_ERR_WORKSPACE;
     uint64_t *Ax = D.t64[0];  // 8 bytes per sample, in sample order
+    const int64_t m = z.n02;
+    {
+        // (j, key) pairs bucketed by the top 8 bits of j: a permutation of
+        // [0, m), so every bucket's size is known without counting
+        uint32_t *kb = D.t32[4];
+        uint64_t *vb = D.t64[1];
+        const int top = bit_width_u64(uint64_t(m > 1 ? m - 1 : 1));
+        const int lo = top > kRadixBits ? top - kRadixBits : 0;
+        k_perm_offsets<<<1, kRadix, 0, st>>>(D.rs.offsets, lo, m);
+        LOR_LAUNCH_CHECK();
+        {
+            ProfScope ps(PK_NONSAMPLE, double(m) * (8 + 4.0 / 3.0 + 4 + 8), st);
+            const int rc = launch_partition<uint32_t, uint64_t>(SampleKeySrc{s, Rl, z.n, z.n0, z.n2}, kb, vb, m,
+                                                                nullptr, lo, digit_mask(lo, top), D.rs.offsets,
+                                                                D.status, st);
+            if (rc) return rc;
+        }
+        LOR_LAUNCH_CHECK();
+        {
+            ProfScope ps(PK_NONSAMPLE, double(m) * (4 + 8 + 8), st);
+            k_scatter_u64<<<grid_for(m, 256), 256, 0, st>>>(kb, vb, m, Ax, m, D.status);
+        }
+        LOR_LAUNCH_CHECK();
+    }
     LOR_CUDA_TRY(cudaMemsetAsync(D.rs.hist, 0, sizeof(uint32_t) * kRadix, st));
     {
         ProfScope ps(PK_NONSAMPLE, double(z.n0), st);
@@ -1843,17 +2011,34 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
         LOR_LAUNCH_CHECK();
     }
     {
-        ProfScope ps(PK_NONSAMPLE, double(z.n02) * 4 + double(z.n0) * (16 + 16), st);
-        const int64_t ntiles = cdiv(z.n02, kNsTile);
-        if (ntiles > D.rs.max_tiles) return LOR_ERR_WORKSPACE;
-        D.rs.epoch++;
-        k_nonsample_rec<<<unsigned(ntiles), kSortThreads, 0, st>>>(SAR, z.n02, z.n0, rec, D.rs.offsets, Bx, Ax,
-                                                                   D.rs.lookback, D.rs.tile_ctr, D.rs.tile_base,
-                                                                   D.rs.epoch, D.status);
-        LOR_LAUNCH_CHECK();
-        D.rs.tile_base += (unsigned long long)ntiles;
+        const int64_t ntiles = cdiv(m, kSpTile);
+        const int64_t per = cdiv(ntiles, kSpRanges);
+        const int nranges = int(cdiv(ntiles, per));
+        uint32_t *cnt = (uint32_t *)(D.ws + D.L.ns_table);
+        uint32_t *part = cnt + ntiles * kRadix;
+        if (ntiles > cdiv(D.L.max_m, kSpTile)) return LOR_ERR_WORKSPACE;
+        const unsigned grid = unsigned(min64(ntiles, int64_t(sort_grid_cap()) * 2));
+        {
+            ProfScope ps(PK_NONSAMPLE, double(m) * 4 + double(z.n0) * 8, st);
+            k_ns_count<<<grid, kSortThreads, 0, st>>>(SAR, Ax, m, z.n0, cnt);
+            LOR_LAUNCH_CHECK();
+        }
+        {
+            ProfScope ps(PK_NONSAMPLE, double(ntiles) * kRadix * 12, st);
+            k_ns_scan_ranges<<<unsigned(nranges), kRadix, 0, st>>>(cnt, ntiles, per, part);
+            LOR_LAUNCH_CHECK();
+            k_ns_scan_starts<<<1, kRadix, 0, st>>>(part, nranges, D.rs.offsets);
+            LOR_LAUNCH_CHECK();
+            k_ns_scan_tiles<<<unsigned(nranges), kRadix, 0, st>>>(cnt, ntiles, per, part);
+            LOR_LAUNCH_CHECK();
+        }
+        {
+            ProfScope ps(PK_NONSAMPLE, double(m) * 4 + double(z.n0) * (8 + 16), st);
+            k_ns_write<<<grid, kSortThreads, 0, st>>>(SAR, Ax, m, z.n0, cnt, Bx, D.status);
+            LOR_LAUNCH_CHECK();
+        }
     }
-    return merge_run<uint8_t>(D, z, rec, SAR, nullptr, Bx, Ax, out);
+    return merge_run<uint8_t>(D, z, nullptr, SAR, nullptr, Bx, Ax, out);
 }
 
 template <typename CharT>

@@ -228,42 +228,51 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         const int64_t tile = S.next;
         if (tile >= ntiles) break;  // uniform over the block
         const int64_t base = tile * kTile;
-        const int64_t wbase = base + int64_t(warp) * (kItems * 32);
+        // positions inside the tile are 32-bit; the tile's pointers carry the base
+        const int cnt_tile = int(min64(int64_t(kTile), m - base));
+        const KeyT *kt = kin + base;
+        const int wloc = warp * (kItems * 32) + lane;
 
         KeyT k[kItems];
         ValT v[kItems];
         uint32_t r[kItems];
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
-            const int64_t idx = wbase + i * 32 + lane;
-            const bool valid = idx < m;
-            k[i] = valid ? kin[idx] : KeyT(0);
-            if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[idx] : ValT(0);
+            const int loc = wloc + i * 32;
+            const bool valid = loc < cnt_tile;
+            k[i] = valid ? kt[loc] : KeyT(0);
+            if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[base + loc] : ValT(0);
             if constexpr (kVMode == VM_IDX_PREV)
-                v[i] = uint64_t(uint32_t(idx)) |
-                       (uint64_t(valid && idx > 0 ? uint32_t(kin[idx - 1]) : 0xFFFFFFFFu) << 32);
+                v[i] = uint64_t(uint32_t(base) + uint32_t(loc)) |
+                       (uint64_t(valid && base + loc > 0 ? uint32_t(kt[loc - 1]) : 0xFFFFFFFFu) << 32);
         }
         // Early counts: the tile's digit totals from shared-memory atomics,
         // published before the (slower) stable ranking, so that later tiles'
         // look-back finds this tile's aggregate sooner.
 #pragma unroll
         for (int i = 0; i < kItems; ++i)
-            if (wbase + i * 32 + lane < m) atomicAdd(&S.early[digit_of(k[i], shift, dmask)], 1u);
+            if (wloc + i * 32 < cnt_tile) atomicAdd(&S.early[digit_of(k[i], shift, dmask)], 1u);
         __syncthreads();
         if (!(starve && tile == 0)) {
             const uint32_t e = S.early[tid];
             st_volatile_u64(&lookback[tile * kRadix + tid], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, e));
         }
-        // Stable rank inside the warp: items in order, lanes in order.  Slots
-        // past the end of the input use digit 256 and are never counted (a
-        // whole tile has none, and its ranking needs one ballot fewer).
+        // Stable rank inside the warp: items in order, lanes in order.  The
+        // lanes sharing each item's digit are found first for every item (the
+        // ballots are independent of each other), then the warp's running
+        // digit counts are walked item by item.  Slots past the end of the
+        // input use digit 256 and are never counted (a whole tile has none,
+        // and its ranking needs one ballot fewer).
         uint32_t *wh = S.warp_hist[warp];
-        if (base + kTile <= m) {
+        const uint32_t lt_mask = lanemask_lt();
+        if (cnt_tile == kTile) {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) r[i] = warp_peers8(digit_of(k[i], shift, dmask));
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
                 const uint32_t d = digit_of(k[i], shift, dmask);
-                const uint32_t peers = warp_peers8(d);
-                const uint32_t lt = __popc(peers & lanemask_lt());
+                const uint32_t peers = r[i];
+                const uint32_t lt = __popc(peers & lt_mask);
                 const uint32_t cnt = wh[d];
                 r[i] = cnt + lt;
                 __syncwarp();
@@ -273,10 +282,15 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         } else {
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
-                const bool valid = wbase + i * 32 + lane < m;
-                const uint32_t d = valid ? digit_of(k[i], shift, dmask) : 0x100u;
-                const uint32_t peers = warp_peers9(d);
-                const uint32_t lt = __popc(peers & lanemask_lt());
+                const bool valid = wloc + i * 32 < cnt_tile;
+                r[i] = warp_peers9(valid ? digit_of(k[i], shift, dmask) : 0x100u);
+            }
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                const bool valid = wloc + i * 32 < cnt_tile;
+                const uint32_t d = valid ? digit_of(k[i], shift, dmask) : 0u;
+                const uint32_t peers = r[i];
+                const uint32_t lt = __popc(peers & lt_mask);
                 const uint32_t cnt = valid ? wh[d] : 0u;
                 r[i] = cnt + lt;
                 __syncwarp();
@@ -309,16 +323,15 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
-            const int64_t idx = wbase + i * 32 + lane;
-            if (idx < m) {
+            const int loc = wloc + i * 32;
+            if (loc < cnt_tile) {
                 const uint32_t d = digit_of(k[i], shift, dmask);
                 const uint32_t pos = S.local_start[d] + S.warp_hist[warp][d] + r[i];
                 S.keys[pos] = k[i];
-                S.vals[pos] = kVMode == VM_IOTA ? ValT(uint32_t(idx)) : v[i];
+                S.vals[pos] = kVMode == VM_IOTA ? ValT(uint32_t(base) + uint32_t(loc)) : v[i];
             }
         }
         __syncthreads();
-        const int cnt_tile = int(min64(int64_t(kTile), m - base));
         for (int i = tid; i < cnt_tile; i += kSortThreads) {
             const KeyT kk = S.keys[i];
             const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
@@ -329,96 +342,295 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     }
 }
 
-// One non-stable partition pass (for the bucketed scatters, where the order
-// inside a bucket does not matter): an element's place inside its tile's
-// digit run comes from a shared-memory atomic instead of the stable warp
-// ranking; the look-back and the staged write are those of k_onesweep, and
-// so is the persistent grid (blocks claim tiles until one past the end).
-template <typename ValT, int kVMode>
+// Where a partition pass takes its (key, value) pairs: arrays, with the
+// values loaded, generated as the index, or generated as the index and the
+// previous key (the {ISA, PHI} scatter).  Other sources (pairs computed from
+// other arrays) provide the same two members.
+template <typename KeyT, typename ValT, int kVMode>
+struct ArrayPairs {
+    const KeyT *kin;
+    const ValT *vin;
+    __device__ __forceinline__ void load(int64_t idx, bool valid, KeyT &k, ValT &v) const {
+        k = valid ? kin[idx] : KeyT(0);
+        if constexpr (kVMode == VM_LOAD) v = valid ? vin[idx] : ValT(0);
+        if constexpr (kVMode == VM_IOTA) v = ValT(uint32_t(idx));
+        if constexpr (kVMode == VM_IDX_PREV)
+            v = uint64_t(uint32_t(idx)) |
+                (uint64_t(valid && idx > 0 ? uint32_t(kin[idx - 1]) : 0xFFFFFFFFu) << 32);
+    }
+    // asks the L2 for pairs [b, b + c) ahead of their use
+    __device__ __forceinline__ void prefetch(int64_t b, int64_t c) const {
+        const uint32_t kb = uint32_t(c * int64_t(sizeof(KeyT))) & ~15u;
+        if (kb && ((uintptr_t(kin + b) & 15) == 0)) prefetch_l2_bulk(kin + b, kb);
+        if (kVMode == VM_LOAD) {
+            const uint32_t vb = uint32_t(c * int64_t(sizeof(ValT))) & ~15u;
+            if (vb && ((uintptr_t(vin + b) & 15) == 0)) prefetch_l2_bulk(vin + b, vb);
+        }
+    }
+};
+
+// One non-stable partition pass, for passes where the order of the elements
+// inside a digit bucket does not matter: the bucketed scatters (every bucket
+// is read as a set) and the first LSD pass of a sort whose ties may come out
+// in any order.  An element's place inside its tile's digit run comes from a
+// shared-memory atomic, and the tile's run of each digit is reserved in the
+// digit's bucket by one global atomic on the bucket's cursor (cursor[d]
+// starts at the bucket's offset): tiles fill their buckets in the order they
+// get there, so no tile waits on another (no look-back).  The write is
+// staged through shared memory like k_onesweep's.  A persistent grid walks
+// the tiles with a grid stride; m_dev, when given, holds the element count.
+template <typename KeyT, typename ValT, typename Src>
 __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
-    const uint32_t *__restrict__ kin, const ValT *__restrict__ vin, uint32_t *__restrict__ kout,
-    ValT *__restrict__ vout, int64_t m, int shift, uint32_t dmask, const uint32_t *__restrict__ offsets,
-    uint64_t *__restrict__ lookback, unsigned long long *tile_ctr, unsigned long long tile_base,
-    uint32_t epoch, int *status, int64_t ahead) {
-    constexpr int kItems = sort_items<uint32_t, ValT>();
-    constexpr int kTile = sort_tile<uint32_t, ValT>();
+    Src src, KeyT *__restrict__ kout, ValT *__restrict__ vout, int64_t m, const uint32_t *m_dev, int shift,
+    uint32_t dmask, uint32_t *__restrict__ cursor, int *status, int64_t ahead) {
+    constexpr int kItems = sort_items<KeyT, ValT>();
+    constexpr int kTile = sort_tile<KeyT, ValT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    OnesweepSmem<uint32_t, ValT> &S = *reinterpret_cast<OnesweepSmem<uint32_t, ValT> *>(smem_raw);
+    OnesweepSmem<KeyT, ValT> &S = *reinterpret_cast<OnesweepSmem<KeyT, ValT> *>(smem_raw);
     uint32_t *cnt = S.warp_hist[0];
     const int tid = threadIdx.x;
+    if (m_dev) m = int64_t(*m_dev);
     const int64_t ntiles = cdiv(m, kTile);
-    for (;;) {
-    if (tid == 0) {
-        S.tile = (long long)(atomicAdd(tile_ctr, 1ull) - tile_base);
-        const int64_t b2 = (S.tile + ahead) * kTile;
-        if (ahead > 0 && b2 < m) {
-            const int64_t c2 = min64(int64_t(kTile), m - b2);
-            const uint32_t kb = uint32_t(c2 * 4) & ~15u;
-            if (kb) prefetch_l2_bulk(kin + b2, kb);
-            if (kVMode == VM_LOAD) {
-                const uint32_t vb = uint32_t(c2 * int64_t(sizeof(ValT))) & ~15u;
-                if (vb) prefetch_l2_bulk(vin + b2, vb);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (tid == 0 && ahead > 0) {
+            const int64_t b2 = (tile + ahead) * kTile;
+            if (b2 < m) src.prefetch(b2, min64(int64_t(kTile), m - b2));
+        }
+        cnt[tid] = 0;
+        __syncthreads();
+        const int64_t base = tile * kTile;
+        KeyT k[kItems];
+        uint32_t r[kItems];
+        ValT v[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t idx = base + i * kSortThreads + tid;
+            const bool valid = idx < m;
+            src.load(idx, valid, k[i], v[i]);
+            r[i] = valid ? atomicAdd(&cnt[digit_of(k[i], shift, dmask)], 1u) : 0u;
+        }
+        __syncthreads();
+        const int dg = tid;
+        const uint32_t total = cnt[dg];
+        // this tile's run of digit dg inside the digit's bucket
+        const uint32_t run = total ? atomicAdd(&cursor[dg], total) : 0u;
+        uint32_t tile_total;
+        const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
+        S.local_start[dg] = lstart;
+        S.gbase[dg] = (long long)run - lstart;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t idx = base + i * kSortThreads + tid;
+            if (idx < m) {
+                const uint32_t pos = S.local_start[digit_of(k[i], shift, dmask)] + r[i];
+                S.keys[pos] = k[i];
+                S.vals[pos] = v[i];
             }
         }
-    }
-    cnt[tid] = 0;
-    __syncthreads();
-    const int64_t tile = S.tile;
-    if (tile >= ntiles) break;  // uniform over the block
-    const int64_t base = tile * kTile;
-    uint32_t k[kItems], r[kItems];
-    ValT v[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int64_t idx = base + i * kSortThreads + tid;
-        const bool valid = idx < m;
-        k[i] = valid ? kin[idx] : 0u;
-        if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[idx] : ValT(0);
-        if constexpr (kVMode == VM_IOTA) v[i] = ValT(uint32_t(idx));
-        if constexpr (kVMode == VM_IDX_PREV)
-            v[i] = uint64_t(uint32_t(idx)) |
-                   (uint64_t(valid && idx > 0 ? kin[idx - 1] : 0xFFFFFFFFu) << 32);
-        r[i] = valid ? atomicAdd(&cnt[digit_of(k[i], shift, dmask)], 1u) : 0u;
-    }
-    __syncthreads();
-    const int dg = tid;
-    const uint32_t total = cnt[dg];
-    uint64_t *lb = lookback;
-    // The aggregate goes out before the block scan: later tiles wait on it.
-    st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, tile == 0 ? kFlagIncl : kFlagAgg, total));
-    uint32_t tile_total;
-    const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
-    S.local_start[dg] = lstart;
-    uint32_t excl = 0;
-    if (tile != 0) {
-        excl = lookback_digit(lb, tile, dg, epoch, status);
-        st_volatile_u64(&lb[tile * kRadix + dg], lb_pack(epoch, kFlagIncl, excl + total));
-    }
-    S.gbase[dg] = (long long)offsets[dg] + excl - lstart;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int64_t idx = base + i * kSortThreads + tid;
-        if (idx < m) {
-            const uint32_t pos = S.local_start[digit_of(k[i], shift, dmask)] + r[i];
-            S.keys[pos] = k[i];
-            S.vals[pos] = v[i];
+        __syncthreads();
+        const int cnt_tile = int(min64(int64_t(kTile), m - base));
+        for (int i = tid; i < cnt_tile; i += kSortThreads) {
+            const KeyT kk = S.keys[i];
+            const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
+            if (o < 0 || o >= m) {  // counts that did not match the keys (keys meant to be a permutation)
+                atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+                continue;
+            }
+            kout[o] = kk;
+            vout[o] = S.vals[i];
         }
+        __syncthreads();  // counts and staging are reused by the next tile
+    }
+}
+
+// The same pass for pairs held in arrays, software-pipelined: while a block
+// partitions one tile, the next tile of its grid stride is already on its way
+// into shared memory by a bulk (TMA) copy completing on an mbarrier, so the
+// DRAM latency of the loads is hidden behind the work of the tile before.
+// Whole tiles with 16-byte aligned rows are copied in bulk; a partial or
+// unaligned tile is read with plain loads.  Every wait is bounded by the wait
+// limit (then LOR_ERR_TIMEOUT, after a bounded wait for the block's own copy
+// in flight).
+template <typename KeyT, typename ValT, int kVMode>
+struct PipeSmem {
+    static constexpr int kTile = sort_tile<KeyT, ValT>();
+    static constexpr int kInV = kVMode == VM_LOAD ? kTile : 1;
+    KeyT in_k[2][kTile];
+    ValT in_v[2][kInV];
+    KeyT keys[kTile];
+    ValT vals[kTile];
+    uint32_t cnt[kRadix];
+    uint32_t local_start[kRadix];
+    long long gbase[kRadix];
+    uint32_t scratch[kSortWarps + 1];
+    uint64_t bar[2];
+};
+
+template <typename KeyT, typename ValT, int kVMode>
+__global__ void __launch_bounds__(kSortThreads) k_partition_pipe(
+    const KeyT *__restrict__ kin, const ValT *__restrict__ vin, KeyT *__restrict__ kout, ValT *__restrict__ vout,
+    int64_t m, const uint32_t *m_dev, int shift, uint32_t dmask, uint32_t *__restrict__ cursor, int *status) {
+    using Smem = PipeSmem<KeyT, ValT, kVMode>;
+    constexpr int kItems = sort_items<KeyT, ValT>();
+    constexpr int kTile = Smem::kTile;
+    constexpr bool kLoadV = kVMode == VM_LOAD;
+    constexpr uint32_t kBytes = uint32_t(kTile * sizeof(KeyT)) + (kLoadV ? uint32_t(kTile * sizeof(ValT)) : 0u);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const int tid = threadIdx.x;
+    if (m_dev) m = int64_t(*m_dev);
+    const int64_t ntiles = cdiv(m, kTile);
+    auto bulk_ok = [&](int64_t t) {
+        if (t >= ntiles || (t + 1) * kTile > m) return false;
+        if (uintptr_t(kin + t * kTile) & 15) return false;
+        return !kLoadV || (uintptr_t(vin + t * kTile) & 15) == 0;
+    };
+    auto issue = [&](int64_t t, int b) {  // one thread
+        mbar_arrive_expect_tx(&S.bar[b], kBytes);
+        bulk_g2s(S.in_k[b], kin + t * kTile, uint32_t(kTile * sizeof(KeyT)), &S.bar[b]);
+        if (kLoadV) bulk_g2s(S.in_v[b], vin + t * kTile, uint32_t(kTile * sizeof(ValT)), &S.bar[b]);
+    };
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
     }
     __syncthreads();
-    const int cnt_tile = int(min64(int64_t(kTile), m - base));
-    for (int i = tid; i < cnt_tile; i += kSortThreads) {
-        const uint32_t kk = S.keys[i];
-        const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
-        if (o < 0 || o >= m) {  // keys that were to be a permutation were not
-            atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
-            continue;
+    const uint64_t limit = wait_limit_ns();
+    int64_t tile = blockIdx.x;
+    if (tid == 0 && bulk_ok(tile)) issue(tile, 0);
+    uint32_t phase = 0;  // bit b: parity of buffer b's next completion
+    for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
+        const int64_t nxt = tile + gridDim.x;
+        // the other buffer was last read in the previous round, before its
+        // closing barrier
+        const bool nxt_bulk = bulk_ok(nxt);
+        if (tid == 0 && nxt_bulk) {
+            fence_proxy_async_smem();
+            issue(nxt, b ^ 1);
         }
-        kout[o] = kk;
-        vout[o] = S.vals[i];
+        S.cnt[tid] = 0;
+        const bool bulk = bulk_ok(tile);
+        bool failed = false;
+        if (bulk) {
+            failed = !mbar_wait_bounded(&S.bar[b], (phase >> b) & 1u, limit);
+            phase ^= 1u << b;
+        }
+        if (__syncthreads_or(failed)) {
+            // give the block's copies in flight a bounded time to land, then leave
+            if (tid == 0) {
+                atomicCAS(status, 0, LOR_ERR_TIMEOUT);
+                mbar_wait_bounded(&S.bar[b], ((phase >> b) & 1u) ^ 1u, limit);
+                if (nxt_bulk) mbar_wait_bounded(&S.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, limit);
+            }
+            __syncthreads();
+            return;
+        }
+        const int64_t base = tile * kTile;
+        KeyT k[kItems];
+        uint32_t r[kItems];
+        ValT v[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int loc = i * kSortThreads + tid;
+            const int64_t idx = base + loc;
+            const bool valid = idx < m;
+            if (bulk) {
+                k[i] = S.in_k[b][loc];
+                if constexpr (kVMode == VM_LOAD) v[i] = S.in_v[b][loc];
+            } else {
+                k[i] = valid ? kin[idx] : KeyT(0);
+                if constexpr (kVMode == VM_LOAD) v[i] = valid ? vin[idx] : ValT(0);
+            }
+            if constexpr (kVMode == VM_IOTA) v[i] = ValT(uint32_t(idx));
+            if constexpr (kVMode == VM_IDX_PREV) {
+                uint32_t prev = 0xFFFFFFFFu;
+                if (valid && idx > 0) prev = (bulk && loc > 0) ? uint32_t(S.in_k[b][loc - 1]) : uint32_t(kin[idx - 1]);
+                v[i] = uint64_t(uint32_t(idx)) | (uint64_t(prev) << 32);
+            }
+            r[i] = valid ? atomicAdd(&S.cnt[digit_of(k[i], shift, dmask)], 1u) : 0u;
+        }
+        __syncthreads();
+        const int dg = tid;
+        const uint32_t total = S.cnt[dg];
+        // this tile's run of digit dg inside the digit's bucket
+        const uint32_t run = total ? atomicAdd(&cursor[dg], total) : 0u;
+        uint32_t tile_total;
+        const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
+        S.local_start[dg] = lstart;
+        S.gbase[dg] = (long long)run - lstart;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t idx = base + i * kSortThreads + tid;
+            if (idx < m) {
+                const uint32_t pos = S.local_start[digit_of(k[i], shift, dmask)] + r[i];
+                S.keys[pos] = k[i];
+                S.vals[pos] = v[i];
+            }
+        }
+        __syncthreads();
+        const int cnt_tile = int(min64(int64_t(kTile), m - base));
+        for (int i = tid; i < cnt_tile; i += kSortThreads) {
+            const KeyT kk = S.keys[i];
+            const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
+            if (o < 0 || o >= m) {  // counts that did not match the keys (keys meant to be a permutation)
+                atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+                continue;
+            }
+            kout[o] = kk;
+            vout[o] = S.vals[i];
+        }
+        __syncthreads();  // counts, staging and the input buffer are reused
     }
-    __syncthreads();  // counts, staging and S.tile are reused by the next tile
+}
+
+// Blocks of a pipelined partition pass: as many as fit an SM, times the SMs.
+template <typename KeyT, typename ValT, int kVMode>
+int partition_pipe_grid(int64_t ntiles, size_t smem) {
+    static thread_local int dev = -1, cap = 0;
+    int cur = 0;
+    LOR_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != dev) {
+        int sms = 0, per = 0;
+        LOR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur));
+        LOR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_partition_pipe<KeyT, ValT, kVMode>,
+                                                                  kSortThreads, smem));
+        cap = (per > 0 ? per : 1) * sms;
+        dev = cur;
     }
+    return int(min64(ntiles > 0 ? ntiles : 1, cap));
+}
+
+template <typename KeyT, typename ValT, int kVMode>
+int launch_partition_pipe(const KeyT *kin, const ValT *vin, KeyT *kout, ValT *vout, int64_t m, const uint32_t *m_dev,
+                          int shift, uint32_t dmask, uint32_t *cursor, int *status, cudaStream_t s) {
+    const size_t smem = sizeof(PipeSmem<KeyT, ValT, kVMode>) + 128;
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_partition_pipe<KeyT, ValT, kVMode>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    const int grid = partition_pipe_grid<KeyT, ValT, kVMode>(cdiv(m, sort_tile<KeyT, ValT>()), smem);
+    if (grid < 0) return grid;
+    k_partition_pipe<KeyT, ValT, kVMode><<<unsigned(grid), kSortThreads, smem, s>>>(kin, vin, kout, vout, m, m_dev,
+                                                                                   shift, dmask, cursor, status);
+    return LOR_OK;
+}
+
+inline int sort_grid_cap();
+
+// Launches k_partition on m pairs from `src` by digit bits [shift, shift +
+// width of dmask), consuming `cursor` (the buckets' offsets) as the buckets'
+// fill positions.  The caller accounts the launch.
+template <typename KeyT, typename ValT, typename Src>
+int launch_partition(const Src &src, KeyT *kout, ValT *vout, int64_t m, const uint32_t *m_dev, int shift,
+                     uint32_t dmask, uint32_t *cursor, int *status, cudaStream_t s) {
+    const size_t smem = sizeof(OnesweepSmem<KeyT, ValT>);
+    LOR_CUDA_TRY(cudaFuncSetAttribute(k_partition<KeyT, ValT, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(smem)));
+    const unsigned grid = unsigned(min64(cdiv(m > 0 ? m : 1, sort_tile<KeyT, ValT>()), sort_grid_cap()));
+    k_partition<KeyT, ValT, Src><<<grid, kSortThreads, smem, s>>>(src, kout, vout, m, m_dev, shift, dmask, cursor,
+                                                                  status, int64_t(grid));
+    return LOR_OK;
 }
 
 static __global__ void k_iota_u32(uint32_t *__restrict__ v, int64_t m) {
@@ -516,7 +728,7 @@ inline size_t radix_lookback_bytes(int64_t max_m) {
 template <typename KeyT, int kItems>
 int radix_passes(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v1, int64_t m, int begin_bit,
                  int end_bit, int dbits, int npasses, const uint32_t *hh, bool vals_ready,
-                 const uint32_t *m_dev, KeyT **kres, uint32_t **vres) {
+                 const uint32_t *m_dev, KeyT **kres, uint32_t **vres, bool ties_any_order) {
     cudaStream_t s = rs.stream;
     constexpr int kTile = kSortThreads * kItems;
     if (cdiv(m, kTile) > rs.max_tiles) return LOR_ERR_WORKSPACE;
@@ -529,6 +741,7 @@ int radix_passes(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v
     uint32_t *vi = v0, *vo = v1;
     const int64_t ntiles = cdiv(m, kTile);
     const unsigned grid = unsigned(min64(ntiles, sort_grid_cap()));
+    bool first = true;
     for (int p = 0; p < npasses; ++p) {
         if (hh) {
             bool trivial = false;
@@ -538,20 +751,44 @@ int radix_passes(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v
         }
         const int shift = begin_bit + p * dbits;
         const uint32_t dmask = digit_mask(shift, end_bit, dbits);
+        if (first && ties_any_order) {
+            // The first pass keeps no earlier order, so when equal keys may come
+            // out in any order it need not be stable: a partition pass (no
+            // stable ranking, no look-back) on this pass's digit.  The pass's
+            // offsets serve as its bucket cursors.
+            first = false;
+            {
+                ProfScope ps(PK_RADIX_PASS, double(m) * (sizeof(KeyT) + (vals_ready ? 4.0 : 0.0) + sizeof(KeyT) + 4),
+                             s);
+                const int rc = vals_ready
+                    ? launch_partition_pipe<KeyT, uint32_t, VM_LOAD>(ki, vi, ko, vo, m, m_dev, shift, dmask,
+                                                                      rs.offsets + p * kRadix, rs.status, s)
+                    : launch_partition_pipe<KeyT, uint32_t, VM_IOTA>(ki, vi, ko, vo, m, m_dev, shift, dmask,
+                                                                      rs.offsets + p * kRadix, rs.status, s);
+                if (rc) return rc;
+            }
+            LOR_LAUNCH_CHECK();
+            vals_ready = true;
+            KeyT *tk = ki; ki = ko; ko = tk;
+            uint32_t *tv = vi; vi = vo; vo = tv;
+            continue;
+        }
+        first = false;
         rs.epoch++;
         unsigned long long *ctr, base;
         int rc = take_counter(rs, m_dev != nullptr, &ctr, &base);
         if (rc) return rc;
         {
             ProfScope ps(PK_RADIX_PASS, double(m) * 2.0 * (sizeof(KeyT) + 4), s);
-            if (vals_ready)
+            if (vals_ready) {
                 k_onesweep<KeyT, uint32_t, VM_LOAD, kItems><<<grid, kSortThreads, smem, s>>>(
                     ki, vi, ko, vo, m, m_dev, shift, dmask, rs.offsets + p * kRadix, rs.lookback, ctr, base,
                     rs.epoch, rs.status, prefetch_ahead(ki, vi, grid));
-            else
+            } else {
                 k_onesweep<KeyT, uint32_t, VM_IOTA, kItems><<<grid, kSortThreads, smem, s>>>(
                     ki, vi, ko, vo, m, m_dev, shift, dmask, rs.offsets + p * kRadix, rs.lookback, ctr, base,
                     rs.epoch, rs.status, prefetch_ahead(ki, ki, grid));
+            }
         }
         LOR_LAUNCH_CHECK();
         rc = end_counter(rs, m_dev != nullptr, ctr, (unsigned long long)(ntiles + grid));
@@ -582,7 +819,7 @@ int radix_passes(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v
 template <typename KeyT>
 int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_t *v1, int64_t m,
                      int begin_bit, int end_bit, bool iota_vals, KeyT **kres, uint32_t **vres,
-                     bool hist_ready = false, const uint32_t *m_dev = nullptr) {
+                     bool hist_ready = false, const uint32_t *m_dev = nullptr, bool ties_any_order = false) {
     cudaStream_t s = rs.stream;
     *kres = k0;
     *vres = v0;
@@ -619,15 +856,15 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
     if (sizeof(KeyT) == 8) {
         if (items == 8)
             return radix_passes<KeyT, 8>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
-                                         m_dev, kres, vres);
+                                         m_dev, kres, vres, ties_any_order);
         return radix_passes<KeyT, 12>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
-                                      m_dev, kres, vres);
+                                      m_dev, kres, vres, ties_any_order);
     }
     if (items == 12)
         return radix_passes<KeyT, 12>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
-                                      m_dev, kres, vres);
+                                      m_dev, kres, vres, ties_any_order);
     return radix_passes<KeyT, 16>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
-                                  m_dev, kres, vres);
+                                  m_dev, kres, vres, ties_any_order);
 }
 
 // ---- bucketed scatter: dst[key[i]] = val[i] + add for distinct keys in
@@ -689,7 +926,6 @@ template <typename ValT, int kVMode>
 int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int64_t m, int lo, int top,
                    uint32_t *kout, ValT *vout, bool perm = false) {
     cudaStream_t s = rs.stream;
-    if (cdiv(m, sort_tile<uint32_t, ValT>()) > rs.max_tiles) return LOR_ERR_WORKSPACE;
     if (perm) {
         k_perm_offsets<<<1, kRadix, 0, s>>>(rs.offsets, lo, m);
         LOR_LAUNCH_CHECK();
@@ -704,21 +940,15 @@ int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int
         k_radix_offsets<<<1, kRadix, 0, s>>>(rs.hist, rs.offsets);
         LOR_LAUNCH_CHECK();
     }
-    const size_t smem = sizeof(OnesweepSmem<uint32_t, ValT>);
-    LOR_CUDA_TRY(cudaFuncSetAttribute(k_partition<ValT, kVMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(smem)));
-    const int64_t ntiles = cdiv(m, sort_tile<uint32_t, ValT>());
-    const unsigned grid = unsigned(min64(ntiles, sort_grid_cap()));
-    rs.epoch++;
     {
         ProfScope ps(PK_RADIX_PASS, double(m) * (4 + (kVMode == VM_LOAD ? sizeof(ValT) : 0) + 4 + sizeof(ValT)),
                      s);
-        k_partition<ValT, kVMode><<<grid, kSortThreads, smem, s>>>(
-            keys, vals, kout, vout, m, lo, digit_mask(lo, top), rs.offsets, rs.lookback, rs.tile_ctr,
-            rs.tile_base, rs.epoch, rs.status, prefetch_ahead(keys, kVMode == VM_LOAD ? (const void *)vals : keys));
+        // the offsets are consumed as the buckets' cursors
+        const int rc = launch_partition_pipe<uint32_t, ValT, kVMode>(keys, vals, kout, vout, m, nullptr, lo,
+                                                                     digit_mask(lo, top), rs.offsets, rs.status, s);
+        if (rc) return rc;
     }
     LOR_LAUNCH_CHECK();
-    rs.tile_base += (unsigned long long)ntiles + grid;  // every block claims once past the end
     return LOR_OK;
 }
 

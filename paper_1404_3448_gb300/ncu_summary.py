@@ -31,7 +31,8 @@ KINDS = [
     ("k_name", "naming"), ("k_par_name", "naming"), ("k_dense_scan", "naming"), ("k_dense_write", "naming"),
     ("k_dbl_", "naming"),
     ("k_rank_scatter", "rank_scatter"), ("k_scatter_pairs", "rank_scatter"), ("k_dense_sorted", "rank_scatter"),
-    ("k_nonsample", "nonsample"), ("k_first_sym_hist", "nonsample"), ("k_par_nonsamples", "nonsample"),
+    ("k_nonsample", "nonsample"), ("k_first_sym_hist", "nonsample"), ("k_scatter_u64", "nonsample"),
+    ("k_ns_", "nonsample"), ("k_par_nonsamples", "nonsample"),
     ("k_par_ns_", "nonsample"), ("k_perm_offsets", "radix_hist"),
     ("k_gather_pri", "nonsample"), ("k_par_dup_writeback", "nonsample"),
     ("k_group_records", "merge"), ("k_merge", "merge"),
@@ -47,6 +48,8 @@ KINDS = [
 
 
 def kind_of(kernel: str) -> str:
+    if "SampleKeySrc" in kernel:  # the partition of the level-0 merge keys (Step 2/3)
+        return "nonsample"
     for prefix, kind in KINDS:
         if kernel.startswith(prefix):
             return kind
