@@ -332,7 +332,7 @@ int lor_multi_query_overlap(const uint8_t *d_ref, int64_t ref_len, const uint8_t
  *                   level 0 names the longest prefix whose key in base
  *                   (largest code + 1) fits it, so wider keys cost radix passes
  *                   and leave fewer repeated names for the later rounds
- *   sort_items_64   keys per thread of a sort pass over 64-bit keys: 8 or 12 (12)
+ *   sort_items_64   keys per thread of a sort pass over 64-bit keys: 8, 12 or 16 (12)
  *   sort_items_32   keys per thread over 32-bit keys: 12 or 16 (16)
  *   merge_items     merged suffixes per thread of the Step-3 merge: 2, 4 or 8
  *                   (512-, 256- or 128-thread blocks); default 4

@@ -89,7 +89,7 @@ TuneConfig tune_config() {
 
 static bool tune_valid(const lor_tune &c) {
     return c.digit_bits >= 5 && c.digit_bits <= 8 && c.level0_key_bits >= 24 && c.level0_key_bits <= 60 &&
-           (c.sort_items_64 == 8 || c.sort_items_64 == 12) && (c.sort_items_32 == 12 || c.sort_items_32 == 16) &&
+           (c.sort_items_64 == 8 || c.sort_items_64 == 12 || c.sort_items_64 == 16) && (c.sort_items_32 == 12 || c.sort_items_32 == 16) &&
            (c.merge_items == 2 || c.merge_items == 4 || c.merge_items == 8);
 }
 

@@ -60,7 +60,7 @@ bool prof_enabled();
 struct TuneConfig {
     int digit_bits = 8;        // radix digit width of the sorts, 5..8 bits
     int level0_key_bits = 48;  // width of the level-0 sample keys (the symbols named at level 0)
-    int sort_items_64 = 12;    // keys per thread of a sort pass over 64-bit keys: 8 or 12
+    int sort_items_64 = 12;    // keys per thread of a sort pass over 64-bit keys: 8, 12 or 16
     int sort_items_32 = 16;    // ... over 32-bit keys: 12 or 16
     int merge_items = 4;       // merged suffixes per thread of the Step-3 merge: 2, 4 or 8 (512, 256, 128 threads)
 };

@@ -707,6 +707,10 @@ struct NsSmem {
     long long tile;
 };
 
+// Marks a B1 sample's merge key (bit 63 of the packed key; no reader of the
+// key's comparison bytes looks at it).
+constexpr uint64_t kB1Flag = uint64_t(1) << 63;
+
 // Every sample's merge key (Step 3), made in reduced-string order x from the
 // text and the ranks (all read in sequence) and keyed by the sample's index
 // in sample order, j = rank(S_x) - 1, for a bucketed scatter into Ax[j]:
@@ -729,7 +733,7 @@ struct SampleKeySrc {
             const int64_t p = 3 * x + 1;
             const uint64_t c0 = p < n ? s[p] : 0, cm = s[p - 1];
             const uint32_t r = x < n2 ? uint32_t(Rl[n0 + x]) : 0u;
-            v = uint64_t(r) | (c0 << 32) | (cm << 40);
+            v = uint64_t(r) | (c0 << 32) | (cm << 40) | kB1Flag;
         } else {
             const int64_t xp = x - n0, p = 3 * xp + 2;
             const uint64_t c0 = p < n ? s[p] : 0, c1 = p + 1 < n ? s[p + 1] : 0;
@@ -778,10 +782,10 @@ __global__ void k_scatter_u64(const uint32_t *__restrict__ key, const uint64_t *
 // its tile's start plus its stable rank inside the tile.
 
 __global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__restrict__ SAR,
-                                                          const uint64_t *__restrict__ Ax, int64_t n02, int64_t n0,
+                                                          const uint64_t *__restrict__ Ax, int64_t n02,
                                                           uint32_t *__restrict__ cnt) {
     __shared__ uint32_t h[kRadix];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int64_t ntiles = cdiv(n02, kSpTile);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         h[tid] = 0;
@@ -794,7 +798,7 @@ __global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__rest
             const int64_t idx = tile * kSpTile + i * kSortThreads + tid;
             const int32_t x = idx < n02 ? SAR[idx] : -1;
             const uint64_t w = idx < n02 ? Ax[idx] : 0;
-            d[i] = (x >= 0 && x < n0) ? uint32_t(w >> 40) & 0xFFu : 0x100u;
+            d[i] = (x >= 0 && (w & kB1Flag)) ? uint32_t(w >> 40) & 0xFFu : 0x100u;
         }
         // one shared-memory add per distinct symbol of a warp (few symbols:
         // per-lane adds would all queue on the same words)
@@ -803,7 +807,6 @@ __global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__rest
             const uint32_t peers = warp_peers9(d[i]);
             if (d[i] < 0x100u && __popc(peers & lanemask_lt()) == 0) atomicAdd(&h[d[i]], uint32_t(__popc(peers)));
         }
-        (void)lane;
         __syncthreads();
         cnt[tile * kRadix + tid] = h[tid];
         __syncthreads();
@@ -2019,8 +2022,8 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
         if (ntiles > cdiv(D.L.max_m, kSpTile)) return LOR_ERR_WORKSPACE;
         const unsigned grid = unsigned(min64(ntiles, int64_t(sort_grid_cap()) * 2));
         {
-            ProfScope ps(PK_NONSAMPLE, double(m) * 4 + double(z.n0) * 8, st);
-            k_ns_count<<<grid, kSortThreads, 0, st>>>(SAR, Ax, m, z.n0, cnt);
+            ProfScope ps(PK_NONSAMPLE, double(m) * (4 + 8), st);
+            k_ns_count<<<grid, kSortThreads, 0, st>>>(SAR, Ax, m, cnt);
             LOR_LAUNCH_CHECK();
         }
         {

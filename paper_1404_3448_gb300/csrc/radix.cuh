@@ -189,8 +189,13 @@ __device__ __forceinline__ uint32_t lookback_digit(const uint64_t *lb, int64_t t
 // the counter by ntiles + gridDim.x.  When m_dev is given the element count
 // is read from device memory (the count of an earlier kernel), so that the
 // launch needs no host round trip.
+// Four blocks per SM at 64 registers a thread; the widest tile of 64-bit keys
+// (16 a thread) takes three blocks with more registers instead of spilling.
+template <typename KeyT, int kItems>
+__host__ __device__ constexpr int onesweep_min_blocks() { return sizeof(KeyT) == 8 && kItems > 12 ? 3 : 4; }
+
 template <typename KeyT, typename ValT, int kVMode, int kItems>
-__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
+__global__ void __launch_bounds__(kSortThreads, onesweep_min_blocks<KeyT, kItems>()) k_onesweep(
     const KeyT *__restrict__ kin, const ValT *__restrict__ vin, KeyT *__restrict__ kout,
     ValT *__restrict__ vout, int64_t m, const uint32_t *m_dev, int shift, uint32_t dmask,
     const uint32_t *__restrict__ offsets,
@@ -857,6 +862,9 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
         if (items == 8)
             return radix_passes<KeyT, 8>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
                                          m_dev, kres, vres, ties_any_order);
+        if (items == 16)
+            return radix_passes<KeyT, 16>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
+                                          m_dev, kres, vres, ties_any_order);
         return radix_passes<KeyT, 12>(rs, k0, v0, k1, v1, m, begin_bit, end_bit, dbits, npasses, h, !iota_vals,
                                       m_dev, kres, vres, ties_any_order);
     }

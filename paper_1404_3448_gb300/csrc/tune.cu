@@ -57,7 +57,7 @@ extern "C" int lor_autotune_batch(const uint8_t *d_ascii, const int64_t *h_lens,
     const Knob knobs[] = {
         {&lor_tune::level0_key_bits, {30, 40, 48, 56}},
         {&lor_tune::digit_bits, {6, 7, 8}},
-        {&lor_tune::sort_items_64, {8, 12}},
+        {&lor_tune::sort_items_64, {8, 12, 16}},
         {&lor_tune::sort_items_32, {12, 16}},
         {&lor_tune::merge_items, {2, 4, 8}},
     };

@@ -175,7 +175,7 @@ def test_tune_configuration_round_trip_and_range_checks(lib):
         assert P.tune_set(digit_bits=6, merge_items=8)["digit_bits"] == 6
         assert P.tune_get()["merge_items"] == 8
         for bad in [dict(digit_bits=4), dict(digit_bits=9), dict(level0_key_bits=23),
-                    dict(level0_key_bits=61), dict(sort_items_64=16), dict(sort_items_32=8),
+                    dict(level0_key_bits=61), dict(sort_items_64=20), dict(sort_items_32=8),
                     dict(merge_items=3), dict(merge_items=16)]:
             before = P.tune_get()
             with pytest.raises(L.LorError):

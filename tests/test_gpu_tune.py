@@ -31,7 +31,7 @@ def O():
 
 
 CONFIGS = [dict(digit_bits=6), dict(digit_bits=7), dict(level0_key_bits=30), dict(level0_key_bits=56),
-           dict(sort_items_64=8), dict(sort_items_32=12), dict(merge_items=2), dict(merge_items=8),
+           dict(sort_items_64=8), dict(sort_items_64=16), dict(sort_items_32=12), dict(merge_items=2), dict(merge_items=8),
            dict(digit_bits=5, level0_key_bits=24, sort_items_64=8, sort_items_32=12, merge_items=2)]
 
 
