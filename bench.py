@@ -36,6 +36,9 @@ WORKLOADS = {
     "noncoding": (None, 1_000_000,
                   "2x16777216 noncoding-like DNA (40% GC, repeats, microsatellites, 10 kb shared "
                   "region with exact 2 kb core), S1#S2$; 1M uniform LCP queries"),
+    "medium": (dict(n_each=33_554_432, seed=140434483), 1_000_000,
+               "2x33554432 iid-uniform DNA with one 500-base plant, S1#S2$ (n=67108866); 1M uniform LCP "
+               "queries (the large workload's generator at a quarter of its size, for DRAM-counter captures)"),
     "tiny": (dict(n_each=100_000, seed=140434481), 100_000,
              "2x100000 iid-uniform DNA with one 500-base plant, S1#S2$; 100k LCP queries"),
 }
@@ -162,13 +165,19 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-TRAFFIC_PROFILES = {"large": "dram_by_kind_2x134217728.md"}
+# DRAM counters are captured on the large workload's generator at a quarter
+# of its size (a capture of several metrics holds the workload on the device
+# through many replays, so it is kept to a few GB); the summary gives DRAM
+# bytes / algorithmic bytes per kind, which scales to the full launch.
+TRAFFIC_PROFILES = {"large": "dram_by_kind_2x33554432.md", "medium": "dram_by_kind_2x33554432.md"}
 
 
-def ncu_traffic(kind, workload):
-    """DRAM bytes per launch of `kind` from the committed ncu summary of this
+def ncu_traffic(kind, workload, model_bytes_per_launch=None):
+    """DRAM bytes per launch of `kind` from the committed ncu summary for this
     workload (profiles/, written by paper_1404_3448_gb300.ncu_summary), only
-    when it was taken on the current kernel sources."""
+    when it was taken on the current kernel sources: the summary's DRAM /
+    model ratio times this run's algorithmic bytes per launch when it has
+    one, else its DRAM bytes per launch."""
     name = TRAFFIC_PROFILES.get(workload)
     if not name:
         return None
@@ -182,8 +191,10 @@ def ncu_traffic(kind, workload):
         return None
     for line in text.splitlines():
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) == 6 and cells[0] == kind:
+        if len(cells) in (6, 8) and cells[0] == kind:
             try:
+                if len(cells) == 8 and model_bytes_per_launch:
+                    return float(cells[7]) * float(model_bytes_per_launch)
                 return float(cells[5])
             except ValueError:
                 return None
@@ -1012,7 +1023,7 @@ def run_lor(args):
                     "launches_per_step": d["launches"] / args.steps,
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                     "avg_launch_ms": d["ms"] / d["launches"],
-                    "traffic": ncu_traffic(dom, args.workload)}
+                    "traffic": ncu_traffic(dom, args.workload, d["bytes"] / d["launches"])}
         path_bytes = sum(v["bytes"] for v in prof.values()) / args.steps
         # a1-a10 alone (the metric's SA + LCP + longest overlap): every kind but
         # the sparse table and the queries
@@ -1042,6 +1053,7 @@ def run_lor(args):
             "path_model_bytes_per_step": path_bytes,
             "path_model_gbs": path_bytes / (ms / 1000.0) / 1e9,
             "stage_ms": stage_ms,
+            "stage_model_bytes": {k: v["bytes"] / args.steps for k, v in prof.items()},
             "step_latency_ms": {"p50": p50, "p99": p99, "mean": ms_all, "steps": args.steps},
             "overlap": {"length": int(host_out[0]), "n_pos": int(host_out[6])},
             "dc3_levels": len(lor.last_dc3_trace()),

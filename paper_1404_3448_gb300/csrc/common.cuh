@@ -210,6 +210,63 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// Double-buffered bulk loads for a grid-stride loop over tiles of kN
+// elements of two arrays: while a block works on one tile, the next tile of
+// its stride is on its way into the other buffer.  A whole tile with 16-byte
+// aligned rows is copied in bulk; a partial or unaligned one is read from
+// global memory by the caller (whole() says which).  Thread 0 issues; every
+// thread waits, for at most the wait limit.
+template <typename A, typename B, int kN>
+struct BulkPair {
+    A a[2][kN];
+    B b[2][kN];
+    uint64_t bar[2];
+};
+
+template <typename A, typename B, int kN>
+struct BulkPairLoader {
+    BulkPair<A, B, kN> &S;
+    const A *ga;
+    const B *gb;
+    int64_t n;
+    uint32_t phase;
+    __device__ __forceinline__ BulkPairLoader(BulkPair<A, B, kN> &s, const A *a, const B *b, int64_t count)
+        : S(s), ga(a), gb(b), n(count), phase(0) {
+        if (threadIdx.x == 0) {
+            mbar_init(&S.bar[0], 1);
+            mbar_init(&S.bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ bool whole(int64_t t) const {
+        return t >= 0 && (t + 1) * kN <= n && (uintptr_t(ga + t * kN) & 15) == 0 &&
+               (uintptr_t(gb + t * kN) & 15) == 0;
+    }
+    // thread 0: start the copy of tile t into buffer buf (after the buffer's
+    // last readers passed a barrier)
+    __device__ __forceinline__ void issue(int64_t t, int buf) {
+        if (!whole(t)) return;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&S.bar[buf], uint32_t(kN * (sizeof(A) + sizeof(B))));
+        bulk_g2s(S.a[buf], ga + t * kN, uint32_t(kN * sizeof(A)), &S.bar[buf]);
+        bulk_g2s(S.b[buf], gb + t * kN, uint32_t(kN * sizeof(B)), &S.bar[buf]);
+    }
+    // every thread: wait for tile t in buffer buf; false when the wait ran out
+    __device__ __forceinline__ bool wait(int64_t t, int buf, uint64_t limit) {
+        if (!whole(t)) return true;
+        const bool ok = mbar_wait_bounded(&S.bar[buf], (phase >> buf) & 1u, limit);
+        phase ^= 1u << buf;
+        return ok;
+    }
+    // thread 0, on the way out after a wait ran out: give the copies still in
+    // flight a bounded time to land
+    __device__ __forceinline__ void drain(int64_t t, int buf, int64_t nxt, uint64_t limit) {
+        if (whole(t)) mbar_wait_bounded(&S.bar[buf], ((phase >> buf) & 1u) ^ 1u, limit);
+        if (whole(nxt)) mbar_wait_bounded(&S.bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, limit);
+    }
+};
+
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
     uint64_t v;
     asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

@@ -781,23 +781,60 @@ __global__ void k_scatter_u64(const uint32_t *__restrict__ key, const uint64_t *
 // over the tiles, from the symbols' starts); per tile, each record written at
 // its tile's start plus its stable rank inside the tile.
 
+// The split's kernels read SAR and the keys tile by tile, the next tile of a
+// block's stride prefetched into shared memory by bulk copies.
+// (dynamic shared memory: more than the 48 KB a static allocation may take)
+using NsTiles = BulkPair<int32_t, uint64_t, kSpTile>;
+struct NsCountSmem {
+    NsTiles T;
+    uint32_t h[kRadix];
+};
+struct NsWriteSmem {
+    NsTiles T;
+    uint32_t wh[kSortWarps][kRadix];
+};
+
 __global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__restrict__ SAR,
                                                           const uint64_t *__restrict__ Ax, int64_t n02,
-                                                          uint32_t *__restrict__ cnt) {
-    __shared__ uint32_t h[kRadix];
+                                                          uint32_t *__restrict__ cnt, int *status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    NsCountSmem &S = *reinterpret_cast<NsCountSmem *>(smem_raw);
+    NsTiles &T = S.T;
+    uint32_t *h = S.h;
     const int tid = threadIdx.x;
     const int64_t ntiles = cdiv(n02, kSpTile);
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t limit = wait_limit_ns();
+    BulkPairLoader<int32_t, uint64_t, kSpTile> ld(T, SAR, Ax, n02);
+    int64_t tile = blockIdx.x;
+    if (tid == 0) ld.issue(tile, 0);
+    for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
+        const int64_t nxt = tile + gridDim.x;
+        if (tid == 0 && nxt < ntiles) ld.issue(nxt, b ^ 1);
         h[tid] = 0;
-        __syncthreads();
+        const bool whole = ld.whole(tile);
+        const bool ok = ld.wait(tile, b, limit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(status, 0, LOR_ERR_TIMEOUT);
+                ld.drain(tile, b, nxt, limit);
+            }
+            __syncthreads();
+            return;
+        }
         uint32_t d[kSpItems];
 #pragma unroll
         for (int i = 0; i < kSpItems; ++i) {
-            // both loads issued at once (a sector of Ax almost always holds a
-            // B1 sample, so reading it whole costs nothing extra)
-            const int64_t idx = tile * kSpTile + i * kSortThreads + tid;
-            const int32_t x = idx < n02 ? SAR[idx] : -1;
-            const uint64_t w = idx < n02 ? Ax[idx] : 0;
+            const int loc = i * kSortThreads + tid;
+            const int64_t idx = tile * kSpTile + loc;
+            int32_t x = -1;
+            uint64_t w = 0;
+            if (whole) {
+                x = T.a[b][loc];
+                w = T.b[b][loc];
+            } else if (idx < n02) {
+                x = SAR[idx];
+                w = Ax[idx];
+            }
             d[i] = (x >= 0 && (w & kB1Flag)) ? uint32_t(w >> 40) & 0xFFu : 0x100u;
         }
         // one shared-memory add per distinct symbol of a warp (few symbols:
@@ -809,7 +846,7 @@ __global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__rest
         }
         __syncthreads();
         cnt[tile * kRadix + tid] = h[tid];
-        __syncthreads();
+        __syncthreads();  // the counts and the buffer are reused
     }
 }
 
@@ -851,25 +888,51 @@ __global__ void __launch_bounds__(kRadix) k_ns_scan_tiles(uint32_t *__restrict__
 // Every record at its tile's start for its first symbol plus its stable rank
 // in the tile (each warp owns a run of 512 consecutive entries: items in
 // order, lanes in order).
-__global__ void __launch_bounds__(kSortThreads, 4) k_ns_write(const int32_t *__restrict__ SAR,
+__global__ void __launch_bounds__(kSortThreads, 3) k_ns_write(const int32_t *__restrict__ SAR,
                                                              const uint64_t *__restrict__ Ax, int64_t n02, int64_t n0,
                                                              const uint32_t *__restrict__ start,
                                                              BRec16 *__restrict__ out, int *status) {
-    __shared__ uint32_t wh[kSortWarps][kRadix];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    NsWriteSmem &S = *reinterpret_cast<NsWriteSmem *>(smem_raw);
+    NsTiles &T = S.T;
+    uint32_t(&wh)[kSortWarps][kRadix] = S.wh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ntiles = cdiv(n02, kSpTile);
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t limit = wait_limit_ns();
+    BulkPairLoader<int32_t, uint64_t, kSpTile> ld(T, SAR, Ax, n02);
+    int64_t tile = blockIdx.x;
+    if (tid == 0) ld.issue(tile, 0);
+    for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
+        const int64_t nxt = tile + gridDim.x;
+        if (tid == 0 && nxt < ntiles) ld.issue(nxt, b ^ 1);
         for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&wh[0][0])[i] = 0;
-        __syncthreads();
-        const int64_t wbase = tile * kSpTile + int64_t(warp) * (kSpItems * 32);
+        const bool whole = ld.whole(tile);
+        const bool ok = ld.wait(tile, b, limit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(status, 0, LOR_ERR_TIMEOUT);
+                ld.drain(tile, b, nxt, limit);
+            }
+            __syncthreads();
+            return;
+        }
+        const int wloc = warp * (kSpItems * 32) + lane;
+        const int64_t wbase = tile * kSpTile + wloc;
         int32_t xs[kSpItems];
         uint64_t ws[kSpItems];
         uint32_t dig[kSpItems], r[kSpItems];
 #pragma unroll
         for (int i = 0; i < kSpItems; ++i) {
-            const int64_t idx = wbase + i * 32 + lane;
-            xs[i] = idx < n02 ? SAR[idx] : -1;
-            ws[i] = idx < n02 ? Ax[idx] : 0;  // issued with the SAR load, not after it
+            const int64_t idx = wbase + i * 32;
+            xs[i] = -1;
+            ws[i] = 0;
+            if (whole) {
+                xs[i] = T.a[b][wloc + i * 32];
+                ws[i] = T.b[b][wloc + i * 32];
+            } else if (idx < n02) {
+                xs[i] = SAR[idx];
+                ws[i] = Ax[idx];
+            }
             dig[i] = 0x100u;
             if (xs[i] >= 0 && xs[i] < n0) {
                 dig[i] = uint32_t(ws[i] >> 40) & 0xFFu;
@@ -916,11 +979,11 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_ns_write(const int32_t *__r
             BRec16 v;
             v.t = xs[i];
             v.c01 = dig[i] | ((uint32_t(ws[i] >> 32) & 0xFFu) << 8);
-            v.r1 = int32_t(wbase + i * 32 + lane + 1);
+            v.r1 = int32_t(wbase + i * 32 + 1);
             v.r2 = int32_t(uint32_t(ws[i]));
             out[o] = v;
         }
-        __syncthreads();  // the warp counts are reused by the next tile
+        __syncthreads();  // the warp counts and the buffer are reused by the next tile
     }
 }
 
@@ -2020,10 +2083,14 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
         uint32_t *cnt = (uint32_t *)(D.ws + D.L.ns_table);
         uint32_t *part = cnt + ntiles * kRadix;
         if (ntiles > cdiv(D.L.max_m, kSpTile)) return LOR_ERR_WORKSPACE;
-        const unsigned grid = unsigned(min64(ntiles, int64_t(sort_grid_cap()) * 2));
+        // resident grids: four count blocks, three write blocks per SM
+        const unsigned grid = unsigned(min64(ntiles, int64_t(sort_grid_cap())));
+        const unsigned wgrid = unsigned(min64(ntiles, int64_t(sort_grid_cap()) / 4 * 3));
         {
             ProfScope ps(PK_NONSAMPLE, double(m) * (4 + 8), st);
-            k_ns_count<<<grid, kSortThreads, 0, st>>>(SAR, Ax, m, cnt);
+            LOR_CUDA_TRY(cudaFuncSetAttribute(k_ns_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(sizeof(NsCountSmem))));
+            k_ns_count<<<grid, kSortThreads, sizeof(NsCountSmem), st>>>(SAR, Ax, m, cnt, D.status);
             LOR_LAUNCH_CHECK();
         }
         {
@@ -2037,7 +2104,9 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
         }
         {
             ProfScope ps(PK_NONSAMPLE, double(m) * 4 + double(z.n0) * (8 + 16), st);
-            k_ns_write<<<grid, kSortThreads, 0, st>>>(SAR, Ax, m, z.n0, cnt, Bx, D.status);
+            LOR_CUDA_TRY(cudaFuncSetAttribute(k_ns_write, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(sizeof(NsWriteSmem))));
+            k_ns_write<<<wgrid, kSortThreads, sizeof(NsWriteSmem), st>>>(SAR, Ax, m, z.n0, cnt, Bx, D.status);
             LOR_LAUNCH_CHECK();
         }
     }

@@ -457,14 +457,18 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
 // unaligned tile is read with plain loads.  Every wait is bounded by the wait
 // limit (then LOR_ERR_TIMEOUT, after a bounded wait for the block's own copy
 // in flight).
+// The staging area of a tile's write is the tile's own input buffer (its
+// items are in registers by then; values that are generated, not loaded,
+// get one staging array of their own), so that three blocks fit an SM.  For
+// 64-bit keys a separate staging area at two blocks per SM measured faster
+// (0.93 against 1.06 ms for the 179M-key pass).
 template <typename KeyT, typename ValT, int kVMode>
 struct PipeSmem {
     static constexpr int kTile = sort_tile<KeyT, ValT>();
-    static constexpr int kInV = kVMode == VM_LOAD ? kTile : 1;
-    KeyT in_k[2][kTile];
-    ValT in_v[2][kInV];
-    KeyT keys[kTile];
-    ValT vals[kTile];
+    static constexpr bool kLoadV = kVMode == VM_LOAD;
+    static constexpr bool kOwnStage = sizeof(KeyT) == 8;
+    KeyT in_k[kOwnStage ? 3 : 2][kTile];
+    ValT in_v[kLoadV ? (kOwnStage ? 3 : 2) : 1][kTile];
     uint32_t cnt[kRadix];
     uint32_t local_start[kRadix];
     long long gbase[kRadix];
@@ -473,7 +477,7 @@ struct PipeSmem {
 };
 
 template <typename KeyT, typename ValT, int kVMode>
-__global__ void __launch_bounds__(kSortThreads) k_partition_pipe(
+__global__ void __launch_bounds__(kSortThreads, sizeof(KeyT) == 8 ? 2 : 3) k_partition_pipe(
     const KeyT *__restrict__ kin, const ValT *__restrict__ vin, KeyT *__restrict__ kout, ValT *__restrict__ vout,
     int64_t m, const uint32_t *m_dev, int shift, uint32_t dmask, uint32_t *__restrict__ cursor, int *status) {
     using Smem = PipeSmem<KeyT, ValT, kVMode>;
@@ -565,29 +569,31 @@ __global__ void __launch_bounds__(kSortThreads) k_partition_pipe(
         const uint32_t lstart = block_excl_scan<kSortThreads>(total, S.scratch, &tile_total);
         S.local_start[dg] = lstart;
         S.gbase[dg] = (long long)run - lstart;
-        __syncthreads();
+        __syncthreads();  // every item is in registers: the input buffer becomes the staging area
+        KeyT *stage_k = S.in_k[Smem::kOwnStage ? 2 : b];
+        ValT *stage_v = S.in_v[kLoadV ? (Smem::kOwnStage ? 2 : b) : 0];
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const int64_t idx = base + i * kSortThreads + tid;
             if (idx < m) {
                 const uint32_t pos = S.local_start[digit_of(k[i], shift, dmask)] + r[i];
-                S.keys[pos] = k[i];
-                S.vals[pos] = v[i];
+                stage_k[pos] = k[i];
+                stage_v[pos] = v[i];
             }
         }
         __syncthreads();
         const int cnt_tile = int(min64(int64_t(kTile), m - base));
         for (int i = tid; i < cnt_tile; i += kSortThreads) {
-            const KeyT kk = S.keys[i];
+            const KeyT kk = stage_k[i];
             const long long o = S.gbase[digit_of(kk, shift, dmask)] + i;
             if (o < 0 || o >= m) {  // counts that did not match the keys (keys meant to be a permutation)
                 atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
                 continue;
             }
             kout[o] = kk;
-            vout[o] = S.vals[i];
+            vout[o] = stage_v[i];
         }
-        __syncthreads();  // counts, staging and the input buffer are reused
+        __syncthreads();  // counts and the buffer are reused
     }
 }
 

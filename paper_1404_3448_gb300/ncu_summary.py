@@ -107,16 +107,27 @@ def summarize(launches):
     return per_kernel, per_kind
 
 
-def markdown(per_kernel, per_kind) -> str:
+def markdown(per_kernel, per_kind, model=None) -> str:
+    """Tables of the launch list; with `model` (algorithmic bytes per kind for
+    the same launches, as bench.py's stage_model_bytes) the kind table also
+    gives the model bytes and DRAM bytes / model bytes."""
     total = sum(v[1] for v in per_kernel.values()) or 1.0
     out = ["| kernel | launches | total ms | share |", "|---|---|---|---|"]
     for name, (c, t) in sorted(per_kernel.items(), key=lambda x: -x[1][1]):
         out.append(f"| `{name}` | {c} | {t:.3f} | {100 * t / total:.1f} % |")
     if any(v[4] for v in per_kind.values()):
-        out += ["", "| kind | launches | total ms | DRAM read GB | DRAM write GB | DRAM bytes per launch |",
-                "|---|---|---|---|---|---|"]
+        head = "| kind | launches | total ms | DRAM read GB | DRAM write GB | DRAM bytes per launch |"
+        rule = "|---|---|---|---|---|---|"
+        if model is not None:
+            head += " model GB | DRAM / model |"
+            rule += "---|---|"
+        out += ["", head, rule]
         for kind, (c, t, rd, wr, _) in sorted(per_kind.items(), key=lambda x: -x[1][1]):
-            out.append(f"| {kind} | {c} | {t:.3f} | {rd / 1e9:.3f} | {wr / 1e9:.3f} | {(rd + wr) / max(c, 1):.0f} |")
+            row = f"| {kind} | {c} | {t:.3f} | {rd / 1e9:.3f} | {wr / 1e9:.3f} | {(rd + wr) / max(c, 1):.0f} |"
+            if model is not None:
+                mb = model.get(kind)
+                row += f" {mb / 1e9:.3f} | {(rd + wr) / mb:.3f} |" if mb else " - | - |"
+            out.append(row)
     return "\n".join(out)
 
 
@@ -125,13 +136,21 @@ def main():
     ap.add_argument("csv")
     ap.add_argument("--skip", type=int, default=0, help="launches to drop from the start")
     ap.add_argument("--take", type=int, default=0, help="launches to keep after --skip (0: all)")
+    ap.add_argument("--model-json", help="bench.py output of the same command (one timed step): adds the "
+                                         "algorithmic bytes per kind and DRAM / model")
     args = ap.parse_args()
     launches = read_launches(args.csv)[args.skip:]
     if args.take:
         launches = launches[:args.take]
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     print(f"source hash: `{source_hash(root)}`\n")
-    print(markdown(*summarize(launches)))
+    model = None
+    if args.model_json:
+        import json
+        with open(args.model_json) as fh:
+            line = [ln for ln in fh if ln.startswith("{")][-1]
+        model = json.loads(line).get("stage_model_bytes")
+    print(markdown(*summarize(launches), model=model))
 
 
 if __name__ == "__main__":

@@ -46,9 +46,22 @@ def test_bench_reads_traffic_only_for_current_sources(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc123")
-    (tmp_path / "profiles" / "dram_by_kind_2x134217728.md").write_text(md % "abc123")
+    name = bench.TRAFFIC_PROFILES["large"]
+    (tmp_path / "profiles" / name).write_text(md % "abc123")
     assert bench.ncu_traffic("radix_pass", "large") == 12345.0
     assert bench.ncu_traffic("merge", "large") is None
     assert bench.ncu_traffic("radix_pass", "tiny") is None
-    (tmp_path / "profiles" / "dram_by_kind_2x134217728.md").write_text(md % "ffff00")
+    (tmp_path / "profiles" / name).write_text(md % "ffff00")
     assert bench.ncu_traffic("radix_pass", "large") is None
+
+
+def test_bench_scales_traffic_by_the_dram_to_model_ratio(tmp_path, monkeypatch):
+    launches = [("k_onesweep<unsigned long, unsigned int, 0, 12>", {"gpu__time_duration.sum": 1.0,
+                 "dram__bytes_read.sum": 3e9, "dram__bytes_write.sum": 1e9})]
+    md = S.markdown(*S.summarize(launches), model={"radix_pass": 2e9})
+    assert "| radix_pass | 1 | 1.000 | 3.000 | 1.000 | 4000000000 | 2.000 | 2.000 |" in md
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc123")
+    (tmp_path / "profiles" / bench.TRAFFIC_PROFILES["large"]).write_text("source hash: `abc123`\n\n" + md)
+    assert bench.ncu_traffic("radix_pass", "large", 5e8) == 1e9
