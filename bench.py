@@ -612,8 +612,8 @@ class PinnedRing:
         self.live.append((start, start + nbytes, key))
 
 
-def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, subset=1500,
-            src_bases=1 << 27, seed=140434485):
+def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, subset=1500, max_pairs=64,
+            src_bases=1 << 27, src_copies=8, seed=140434485):
     """Requests arrive as a Poisson process (``rate`` per second for
     ``seconds``).  Every request is a fresh pair: per-sequence lengths
     log-uniform in [1k, 4M]; S1 a window of one noncoding-like source
@@ -636,20 +636,33 @@ def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, sub
 
     rng = gen._rng(seed)
     consensi = [gen.random_bases(rng, 300) for _ in range(5)]
+    # Each source is `src_copies` blocks: one generated noncoding-like sequence
+    # written out under distinct permutations of A, C, G, T, so that windows of
+    # different requests rarely share a long stretch (a shared stretch would
+    # be a long repeat in the batch text, which independent pairs do not have)
+    # while generation stays at one sequence per source.
+    import itertools
+    perms = list(itertools.permutations(b"ACGT"))
     src = []
     for _ in range(2):
         x, _ = gen.noncoding_sequence(rng, src_bases, consensi, None)
-        t = torch.from_numpy(x).pin_memory()
+        t = torch.empty(src_bases * src_copies, dtype=torch.uint8, pin_memory=True)
+        tv = t.numpy()
+        for c, pi in enumerate(rng.choice(len(perms), size=src_copies, replace=False)):
+            lut = np.arange(256, dtype=np.uint8)
+            lut[list(b"ACGT")] = perms[int(pi)]
+            tv[c * src_bases:(c + 1) * src_bases] = lut[x]
         src.append(t)
     src_np = [t.numpy() for t in src]
+    src_len = src_bases * src_copies
     arrivals = gen.poisson_arrivals(rate, seconds, seed=seed + 1)
     nreq = len(arrivals)
     r2 = gen._rng(seed + 2)
     lo, hi = np.log(1_000), np.log(4_000_000)
     l1 = np.rint(np.exp(r2.uniform(lo, hi, nreq))).astype(np.int64)
     l2 = np.rint(np.exp(r2.uniform(lo, hi, nreq))).astype(np.int64)
-    o1 = (r2.random(nreq) * (src_bases - l1 + 1)).astype(np.int64)
-    o2 = (r2.random(nreq) * (src_bases - l2 + 1)).astype(np.int64)
+    o1 = (r2.random(nreq) * (src_len - l1 + 1)).astype(np.int64)
+    o2 = (r2.random(nreq) * (src_len - l2 + 1)).astype(np.int64)
     plen = np.minimum(r2.integers(50, 5001, nreq), np.minimum(l1, l2))
     ps = (r2.random(nreq) * (l1 - plen + 1)).astype(np.int64)
     pd = (r2.random(nreq) * (l2 - plen + 1)).astype(np.int64)
@@ -671,7 +684,7 @@ def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, sub
         ring.hold(off, int(l2[k]), k)
         return src[0].data_ptr() + int(o1[k]), ring.buf.data_ptr() + off
 
-    srv = lor.Server(int(budget_gb * (1 << 30)), workers=workers, max_batch_pairs=512)
+    srv = lor.Server(int(budget_gb * (1 << 30)), workers=workers, max_batch_pairs=max_pairs)
     try:
         # warm-up: the first 64 requests, so first-launch setup is not timed
         for k in range(min(64, nreq)):
@@ -743,10 +756,11 @@ def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, sub
         done_flags[:] = False
         ring.live.clear()
         sat_records = {}
+        # staged first (host copies are not the server's work), then submitted at once
+        staged = [stage(k) for k in range(m)]
         s0 = srv.now()
         for k in range(m):
-            pa, pb = stage(k)
-            srv.submit_ptr(pa, int(l1[k]), pb, int(l2[k]), tag=k)
+            srv.submit_ptr(staged[k][0], int(l1[k]), staged[k][1], int(l2[k]), tag=k)
         got = 0
         while got < m:
             for r in srv.poll(timeout_ms=50):
@@ -765,8 +779,6 @@ def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, sub
 
     # the same first requests one pair per call through the plain path
     nmax = int((l1[:m] + l2[:m]).max()) + 2
-    host_pair = torch.empty(nmax, dtype=torch.uint8, pin_memory=True)
-    hp = host_pair.numpy()
     dev_pair = torch.empty(nmax, dtype=torch.uint8, device=dev)
     text = torch.empty(nmax, dtype=torch.uint8, device=dev)
     starts = torch.empty(3, dtype=torch.int32, device=dev)
@@ -784,11 +796,14 @@ def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, sub
     torch.cuda.synchronize(dev)
     t_plain = time.perf_counter()
     for k in range(m):
+        # the same staged bytes (S1 in its source, S2 in the ring), copied from pinned memory
         a, b = int(l1[k]), int(l2[k])
-        hp[:a] = src_np[0][o1[k]:o1[k] + a]
-        hp[a:a + b] = src_np[1][o2[k]:o2[k] + b]
-        hp[a + pd[k]:a + pd[k] + plen[k]] = src_np[0][o1[k] + ps[k]:o1[k] + ps[k] + plen[k]]
-        dev_pair[:a + b].copy_(host_pair[:a + b], non_blocking=True)
+        sa_off = staged[k][0] - src[0].data_ptr()
+        sb_off = staged[k][1] - ring.buf.data_ptr()
+        if a:
+            dev_pair[:a].copy_(src[0][sa_off:sa_off + a], non_blocking=True)
+        if b:
+            dev_pair[a:a + b].copy_(ring.buf[sb_off:sb_off + b], non_blocking=True)
         l2a = np.array([a, b], dtype=np.int64)
         n = a + b + 2
         C._check(C.lor_encode_concat(dev_pair.data_ptr(), l2a.ctypes.data, 2, text.data_ptr(),
@@ -816,9 +831,11 @@ def serving(seconds, rate, workers, budget_gb, dev, queries=16, ring_gb=8.0, sub
     return {
         "workload": f"Poisson arrivals at {rate:g} pair requests/s for {seconds:g} s; every request a fresh "
                     f"noncoding-like pair (per-sequence lengths log-uniform in [1k, 4M]; windows of two "
-                    f"{src_bases}-base source sequences, one exact 50-5000-base piece of S1 planted in S2), "
+                    f"{src_len}-base source sequences, each {src_copies} copies of one generated sequence under distinct "
+                    f"permutations of ACGT; one exact 50-5000-base piece of S1 planted in S2), "
                     f"staged in pinned host memory on the arrival clock; {queries} follow-up LCP queries per "
-                    f"pair on resident state; {budget_gb:g} GB device budget; {workers} workers",
+                    f"pair on resident state; {budget_gb:g} GB device budget; {workers} workers, batches of at most "
+                    f"{max_pairs} pairs",
         "seconds": seconds, "requests": nreq, "input_bases": bases,
         "offered_bases_per_s": bases / float(arrivals[-1]) if nreq else 0.0,
         "value": served, "unit": UNIT,
@@ -1083,7 +1100,8 @@ def run_lor(args):
         if args.serve_seconds > 0:
             torch.cuda.empty_cache()
             line["serving"] = serving(args.serve_seconds, args.serve_rate, args.serve_workers,
-                                      args.serve_budget_gb, dev, subset=args.serve_subset)
+                                      args.serve_budget_gb, dev, subset=args.serve_subset,
+                                      max_pairs=args.serve_max_pairs)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -1113,6 +1131,8 @@ def main():
     ap.add_argument("--serve-subset", type=int, default=1500,
                     help="first requests rerun saturated and one pair per call through the plain path")
     ap.add_argument("--serve-workers", type=int, default=2)
+    ap.add_argument("--serve-max-pairs", type=int, default=64,
+                    help="largest batch a server worker takes (64 measured faster than 512 when saturated)")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--recursion-steps", type=int, default=5,
                     help="timed steps of the DC3-recursion route (0 skips it)")
