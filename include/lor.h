@@ -331,7 +331,9 @@ int lor_multi_query_overlap(const uint8_t *d_ref, int64_t ref_len, const uint8_t
  *   level0_key_bits width of the level-0 sample keys, 24..60 (default 48): DC3
  *                   level 0 names the longest prefix whose key in base
  *                   (largest code + 1) fits it, so wider keys cost radix passes
- *                   and leave fewer repeated names for the later rounds
+ *                   and leave fewer repeated names for the later rounds (texts
+ *                   that take 2-bit keys, see lor_dc3_route_set, and the
+ *                   batched pipeline's graph-captured route excepted)
  *   sort_items_64   keys per thread of a sort pass over 64-bit keys: 8, 12 or 16 (12)
  *   sort_items_32   keys per thread over 32-bit keys: 12 or 16 (16)
  *   merge_items     merged suffixes per thread of the Step-3 merge: 2, 4 or 8
@@ -554,7 +556,8 @@ uint64_t lor_launch_count(void);
 
 /* Per-level trace of the most recent lor_build_sa call on the calling thread:
  * fills up to cap entries of level length n_l, distinct names found at that
- * level, key bits of the sample keys, how the sample was ordered (0 radix
+ * level, key bits of the sample keys (33 for level 0's 2-bit keys: 32 bits
+ * and the exception bit), how the sample was ordered (0 radix
  * sort, 1 dense naming table, 2 the parent level's order, 3 prefix doubling
  * of the reduced string in place of a DC3 level) and how many samples shared
  * their first symbol (strategy 2) or their name (strategy 3); any pointer
@@ -579,8 +582,12 @@ int lor_profile_read(int kind, int64_t *h_launches, double *h_ms, double *h_byte
  * tests can force every route and a measurement can time the plain
  * recursion.  Process-wide; read once at the start of each lor_build_sa call
  * (also inside the batched, served and no-workspace calls).
- *   level0_symbols: symbols named at level 0; 0 = the longest prefix whose key
- *                   fits the tuned level-0 key width, else at least 3.
+ *   level0_symbols: symbols named at level 0.  0 = automatic: for a text whose
+ *                   symbols are the four largest codes but for at most 4096
+ *                   sample windows (DNA with its separators), the first 16
+ *                   symbols at 2 bits each; otherwise as 1.  1 = the longest
+ *                   prefix whose key, in base sigma, fits the tuned level-0
+ *                   key width.  3..64 = that many symbols, in base sigma.
  *   strategy      : 0 = pick per level (dense table, parent order or sort),
  *                   1 = radix sort at every level.
  *   doubling      : 0 = never (recurse while names repeat, as the paper

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "dc3_packed.cuh"
 #include "radix.cuh"
 #include "scan.cuh"
 
@@ -1625,7 +1626,7 @@ thread_local std::vector<TraceRow> g_trace;
 
 // Route controls (lor_dc3_route_set): they pick how the sample is ordered,
 // never what the suffix array is.
-std::atomic<int> g_route_k0{0};        // symbols named at level 0 (0: from the key width)
+std::atomic<int> g_route_k0{0};        // symbols named at level 0 (0: 2-bit keys when the text allows, 1: from the key width)
 std::atomic<int> g_route_strategy{0};  // 1: radix sort at every level
 std::atomic<int> g_route_doubling{1};  // 0 never, 1 when names are almost unique, 2 whenever names repeat
 
@@ -1801,6 +1802,65 @@ int sample_sort_and_name_wide(Dc3Run &D, const CharT *s, const LevelSizes &z, in
     return LOR_OK;  // large levels: R is written by dc3_level once it knows how to continue
 }
 
+// ---- Step 1 at level 0 for DNA texts: 16-symbol keys at 2 bits a symbol
+// (dc3_packed.cuh): a counting pre-pass over the text, one partition pass
+// that makes the keys as it goes, three stable passes on (u32, u32) pairs,
+// the exception windows put in order, naming.  When the text has more
+// exception windows than the fix-up can order, *used stays false and nothing
+// a later route reads has been changed.
+int sample_packed_sort_and_name(Dc3Run &D, const uint8_t *s, const LevelSizes &z, int64_t maxc, int32_t *Rl,
+                                int32_t *SAR, int32_t *NSl, bool *used) {
+    cudaStream_t st = D.s;
+    *used = false;
+    const int64_t m = z.n02;
+    const uint32_t mc = uint32_t(maxc), lo = maxc > 4 ? uint32_t(maxc - 3) : 1u;
+    uint32_t *exc_list = D.t32[4];  // at most m entries are written
+    LOR_CUDA_TRY(cudaMemsetAsync(D.rs.hist, 0, sizeof(uint32_t) * kPkHistWords, st));
+    {
+        ProfScope ps(PK_SAMPLE_KEYS, double(z.n), st);
+        const dim3 grid(unsigned(cdiv(max64(z.n0, z.n2), kPkTile)), 2);
+        k_pk_count<<<grid, kPkThreads, 0, st>>>(s, z.n, z.n0, z.n2, mc, lo, D.rs.hist, exc_list, D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    k_pk_offsets<<<1, kRadix, 0, st>>>(D.rs.hist, D.rs.offsets);
+    LOR_LAUNCH_CHECK();
+    uint32_t hh[kPkHistWords];
+    LOR_CUDA_TRY(cudaMemcpyAsync(hh, D.rs.hist, sizeof(hh), cudaMemcpyDeviceToHost, st));
+    LOR_CUDA_TRY(cudaStreamSynchronize(st));
+    const uint32_t nexc = hh[kPkExcCount];
+    if (nexc > uint32_t(kPkExcMax)) return LOR_OK;
+    *used = true;
+    uint32_t *k0 = D.t32[0], *v0 = D.t32[1], *k1 = D.t32[2], *v1 = D.t32[3];
+    {
+        ProfScope ps(PK_RADIX_PASS, double(z.n) + double(m) * 8, st);
+        const size_t smem = sizeof(PkPartSmem);
+        LOR_CUDA_TRY(cudaFuncSetAttribute(k_pk_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        const int64_t ntiles = cdiv(z.n0, kPkTile) + cdiv(z.n2, kPkTile);
+        const unsigned grid = unsigned(min64(ntiles, sort_grid_cap()));
+        k_pk_partition<<<grid, kPkThreads, smem, st>>>(s, z.n, z.n0, z.n2, mc, lo, k0, v0, D.rs.offsets + kPkHist0,
+                                                      D.status);
+    }
+    LOR_LAUNCH_CHECK();
+    uint32_t *kr, *vr;
+    int rc = radix_passes<uint32_t, 16>(D.rs, k0, v0, k1, v1, m, 8, 32, 8, 3, hh, true, nullptr, &kr, &vr, false);
+    if (rc) return rc;
+    if (nexc > 0) {
+        ProfScope ps(PK_NAMING, double(nexc) * 48, st);
+        const size_t smem = sizeof(PkFixSmem);
+        LOR_CUDA_TRY(cudaFuncSetAttribute(k_pk_fixup, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        k_pk_fixup<<<1, 1024, smem, st>>>(s, z.n, z.n0, mc, lo, D.rs.hist, exc_list, kr, vr, m, D.status);
+        LOR_LAUNCH_CHECK();
+    }
+    {
+        ProfScope ps(PK_NAMING, double(m) * 16, st);
+        // the unresolved list goes to t32[5], which the rank scatter leaves alone
+        LOR_PTILE_LAUNCH(D, m, k_pk_name, kr, vr, m, s, z.n, z.n0, mc, bucket_names(D, z) ? nullptr : Rl, SAR, NSl,
+                         D.d_names, D.t32[5], D.d_count, D.rs.lookback,
+                         D.rs.lookback + cdiv(m, kScanTile), D.rs.tile_ctr, D.rs.tile_base, D.rs.epoch, D.status);
+    }
+    return LOR_OK;  // large levels: R is written by dc3_level once it knows how to continue
+}
+
 // ---- Step 1, strategy "dense": names from a table of present keys.
 template <typename CharT>
 int sample_dense_names(Dc3Run &D, int lvl, const CharT *s, const LevelSizes &z, int kchars, int64_t T,
@@ -1910,11 +1970,36 @@ thread_local std::vector<TraceExtra> g_trace_extra;
 // samples in name order in SAR with their names in NSl) by prefix doubling;
 // leaves SA_R in SAR and rank(R-suffix) in Rl, like a returned recursion
 // followed by the rank scatter.  *U0 receives the initial unresolved count.
+// When ul_ready is set (D.t32[5]) the naming kernel has already listed the
+// unresolved positions there, with their count in D.d_count.  Level 0 passes
+// its text (T0 != nullptr; names are the first kchars symbols of each
+// sample): the groups of two are then settled on the text first.
+struct Level0Text {
+    const uint8_t *s = nullptr;
+    int64_t n = 0, n0 = 0;
+    uint32_t maxc = 0;
+    int kchars = 0;
+};
+
+// Entries of the unresolved list whose group still holds more than one.
+__global__ void __launch_bounds__(kScanThreads) k_dbl_keep(
+    const uint32_t *__restrict__ keep, const uint32_t *__restrict__ ul, int64_t U, uint32_t *__restrict__ ul2,
+    uint32_t *count, uint64_t *lb, unsigned long long *ctr, unsigned long long tile_base, uint32_t epoch,
+    int *status, int64_t ntiles) {
+    tile_compact(
+        U, [&](int64_t i) { return keep[i] != 0; }, [&](int64_t i, uint32_t d) { ul2[d] = ul[i]; }, lb, ctr,
+        tile_base, epoch, status, count, ntiles);
+}
+
 int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_t *NSl, bool r_unwritten,
-                   int64_t *U0) {
+                   int64_t *U0, bool ul_ready = false, const Level0Text *T0 = nullptr) {
     cudaStream_t st = D.s;
     int32_t *headof = (int32_t *)D.t32[0];
     uint32_t *ul = D.t32[1], *ul2 = D.t32[2], *runid = D.t32[3], *val = D.t32[4], *rstart = D.t32[5];
+    if (ul_ready) {
+        ul = D.t32[5];
+        rstart = D.t32[1];
+    }
     uint32_t *valt = D.t32[0];  // headof is dead once the ranks are initialised
     uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
     if (r_unwritten) {
@@ -1934,7 +2019,7 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
         k_dbl_init<<<grid_for(m, 256), 256, 0, st>>>(Rl, m, headof);
         LOR_LAUNCH_CHECK();
     }
-    {
+    if (!ul_ready) {
         ProfScope ps(PK_NAMING, double(m) * 8, st);
         const int64_t ntiles = cdiv(m, kScanTile);
         LOR_PTILE_LAUNCH(D, m, k_dbl_unresolved, NSl, m, ul, D.d_count, LB_ARGS(D), ntiles);
@@ -1942,7 +2027,33 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
     uint32_t hU = 0;
     int rc = read_u32(D, D.d_count, &hU);
     if (rc) return rc;
-    if (r_unwritten && hU > 0) {
+    *U0 = hU;
+    if (T0 && hU > 0) {
+        // groups of two settled on the text; larger groups take their head's
+        // rank (large levels) and stay
+        const unsigned g = unsigned(min64(cdiv(hU, 256), 152 * 8));
+        if (r_unwritten) {
+            ProfScope ps(PK_NAMING, double(hU) * 12, st);
+            k_dbl_group_heads<<<g, 256, 0, st>>>(ul, D.d_count, NSl, headof);
+            LOR_LAUNCH_CHECK();
+        }
+        {
+            ProfScope ps(PK_NAMING, double(hU) * (8 + 16 + 4), st);
+            k_dbl_text_pairs<<<g, 256, 0, st>>>(ul, int64_t(hU), NSl, SAR, Rl, r_unwritten ? headof : nullptr, T0->s,
+                                                T0->n, T0->n0, T0->maxc, T0->kchars, runid);
+            LOR_LAUNCH_CHECK();
+        }
+        {
+            ProfScope ps(PK_NAMING, double(hU) * 8, st);
+            const int64_t ntiles = cdiv(hU, kScanTile);
+            LOR_TILE_LAUNCH(D, hU, k_dbl_keep, runid, ul, int64_t(hU), ul2, D.d_count, LB_ARGS(D), ntiles);
+        }
+        rc = read_u32(D, D.d_count, &hU);
+        if (rc) return rc;
+        uint32_t *t = ul;
+        ul = ul2;
+        ul2 = t;
+    } else if (r_unwritten && hU > 0) {
         ProfScope ps(PK_NAMING, double(hU) * 24, st);
         const unsigned g = unsigned(min64(cdiv(hU, 256), 152 * 8));
         k_dbl_group_heads<<<g, 256, 0, st>>>(ul, D.d_count, NSl, headof);
@@ -1950,7 +2061,6 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
         k_dbl_group_ranks<<<g, 256, 0, st>>>(ul, D.d_count, NSl, SAR, headof, Rl);
         LOR_LAUNCH_CHECK();
     }
-    *U0 = hU;
     const int shift = bit_width_u64(uint64_t(m));
     for (int64_t h = 1; hU > 0; h *= 2) {
         if (h >= m) return LOR_ERR_BAD_INPUT;  // cannot happen for a valid R
@@ -2296,7 +2406,7 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     uint64_t T = 1;
     for (int t = 0; t < kchars && T; ++t)
         T = T > ~uint64_t(0) / (uint64_t(maxc) + 1) ? 0 : T * (uint64_t(maxc) + 1);
-    const int key_bits = T ? bit_width_u64(T - 1) : kchars * bits;
+    int key_bits = T ? bit_width_u64(T - 1) : kchars * bits;
 
     LOR_CUDA_TRY(cudaMemsetAsync(Rl + z.n02, 0, sizeof(int32_t) * kPad, st));
     int rc;
@@ -2304,7 +2414,18 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     int strategy;
     int64_t dups = 0;
     bool sorted_list = true;  // SAR / NSl hold the samples in key order
-    if (PS && !D.force_lsd) {
+    bool packed = false;
+    if constexpr (sizeof(CharT) == 1) {
+        if (lvl == 0 && g_route_k0.load(std::memory_order_relaxed) == 0) {
+            rc = sample_packed_sort_and_name(D, s, z, maxc, Rl, SAR, NSl, &packed);
+            if (rc) return rc;
+        }
+    }
+    if (packed) {
+        strategy = 0;
+        key_bits = 33;
+        rc = read_u32(D, D.d_names, &names);
+    } else if (PS && !D.force_lsd) {
         strategy = 2;
         rc = sample_from_parent<CharT>(D, s, z, bits, PS, PNS, Rl, SAR, NSl, &dups);
         if (rc) return rc;
@@ -2337,7 +2458,17 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
     }
     if (doubling) {
         int64_t u0 = 0;
-        rc = sa_by_doubling(D, Rl, z.n02, SAR, NSl, r_unwritten, &u0);
+        Level0Text T0;
+        if constexpr (sizeof(CharT) == 1) {
+            if (lvl == 0) {
+                T0.s = s;
+                T0.n = z.n;
+                T0.n0 = z.n0;
+                T0.maxc = uint32_t(maxc);
+                T0.kchars = packed ? kPkChars : kchars;
+            }
+        }
+        rc = sa_by_doubling(D, Rl, z.n02, SAR, NSl, r_unwritten, &u0, packed, T0.s ? &T0 : nullptr);
         if (rc) return rc;
         g_trace.push_back(TraceRow{z.n02, z.n02, 0});
         g_trace_extra.push_back(TraceExtra{3, u0});
@@ -2447,7 +2578,7 @@ int lor::build_sa_impl(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t 
 }
 
 extern "C" int lor_dc3_route_set(int32_t level0_symbols, int32_t strategy, int32_t doubling) {
-    if (level0_symbols < 0 || level0_symbols > kKeyMaxChars || (level0_symbols > 0 && level0_symbols < 3) ||
+    if (level0_symbols < 0 || level0_symbols > kKeyMaxChars || level0_symbols == 2 ||
         strategy < 0 || strategy > 1 || doubling < 0 || doubling > 2)
         return LOR_ERR_INVALID_ARG;
     g_route_k0.store(level0_symbols);

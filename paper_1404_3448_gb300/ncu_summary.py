@@ -44,6 +44,8 @@ KINDS = [
     ("k_sa64_settle", "rank_scatter"), ("k_narrow_sa64", "isa_scatter"),
     ("k_rmq_query", "rmq_query"), ("k_rmqb_query", "rmq_query"), ("k_rmq_", "rmq_level"),
     ("k_rmqb_", "rmq_level"),
+    ("k_pk_count", "sample_keys"), ("k_pk_offsets", "radix_hist"), ("k_pk_partition", "radix_pass"),
+    ("k_pk_fixup", "naming"), ("k_pk_name", "naming"),
 ]
 
 

@@ -252,6 +252,47 @@ def test_wide_triples_two_stage_sort(L, O, route):
     assert_full_parity(O, g, e, table=False)
 
 
+# ------------------------------------------------------------------ level-0 key forms
+
+def _raw_text_case(case, rng):
+    """Raw code texts (no separators; the padding past the end is the only
+    implicit smallest symbol) that reach the level-0 key forms."""
+    if case == "dna_few_low_codes":
+        # the four largest codes of sigma 21 plus a repeated motif holding the
+        # low code 3 twice, so that several exception windows are equal
+        t = rng.integers(17, 21, 200_000).astype(np.uint8)
+        motif = np.array([18, 19, 3, 20, 17, 3, 3, 18, 18, 20, 17, 19, 20, 20, 17, 18, 19, 20], np.uint8)
+        for pos in rng.choice(t.size - 64, 120, replace=False):
+            t[pos:pos + motif.size] = motif
+        t[rng.choice(t.size, 40, replace=False)] = rng.integers(1, 17, 40)
+        return t, 21
+    if case == "many_low_codes":  # exception windows everywhere: base-sigma keys
+        return rng.integers(1, 21, 150_000).astype(np.uint8), 21
+    if case == "two_codes":  # sigma 3: both codes take 2-bit values
+        return rng.integers(1, 3, 100_000).astype(np.uint8), 3
+    if case == "tail_run":  # a run of one symbol to the end: exception windows share keys
+        t = rng.integers(1, 5, 50_000).astype(np.uint8)
+        t[-300:] = 1
+        return t, 5
+    raise ValueError(case)
+
+
+@pytest.mark.parametrize("case", ["dna_few_low_codes", "many_low_codes", "two_codes", "tail_run"])
+@pytest.mark.parametrize("k0", [0, 1])
+def test_level0_key_forms_on_raw_codes(L, O, case, k0, route):
+    """Level 0's 2-bit keys (16 symbols, an exception bit, exception windows
+    ordered by their symbols) and the base-sigma keys give the suffix array
+    of the definition; a text with too many exception windows takes the
+    base-sigma keys."""
+    route("auto", k0)
+    t, sigma = _raw_text_case(case, np.random.default_rng(sum(map(ord, case))))
+    sa = L.build_sa(to_dev(t), sigma)
+    L.check_device()
+    np.testing.assert_array_equal(sa.cpu().numpy(), O.suffix_array(t, nthreads=NCPU))
+    two_bit = k0 == 0 and case != "many_low_codes"
+    assert (L.last_dc3_trace()[0]["key_bits"] == 33) == two_bit, L.last_dc3_trace()
+
+
 # ------------------------------------------------------------------ radix sort primitive
 
 @pytest.mark.parametrize("m,bits", [(0, 8), (1, 8), (4095, 12), (4097, 33), (100_003, 64),
