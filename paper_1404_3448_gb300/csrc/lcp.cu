@@ -1,16 +1,25 @@
 // lcp.cu -- inverse suffix array and LCP array (Section 3, LCP table; the
 // linear-time method of Kasai et al. that the paper cites).
 //
-// Kasai's observation: for text positions i and i+1, the LCP of suffix i+1
-// with its rank predecessor is at least the LCP of suffix i with its rank
-// predecessor minus one.  It is applied here in the "permuted LCP" form:
+// LCP[k] is first computed in rank order by comparing the suffixes SA[k-1]
+// and SA[k] directly on a 2-bit copy of the text (which stays in L2 for
+// DNA), up to 64 symbols; the few ranks that reach that are finished up to
+// 8192 symbols, and ISA[SA[k]] = k is one bucketed scatter.  This reads and
+// writes each array once, in sequence.
+//
+// A text of long repeats (more than n/32 ranks past 64 symbols, or an LCP
+// past 8192) takes Kasai's method instead, whose cost does not depend on the
+// LCP values.  Kasai's observation: for text positions i and i+1, the LCP of
+// suffix i+1 with its rank predecessor is at least the LCP of suffix i with
+// its rank predecessor minus one.  It is applied in the "permuted LCP" form:
 //   1. one scatter per rank k writes {ISA, PHI} = {k, SA[k-1]} at position
 //      SA[k] (one 8-byte write instead of separate ISA / predecessor lookups);
 //   2. text positions are walked in order in chunks (h carried within a
-//      chunk), comparing T[i+h..] with T[PHI[i]+h..] 32 symbols at a time on a
-//      2-bit copy of the text (which stays in L2 for DNA), and PLCP[i] and
-//      ISA[i] are written in text order;
-//   3. LCP[k] = PLCP[SA[k]] is gathered in rank order.
+//      chunk), comparing T[i+h..] with T[PHI[i]+h..] 32 symbols at a time on
+//      the 2-bit copy, and PLCP[i] and ISA[i] are written in text order;
+//   3. LCP[ISA[i]] = PLCP[i] is scattered back to rank order.
+// The choice is made on the device and read back once (one stream
+// synchronisation per call).
 #include "lcp_kernels.cuh"
 #include "radix.cuh"
 
@@ -29,6 +38,18 @@ __global__ void k_lcp_scatter_direct(const int32_t *__restrict__ isa, int64_t n,
     if (i >= n) return;
     const int32_t r = isa[i];
     if (r >= 0 && r < n) lcp[r] = plcp[i];
+}
+
+// ISA[SA[k]] = k (small texts; larger ones go through the bucketed scatter).
+__global__ void k_isa_direct(const int32_t *__restrict__ sa, int64_t n, int32_t *__restrict__ isa, int *status) {
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t p = sa[k];
+    if (p < 0 || p >= n) {
+        atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+        return;
+    }
+    isa[p] = int32_t(k);
 }
 
 struct LcpLayout {
@@ -176,9 +197,52 @@ extern "C" int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, in
     rs.max_tiles = cdiv(n, kMinSortTile);
     rs.status = status;
     rs.stream = s;
+    const PackedText T = packed_text_at(ws + L.packed, n);
+    {
+        // text read twice, 2-bit copy and exception bitmap written
+        ProfScope ps(PK_KASAI, double(n) * (2 + 0.375), s);
+        const int rc = pack_text(d_text, n, T, s);
+        if (rc) return rc;
+    }
+    // LCP in rank order by direct comparison (the long list in the PLCP
+    // buffer), then the ranks that reached the cap
+    LOR_CUDA_TRY(cudaMemsetAsync(T.ctl + kCtlLong, 0, 2 * sizeof(int), s));
+    {
+        // SA read, LCP written, two 16-symbol windows of the 2-bit copy
+        ProfScope ps(PK_KASAI, double(n) * (4 + 4 + 8), s);
+        k_lcp_direct<<<unsigned(cdiv(cdiv(n, kLcpPer), kLcpThreads)), kLcpThreads, 0, s>>>(
+            d_text, T, n, d_sa, d_lcp, reinterpret_cast<uint32_t *>(plcp), status);
+        LOR_LAUNCH_CHECK();
+    }
+    const int64_t max_long = n / 32 + 64;
+    {
+        ProfScope ps(PK_KASAI, 0.0, s);
+        k_lcp_long<<<unsigned(min64(cdiv(max_long, 256), 152 * 8)), 256, 0, s>>>(
+            d_text, T, n, d_sa, d_lcp, reinterpret_cast<const uint32_t *>(plcp), max_long);
+        LOR_LAUNCH_CHECK();
+    }
+    int fallback = 0;
+    LOR_CUDA_TRY(cudaMemcpyAsync(&fallback, T.ctl + kCtlFallback, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOR_CUDA_TRY(cudaStreamSynchronize(s));
     if (bucket) {
         LOR_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, 256, s));
         LOR_CUDA_TRY(cudaMemsetAsync(ws + L.lookback, 0, L.lookback_bytes, s));
+    }
+    if (!fallback) {
+        // ISA[SA[k]] = k
+        if (bucket) {
+            uint32_t *vb0 = reinterpret_cast<uint32_t *>(vbuf);
+            return bucketed_scatter(rs, (const uint32_t *)d_sa, nullptr, n, n, kbuf, vb0, vb0 + n, d_isa, 0,
+                                    PK_ISA_SCATTER);
+        }
+        ProfScope ps(PK_ISA_SCATTER, double(n) * 8, s);
+        k_isa_direct<<<unsigned(cdiv(n, 256)), 256, 0, s>>>(d_sa, n, d_isa, status);
+        LOR_LAUNCH_CHECK();
+        return LOR_OK;
+    }
+    // A text of long repeats: the permuted Kasai passes (cost independent of
+    // the LCP values).
+    if (bucket) {
         const int rc = bucketed_isa_phi(rs, d_sa, n, n, kbuf, vbuf, ip);
         if (rc) return rc;
     } else {
@@ -186,13 +250,6 @@ extern "C" int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, in
         ProfScope ps(PK_ISA_SCATTER, double(n) * 12, s);
         k_isa_phi<<<unsigned(cdiv(n, 256)), 256, 0, s>>>(d_sa, n, nullptr, ip, status);
         LOR_LAUNCH_CHECK();
-    }
-    const PackedText T = packed_text_at(ws + L.packed, n);
-    {
-        // text read twice, 2-bit copy and exception bitmap written
-        ProfScope ps(PK_KASAI, double(n) * (2 + 0.375), s);
-        const int rc = pack_text(d_text, n, T, s);
-        if (rc) return rc;
     }
     {
         // {ISA, PHI} read, ISA + PLCP written, two text windows per position

@@ -347,6 +347,188 @@ __global__ void __launch_bounds__(kPlcpThreads) k_plcp_packed(const uint8_t *__r
     for (int i = threadIdx.x; i < cnt; i += kPlcpThreads) st_i32_hint(plcp + base + i, s_out[chunk_slot(i)], once);
 }
 
+// ---- LCP in rank order by direct comparison
+//
+// On text without long repeats the LCP of two suffixes adjacent in the
+// suffix array is short (about log4 n symbols for uniform DNA), so comparing
+// them directly on the 2-bit copy -- which stays in L2 -- finds almost every
+// LCP[k] in one or two 16-byte reads per side, with no scatter to text order
+// and back.  k_lcp_direct compares up to kLcpCap symbols; the ranks that
+// reach the cap are listed and k_lcp_long goes on to kLcpBudget symbols.
+// When the list or a comparison outgrows those bounds (a text of long
+// repeats) the caller runs the permuted Kasai passes instead, whose cost does
+// not depend on the LCP values.
+constexpr int kLcpCap = 64;
+constexpr int kLcpBudget = 8192;
+constexpr int kLcpPer = 8;  // ranks per thread of k_lcp_direct
+constexpr int kLcpThreads = 256;
+// control words of PackedText::ctl used here: the long list's length and the
+// fallback flag
+constexpr int kCtlLong = 2, kCtlFallback = 3;
+
+// lcp(T[i..], T[j..]) given that the first h symbols match, compared up to
+// `cap` symbols (a result of cap means "at least cap").  Symbols are
+// compared 32 at a time on the 2-bit copy up to the next listed exception on
+// either side, where the bytes are compared (the listed form: at most
+// kExcCap exceptions).
+__device__ __forceinline__ int32_t lcp_listed(const uint8_t *__restrict__ t, const uint64_t *__restrict__ P,
+                                              const int32_t *__restrict__ lst, int nexc, int32_t n, int32_t i,
+                                              int32_t j, int32_t h, int32_t cap, uint64_t keep) {
+    for (;;) {
+        const int32_t a = i + h, b = j + h;
+        const int32_t lim = min(min(next_exc32(lst, nexc, a, n) - a, next_exc32(lst, nexc, b, n) - b),
+                                min(min(n - a, n - b), cap - h));
+        int32_t k = 0;
+        while (k < lim) {
+            int aa, ab;
+            const uint64_t wa = window_chunk32(P, uint32_t(a + k), aa, keep);
+            const uint64_t wb = window_chunk32(P, uint32_t(b + k), ab, keep);
+            int len = aa < ab ? aa : ab;
+            if (lim - k < len) len = lim - k;
+            uint64_t d = wa ^ wb;
+            if (len < 32) d &= (uint64_t(1) << (2 * len)) - 1;
+            if (d) return h + k + ((__ffsll((long long)d) - 1) >> 1);
+            k += len;
+        }
+        h += k;
+        if (h >= cap || i + h >= n || j + h >= n || t[i + h] != t[j + h]) return h;
+        ++h;  // equal exception codes
+    }
+}
+
+// The same on the exception bitmap (more than kExcCap exceptions).
+__device__ __forceinline__ int32_t lcp_bitmap(const uint8_t *__restrict__ t, const PackedText &T, int32_t n,
+                                              int32_t i, int32_t j, int32_t h, int32_t cap) {
+    while (h < cap && i + h + 32 <= n && j + h + 32 <= n) {
+        const uint64_t d = window2(T.P, i + h) ^ window2(T.P, j + h);
+        const uint32_t e = window_exc(T.E, i + h) | window_exc(T.E, j + h);
+        const int dpos = d ? (__ffsll((long long)d) - 1) >> 1 : 32;
+        const int epos = e ? __ffs(int(e)) - 1 : 32;
+        if (dpos < epos) return min(h + dpos, cap);
+        if (epos < 32) {
+            h += epos;
+            if (t[i + h] != t[j + h]) return min(h, cap);
+            ++h;
+        } else {
+            h += 32;
+        }
+    }
+    while (h < cap && i + h < n && j + h < n && t[i + h] == t[j + h]) ++h;
+    return min(h, cap);
+}
+
+// Symbols p .. p+31 of the 2-bit copy (one 16-byte read, or two when p lies
+// in the second half of its chunk).
+__device__ __forceinline__ uint64_t window32(const uint64_t *__restrict__ P, uint32_t p, uint64_t keep) {
+    const ulonglong2 v = ld_u64x2_hint(reinterpret_cast<const ulonglong2 *>(P) + (p >> 6), keep);
+    const uint32_t off = p & 63u;
+    if (off < 32) return off ? (v.x >> (2 * off)) | (v.y << (64 - 2 * off)) : v.x;
+    if (off == 32) return v.y;
+    const ulonglong2 u = ld_u64x2_hint(reinterpret_cast<const ulonglong2 *>(P) + (p >> 6) + 1, keep);
+    return (v.y >> (2 * (off - 32))) | (u.x << (64 - 2 * (off - 32)));
+}
+
+__device__ __forceinline__ int32_t ld_i32_stream(const int32_t *p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// LCP[k] up to kLcpCap for kLcpPer ranks a thread (a block's ranks are
+// kLcpPer * kLcpThreads consecutive ones, a thread's kLcpThreads apart, so
+// that every load and store is coalesced); ranks that reach the cap are
+// appended to `longl` (their LCP is finished by k_lcp_long).  LCP[0] = 0.
+// The 32 symbols at SA[k] are read once by the lane of rank k and passed to
+// the lane of rank k + 1, whose predecessor they are; a comparison that
+// needs more (an exception within 32 symbols, or 32 equal symbols) goes on
+// with lcp_listed.  An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT and
+// gives LCP 0 at the ranks that read it.
+__global__ void __launch_bounds__(kLcpThreads) k_lcp_direct(const uint8_t *__restrict__ t, PackedText T, int64_t n,
+                                                            const int32_t *__restrict__ sa, int32_t *__restrict__ lcp,
+                                                            uint32_t *__restrict__ longl, int *status) {
+    __shared__ int32_t s_exc[kExcShared];
+    const int nexc = T.ctl[1];
+    const bool listed = nexc <= kExcCap;
+    const int32_t *lst = nexc <= kExcShared ? s_exc : T.list;
+    if (nexc <= kExcShared)
+        for (int i = threadIdx.x; i < nexc; i += kLcpThreads) s_exc[i] = T.list[i];
+    __syncthreads();
+    const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
+    const int32_t n32 = int32_t(n);
+    const int lane = threadIdx.x & 31;
+    const int64_t base = int64_t(blockIdx.x) * (kLcpThreads * kLcpPer) + threadIdx.x;
+    bool bad = false;
+    for (int q = 0; q < kLcpPer; ++q) {
+        const int64_t k = base + int64_t(q) * kLcpThreads;
+        if (k - lane >= n) break;  // warp-uniform: the warp's first rank is past the end
+        const bool in = k < n;
+        const int32_t i = in ? ld_i32_stream(sa + k, once) : -1;
+        const int32_t i_ok = i >= 0 && i < n32;
+        // this lane's window, and the predecessor's from the lane before
+        const uint64_t wi = (in && i_ok) ? window32(T.P, uint32_t(i), keep) : 0;
+        uint64_t wj = __shfl_up_sync(0xffffffffu, wi, 1);
+        int32_t j = __shfl_up_sync(0xffffffffu, i, 1);
+        if (lane == 0 && in) {
+            j = k > 0 ? sa[k - 1] : -1;
+            wj = (j >= 0 && j < n32) ? window32(T.P, uint32_t(j), keep) : 0;
+        }
+        if (!in) continue;
+        int32_t h = 0;
+        if (k > 0) {
+            if (!i_ok || j < 0 || j >= n32) {
+                bad = true;
+            } else {
+                // the windows decide when they differ before an exception on
+                // either side (the bitmap form checks its exceptions itself)
+                uint64_t d = 0;
+                int32_t lim = 0;
+                if (listed) {
+                    lim = min(min(min(n32 - i, n32 - j), 32),
+                              min(next_exc32(lst, nexc, i, n32) - i, next_exc32(lst, nexc, j, n32) - j));
+                    d = wi ^ wj;
+                    if (lim < 32) d &= (uint64_t(1) << (2 * lim)) - 1;
+                }
+                if (d) {
+                    h = (__ffsll((long long)d) - 1) >> 1;
+                } else {
+                    h = listed ? lcp_listed(t, T.P, lst, nexc, n32, i, j, lim, kLcpCap, keep)
+                               : lcp_bitmap(t, T, n32, i, j, 0, kLcpCap);
+                    if (h >= kLcpCap) {
+                        const uint32_t slot = atomicAdd(reinterpret_cast<unsigned *>(&T.ctl[kCtlLong]), 1u);
+                        if (slot < uint32_t(n)) longl[slot] = uint32_t(k);
+                    }
+                }
+            }
+        }
+        st_i32_hint(lcp + k, h, once);
+    }
+    if (bad) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
+}
+
+// The listed ranks' LCP from kLcpCap on, up to kLcpBudget symbols.  More
+// listed ranks than `max_long`, or a comparison that reaches the budget,
+// sets the fallback flag (and leaves LCP to the Kasai passes).
+__global__ void k_lcp_long(const uint8_t *__restrict__ t, PackedText T, int64_t n, const int32_t *__restrict__ sa,
+                           int32_t *__restrict__ lcp, const uint32_t *__restrict__ longl, int64_t max_long) {
+    const int64_t cnt = int64_t(uint32_t(T.ctl[kCtlLong]));
+    if (cnt > max_long) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) T.ctl[kCtlFallback] = 1;
+        return;
+    }
+    const int nexc = T.ctl[1];
+    const bool listed = nexc <= kExcCap;
+    const uint64_t keep = l2_policy_evict_last();
+    const int32_t n32 = int32_t(n);
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < cnt; e += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t k = longl[e];
+        const int32_t i = sa[k], j = sa[k - 1];  // both checked by k_lcp_direct
+        const int32_t h = listed ? lcp_listed(t, T.P, T.list, nexc, n32, i, j, kLcpCap, kLcpBudget, keep)
+                                 : lcp_bitmap(t, T, n32, i, j, kLcpCap, kLcpBudget);
+        if (h >= kLcpBudget) T.ctl[kCtlFallback] = 1;
+        else lcp[k] = h;
+    }
+}
+
 // LCP[k] = PLCP[SA[k]] (a position without predecessor has PLCP 0).
 __global__ void k_lcp_gather(const int32_t *__restrict__ sa, int64_t n, const int32_t *__restrict__ plcp,
                              int32_t *__restrict__ lcp) {

@@ -968,7 +968,7 @@ int partition_pass(RadixScratch &rs, const uint32_t *keys, const ValT *vals, int
 
 inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32_t *vals, int64_t m,
                             int64_t bound, uint32_t *kbuf, uint32_t *vbuf0, uint32_t *vbuf1,
-                            int32_t *dst, int32_t add) {
+                            int32_t *dst, int32_t add, int kind = PK_RANK_SCATTER) {
     (void)vbuf1;
     if (m <= 0) return LOR_OK;
     const int top = bit_width_u64(uint64_t(bound > 1 ? bound - 1 : 1));
@@ -977,7 +977,7 @@ inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32
                         : partition_pass<uint32_t, VM_IOTA>(rs, keys, nullptr, m, lo, top, kbuf, vbuf0, m == bound);
     if (rc) return rc;
     {
-        ProfScope ps(PK_RANK_SCATTER, double(m) * 12, rs.stream);
+        ProfScope ps(kind, double(m) * 12, rs.stream);
         k_scatter_pairs<<<unsigned(cdiv(cdiv(m, 4), 256)), 256, 0, rs.stream>>>(kbuf, vbuf0, m, dst, add, bound,
                                                                       rs.status);
     }

@@ -36,7 +36,7 @@ KINDS = [
     ("k_par_ns_", "nonsample"), ("k_perm_offsets", "radix_hist"),
     ("k_gather_pri", "nonsample"), ("k_par_dup_writeback", "nonsample"),
     ("k_group_records", "merge"), ("k_merge", "merge"),
-    ("k_isa_phi", "isa_scatter"), ("k_scatter_isa_phi", "isa_scatter"),
+    ("k_isa_phi", "isa_scatter"), ("k_scatter_isa_phi", "isa_scatter"), ("k_isa_direct", "isa_scatter"),
     ("k_text_max", "kasai"), ("k_pack_text", "kasai"), ("k_sort_exc", "kasai"), ("k_plcp", "kasai"),
     ("k_lcp_", "kasai"),
     ("k_ov_argmax", "overlap_scan"), ("k_ov_", "overlap_collect"), ("k_copy_u32", "overlap_collect"),

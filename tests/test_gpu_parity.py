@@ -286,11 +286,51 @@ def test_level0_key_forms_on_raw_codes(L, O, case, k0, route):
     base-sigma keys."""
     route("auto", k0)
     t, sigma = _raw_text_case(case, np.random.default_rng(sum(map(ord, case))))
-    sa = L.build_sa(to_dev(t), sigma)
+    text = to_dev(t)
+    sa = L.build_sa(text, sigma)
     L.check_device()
-    np.testing.assert_array_equal(sa.cpu().numpy(), O.suffix_array(t, nthreads=NCPU))
+    sa_np = sa.cpu().numpy()
+    np.testing.assert_array_equal(sa_np, O.suffix_array(t, nthreads=NCPU))
+    if k0 == 0:  # the LCP of these texts: exceptions listed, or (many low codes) in the bitmap
+        isa, lcp = L.lcp(text, sa)
+        L.check_device()
+        np.testing.assert_array_equal(lcp.cpu().numpy(), O.lcp_array(t, sa_np, nthreads=NCPU))
+        np.testing.assert_array_equal(isa.cpu().numpy()[sa_np], np.arange(t.size, dtype=np.int32))
     two_bit = k0 == 0 and case != "many_low_codes"
     assert (L.last_dc3_trace()[0]["key_bits"] == 33) == two_bit, L.last_dc3_trace()
+
+
+# ------------------------------------------------------------------ LCP routes
+
+def _repeat_case(case, rng):
+    """Two random sequences with one shared stretch: LCPs past 64 symbols at
+    about 2 * length ranks, the longest about `length`."""
+    length = {"no_repeat": 0, "repeat_5k": 5_000, "repeat_12k": 12_000, "repeat_many": 300_000}[case]
+    a = rng.integers(0, 4, 1_200_000)
+    b = rng.integers(0, 4, 1_000_000)
+    if length:
+        core = rng.integers(0, 4, length)
+        a[100_000:100_000 + length] = core
+        b[400_000:400_000 + length] = core
+    alpha = np.frombuffer(b"ACGT", np.uint8)
+    return [alpha[a], alpha[b]]
+
+
+@pytest.mark.parametrize("case", ["no_repeat", "repeat_5k", "repeat_12k", "repeat_many"])
+def test_lcp_direct_comparison_and_kasai_routes(L, O, case):
+    """LCP in rank order by direct comparison (capped, with the long ranks
+    finished separately) and, for a repeat past the comparison budget or too
+    many long ranks, Kasai's method: both equal to the oracle's LCP by direct
+    comparison, and ISA the inverse of SA."""
+    seqs = _repeat_case(case, np.random.default_rng(sum(map(ord, case))))
+    lens = [len(s) for s in seqs]
+    text, _, sigma = L.encode_concat(to_dev(np.concatenate(seqs)), lens)
+    sa = L.build_sa(text, sigma)
+    isa, lcp = L.lcp(text, sa)
+    L.check_device()
+    t_np, sa_np = text.cpu().numpy(), sa.cpu().numpy()
+    np.testing.assert_array_equal(lcp.cpu().numpy(), O.lcp_array(t_np, sa_np, nthreads=NCPU))
+    np.testing.assert_array_equal(isa.cpu().numpy()[sa_np], np.arange(t_np.size, dtype=np.int32))
 
 
 # ------------------------------------------------------------------ radix sort primitive
