@@ -210,7 +210,7 @@ extern "C" int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, in
     {
         // SA read, LCP written, two 16-symbol windows of the 2-bit copy
         ProfScope ps(PK_KASAI, double(n) * (4 + 4 + 8), s);
-        k_lcp_direct<<<unsigned(cdiv(cdiv(n, kLcpPer), kLcpThreads)), kLcpThreads, 0, s>>>(
+        k_lcp_direct<<<unsigned(min64(cdiv(cdiv(n, kLcpPer), kLcpThreads), 152 * 8)), kLcpThreads, 0, s>>>(
             d_text, T, n, d_sa, d_lcp, reinterpret_cast<uint32_t *>(plcp), status);
         LOR_LAUNCH_CHECK();
     }

@@ -434,73 +434,97 @@ __device__ __forceinline__ int32_t ld_i32_stream(const int32_t *p, uint64_t pol)
     return v;
 }
 
-// LCP[k] up to kLcpCap for kLcpPer ranks a thread (a block's ranks are
-// kLcpPer * kLcpThreads consecutive ones, a thread's kLcpThreads apart, so
-// that every load and store is coalesced); ranks that reach the cap are
-// appended to `longl` (their LCP is finished by k_lcp_long).  LCP[0] = 0.
-// The 32 symbols at SA[k] are read once by the lane of rank k and passed to
-// the lane of rank k + 1, whose predecessor they are; a comparison that
-// needs more (an exception within 32 symbols, or 32 equal symbols) goes on
-// with lcp_listed.  An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT and
-// gives LCP 0 at the ranks that read it.
+// First listed exception at or after p: the bucket table gives it directly
+// unless an exception lies in p's bucket before p (then the list is
+// searched).  ne[b] = first exception at or after b << sh.
+__device__ __forceinline__ int32_t next_exc_tab(const int32_t *__restrict__ ne, int sh, const int32_t *__restrict__ lst,
+                                                int nexc, int32_t p, int32_t n) {
+    const int32_t e = ne[p >> sh];
+    return e >= p ? e : next_exc32(lst, nexc, p, n);
+}
+
+constexpr int kLcpBuckets = 256;
+
+// LCP[k] up to kLcpCap, tiles of kLcpPer * kLcpThreads consecutive ranks,
+// kLcpPer a thread kLcpThreads apart (every load and store coalesced); a
+// resident grid walks the tiles.  Ranks that reach the cap are appended to
+// `longl` (their LCP is finished by k_lcp_long).  LCP[0] = 0.  The 32
+// symbols at SA[k] are read once by the lane of rank k and passed to the
+// lane of rank k + 1, whose predecessor they are; a comparison that needs
+// more (an exception within 32 symbols, or 32 equal symbols) goes on with
+// lcp_listed.  An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT and gives
+// LCP 0 at the ranks that read it.
 __global__ void __launch_bounds__(kLcpThreads) k_lcp_direct(const uint8_t *__restrict__ t, PackedText T, int64_t n,
                                                             const int32_t *__restrict__ sa, int32_t *__restrict__ lcp,
                                                             uint32_t *__restrict__ longl, int *status) {
     __shared__ int32_t s_exc[kExcShared];
+    __shared__ int32_t s_ne[kLcpBuckets];
     const int nexc = T.ctl[1];
     const bool listed = nexc <= kExcCap;
     const int32_t *lst = nexc <= kExcShared ? s_exc : T.list;
     if (nexc <= kExcShared)
         for (int i = threadIdx.x; i < nexc; i += kLcpThreads) s_exc[i] = T.list[i];
+    const int32_t n32 = int32_t(n);
+    int sh = 0;
+    while ((int64_t(kLcpBuckets) << sh) < n) ++sh;
+    __syncthreads();
+    if (listed)
+        for (int b = threadIdx.x; b < kLcpBuckets; b += kLcpThreads) {
+            const int64_t p = int64_t(b) << sh;
+            s_ne[b] = p < n ? next_exc32(lst, nexc, int32_t(p), n32) : n32;
+        }
     __syncthreads();
     const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
-    const int32_t n32 = int32_t(n);
     const int lane = threadIdx.x & 31;
-    const int64_t base = int64_t(blockIdx.x) * (kLcpThreads * kLcpPer) + threadIdx.x;
+    const int64_t ntiles = cdiv(n, int64_t(kLcpThreads) * kLcpPer);
     bool bad = false;
-    for (int q = 0; q < kLcpPer; ++q) {
-        const int64_t k = base + int64_t(q) * kLcpThreads;
-        if (k - lane >= n) break;  // warp-uniform: the warp's first rank is past the end
-        const bool in = k < n;
-        const int32_t i = in ? ld_i32_stream(sa + k, once) : -1;
-        const int32_t i_ok = i >= 0 && i < n32;
-        // this lane's window, and the predecessor's from the lane before
-        const uint64_t wi = (in && i_ok) ? window32(T.P, uint32_t(i), keep) : 0;
-        uint64_t wj = __shfl_up_sync(0xffffffffu, wi, 1);
-        int32_t j = __shfl_up_sync(0xffffffffu, i, 1);
-        if (lane == 0 && in) {
-            j = k > 0 ? sa[k - 1] : -1;
-            wj = (j >= 0 && j < n32) ? window32(T.P, uint32_t(j), keep) : 0;
-        }
-        if (!in) continue;
-        int32_t h = 0;
-        if (k > 0) {
-            if (!i_ok || j < 0 || j >= n32) {
-                bad = true;
-            } else {
-                // the windows decide when they differ before an exception on
-                // either side (the bitmap form checks its exceptions itself)
-                uint64_t d = 0;
-                int32_t lim = 0;
-                if (listed) {
-                    lim = min(min(min(n32 - i, n32 - j), 32),
-                              min(next_exc32(lst, nexc, i, n32) - i, next_exc32(lst, nexc, j, n32) - j));
-                    d = wi ^ wj;
-                    if (lim < 32) d &= (uint64_t(1) << (2 * lim)) - 1;
-                }
-                if (d) {
-                    h = (__ffsll((long long)d) - 1) >> 1;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * (kLcpThreads * kLcpPer) + threadIdx.x;
+        for (int q = 0; q < kLcpPer; ++q) {
+            const int64_t k = base + int64_t(q) * kLcpThreads;
+            if (k - lane >= n) break;  // warp-uniform: the warp's first rank is past the end
+            const bool in = k < n;
+            const int32_t i = in ? ld_i32_stream(sa + k, once) : -1;
+            const int32_t i_ok = i >= 0 && i < n32;
+            // this lane's window, and the predecessor's from the lane before
+            const uint64_t wi = (in && i_ok) ? window32(T.P, uint32_t(i), keep) : 0;
+            uint64_t wj = __shfl_up_sync(0xffffffffu, wi, 1);
+            int32_t j = __shfl_up_sync(0xffffffffu, i, 1);
+            if (lane == 0 && in) {
+                j = k > 0 ? sa[k - 1] : -1;
+                wj = (j >= 0 && j < n32) ? window32(T.P, uint32_t(j), keep) : 0;
+            }
+            if (!in) continue;
+            int32_t h = 0;
+            if (k > 0) {
+                if (!i_ok || j < 0 || j >= n32) {
+                    bad = true;
                 } else {
-                    h = listed ? lcp_listed(t, T.P, lst, nexc, n32, i, j, lim, kLcpCap, keep)
-                               : lcp_bitmap(t, T, n32, i, j, 0, kLcpCap);
-                    if (h >= kLcpCap) {
-                        const uint32_t slot = atomicAdd(reinterpret_cast<unsigned *>(&T.ctl[kCtlLong]), 1u);
-                        if (slot < uint32_t(n)) longl[slot] = uint32_t(k);
+                    // the windows decide when they differ before an exception on
+                    // either side (the bitmap form checks its exceptions itself)
+                    uint64_t d = 0;
+                    int32_t lim = 0;
+                    if (listed) {
+                        lim = min(min(min(n32 - i, n32 - j), 32),
+                                  min(next_exc_tab(s_ne, sh, lst, nexc, i, n32) - i,
+                                      next_exc_tab(s_ne, sh, lst, nexc, j, n32) - j));
+                        d = wi ^ wj;
+                        if (lim < 32) d &= (uint64_t(1) << (2 * lim)) - 1;
+                    }
+                    if (d) {
+                        h = (__ffsll((long long)d) - 1) >> 1;
+                    } else {
+                        h = listed ? lcp_listed(t, T.P, lst, nexc, n32, i, j, lim, kLcpCap, keep)
+                                   : lcp_bitmap(t, T, n32, i, j, 0, kLcpCap);
+                        if (h >= kLcpCap) {
+                            const uint32_t slot = atomicAdd(reinterpret_cast<unsigned *>(&T.ctl[kCtlLong]), 1u);
+                            if (slot < uint32_t(n)) longl[slot] = uint32_t(k);
+                        }
                     }
                 }
             }
+            st_i32_hint(lcp + k, h, once);
         }
-        st_i32_hint(lcp + k, h, once);
     }
     if (bad) atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
 }
