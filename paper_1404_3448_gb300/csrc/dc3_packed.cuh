@@ -441,14 +441,35 @@ __device__ __forceinline__ bool pk_windows_equal(const uint8_t *__restrict__ s, 
     return true;
 }
 
+// The 16 bytes from p as four big-endian words, read as five aligned
+// 32-bit words (p + 20 <= n and s 4-byte aligned).
+__device__ __forceinline__ void pk_load16_be(const uint8_t *__restrict__ s, int64_t p, uint32_t (&o)[4]) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(s + (p & ~int64_t(3)));
+    const uint32_t r = uint32_t(p & 3);
+    uint32_t x[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) x[c] = w[c];
+    // result byte 3 (most significant) = source byte r, ..., byte 0 = r + 3
+    const uint32_t sel = (r + 3) | ((r + 2) << 4) | ((r + 1) << 8) | (r << 12);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[c] = __byte_perm(x[c], x[c + 1], sel);
+}
+
 // Order of the 16 symbols from p and from q (clamped codes, 0 past the
-// end): -1, 0 or 1.  All 32 bytes are loaded before any is compared.
+// end): -1, 0 or 1.  All 32 bytes are loaded before any is compared.  Away
+// from the end of the text the raw bytes are compared (they differ from the
+// clamped codes only at bad symbols, which are reported anyway).
 __device__ __forceinline__ int pk_cmp16(const uint8_t *__restrict__ s, int64_t n, int64_t p, int64_t q, uint32_t maxc) {
     uint32_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+    if (((uintptr_t)s & 3) == 0 && p + 20 <= n && q + 20 <= n) {
+        pk_load16_be(s, p, a);
+        pk_load16_be(s, q, b);
+    } else {
 #pragma unroll
-    for (int t = 0; t < kPkChars; ++t) {
-        a[t >> 2] = (a[t >> 2] << 8) | pk_code(s, n, p + t, maxc);
-        b[t >> 2] = (b[t >> 2] << 8) | pk_code(s, n, q + t, maxc);
+        for (int t = 0; t < kPkChars; ++t) {
+            a[t >> 2] = (a[t >> 2] << 8) | pk_code(s, n, p + t, maxc);
+            b[t >> 2] = (b[t >> 2] << 8) | pk_code(s, n, q + t, maxc);
+        }
     }
 #pragma unroll
     for (int w = 0; w < 4; ++w)

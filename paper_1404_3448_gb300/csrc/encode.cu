@@ -13,6 +13,7 @@ namespace {
 
 struct EncParams {
     int32_t nseq;
+    int64_t n_ascii;  // bytes of the ASCII input (the sum of the lengths)
     int64_t out_start[LOR_MAX_SEQ + 1];  // start of sequence i in the text; [nseq] = n
 };
 
@@ -53,6 +54,40 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint8_t *__restric
     // write when the run is whole and aligned (byte stores from lanes 16
     // bytes apart would each touch a separate sector).
     uint32_t w[kEncItems / 4] = {0, 0, 0, 0};
+    // A run inside one sequence's bases reads its 16 source bytes with two
+    // aligned 16-byte loads (the source is offset by the terminators before
+    // it) and picks them out with byte permutes.
+    const int64_t src = o0 - sq, a0 = src & ~int64_t(15);
+    if (o0 + kEncItems < so[sq + 1] && ((uintptr_t)ascii & 15) == 0 && a0 + 32 <= P.n_ascii) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(ascii + a0);
+        const uint4 v = *reinterpret_cast<const uint4 *>(ascii + a0 + 16);
+        const uint32_t x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+        const int r = int(src - a0);  // bytes to skip, 0..15
+#pragma unroll
+        for (int c = 0; c < kEncItems / 4; ++c) {
+            // the four source bytes r + 4c .. r + 4c + 3 of the 32 loaded
+            const int b = r + 4 * c, wi = b >> 2, sh = b & 3;
+            uint32_t lo4 = x[0], hi4 = x[1];
+#pragma unroll
+            for (int q = 1; q < 7; ++q)
+                if (wi == q) {
+                    lo4 = x[q];
+                    hi4 = x[q + 1];
+                }
+            const uint32_t bytes = __byte_perm(lo4, hi4, uint32_t(0x3210 + 0x1111 * sh));
+            uint32_t out = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                uint32_t code = lut[(bytes >> (8 * e)) & 0xFFu];
+                if (code == 0) {
+                    bad = true;
+                    code = uint32_t(nseq + 1);
+                }
+                out |= code << (8 * e);
+            }
+            w[c] = out;
+        }
+    } else {
 #pragma unroll
     for (int k = 0; k < kEncItems; ++k) {
         const int64_t o = o0 + k;
@@ -70,6 +105,7 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint8_t *__restric
             }
         }
         w[k >> 2] |= v << (8 * (k & 3));
+    }
     }
     if (o0 + kEncItems <= n && ((uintptr_t(text + o0) & 15) == 0)) {
         *reinterpret_cast<uint4 *>(text + o0) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -101,6 +137,7 @@ int encode_impl(const uint8_t *d_ascii, const int64_t *h_lens, int32_t nseq, uin
         if (total > max_n) return LOR_ERR_TOO_LARGE;
     }
     P.out_start[nseq] = total;
+    P.n_ascii = total - nseq;
     if (total > nseq && !d_ascii) return LOR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int *status = tu_status_ptr();
