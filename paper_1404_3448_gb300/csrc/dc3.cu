@@ -1009,7 +1009,7 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge_packed(Merge
                                                                            int32_t *__restrict__ out, int *status) {
     constexpr int kMergeThreads = kMergeTile / kMergeItems;
     __shared__ uint64_t KA[kMergeTile];
-    __shared__ uint64_t KB1[kMergeTile], KB2[kMergeTile];
+    __shared__ ulonglong2 KB[kMergeTile];  // a nonsample's two keys, read together
     __shared__ int32_t PA[kMergeTile], PB[kMergeTile];
     const int64_t t = blockIdx.x;
     const int64_t tot = a.na + a.nb;
@@ -1039,8 +1039,8 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge_packed(Merge
         } else {
             const BRec16 g = a.Bx[b0 + sl - na];
             const uint64_t c0 = g.c01 & 0xFFu, c1 = (g.c01 >> 8) & 0xFFu;
-            KB1[sl - na] = (c0 << 32) | uint64_t(uint32_t(g.r1));
-            KB2[sl - na] = (c0 << 40) | (c1 << 32) | uint64_t(uint32_t(g.r2));
+            KB[sl - na] = make_ulonglong2((c0 << 32) | uint64_t(uint32_t(g.r1)),
+                                          (c0 << 40) | (c1 << 32) | uint64_t(uint32_t(g.r2)));
             PB[sl - na] = 3 * g.t;
         }
     }
@@ -1050,7 +1050,8 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge_packed(Merge
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         const int j = dl - 1 - mid;
-        if (ka_less(KA[mid], KB1[j], KB2[j])) lo = mid + 1;
+        const ulonglong2 kb = KB[j];
+        if (ka_less(KA[mid], kb.x, kb.y)) lo = mid + 1;
         else hi = mid;
     }
     int ia = lo, ib = dl - lo;
@@ -1058,7 +1059,11 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge_packed(Merge
 #pragma unroll
     for (int k = 0; k < kMergeItems; ++k) {
         if (dl + k >= nt) break;
-        const bool take_a = ib >= nb || (ia < na && ka_less(KA[ia], KB1[ib], KB2[ib]));
+        bool take_a = ib >= nb;
+        if (!take_a && ia < na) {
+            const ulonglong2 kb = KB[ib];
+            take_a = ka_less(KA[ia], kb.x, kb.y);
+        }
         o[k] = take_a ? PA[ia++] : PB[ib++];
     }
     __syncthreads();  // the key arrays are dead: reuse PA as the output staging
