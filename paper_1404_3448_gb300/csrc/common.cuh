@@ -267,6 +267,49 @@ struct BulkPairLoader {
     }
 };
 
+// The same for one array.
+template <typename A, int kN>
+struct BulkOne {
+    A a[2][kN];
+    uint64_t bar[2];
+};
+
+template <typename A, int kN>
+struct BulkOneLoader {
+    BulkOne<A, kN> &S;
+    const A *ga;
+    int64_t n;
+    uint32_t phase;
+    __device__ __forceinline__ BulkOneLoader(BulkOne<A, kN> &s, const A *a, int64_t count)
+        : S(s), ga(a), n(count), phase(0) {
+        if (threadIdx.x == 0) {
+            mbar_init(&S.bar[0], 1);
+            mbar_init(&S.bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ bool whole(int64_t t) const {
+        return t >= 0 && (t + 1) * kN <= n && (uintptr_t(ga + t * kN) & 15) == 0;
+    }
+    __device__ __forceinline__ void issue(int64_t t, int buf) {
+        if (!whole(t)) return;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&S.bar[buf], uint32_t(kN * sizeof(A)));
+        bulk_g2s(S.a[buf], ga + t * kN, uint32_t(kN * sizeof(A)), &S.bar[buf]);
+    }
+    __device__ __forceinline__ bool wait(int64_t t, int buf, uint64_t limit) {
+        if (!whole(t)) return true;
+        const bool ok = mbar_wait_bounded(&S.bar[buf], (phase >> buf) & 1u, limit);
+        phase ^= 1u << buf;
+        return ok;
+    }
+    __device__ __forceinline__ void drain(int64_t t, int buf, int64_t nxt, uint64_t limit) {
+        if (whole(t)) mbar_wait_bounded(&S.bar[buf], ((phase >> buf) & 1u) ^ 1u, limit);
+        if (whole(nxt)) mbar_wait_bounded(&S.bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, limit);
+    }
+};
+
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p) {
     uint64_t v;
     asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

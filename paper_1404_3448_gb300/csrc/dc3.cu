@@ -787,7 +787,7 @@ __global__ void k_scatter_u64(const uint32_t *__restrict__ key, const uint64_t *
 // (dynamic shared memory: more than the 48 KB a static allocation may take)
 using NsTiles = BulkPair<int32_t, uint64_t, kSpTile>;
 struct NsCountSmem {
-    NsTiles T;
+    BulkOne<uint64_t, kSpTile> T;  // the count reads the keys only (they carry the B1 flag and t_3x)
     uint32_t h[kRadix];
 };
 struct NsWriteSmem {
@@ -795,17 +795,20 @@ struct NsWriteSmem {
     uint32_t wh[kSortWarps][kRadix];
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__restrict__ SAR,
-                                                          const uint64_t *__restrict__ Ax, int64_t n02,
+// kSymBits: bits of the symbols ranked (4 when every code is below 16, as
+// for DNA: four ballots find a lane's peers instead of nine).
+template <int kSymBits>
+__global__ void __launch_bounds__(kSortThreads) k_ns_count(const uint64_t *__restrict__ Ax, int64_t n02,
                                                           uint32_t *__restrict__ cnt, int *status) {
+    constexpr uint32_t kNone = 1u << kSymBits, kMask = kNone - 1u;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     NsCountSmem &S = *reinterpret_cast<NsCountSmem *>(smem_raw);
-    NsTiles &T = S.T;
+    BulkOne<uint64_t, kSpTile> &T = S.T;
     uint32_t *h = S.h;
     const int tid = threadIdx.x;
     const int64_t ntiles = cdiv(n02, kSpTile);
     const uint64_t limit = wait_limit_ns();
-    BulkPairLoader<int32_t, uint64_t, kSpTile> ld(T, SAR, Ax, n02);
+    BulkOneLoader<uint64_t, kSpTile> ld(T, Ax, n02);
     int64_t tile = blockIdx.x;
     if (tid == 0) ld.issue(tile, 0);
     for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
@@ -827,23 +830,17 @@ __global__ void __launch_bounds__(kSortThreads) k_ns_count(const int32_t *__rest
         for (int i = 0; i < kSpItems; ++i) {
             const int loc = i * kSortThreads + tid;
             const int64_t idx = tile * kSpTile + loc;
-            int32_t x = -1;
             uint64_t w = 0;
-            if (whole) {
-                x = T.a[b][loc];
-                w = T.b[b][loc];
-            } else if (idx < n02) {
-                x = SAR[idx];
-                w = Ax[idx];
-            }
-            d[i] = (x >= 0 && (w & kB1Flag)) ? uint32_t(w >> 40) & 0xFFu : 0x100u;
+            if (whole) w = T.a[b][loc];
+            else if (idx < n02) w = Ax[idx];
+            d[i] = (w & kB1Flag) ? uint32_t(w >> 40) & kMask : kNone;
         }
         // one shared-memory add per distinct symbol of a warp (few symbols:
         // per-lane adds would all queue on the same words)
 #pragma unroll
         for (int i = 0; i < kSpItems; ++i) {
-            const uint32_t peers = warp_peers9(d[i]);
-            if (d[i] < 0x100u && __popc(peers & lanemask_lt()) == 0) atomicAdd(&h[d[i]], uint32_t(__popc(peers)));
+            const uint32_t peers = warp_peers_bits<kSymBits + 1>(d[i]);
+            if (d[i] < kNone && __popc(peers & lanemask_lt()) == 0) atomicAdd(&h[d[i]], uint32_t(__popc(peers)));
         }
         __syncthreads();
         cnt[tile * kRadix + tid] = h[tid];
@@ -889,10 +886,12 @@ __global__ void __launch_bounds__(kRadix) k_ns_scan_tiles(uint32_t *__restrict__
 // Every record at its tile's start for its first symbol plus its stable rank
 // in the tile (each warp owns a run of 512 consecutive entries: items in
 // order, lanes in order).
+template <int kSymBits>
 __global__ void __launch_bounds__(kSortThreads, 3) k_ns_write(const int32_t *__restrict__ SAR,
                                                              const uint64_t *__restrict__ Ax, int64_t n02, int64_t n0,
                                                              const uint32_t *__restrict__ start,
                                                              BRec16 *__restrict__ out, int *status) {
+    constexpr uint32_t kNone = 1u << kSymBits, kMask = kNone - 1u;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     NsWriteSmem &S = *reinterpret_cast<NsWriteSmem *>(smem_raw);
     NsTiles &T = S.T;
@@ -934,26 +933,26 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_ns_write(const int32_t *__r
                 xs[i] = SAR[idx];
                 ws[i] = Ax[idx];
             }
-            dig[i] = 0x100u;
+            dig[i] = kNone;
             if (xs[i] >= 0 && xs[i] < n0) {
-                dig[i] = uint32_t(ws[i] >> 40) & 0xFFu;
+                dig[i] = uint32_t(ws[i] >> 40) & kMask;
             } else if (idx < n02 && (xs[i] < 0 || xs[i] >= n02)) {
                 atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
             }
         }
         uint32_t *h = wh[warp];
 #pragma unroll
-        for (int i = 0; i < kSpItems; ++i) r[i] = warp_peers9(dig[i]);
+        for (int i = 0; i < kSpItems; ++i) r[i] = warp_peers_bits<kSymBits + 1>(dig[i]);
         const uint32_t lt_mask = lanemask_lt();
 #pragma unroll
         for (int i = 0; i < kSpItems; ++i) {
             const uint32_t d = dig[i];
             const uint32_t peers = r[i];
             const uint32_t lt = __popc(peers & lt_mask);
-            const uint32_t c = d < 0x100u ? h[d] : 0u;
+            const uint32_t c = d < kNone ? h[d] : 0u;
             r[i] = c + lt;
             __syncwarp();
-            if (d < 0x100u && lt == 0) h[d] = c + __popc(peers);
+            if (d < kNone && lt == 0) h[d] = c + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
@@ -971,7 +970,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_ns_write(const int32_t *__r
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < kSpItems; ++i) {
-            if (dig[i] >= 0x100u) continue;
+            if (dig[i] >= kNone) continue;
             const uint32_t o = wh[warp][dig[i]] + r[i];
             if (int64_t(o) >= n0) {  // counts that did not match SAR
                 atomicCAS(status, 0, LOR_ERR_BAD_INPUT);
@@ -2153,8 +2152,9 @@ int build_records(Dc3Run &D, const CharT *s, const LevelSizes &z, const int32_t 
 // L2-sized windows), so no step reads a record at random; the nonsample split
 // then reads SAR and Ax in sequence (into t32[0..3]), and the merge reads
 // both orders in sequence.
-int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z, const int32_t *Rl,
+int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z, int64_t maxc, const int32_t *Rl,
                                const int32_t *SAR, int32_t *out) {
+    const bool small_codes = maxc < 16;  // the split ranks 4-bit symbols
     cudaStream_t st = D.s;
     BRec16 *Bx = (BRec16 *)D.t32[0];
     if (size_t((char *)D.t32[4] - (char *)D.t32[0]) < sizeof(BRec16) * size_t(z.n0)) return LOR_ERR_WORKSPACE;
@@ -2202,10 +2202,11 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
         const unsigned grid = unsigned(min64(ntiles, int64_t(sort_grid_cap())));
         const unsigned wgrid = unsigned(min64(ntiles, int64_t(sort_grid_cap()) / 4 * 3));
         {
-            ProfScope ps(PK_NONSAMPLE, double(m) * (4 + 8), st);
-            LOR_CUDA_TRY(cudaFuncSetAttribute(k_ns_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            ProfScope ps(PK_NONSAMPLE, double(m) * 8, st);
+            auto kern = small_codes ? k_ns_count<4> : k_ns_count<8>;
+            LOR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(sizeof(NsCountSmem))));
-            k_ns_count<<<grid, kSortThreads, sizeof(NsCountSmem), st>>>(SAR, Ax, m, cnt, D.status);
+            kern<<<grid, kSortThreads, sizeof(NsCountSmem), st>>>(Ax, m, cnt, D.status);
             LOR_LAUNCH_CHECK();
         }
         {
@@ -2219,9 +2220,10 @@ int level0_nonsample_and_merge(Dc3Run &D, const uint8_t *s, const LevelSizes &z,
         }
         {
             ProfScope ps(PK_NONSAMPLE, double(m) * 4 + double(z.n0) * (8 + 16), st);
-            LOR_CUDA_TRY(cudaFuncSetAttribute(k_ns_write, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            auto kern = small_codes ? k_ns_write<4> : k_ns_write<8>;
+            LOR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(sizeof(NsWriteSmem))));
-            k_ns_write<<<wgrid, kSortThreads, sizeof(NsWriteSmem), st>>>(SAR, Ax, m, z.n0, cnt, Bx, D.status);
+            kern<<<wgrid, kSortThreads, sizeof(NsWriteSmem), st>>>(SAR, Ax, m, z.n0, cnt, Bx, D.status);
             LOR_LAUNCH_CHECK();
         }
     }
@@ -2392,7 +2394,7 @@ int dc3_graph(Dc3Run &D, const uint8_t *s, int64_t n, int64_t maxc, int32_t *out
     if (rc) return rc;
     rc = sa_by_doubling_graph(D, Rl, z.n02, SAR, NSl, bucket_names(D, z));
     if (rc) return rc;
-    return level0_nonsample_and_merge(D, s, z, Rl, SAR, out);
+    return level0_nonsample_and_merge(D, s, z, maxc, Rl, SAR, out);
 }
 
 template <typename CharT>
@@ -2488,7 +2490,7 @@ int dc3_level(Dc3Run &D, int lvl, const CharT *s, int64_t n, int64_t maxc, int32
 
     // Step 2: nonsample order, as group indices t (position 3t).
     if constexpr (sizeof(CharT) == 1) {
-        if (!PS && !D.force_lsd) return level0_nonsample_and_merge(D, s, z, Rl, SAR, out);
+        if (!PS && !D.force_lsd) return level0_nonsample_and_merge(D, s, z, maxc, Rl, SAR, out);
     }
     const uint32_t *B;
     if (PS && !D.force_lsd) {

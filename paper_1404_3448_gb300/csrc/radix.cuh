@@ -53,6 +53,19 @@ __device__ __forceinline__ uint32_t warp_peers9(uint32_t d) {
     return peers;
 }
 
+// The same for an N-bit value.
+template <int N>
+__device__ __forceinline__ uint32_t warp_peers_bits(uint32_t d) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 // The same for an 8-bit value (every slot valid).
 __device__ __forceinline__ uint32_t warp_peers8(uint32_t d) {
     uint32_t peers = 0xffffffffu;
