@@ -904,7 +904,10 @@ int radix_sort_pairs(RadixScratch &rs, KeyT *k0, uint32_t *v0, KeyT *k1, uint32_
 // the pass needs no histogram of them.
 
 // Four pairs per thread (16-byte loads when the four are whole and aligned).
-static __global__ void k_scatter_pairs(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+// kDst only names the destination in profiles (0 ranks and other arrays, 1
+// the inverse suffix array).
+template <int kDst>
+__global__ void k_scatter_pairs(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
                                        int64_t m, int32_t *__restrict__ dst, int32_t add, int64_t bound,
                                        int *status) {
     const int64_t i0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
@@ -991,7 +994,8 @@ inline int bucketed_scatter(RadixScratch &rs, const uint32_t *keys, const uint32
     if (rc) return rc;
     {
         ProfScope ps(kind, double(m) * 12, rs.stream);
-        k_scatter_pairs<<<unsigned(cdiv(cdiv(m, 4), 256)), 256, 0, rs.stream>>>(kbuf, vbuf0, m, dst, add, bound,
+        auto kern = kind == PK_ISA_SCATTER ? k_scatter_pairs<1> : k_scatter_pairs<0>;
+        kern<<<unsigned(cdiv(cdiv(m, 4), 256)), 256, 0, rs.stream>>>(kbuf, vbuf0, m, dst, add, bound,
                                                                       rs.status);
     }
     LOR_LAUNCH_CHECK();

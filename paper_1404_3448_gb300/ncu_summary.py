@@ -30,7 +30,8 @@ KINDS = [
     ("k_onesweep", "radix_pass"), ("k_partition", "radix_pass"), ("k_iota_u32", "radix_pass"),
     ("k_name", "naming"), ("k_par_name", "naming"), ("k_dense_scan", "naming"), ("k_dense_write", "naming"),
     ("k_dbl_", "naming"),
-    ("k_rank_scatter", "rank_scatter"), ("k_scatter_pairs", "rank_scatter"), ("k_dense_sorted", "rank_scatter"),
+    ("k_rank_scatter", "rank_scatter"), ("k_scatter_pairs<1>", "isa_scatter"), ("k_scatter_pairs", "rank_scatter"),
+    ("k_dense_sorted", "rank_scatter"),
     ("k_nonsample", "nonsample"), ("k_first_sym_hist", "nonsample"), ("k_scatter_u64", "nonsample"),
     ("k_ns_", "nonsample"), ("k_par_nonsamples", "nonsample"),
     ("k_par_ns_", "nonsample"), ("k_perm_offsets", "radix_hist"),
