@@ -548,9 +548,11 @@ static __global__ void __launch_bounds__(kScanThreads, 4) k_pk_name(const uint32
                 ucnt += u;
             }
         }
-        uint32_t agg, uagg;
-        const uint32_t excl = block_excl_scan<kScanThreads>(cnt, scratch, &agg);
-        const uint32_t uexcl = block_excl_scan<kScanThreads>(ucnt, scratch, &uagg);
+        // both counts in one scan: each is at most kScanTile < 2^16 per tile
+        uint32_t packed_agg;
+        const uint32_t packed = block_excl_scan<kScanThreads>(cnt | (ucnt << 16), scratch, &packed_agg);
+        const uint32_t excl = packed & 0xFFFFu, uexcl = packed >> 16;
+        const uint32_t agg = packed_agg & 0xFFFFu, uagg = packed_agg >> 16;
         if (tid < 32) {
             const uint32_t p = warp_lookback(lb, tile, agg, epoch, status);
             if (tid == 0) s_prefix = p;

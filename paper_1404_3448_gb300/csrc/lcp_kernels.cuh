@@ -445,15 +445,16 @@ __device__ __forceinline__ int32_t next_exc_tab(const int32_t *__restrict__ ne, 
 
 constexpr int kLcpBuckets = 256;
 
-// LCP[k] up to kLcpCap, tiles of kLcpPer * kLcpThreads consecutive ranks,
-// kLcpPer a thread kLcpThreads apart (every load and store coalesced); a
-// resident grid walks the tiles.  Ranks that reach the cap are appended to
-// `longl` (their LCP is finished by k_lcp_long).  LCP[0] = 0.  The 32
-// symbols at SA[k] are read once by the lane of rank k and passed to the
-// lane of rank k + 1, whose predecessor they are; a comparison that needs
-// more (an exception within 32 symbols, or 32 equal symbols) goes on with
-// lcp_listed.  An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT and gives
-// LCP 0 at the ranks that read it.
+// LCP[k] up to kLcpCap over tiles of kLcpPer * kLcpThreads consecutive
+// ranks; a resident grid walks the tiles.  Each warp takes kLcpPer * 32
+// consecutive ranks of its tile, 32 at a time (coalesced loads and stores).
+// Ranks that reach the cap are appended to `longl` (their LCP is finished by
+// k_lcp_long).  LCP[0] = 0.  The 32 symbols at SA[k] are read once, by the
+// lane of rank k, and passed to the lane of rank k + 1, whose predecessor
+// they are (lane 31's go to lane 0 of the warp's next 32 ranks); a
+// comparison that needs more (an exception within 32 symbols, or 32 equal
+// symbols) goes on with lcp_listed.  An SA entry outside [0, n) sets
+// LOR_ERR_BAD_INPUT and gives LCP 0 at the ranks that read it.
 __global__ void __launch_bounds__(kLcpThreads) k_lcp_direct(const uint8_t *__restrict__ t, PackedText T, int64_t n,
                                                             const int32_t *__restrict__ sa, int32_t *__restrict__ lcp,
                                                             uint32_t *__restrict__ longl, int *status) {
@@ -475,24 +476,41 @@ __global__ void __launch_bounds__(kLcpThreads) k_lcp_direct(const uint8_t *__res
         }
     __syncthreads();
     const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
-    const int lane = threadIdx.x & 31;
-    const int64_t ntiles = cdiv(n, int64_t(kLcpThreads) * kLcpPer);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kTile = kLcpThreads * kLcpPer;
+    const int32_t ntiles = int32_t(cdiv(n, kTile));
     bool bad = false;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t base = tile * (kLcpThreads * kLcpPer) + threadIdx.x;
+    for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // this warp's ranks, in 32 bits (n < 2^31)
+        const int64_t wb64 = int64_t(tile) * kTile + warp * (32 * kLcpPer);
+        if (wb64 >= n) continue;  // warp-uniform
+        const int32_t wb = int32_t(wb64);
+        // the window of the rank before the warp's first
+        int32_t jprev = -1;
+        uint64_t wprev = 0;
+        if (lane == 0 && wb > 0) {
+            jprev = sa[wb - 1];
+            if (jprev >= 0 && jprev < n32) wprev = window32(T.P, uint32_t(jprev), keep);
+        }
         for (int q = 0; q < kLcpPer; ++q) {
-            const int64_t k = base + int64_t(q) * kLcpThreads;
-            if (k - lane >= n) break;  // warp-uniform: the warp's first rank is past the end
-            const bool in = k < n;
+            const int32_t base = wb + q * 32;
+            if (base >= n32) break;  // warp-uniform
+            const int32_t k = base + lane;
+            const bool in = k < n32;
             const int32_t i = in ? ld_i32_stream(sa + k, once) : -1;
-            const int32_t i_ok = i >= 0 && i < n32;
-            // this lane's window, and the predecessor's from the lane before
+            const bool i_ok = i >= 0 && i < n32;
             const uint64_t wi = (in && i_ok) ? window32(T.P, uint32_t(i), keep) : 0;
+            // the predecessor's window: from the lane before, or for lane 0
+            // the last lane's of the previous 32 ranks
             uint64_t wj = __shfl_up_sync(0xffffffffu, wi, 1);
             int32_t j = __shfl_up_sync(0xffffffffu, i, 1);
-            if (lane == 0 && in) {
-                j = k > 0 ? sa[k - 1] : -1;
-                wj = (j >= 0 && j < n32) ? window32(T.P, uint32_t(j), keep) : 0;
+            const uint64_t w31 = __shfl_sync(0xffffffffu, wi, 31);
+            const int32_t i31 = __shfl_sync(0xffffffffu, i, 31);
+            if (lane == 0) {
+                wj = wprev;
+                j = jprev;
+                wprev = w31;
+                jprev = i31;
             }
             if (!in) continue;
             int32_t h = 0;
