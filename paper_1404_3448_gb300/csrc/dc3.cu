@@ -1607,6 +1607,22 @@ __global__ void k_dbl_group_heads(const uint32_t *__restrict__ ul, const uint32_
         if (i == 0 || NS[ul[i - 1]] != v) headof[v] = int32_t(k + 1);
     }
 }
+// The same from the names listed beside the unresolved positions.
+__global__ void k_dbl_group_heads_named(const uint32_t *__restrict__ ul, const int32_t *__restrict__ names,
+                                        const uint32_t *U_dev, int32_t *__restrict__ headof) {
+    const int64_t U = int64_t(*U_dev);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < U; i += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t v = names[i];
+        if (i == 0 || names[i - 1] != v) headof[v] = int32_t(ul[i] + 1);
+    }
+}
+// names[i] = NS[ul[i]] (the names beside the list, for the text round).
+__global__ void k_dbl_list_names(const uint32_t *__restrict__ ul, const uint32_t *U_dev, const int32_t *__restrict__ NS,
+                                 int32_t *__restrict__ names) {
+    const int64_t U = int64_t(*U_dev);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < U; i += int64_t(gridDim.x) * blockDim.x)
+        names[i] = NS[ul[i]];
+}
 __global__ void k_dbl_group_ranks(const uint32_t *__restrict__ ul, const uint32_t *U_dev,
                                   const int32_t *__restrict__ NS, const int32_t *__restrict__ SAR,
                                   const int32_t *__restrict__ headof, int32_t *__restrict__ R) {
@@ -1857,9 +1873,10 @@ int sample_packed_sort_and_name(Dc3Run &D, const uint8_t *s, const LevelSizes &z
     }
     {
         ProfScope ps(PK_NAMING, double(m) * 16, st);
-        // the unresolved list goes to t32[5], which the rank scatter leaves alone
+        // the unresolved list goes to t32[5] and its names to t64[2], which the
+        // rank scatter leaves alone
         LOR_PTILE_LAUNCH(D, m, k_pk_name, kr, vr, m, s, z.n, z.n0, mc, bucket_names(D, z) ? nullptr : Rl, SAR, NSl,
-                         D.d_names, D.t32[5], D.d_count, D.rs.lookback,
+                         D.d_names, D.t32[5], (int32_t *)D.t64[2], D.d_count, D.rs.lookback,
                          D.rs.lookback + cdiv(m, kScanTile), D.rs.tile_ctr, D.rs.tile_base, D.rs.epoch, D.status);
     }
     return LOR_OK;  // large levels: R is written by dc3_level once it knows how to continue
@@ -1975,7 +1992,8 @@ thread_local std::vector<TraceExtra> g_trace_extra;
 // leaves SA_R in SAR and rank(R-suffix) in Rl, like a returned recursion
 // followed by the rank scatter.  *U0 receives the initial unresolved count.
 // When ul_ready is set (D.t32[5]) the naming kernel has already listed the
-// unresolved positions there, with their count in D.d_count.  Level 0 passes
+// unresolved positions there, with their names in D.t64[2] and their count
+// in D.d_count.  Level 0 passes
 // its text (T0 != nullptr; names are the first kchars symbols of each
 // sample): the groups of two are then settled on the text first.
 struct Level0Text {
@@ -2004,6 +2022,7 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
         ul = D.t32[5];
         rstart = D.t32[1];
     }
+    int32_t *ul_names = (int32_t *)D.t64[2];  // names beside the list (level 0's text round)
     uint32_t *valt = D.t32[0];  // headof is dead once the ranks are initialised
     uint64_t *k0 = D.t64[0], *k1 = D.t64[1];
     if (r_unwritten) {
@@ -2038,12 +2057,19 @@ int sa_by_doubling(Dc3Run &D, int32_t *Rl, int64_t m, int32_t *SAR, const int32_
         const unsigned g = unsigned(min64(cdiv(hU, 256), 152 * 8));
         if (r_unwritten) {
             ProfScope ps(PK_NAMING, double(hU) * 12, st);
-            k_dbl_group_heads<<<g, 256, 0, st>>>(ul, D.d_count, NSl, headof);
+            if (ul_ready) k_dbl_group_heads_named<<<g, 256, 0, st>>>(ul, ul_names, D.d_count, headof);
+            else k_dbl_group_heads<<<g, 256, 0, st>>>(ul, D.d_count, NSl, headof);
+            LOR_LAUNCH_CHECK();
+        }
+        if (!ul_ready) {
+            // the names beside the list, for the text round
+            ProfScope ps(PK_NAMING, double(hU) * 8, st);
+            k_dbl_list_names<<<g, 256, 0, st>>>(ul, D.d_count, NSl, ul_names);
             LOR_LAUNCH_CHECK();
         }
         {
             ProfScope ps(PK_NAMING, double(hU) * (8 + 16 + 4), st);
-            k_dbl_text_pairs<<<g, 256, 0, st>>>(ul, int64_t(hU), NSl, SAR, Rl, r_unwritten ? headof : nullptr, T0->s,
+            k_dbl_text_pairs<<<g, 256, 0, st>>>(ul, ul_names, int64_t(hU), SAR, Rl, r_unwritten ? headof : nullptr, T0->s,
                                                 T0->n, T0->n0, T0->maxc, T0->kchars, runid);
             LOR_LAUNCH_CHECK();
         }

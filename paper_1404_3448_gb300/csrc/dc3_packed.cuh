@@ -491,7 +491,8 @@ static __global__ void __launch_bounds__(kScanThreads, 4) k_pk_name(const uint32
                                                                  uint32_t maxc, int32_t *__restrict__ R,
                                                                  int32_t *__restrict__ SAR, int32_t *__restrict__ NS,
                                                                  uint32_t *n_names, uint32_t *__restrict__ ul,
-                                                                 uint32_t *ul_count, uint64_t *lb, uint64_t *lb2,
+                                                                 int32_t *__restrict__ ul_names, uint32_t *ul_count,
+                                                                 uint64_t *lb, uint64_t *lb2,
                                                                  unsigned long long *ctr, unsigned long long tile_base,
                                                                  uint32_t epoch, int *status) {
     constexpr int kW = kScanItems + 2;  // positions base-1 .. base+16
@@ -575,7 +576,10 @@ static __global__ void __launch_bounds__(kScanThreads, 4) k_pk_name(const uint32
             if (pos < m) {
                 if (R) R[sa[i]] = int32_t(name);
                 if (pos == m - 1) *n_names = name;
-                if ((uflags >> i) & 1u) ul[uo++] = uint32_t(pos);
+                if ((uflags >> i) & 1u) {
+                    ul[uo] = uint32_t(pos);
+                    ul_names[uo++] = int32_t(name);
+                }
             }
         }
         store_run<int32_t, kScanItems>(SAR, base, m, sa);
@@ -594,18 +598,19 @@ static __global__ void __launch_bounds__(kScanThreads, 4) k_pk_name(const uint32
 // groups take the rank head + 1 (headof[name], when `headof` is given: the
 // ranks were set to 1 + position before) and stay for the rank rounds.
 // keep[i] marks list entries still unresolved.  One thread per entry of the
-// ordered unresolved list ul.
-static __global__ void k_dbl_text_pairs(const uint32_t *__restrict__ ul, int64_t U, const int32_t *__restrict__ NS,
+// ordered unresolved list ul, whose names come beside it (names[i]).
+static __global__ void k_dbl_text_pairs(const uint32_t *__restrict__ ul, const int32_t *__restrict__ names,
+                                        int64_t U,
                                         int32_t *__restrict__ SAR, int32_t *__restrict__ R,
                                         const int32_t *__restrict__ headof, const uint8_t *__restrict__ s,
                                         int64_t n, int64_t n0, uint32_t maxc, int kchars,
                                         uint32_t *__restrict__ keep) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < U; i += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t k = ul[i];
-        const int32_t v = NS[k];
-        const bool start = i == 0 || NS[ul[i - 1]] != v;
-        const bool second = !start && (i < 2 || NS[ul[i - 2]] != v);
-        const bool pair = (start && (i + 2 >= U || NS[ul[i + 2]] != v)) || (second && (i + 1 >= U || NS[ul[i + 1]] != v));
+        const int32_t v = names[i];
+        const bool start = i == 0 || names[i - 1] != v;
+        const bool second = !start && (i < 2 || names[i - 2] != v);
+        const bool pair = (start && (i + 2 >= U || names[i + 2] != v)) || (second && (i + 1 >= U || names[i + 1] != v));
         if (!pair) {
             if (headof) R[SAR[k]] = headof[v];
             keep[i] = 1u;
