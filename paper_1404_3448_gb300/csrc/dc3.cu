@@ -1862,7 +1862,9 @@ int sample_packed_sort_and_name(Dc3Run &D, const uint8_t *s, const LevelSizes &z
     }
     LOR_LAUNCH_CHECK();
     uint32_t *kr, *vr;
-    int rc = radix_passes<uint32_t, 16>(D.rs, k0, v0, k1, v1, m, 8, 32, 8, 3, hh, true, nullptr, &kr, &vr, false);
+    int rc = tune_config().sort_items_32 == 12
+                 ? radix_passes<uint32_t, 12>(D.rs, k0, v0, k1, v1, m, 8, 32, 8, 3, hh, true, nullptr, &kr, &vr, false)
+                 : radix_passes<uint32_t, 16>(D.rs, k0, v0, k1, v1, m, 8, 32, 8, 3, hh, true, nullptr, &kr, &vr, false);
     if (rc) return rc;
     if (nexc > 0) {
         ProfScope ps(PK_NAMING, double(nexc) * 48, st);
