@@ -169,7 +169,8 @@ def measured_peak_gbs():
 # of its size (a capture of several metrics holds the workload on the device
 # through many replays, so it is kept to a few GB); the summary gives DRAM
 # bytes / algorithmic bytes per kind, which scales to the full launch.
-TRAFFIC_PROFILES = {"large": "dram_by_kind_2x33554432.md", "medium": "dram_by_kind_2x33554432.md"}
+TRAFFIC_PROFILES = {"large": ["dram_by_kind_2x33554432.md", "dram_rmq_2x134217728.md"],
+                    "medium": ["dram_by_kind_2x33554432.md"]}
 
 
 def ncu_traffic(kind, workload, model_bytes_per_launch=None):
@@ -178,26 +179,24 @@ def ncu_traffic(kind, workload, model_bytes_per_launch=None):
     when it was taken on the current kernel sources: the summary's DRAM /
     model ratio times this run's algorithmic bytes per launch when it has
     one, else its DRAM bytes per launch."""
-    name = TRAFFIC_PROFILES.get(workload)
-    if not name:
-        return None
-    try:
-        with open(os.path.join(ROOT, "profiles", name)) as fh:
-            text = fh.read()
-    except OSError:
-        return None
-    m = re.search(r"source hash: `([0-9a-f]+)`", text)
-    if not m or m.group(1) != kernel_source_hash():
-        return None
-    for line in text.splitlines():
-        cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) in (6, 8) and cells[0] == kind:
-            try:
-                if len(cells) == 8 and model_bytes_per_launch:
-                    return float(cells[7]) * float(model_bytes_per_launch)
-                return float(cells[5])
-            except ValueError:
-                return None
+    for name in TRAFFIC_PROFILES.get(workload, []):
+        try:
+            with open(os.path.join(ROOT, "profiles", name)) as fh:
+                text = fh.read()
+        except OSError:
+            continue
+        m = re.search(r"source hash: `([0-9a-f]+)`", text)
+        if not m or m.group(1) != kernel_source_hash():
+            continue
+        for line in text.splitlines():
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) in (6, 8) and cells[0] == kind:
+                try:
+                    if len(cells) == 8 and model_bytes_per_launch:
+                        return float(cells[7]) * float(model_bytes_per_launch)
+                    return float(cells[5])
+                except ValueError:
+                    return None
     return None
 
 

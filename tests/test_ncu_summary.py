@@ -46,11 +46,15 @@ def test_bench_reads_traffic_only_for_current_sources(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc123")
-    name = bench.TRAFFIC_PROFILES["large"]
+    name = bench.TRAFFIC_PROFILES["large"][0]
     (tmp_path / "profiles" / name).write_text(md % "abc123")
     assert bench.ncu_traffic("radix_pass", "large") == 12345.0
     assert bench.ncu_traffic("merge", "large") is None
     assert bench.ncu_traffic("radix_pass", "tiny") is None
+    # a kind the first summary lacks is read from the next one
+    rmq = md.replace("radix_pass", "rmq_level").replace("12345", "777")
+    (tmp_path / "profiles" / bench.TRAFFIC_PROFILES["large"][1]).write_text(rmq % "abc123")
+    assert bench.ncu_traffic("rmq_level", "large") == 777.0
     (tmp_path / "profiles" / name).write_text(md % "ffff00")
     assert bench.ncu_traffic("radix_pass", "large") is None
 
@@ -63,5 +67,5 @@ def test_bench_scales_traffic_by_the_dram_to_model_ratio(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc123")
-    (tmp_path / "profiles" / bench.TRAFFIC_PROFILES["large"]).write_text("source hash: `abc123`\n\n" + md)
+    (tmp_path / "profiles" / bench.TRAFFIC_PROFILES["large"][0]).write_text("source hash: `abc123`\n\n" + md)
     assert bench.ncu_traffic("radix_pass", "large", 5e8) == 1e9
