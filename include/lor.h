@@ -148,8 +148,9 @@ int lor_build_sa_noalloc(const uint8_t *d_text, int64_t n, int32_t sigma, int32_
  * d_ws      : device workspace of lor_lcp_workspace_size(n) bytes (about 25
  *             bytes per symbol), 256-byte aligned.
  * An SA entry outside [0, n) sets LOR_ERR_BAD_INPUT (and is skipped).
- * Synchronises `stream` once (the choice between the direct comparison in
- * rank order and Kasai's method for texts of long repeats is read back).
+ * For n >= 2^20 synchronises `stream` once (the choice between the direct
+ * comparison in rank order and Kasai's method for texts of long repeats is
+ * read back); smaller texts take Kasai's method without a read-back.
  * ------------------------------------------------------------------------- */
 size_t lor_lcp_workspace_size(int64_t n);
 int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, int32_t *d_isa,

@@ -19,7 +19,8 @@
 //      the 2-bit copy, and PLCP[i] and ISA[i] are written in text order;
 //   3. LCP[ISA[i]] = PLCP[i] is scattered back to rank order.
 // The choice is made on the device and read back once (one stream
-// synchronisation per call).
+// synchronisation per call); texts below 2^20 symbols, whose call is bound by
+// launches, take Kasai's passes directly.
 #include "lcp_kernels.cuh"
 #include "radix.cuh"
 
@@ -31,6 +32,8 @@ namespace {
 // Inputs of at least this many symbols scatter through bucketing (one radix
 // pass on the destination's top bits, then writes that combine in L2).
 constexpr int64_t kBucketMin = int64_t(1) << 22;
+// Texts of at least this many symbols try the direct LCP route first.
+constexpr int64_t kDirectMin = int64_t(1) << 20;
 
 __global__ void k_lcp_scatter_direct(const int32_t *__restrict__ isa, int64_t n,
                                      const int32_t *__restrict__ plcp, int32_t *__restrict__ lcp) {
@@ -204,26 +207,31 @@ extern "C" int lor_lcp(const uint8_t *d_text, const int32_t *d_sa, int64_t n, in
         const int rc = pack_text(d_text, n, T, s);
         if (rc) return rc;
     }
-    // LCP in rank order by direct comparison (the long list in the PLCP
-    // buffer), then the ranks that reached the cap
-    LOR_CUDA_TRY(cudaMemsetAsync(T.ctl + kCtlLong, 0, 2 * sizeof(int), s));
-    {
-        // SA read, LCP written, two 16-symbol windows of the 2-bit copy
-        ProfScope ps(PK_KASAI, double(n) * (4 + 4 + 8), s);
-        k_lcp_direct<<<unsigned(min64(cdiv(cdiv(n, kLcpPer), kLcpThreads), 152 * 8)), kLcpThreads, 0, s>>>(
-            d_text, T, n, d_sa, d_lcp, reinterpret_cast<uint32_t *>(plcp), status);
-        LOR_LAUNCH_CHECK();
+    // Texts below kDirectMin symbols take Kasai's passes at once: there the
+    // call is bound by launches and the route's read-back would cost more
+    // than it saves.
+    int fallback = n < kDirectMin ? 1 : 0;
+    if (!fallback) {
+        // LCP in rank order by direct comparison (the long list in the PLCP
+        // buffer), then the ranks that reached the cap
+        LOR_CUDA_TRY(cudaMemsetAsync(T.ctl + kCtlLong, 0, 2 * sizeof(int), s));
+        {
+            // SA read, LCP written, two 16-symbol windows of the 2-bit copy
+            ProfScope ps(PK_KASAI, double(n) * (4 + 4 + 8), s);
+            k_lcp_direct<<<unsigned(min64(cdiv(cdiv(n, kLcpPer), kLcpThreads), 152 * 8)), kLcpThreads, 0, s>>>(
+                d_text, T, n, d_sa, d_lcp, reinterpret_cast<uint32_t *>(plcp), status);
+            LOR_LAUNCH_CHECK();
+        }
+        const int64_t max_long = n / 32 + 64;
+        {
+            ProfScope ps(PK_KASAI, 0.0, s);
+            k_lcp_long<<<unsigned(min64(cdiv(max_long, 256), 152 * 8)), 256, 0, s>>>(
+                d_text, T, n, d_sa, d_lcp, reinterpret_cast<const uint32_t *>(plcp), max_long);
+            LOR_LAUNCH_CHECK();
+        }
+        LOR_CUDA_TRY(cudaMemcpyAsync(&fallback, T.ctl + kCtlFallback, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LOR_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    const int64_t max_long = n / 32 + 64;
-    {
-        ProfScope ps(PK_KASAI, 0.0, s);
-        k_lcp_long<<<unsigned(min64(cdiv(max_long, 256), 152 * 8)), 256, 0, s>>>(
-            d_text, T, n, d_sa, d_lcp, reinterpret_cast<const uint32_t *>(plcp), max_long);
-        LOR_LAUNCH_CHECK();
-    }
-    int fallback = 0;
-    LOR_CUDA_TRY(cudaMemcpyAsync(&fallback, T.ctl + kCtlFallback, sizeof(int), cudaMemcpyDeviceToHost, s));
-    LOR_CUDA_TRY(cudaStreamSynchronize(s));
     if (bucket) {
         LOR_CUDA_TRY(cudaMemsetAsync(ws + L.ctrl, 0, 256, s));
         LOR_CUDA_TRY(cudaMemsetAsync(ws + L.lookback, 0, L.lookback_bytes, s));

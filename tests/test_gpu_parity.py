@@ -256,22 +256,23 @@ def test_wide_triples_two_stage_sort(L, O, route):
 
 def _raw_text_case(case, rng):
     """Raw code texts (no separators; the padding past the end is the only
-    implicit smallest symbol) that reach the level-0 key forms."""
+    implicit smallest symbol) that reach the level-0 key forms, long enough
+    (past 2^20 symbols) for the LCP's direct route."""
     if case == "dna_few_low_codes":
         # the four largest codes of sigma 21 plus a repeated motif holding the
         # low code 3 twice, so that several exception windows are equal
-        t = rng.integers(17, 21, 200_000).astype(np.uint8)
+        t = rng.integers(17, 21, 1_200_000).astype(np.uint8)
         motif = np.array([18, 19, 3, 20, 17, 3, 3, 18, 18, 20, 17, 19, 20, 20, 17, 18, 19, 20], np.uint8)
-        for pos in rng.choice(t.size - 64, 120, replace=False):
+        for pos in rng.choice(t.size - 64, 600, replace=False):
             t[pos:pos + motif.size] = motif
         t[rng.choice(t.size, 40, replace=False)] = rng.integers(1, 17, 40)
         return t, 21
     if case == "many_low_codes":  # exception windows everywhere: base-sigma keys
-        return rng.integers(1, 21, 150_000).astype(np.uint8), 21
+        return rng.integers(1, 21, 1_100_000).astype(np.uint8), 21
     if case == "two_codes":  # sigma 3: both codes take 2-bit values
-        return rng.integers(1, 3, 100_000).astype(np.uint8), 3
+        return rng.integers(1, 3, 1_100_000).astype(np.uint8), 3
     if case == "tail_run":  # a run of one symbol to the end: exception windows share keys
-        t = rng.integers(1, 5, 50_000).astype(np.uint8)
+        t = rng.integers(1, 5, 1_100_000).astype(np.uint8)
         t[-300:] = 1
         return t, 5
     raise ValueError(case)
