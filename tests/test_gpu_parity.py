@@ -263,7 +263,7 @@ def _raw_text_case(case, rng):
         # low code 3 twice, so that several exception windows are equal
         t = rng.integers(17, 21, 1_200_000).astype(np.uint8)
         motif = np.array([18, 19, 3, 20, 17, 3, 3, 18, 18, 20, 17, 19, 20, 20, 17, 18, 19, 20], np.uint8)
-        for pos in rng.choice(t.size - 64, 600, replace=False):
+        for pos in rng.choice(t.size - 64, 120, replace=False):
             t[pos:pos + motif.size] = motif
         t[rng.choice(t.size, 40, replace=False)] = rng.integers(1, 17, 40)
         return t, 21
