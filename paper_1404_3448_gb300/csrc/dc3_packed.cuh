@@ -429,10 +429,11 @@ static __global__ void __launch_bounds__(1024) k_pk_fixup(const uint8_t *__restr
     }
 }
 
-// Two windows' 16 symbols, equal or not (exception windows of one key).
+// Text position of sample j (class 0: 3j + 1; class 1: 3(j - n0) + 2).
 __device__ __forceinline__ int64_t pk_sample_pos(uint32_t j, int64_t n0) {
     return int64_t(j) < n0 ? 3 * int64_t(j) + 1 : 3 * (int64_t(j) - n0) + 2;
 }
+// Two windows' 16 symbols, equal or not (exception windows of one key).
 __device__ __forceinline__ bool pk_windows_equal(const uint8_t *__restrict__ s, int64_t n, int64_t n0, uint32_t maxc,
                                                  uint32_t ja, uint32_t jb) {
     const int64_t pa = pk_sample_pos(ja, n0), pb = pk_sample_pos(jb, n0);
@@ -481,10 +482,10 @@ __device__ __forceinline__ int pk_cmp16(const uint8_t *__restrict__ s, int64_t n
 // or (between exception windows of one key) the symbols change.  Writes
 // SA_R[j] = sample index, NS[j] = name, R[index] = name when R is given, the
 // name count, and the positions j whose name is shared with a neighbour (the
-// doubling's unresolved list, in order) with their count.  Each thread reads
-// the entries on either side of its own sixteen.  Persistent, as k_name; the
-// two look-backs (names in lb, unresolved positions in lb2) run in warps 0
-// and 1.
+// doubling's unresolved list, in order) with their names and count.  Each
+// thread reads the entries on either side of its own sixteen.  Persistent, as
+// k_name; the two counts share one block scan, and the two look-backs (names
+// in lb, unresolved positions in lb2) run in warps 0 and 1.
 static __global__ void __launch_bounds__(kScanThreads, 4) k_pk_name(const uint32_t *__restrict__ keys,
                                                                  const uint32_t *__restrict__ vals, int64_t m,
                                                                  const uint8_t *__restrict__ s, int64_t n, int64_t n0,
