@@ -127,10 +127,10 @@ int lor_build_sa(const uint8_t *d_text, int64_t n, int32_t sigma, int32_t *d_sa,
  * device; device-side errors as for lor_build_sa.  The scratch is one 32 MiB
  * array compiled into the library: every GPU that loads liblor holds it until
  * the process exits.  The first call on a device looks up the array's device
- * address and keeps it; make that first call before any stream capture
- * begins, and do not call this entry point again after cudaDeviceReset in
- * the same process.  Like lor_build_sa it reads counts back and synchronises
- * `stream` during the call.  All calls share the array, so calls that can
+ * address and keeps it; do not call this entry point again after
+ * cudaDeviceReset in the same process.  Like lor_build_sa it reads counts
+ * back and synchronises `stream` during the call, so it cannot be captured
+ * into a CUDA graph.  All calls share the array, so calls that can
  * overlap on the GPU race and must be serialised by the caller.  Allocates
  * nothing.
  * ------------------------------------------------------------------------- */

@@ -1023,11 +1023,28 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge_packed(Merge
     a1 = a1c;
     const int64_t b0 = d0 - a0, b1 = d1 - a1;
     const int na = int(a1 - a0), nb = int(b1 - b0), nt = int(d1 - d0);
-    for (int sl = threadIdx.x; sl < nt; sl += kMergeThreads) {
+    // Every slot's input is loaded before any is used, so that a thread keeps
+    // all its loads in flight: a sample's index and key word, or a
+    // nonsample's 16-byte record, in the same four registers.
+    uint4 in[kMergeItems];
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k) {
+        const int sl = int(threadIdx.x) + k * kMergeThreads;
+        in[k] = make_uint4(0u, 0u, 0u, 0u);
         if (sl < na) {
-            const int32_t r = a.A[a0 + sl];
             const uint64_t w = a.Ax[a0 + sl];
-            const uint64_t rk = w & 0xFFFFFFFFull, c0 = (w >> 32) & 0xFFu, c1 = (w >> 40) & 0xFFu;
+            in[k] = make_uint4(uint32_t(a.A[a0 + sl]), uint32_t(w), uint32_t(w >> 32), 0u);
+        } else if (sl < nt) {
+            const BRec16 g = a.Bx[b0 + sl - na];
+            in[k] = make_uint4(uint32_t(g.t), g.c01, uint32_t(g.r1), uint32_t(g.r2));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMergeItems; ++k) {
+        const int sl = int(threadIdx.x) + k * kMergeThreads;
+        if (sl < na) {
+            const int32_t r = int32_t(in[k].x);
+            const uint64_t rk = in[k].y, c0 = in[k].z & 0xFFu, c1 = (in[k].z >> 8) & 0xFFu;
             if (r < a.n0) {
                 KA[sl] = (c0 << 32) | rk;
                 PA[sl] = 3 * r + 1;
@@ -1035,12 +1052,10 @@ __global__ void __launch_bounds__(kMergeTile / kMergeItems) k_merge_packed(Merge
                 KA[sl] = kClass2 | (c0 << 40) | (c1 << 32) | rk;
                 PA[sl] = 3 * (r - a.n0) + 2;
             }
-        } else {
-            const BRec16 g = a.Bx[b0 + sl - na];
-            const uint64_t c0 = g.c01 & 0xFFu, c1 = (g.c01 >> 8) & 0xFFu;
-            KB[sl - na] = make_ulonglong2((c0 << 32) | uint64_t(uint32_t(g.r1)),
-                                          (c0 << 40) | (c1 << 32) | uint64_t(uint32_t(g.r2)));
-            PB[sl - na] = 3 * g.t;
+        } else if (sl < nt) {
+            const uint64_t c0 = in[k].y & 0xFFu, c1 = (in[k].y >> 8) & 0xFFu;
+            KB[sl - na] = make_ulonglong2((c0 << 32) | uint64_t(in[k].z), (c0 << 40) | (c1 << 32) | uint64_t(in[k].w));
+            PB[sl - na] = 3 * int32_t(in[k].x);
         }
     }
     __syncthreads();

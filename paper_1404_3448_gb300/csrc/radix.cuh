@@ -420,12 +420,16 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_partition(
         KeyT k[kItems];
         uint32_t r[kItems];
         ValT v[kItems];
+        // all items' loads are issued before the first shared-memory atomic
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const int64_t idx = base + i * kSortThreads + tid;
-            const bool valid = idx < m;
-            src.load(idx, valid, k[i], v[i]);
-            r[i] = valid ? atomicAdd(&cnt[digit_of(k[i], shift, dmask)], 1u) : 0u;
+            src.load(idx, idx < m, k[i], v[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t idx = base + i * kSortThreads + tid;
+            r[i] = idx < m ? atomicAdd(&cnt[digit_of(k[i], shift, dmask)], 1u) : 0u;
         }
         __syncthreads();
         const int dg = tid;

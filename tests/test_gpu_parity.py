@@ -336,13 +336,17 @@ def test_lcp_direct_comparison_and_kasai_routes(L, O, case):
 
 # ------------------------------------------------------------------ radix sort primitive
 
-@pytest.mark.parametrize("m,bits", [(0, 8), (1, 8), (4095, 12), (4097, 33), (100_003, 64),
-                                    (300_000, 9)])
-def test_radix_sort_primitive(L, O, m, bits):
+@pytest.mark.parametrize("m,bits,dups", [(0, 8, True), (1, 8, True), (4095, 12, True), (4097, 33, True),
+                                         (100_003, 64, True), (300_000, 9, True),
+                                         (200_000, 40, False), (70_001, 16, False)])
+def test_radix_sort_primitive(L, O, m, bits, dups):
+    """Stable sort against the paper's split sort (Section 4, Algorithm 1),
+    with a third of the keys equal (one digit crowded in every pass) and with
+    spread keys (equal low bits only by chance)."""
     rng = np.random.default_rng(m + bits)
     hi = (1 << min(bits + 2, 63)) - 1
     keys = rng.integers(0, hi, m, dtype=np.int64).astype(np.uint64)
-    if m > 10:
+    if dups and m > 10:
         keys[: m // 3] = keys[m // 3]  # heavy duplicates exercise stability
     vals = np.arange(m, dtype=np.uint32)[::-1].copy()
     k_t = to_dev(keys.view(np.int64))
