@@ -554,3 +554,41 @@ def test_overlap_max_scan_chunks_do_not_change_the_answer(oracle_mod):
     ov = oracle_mod.longest_overlap(text, sa, lcp, starts)
     for chunk in (1, 7, 4096, 1 << 24):
         assert oracle_mod.overlap_max_scan(sa, lcp, starts, chunk=chunk) == (ov["length"], ov["rank"])
+
+
+# ---------------------------------------------------------------- many independent pairs
+
+def test_pair_overlaps_against_the_dp_and_direct_comparison(oracle_mod):
+    """The per-pair oracle of the batched and served workloads: each pair's
+    length and position set equal the longest-common-substring DP's on that
+    pair alone (Section 3 problem statement); each (p, q) answer equals the
+    common prefix of the two suffixes of S1#S2$ counted by plain Python
+    comparison; the records come back in pair order from the spawned worker
+    pool (interleaved chunks put back in place) exactly as from one process."""
+    rng = np.random.default_rng(31)
+    pairs, queries = [], []
+    for i in range(11):
+        alpha = b"AC" if i % 4 == 0 else b"ACGT"
+        la, lb = int(rng.integers(1, 90)), int(rng.integers(1, 90))
+        a = np.frombuffer(alpha, np.uint8)[rng.integers(0, len(alpha), la)]
+        b = np.frombuffer(alpha, np.uint8)[rng.integers(0, len(alpha), lb)]
+        if i % 3 == 1 and la > 10:
+            b = np.concatenate([b, a[3:3 + int(rng.integers(1, la - 3))]])  # a planted shared piece
+        pairs.append((a, b))
+        n = la + b.size + 2
+        queries.append((rng.integers(0, n, 20).astype(np.int32), rng.integers(0, n, 20).astype(np.int32)))
+    one = [oracle_mod.pair_overlap(a, b, q) for (a, b), q in zip(pairs, queries)]
+    pooled = oracle_mod.pair_overlaps(pairs, queries=queries, processes=2)
+    for (a, b), q, r, s in zip(pairs, queries, one, pooled):
+        L, pos = oracle_mod.overlap_by_dp([a, b])
+        assert r["length"] == L
+        assert r["positions"].tolist() == pos.tolist()
+        text = bytes(a) + b"#" + bytes(b) + b"$"  # the pair's text; separators are unique symbols
+        for p_, q_, got in zip(q[0].tolist(), q[1].tolist(), r["answers"].tolist()):
+            x, y, h = text[p_:], text[q_:], 0
+            while h < min(len(x), len(y)) and x[h] == y[h]:
+                h += 1
+            assert got == h, (p_, q_)
+        assert set(r) == set(s)
+        for key in r:
+            assert np.array_equal(np.asarray(r[key]), np.asarray(s[key])), key
