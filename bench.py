@@ -165,10 +165,14 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-# DRAM counters are captured on the large workload's generator at a quarter
-# of its size (a capture of several metrics holds the workload on the device
-# through many replays, so it is kept to a few GB); the summary gives DRAM
-# bytes / algorithmic bytes per kind, which scales to the full launch.
+# DRAM counters of the a1-a10 kinds are captured on the large workload's
+# generator at a quarter of its size (a capture of several metrics holds the
+# workload on the device through its replays, so it is kept to a few GB);
+# the summary gives DRAM bytes / algorithmic bytes per kind, which scales to
+# the full launch.  The sparse table's kind has a full-size summary of its
+# own: its metric set takes one pass (nothing saved or restored), and its
+# passes re-read from DRAM once a level outgrows L2, so its ratio depends on
+# the size.  The first summary that lists a kind gives its figure.
 TRAFFIC_PROFILES = {"large": ["dram_by_kind_2x33554432.md", "dram_rmq_2x134217728.md"],
                     "medium": ["dram_by_kind_2x33554432.md"]}
 
